@@ -1,0 +1,160 @@
+"""CPU oracle for D8 flow accumulation -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never calls it, and
+the two share no code: the oracle is plain C (``fa_oracle.c``, compiled with
+gcc) plus the numpy marshalling below.
+
+Functions (all on numpy arrays, row-major, row 0 = north):
+  counts(codes, mask)            -> uint64 upslope counts (Eq. 1, w = 1)
+  weighted(codes, w, mask)       -> FP64 weighted accumulation (Eq. 1)
+  adjoint(codes, g, mask)        -> FP64 lam = (I - P)^-T g (downstream path sums)
+  bruteforce(codes, w, mask)     -> FP64 path-walking sums straight from the
+                                    definition (small rasters only)
+  residual_u32(codes, A, mask)   -> number of cells violating Eq. 1 (mod 2^32)
+
+Each returns the values plus a ``state`` array: 0 NoData, 1 exact,
+2 unspecified (on a cycle; for the adjoint, on or upstream of a cycle).
+
+Parity status: every function is pinned by tests/test_oracle.py (hand-worked
+examples, closed forms, conservation, brute force, cycle cases, the adjoint
+dot-product identity and central finite differences).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fa_oracle.c")
+_LIB = os.path.join(_HERE, "libfa_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile fa_oracle.c with gcc into libfa_oracle.so next to it."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        pi64 = ctypes.POINTER(ctypes.c_int64)
+        lib.fa_oracle_counts.argtypes = [p, i64, i64, i64, p, i64, p, p, pi64, pi64]
+        lib.fa_oracle_counts.restype = ctypes.c_int
+        lib.fa_oracle_weighted.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p, pi64, pi64]
+        lib.fa_oracle_weighted.restype = ctypes.c_int
+        lib.fa_oracle_adjoint.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p, pi64, pi64]
+        lib.fa_oracle_adjoint.restype = ctypes.c_int
+        lib.fa_oracle_bruteforce.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p]
+        lib.fa_oracle_bruteforce.restype = ctypes.c_int
+        lib.fa_oracle_residual_u32.argtypes = [p, i64, i64, i64, p, i64, p, i64, pi64]
+        lib.fa_oracle_residual_u32.restype = ctypes.c_int64
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class Result:
+    values: np.ndarray
+    state: np.ndarray  # 0 NoData, 1 exact, 2 unspecified (cycle)
+    n_cycle: int
+    n_bad: int
+
+
+def _prep(codes, mask):
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    if codes.ndim != 2:
+        raise ValueError("codes must be 2-D")
+    if mask is not None:
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        if mask.shape != codes.shape:
+            raise ValueError("mask shape differs from codes")
+    return codes, mask
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def counts(codes, mask=None) -> Result:
+    """Unit-weight accumulation, uint64 (Algorithm 1 over the whole raster)."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    out = np.empty((R, C), dtype=np.uint64)
+    st = np.empty((R, C), dtype=np.uint8)
+    nc, nb = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = _load().fa_oracle_counts(_p(codes), R, C, C, _p(mask), C, _p(out), _p(st),
+                                  ctypes.byref(nc), ctypes.byref(nb))
+    if rc:
+        raise MemoryError("oracle: allocation failed")
+    return Result(out, st, nc.value, nb.value)
+
+
+def weighted(codes, w, mask=None) -> Result:
+    """Weighted accumulation in FP64 from float32 weights."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    if w.shape != codes.shape:
+        raise ValueError("weights shape differs from codes")
+    out = np.empty((R, C), dtype=np.float64)
+    st = np.empty((R, C), dtype=np.uint8)
+    nc, nb = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = _load().fa_oracle_weighted(_p(codes), R, C, C, _p(mask), C, _p(w), C, _p(out), _p(st),
+                                    ctypes.byref(nc), ctypes.byref(nb))
+    if rc:
+        raise MemoryError("oracle: allocation failed")
+    return Result(out, st, nc.value, nb.value)
+
+
+def adjoint(codes, g, mask=None) -> Result:
+    """lam = (I - P)^-T g: sum of g along each cell's downstream path, FP64."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    g = np.ascontiguousarray(g, dtype=np.float32)
+    if g.shape != codes.shape:
+        raise ValueError("g shape differs from codes")
+    out = np.empty((R, C), dtype=np.float64)
+    st = np.empty((R, C), dtype=np.uint8)
+    nc, nb = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = _load().fa_oracle_adjoint(_p(codes), R, C, C, _p(mask), C, _p(g), C, _p(out), _p(st),
+                                   ctypes.byref(nc), ctypes.byref(nb))
+    if rc:
+        raise MemoryError("oracle: allocation failed")
+    return Result(out, st, nc.value, nb.value)
+
+
+def bruteforce(codes, w=None, mask=None) -> Result:
+    """Every valid cell adds its weight to each cell on its downstream path."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float32)
+    out = np.empty((R, C), dtype=np.float64)
+    st = np.empty((R, C), dtype=np.uint8)
+    _load().fa_oracle_bruteforce(_p(codes), R, C, C, _p(mask), C, _p(w), C, _p(out), _p(st))
+    return Result(out, st, int((st == 2).sum()), int((codes > 9).sum()))
+
+
+def residual_u32(codes, A, mask=None):
+    """(mismatches, first_index) of the Eq. 1 residual check on uint32 counts."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    A = np.ascontiguousarray(A, dtype=np.uint32)
+    first = ctypes.c_int64(-1)
+    bad = _load().fa_oracle_residual_u32(_p(codes), R, C, C, _p(mask), C, _p(A), C,
+                                         ctypes.byref(first))
+    return int(bad), int(first.value)

@@ -1,0 +1,308 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compare the oracle with itself: they use hand-worked examples
+(tests/golden), closed forms, conservation of flow, a brute-force path walker
+written here in plain Python, the structure of cycles, and for the adjoint the
+dot-product identity and central finite differences.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests import _golden
+
+# code -> (dr, dc), written out from the encoding: E NE N NW W SW S SE
+STEP = {1: (0, 1), 2: (-1, 1), 3: (-1, 0), 4: (-1, -1), 5: (0, -1), 6: (1, -1), 7: (1, 0),
+        8: (1, 1)}
+
+
+def _valid(codes, mask, r, c):
+    R, C = codes.shape
+    if not (0 <= r < R and 0 <= c < C):
+        return False
+    k = int(codes[r, c])
+    if k == 0 or k > 9:
+        return False
+    return mask is None or mask[r, c] == 0
+
+
+def _down(codes, mask, r, c):
+    k = int(codes[r, c])
+    if k not in STEP:
+        return None
+    rr, cc = r + STEP[k][0], c + STEP[k][1]
+    return (rr, cc) if _valid(codes, mask, rr, cc) else None
+
+
+def py_walk(codes, w=None, mask=None):
+    """Definition of flow accumulation by path walking (pure Python): each
+    valid cell adds its weight to every cell on its downstream path.  Returns
+    (values, on_cycle) where on_cycle marks cells whose walk never ends."""
+    R, C = codes.shape
+    out = np.zeros((R, C))
+    cyc = np.zeros((R, C), dtype=bool)
+    for r in range(R):
+        for c in range(C):
+            if not _valid(codes, mask, r, c):
+                continue
+            wy = 1.0 if w is None else float(w[r, c])
+            cur, seen = (r, c), set()
+            while cur is not None and cur not in seen:
+                seen.add(cur)
+                out[cur] += wy
+                cur = _down(codes, mask, *cur)
+            if cur is not None:  # re-entered a visited cell: the cycle
+                s = cur
+                while True:
+                    cyc[s] = True
+                    s = _down(codes, mask, *s)
+                    if s == cur:
+                        break
+    return out, cyc
+
+
+def py_path_sum(codes, g, mask=None):
+    """sum of g over each valid cell's downstream path (itself included)."""
+    R, C = codes.shape
+    lam = np.zeros((R, C))
+    for r in range(R):
+        for c in range(C):
+            if not _valid(codes, mask, r, c):
+                continue
+            cur, n = (r, c), 0
+            while cur is not None and n <= R * C:
+                lam[r, c] += float(g[cur])
+                cur = _down(codes, mask, *cur)
+                n += 1
+    return lam
+
+
+# ---------------------------------------------------------------------------
+# hand-worked examples
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", _golden.names())
+def test_golden(oracle_mod, name):
+    fx = _golden.load(name)
+    codes = fx["codes"]
+    mask = fx.get("mask")
+    res = oracle_mod.counts(codes, mask)
+    state = fx.get("state")
+    exact = (state == 1) if state is not None else np.ones(codes.shape, bool)
+    if "counts" in fx:
+        np.testing.assert_array_equal(res.values[exact].astype(np.int64), fx["counts"][exact])
+    if state is not None:
+        np.testing.assert_array_equal(res.state, state)
+    if "n_cycle" in fx:
+        assert res.n_cycle == fx["n_cycle"]
+    if "n_bad" in fx:
+        assert res.n_bad == fx["n_bad"]
+    if "weighted" in fx:
+        rw = oracle_mod.weighted(codes, fx["weights"], mask)
+        np.testing.assert_array_equal(rw.values, fx["weighted"])
+    if "adjoint" in fx:
+        ra = oracle_mod.adjoint(codes, fx["g"], mask)
+        np.testing.assert_array_equal(ra.values, fx["adjoint"])
+
+
+def test_nodata_outputs_zero(oracle_mod):
+    fx = _golden.load("hand_5x5.txt")
+    res = oracle_mod.counts(fx["codes"])
+    assert res.values[2, 2] == 0 and res.state[2, 2] == 0
+
+
+# ---------------------------------------------------------------------------
+# closed forms
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("R,C", [(1, 1), (1, 7), (5, 1), (13, 29)])
+def test_all_east_west_north_south(oracle_mod, R, C):
+    rr, cc = np.indices((R, C))
+    for code, expect in ((1, cc + 1), (5, C - cc), (7, rr + 1), (3, R - rr)):
+        res = oracle_mod.counts(np.full((R, C), code, np.uint8))
+        np.testing.assert_array_equal(res.values, expect.astype(np.uint64))
+
+
+@pytest.mark.parametrize("R,C", [(6, 6), (4, 9), (9, 4)])
+def test_all_diagonal(oracle_mod, R, C):
+    rr, cc = np.indices((R, C))
+    # SE: each cell's upslope cells are (r-t, c-t), t >= 0
+    res = oracle_mod.counts(np.full((R, C), 8, np.uint8))
+    np.testing.assert_array_equal(res.values, (np.minimum(rr, cc) + 1).astype(np.uint64))
+    # NW: mirrored
+    res = oracle_mod.counts(np.full((R, C), 4, np.uint8))
+    np.testing.assert_array_equal(res.values,
+                                  (np.minimum(R - 1 - rr, C - 1 - cc) + 1).astype(np.uint64))
+
+
+@pytest.mark.parametrize("R,C", [(1, 9), (2, 5), (7, 11), (64, 33)])
+def test_serpentine(oracle_mod, R, C):
+    codes = synth.serpentine_codes(R, C)
+    k = synth.serpentine_index(R, C)
+    res = oracle_mod.counts(codes)
+    np.testing.assert_array_equal(res.values, (k + 1).astype(np.uint64))
+    w = synth.uniform_weights((R, C), 7)
+    order = np.argsort(k.ravel())
+    prefix = np.cumsum(w.ravel()[order].astype(np.float64))
+    expect = np.empty(R * C)
+    expect[order] = prefix
+    rw = oracle_mod.weighted(codes, w)
+    np.testing.assert_allclose(rw.values.ravel(), expect, rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# conservation and brute force
+# ---------------------------------------------------------------------------
+def _terminal(codes, mask=None):
+    R, C = codes.shape
+    t = np.zeros((R, C), dtype=bool)
+    for r in range(R):
+        for c in range(C):
+            t[r, c] = _valid(codes, mask, r, c) and _down(codes, mask, r, c) is None
+    return t
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_conservation(oracle_mod, seed):
+    codes = synth.acyclic_random_codes(37, 23, seed)
+    w = synth.lognormal_weights(codes.shape, seed + 10)
+    valid = (codes > 0) & (codes <= 9)
+    term = _terminal(codes)
+    rc = oracle_mod.counts(codes)
+    assert rc.n_cycle == 0
+    assert int(rc.values[term].sum()) == int(valid.sum())
+    rw = oracle_mod.weighted(codes, w)
+    assert rw.values[term].sum() == pytest.approx(w[valid].astype(np.float64).sum(), rel=1e-12)
+
+
+def test_conservation_dem(oracle_mod):
+    codes = synth.dem_codes(120, 150, 11)
+    valid = (codes > 0) & (codes <= 9)
+    rc = oracle_mod.counts(codes)
+    assert rc.n_cycle == 0 and rc.n_bad == 0
+    assert int(rc.values[_terminal(codes)].sum()) == int(valid.sum())
+
+
+@pytest.mark.parametrize("seed,R,C", [(5, 1, 40), (6, 17, 19), (7, 64, 64), (8, 31, 57)])
+def test_bruteforce_random_with_cycles(oracle_mod, seed, R, C):
+    codes = synth.random_codes(R, C, seed)
+    mask = (synth.rng(seed + 99).random((R, C)) < 0.03).astype(np.uint8)
+    w = synth.uniform_weights((R, C), seed + 1)
+    expect, cyc = py_walk(codes, w, mask)
+    res = oracle_mod.weighted(codes, w, mask)
+    np.testing.assert_array_equal(res.state == 2, cyc)
+    ok = res.state == 1
+    np.testing.assert_allclose(res.values[ok], expect[ok], rtol=1e-12, atol=1e-12)
+    cnt_expect, _ = py_walk(codes, None, mask)
+    rc = oracle_mod.counts(codes, mask)
+    np.testing.assert_array_equal(rc.values[ok], cnt_expect[ok].astype(np.uint64))
+    # the C brute-force walker agrees with the Python one on exact cells
+    bf = oracle_mod.bruteforce(codes, w, mask)
+    np.testing.assert_allclose(bf.values[ok], expect[ok], rtol=1e-12, atol=1e-12)
+
+
+def test_mask_equals_nodata_code(oracle_mod):
+    codes = synth.random_codes(30, 40, 21)
+    mask = (synth.rng(22).random(codes.shape) < 0.1).astype(np.uint8)
+    c2 = codes.copy()
+    c2[mask != 0] = 0
+    a = oracle_mod.counts(codes, mask)
+    b = oracle_mod.counts(c2)
+    np.testing.assert_array_equal(a.values, b.values)
+    np.testing.assert_array_equal(a.state, b.state)
+
+
+def test_cycles(oracle_mod):
+    two = np.array([[1, 5]], np.uint8)
+    r = oracle_mod.counts(two)
+    assert r.n_cycle == 2 and (r.state == 2).all()
+    four = np.array([[1, 7], [3, 5]], np.uint8)
+    r = oracle_mod.counts(four)
+    assert r.n_cycle == 4
+
+
+def test_bad_codes_counted(oracle_mod):
+    codes = np.array([[1, 10, 255], [9, 0, 3]], np.uint8)
+    r = oracle_mod.counts(codes)
+    assert r.n_bad == 2
+    assert r.state[0, 1] == 0 and r.state[0, 2] == 0
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [31, 32])
+def test_adjoint_dot_product_identity(oracle_mod, seed):
+    codes = synth.acyclic_random_codes(29, 41, seed)
+    g = synth.rng(seed).standard_normal(codes.shape).astype(np.float32)
+    w = synth.uniform_weights(codes.shape, seed + 3)
+    A = oracle_mod.weighted(codes, w).values
+    lam = oracle_mod.adjoint(codes, g).values
+    lhs = float((A * g.astype(np.float64)).sum())
+    rhs = float((w.astype(np.float64) * lam).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-9)
+
+
+def test_adjoint_path_sum_bruteforce(oracle_mod):
+    codes = synth.random_codes(23, 27, 41)
+    g = synth.rng(42).standard_normal(codes.shape).astype(np.float32)
+    res = oracle_mod.adjoint(codes, g)
+    expect = py_path_sum(codes, g)
+    ok = res.state == 1
+    assert ok.sum() > 100
+    np.testing.assert_allclose(res.values[ok], expect[ok], rtol=1e-12, atol=1e-12)
+    # cells on cycles or upstream of one are marked unspecified
+    _, cyc = py_walk(codes)
+    assert (res.state[cyc] == 2).all()
+
+
+def test_adjoint_central_fd(oracle_mod):
+    """L(w) = sum_g (A[g] - t[g])^2 is quadratic in w, so central differences
+    are exact up to rounding; dL/dw = adjoint of 2 (A - t) on the gauges."""
+    codes = synth.dem_codes(40, 50, 51)
+    valid = (codes > 0) & (codes <= 9)
+    w = synth.uniform_weights(codes.shape, 52, 0.0, 2.0).astype(np.float64)
+    cnt = oracle_mod.counts(codes).values
+    gauges = synth.gauges(valid, cnt, 12, 53, min_count=5)
+    A0 = oracle_mod.weighted(codes, w.astype(np.float32)).values
+    tgt = A0.ravel()[gauges] * 0.9
+
+    def loss(wv):
+        A = oracle_mod.weighted(codes, wv.astype(np.float32)).values
+        return float(((A.ravel()[gauges] - tgt) ** 2).sum())
+
+    wf = w.astype(np.float32)
+    A = oracle_mod.weighted(codes, wf).values
+    gA = np.zeros(codes.size)
+    gA[gauges] = 2.0 * (A.ravel()[gauges] - tgt)
+    grad = oracle_mod.adjoint(codes, gA.reshape(codes.shape).astype(np.float32)).values
+    cells = synth.rng(54).choice(np.flatnonzero(valid.ravel()), 16, replace=False)
+    h = 0.5
+    for i in cells:
+        wp = wf.astype(np.float64).copy().ravel()
+        wm = wp.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (loss(wp.reshape(codes.shape)) - loss(wm.reshape(codes.shape))) / (2 * h)
+        assert fd == pytest.approx(grad.ravel()[i], rel=1e-5, abs=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# streaming residual verifier
+# ---------------------------------------------------------------------------
+def test_residual_verifier(oracle_mod):
+    codes = synth.dem_codes(64, 80, 61)
+    A = oracle_mod.counts(codes).values.astype(np.uint32)
+    bad, first = oracle_mod.residual_u32(codes, A)
+    assert bad == 0 and first == -1
+    B = A.copy()
+    B[10, 20] += 1  # planted mistake: the cell and its downstream cell disagree
+    bad, first = oracle_mod.residual_u32(codes, B)
+    assert bad >= 1 and first <= 10 * 80 + 20 + 80 + 1
+
+
+def test_synth_dem_is_drained(oracle_mod):
+    codes = synth.dem_codes(200, 173, 71)
+    r = oracle_mod.counts(codes)
+    assert r.n_cycle == 0 and r.n_bad == 0
+    assert not (codes == 9).any()
+    nd = (codes == 0).mean()
+    assert 0.005 < nd < 0.02
