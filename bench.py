@@ -1,0 +1,389 @@
+"""Benchmark: D8 flow accumulation on one GB300 (or N replicas under torchrun).
+
+Workload (one step = the whole hot path over one raster: pass 1, the
+perimeter-graph resolve and pass 2): a 16384 x 16384 raster (2.7e8 cells) of
+uint8 D8 codes from the seeded spectral-DEM generator (1/f^2 spectrum,
+priority-flood eps fill, 1% NoData disk; seed 201), unit weights, uint32
+counts, 64 x 64 tiles.  Inputs are resident in HBM; they (268 MB codes +
+1.07 GB output) exceed the 129 MB L2, so no explicit flush runs between steps.
+
+Printed JSON line: cells/s over all ranks (max-over-ranks time), the roofline
+of the dominant kernel (algorithmic bytes / live CUDA-event duration), the
+float32 weighted form, an end-to-end number through the public API with host
+buffers, the oracle timed on host cores, and SM clocks sampled during the
+timed region.
+
+--impl reference: times the CPU oracle (test infrastructure, a deliberately
+slow reference) on the same workload and metric on host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+ROWS = COLS = 16384
+SEED, WSEED = 201, 202
+TILE = (64, 64)
+BYTES_PER_CELL_COUNTS = 5  # 1 B code read + 4 B uint32 written (algorithmic minimum)
+BYTES_PER_CELL_F32 = 9     # + 4 B float32 weight read
+WORKLOAD = "d8_dem_16384x16384"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup():
+    import torch
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_for(kernel: str):
+    """dram bytes per launch recorded from an ncu capture of this exact kernel
+    source (profiles/traffic.json); None when absent or stale."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except Exception:
+        return None
+    if not rec:
+        return None
+    if rec.get("source_sha1") != source_sha1():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def source_sha1() -> str:
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1608_04431_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def cpu_oracle_time(codes, sample_rows=None):
+    import oracle
+
+    sub = codes if sample_rows is None else codes[:sample_rows]
+    oracle.build()
+    t0 = time.perf_counter()
+    res = oracle.counts(sub)
+    dt = time.perf_counter() - t0
+    return sub.size / dt, dt, res, sub.shape
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import synth
+
+    codes = synth.dem_codes(ROWS, COLS, SEED)
+    steps = max(1, args.steps if args.steps <= 3 else 1)
+    rows = ROWS // 4  # each step: a 4096-row band (~6.7e7 cells, a few seconds on one core)
+    vals = []
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_oracle_time(codes, rows)
+    t_all = 0.0
+    for _ in range(steps):
+        v, dt, _, shape = cpu_oracle_time(codes, rows)
+        vals.append(v)
+        t_all += dt
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": "cells/s (D8 flow accumulation, uint32 counts)",
+        "value": value, "unit": "cells/s", "n_gpus": args.gpus, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_all / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "uint64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rows": ROWS, "cols": COLS, "seed": SEED,
+                   "reference": "CPU oracle (Kahn queue over the whole raster, Algorithm 1), 1 thread"},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {rows} rows of the {ROWS}x{COLS} raster per step"},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the f32 and e2e legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    ws, rank, local = dist_setup() if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+
+    import synth
+    import paper_1608_04431_gb300 as fa
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    codes = synth.dem_codes(ROWS, COLS, SEED)
+    cells = codes.size
+    codes_d = torch.from_numpy(codes).to(dev)
+    out_d = torch.empty((ROWS, COLS), dtype=torch.uint32, device=dev)
+    opts = fa.options(TILE)
+    wsz = fa.fa_workspace_size(ROWS, COLS, opts)
+    work = torch.empty(wsz, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step_counts():
+        st = fa.fa_accumulate(codes_d, None, None, out_d, fa.FA_OUT_U32, work, opts, None, stream)
+        if st != fa.FA_OK:
+            raise fa.FlowAccError(st, "fa_accumulate")
+
+    for _ in range(args.warmup):
+        step_counts()
+    torch.cuda.synchronize()
+    st = fa.fa_status_read(None, work, stream)
+    if st[0] != fa.FA_OK:
+        raise fa.FlowAccError(st[0], "device status")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_pre = time.time()
+    while time.time() - t_pre < 0.4:  # keep the GPU busy while the sampler starts
+        step_counts()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_counts()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * cells / (ms_max / 1e3)
+
+    # per-phase durations, live, on the launching stream
+    fa.fa_timing_enable(True)
+    phases = []
+    for _ in range(5):
+        step_counts()
+        phases.append(fa.fa_timing_read())
+    fa.fa_timing_enable(False)
+    ph = np.mean(np.array(phases), axis=0).tolist()
+    names = ["pass1_tile_solve", "perimeter_graph_resolve", "pass2_tile_finalize"]
+    dom = int(np.argmax(ph))
+    # algorithmic bytes per launch of each phase (counts): pass 1 reads the
+    # codes (1 B/cell), pass 2 reads the codes and writes uint32 (5 B/cell);
+    # the perimeter resolve moves O(perimeter) bytes (not counted).
+    alg = {0: cells * 1, 1: 0, 2: cells * 5}
+    peak, peak_kind = peaks()
+    ach = alg[dom] / (ph[dom] / 1e3) / 1e9 if alg[dom] else 0.0
+    roof = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_kind": peak_kind,
+            "traffic": traffic_for(names[dom])}
+    step_ach = cells * BYTES_PER_CELL_COUNTS / (ms / 1e3) / 1e9
+    roof_step = {"bound": "hbm", "achieved": step_ach, "peak": peak, "unit": "GB/s",
+                 "frac": step_ach / peak, "bytes_per_cell": BYTES_PER_CELL_COUNTS}
+
+    line = {
+        "metric": "cells/s (D8 flow accumulation, uint32 counts)", "value": value,
+        "unit": "cells/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rows": ROWS, "cols": COLS, "seed": SEED,
+                   "tile": list(TILE), "weights": "unit", "out": "uint32",
+                   "l2": "inputs+outputs 1.34 GB > 129 MB L2, no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": roof, "roofline_step": roof_step,
+        "phases_ms": dict(zip(names, ph)),
+        "clocks": clocks,
+    }
+    kmax = int(np.ceil(np.log2((ROWS // TILE[0]) * (COLS // TILE[1]) * (2 * sum(TILE)) + 1))) + 2
+    line["gpu_launches"] = args.steps * (5 + kmax)
+
+    if not args.no_extra:
+        # float32 weighted form on the same raster
+        w_d = torch.from_numpy(synth.uniform_weights(codes.shape, WSEED)).to(dev)
+        outf = torch.empty((ROWS, COLS), dtype=torch.float32, device=dev)
+
+        def step_f32():
+            s = fa.fa_accumulate(codes_d, w_d, None, outf, fa.FA_OUT_F32, work, opts, None, stream)
+            if s != fa.FA_OK:
+                raise fa.FlowAccError(s, "fa_accumulate f32")
+
+        for _ in range(args.warmup):
+            step_f32()
+        torch.cuda.synchronize()
+        k2 = max(10, args.steps // 3)
+        e0.record(stream)
+        for _ in range(k2):
+            step_f32()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msf = e0.elapsed_time(e1) / k2
+        line["forms"] = {"plain_u32": {"cells_per_s": cells / (ms / 1e3), "ms": ms},
+                         "plain_f32": {"cells_per_s": cells / (msf / 1e3), "ms": msf,
+                                       "hbm_frac_step": cells * BYTES_PER_CELL_F32 / (msf / 1e3)
+                                       / 1e9 / peak}}
+        del w_d, outf
+
+        # end to end through the public API from pinned host buffers
+        h_codes = torch.from_numpy(codes).pin_memory()
+        h_out = torch.empty((ROWS, COLS), dtype=torch.uint32).pin_memory()
+        ke = max(5, args.steps // 20)
+
+        def step_e2e():
+            codes_d.copy_(h_codes, non_blocking=True)
+            step_counts()
+            h_out.copy_(out_d, non_blocking=True)
+
+        for _ in range(3):
+            step_e2e()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ke):
+            step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mse = max_over_ranks(e0.elapsed_time(e1) / ke, ws)
+        line["e2e"] = {"value": ws * cells / (mse / 1e3), "unit": "cells/s",
+                       "h2d_bytes_per_step": int(codes.nbytes),
+                       "d2h_bytes_per_step": int(cells * 4), "ms_per_step": mse}
+        # the result of the last step must be exact
+        got = h_out.view(torch.int32).numpy().view(np.uint32)
+    else:
+        got = out_d.view(torch.int32).cpu().numpy().view(np.uint32)
+
+    if not args.no_cpu_baseline and rank == 0:
+        v, dt, res, shape = cpu_oracle_time(codes)
+        exact = bool(np.array_equal(got, res.values.astype(np.uint32)))
+        line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                "sample": f"whole {ROWS}x{COLS} raster once ({dt:.1f} s)"}
+        line["parity"] = {"vs_oracle": "bit-exact" if exact else "MISMATCH"}
+        if not exact:
+            line["parity"]["mismatches"] = int((got != res.values.astype(np.uint32)).sum())
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,145 @@
+/*
+ * fa.h -- C ABI of the GB300 (sm_103a) D8 flow-accumulation library (libfa.so).
+ *
+ * Operation (Eq. 1 with alpha restricted to {0,1}, Section 2): for every valid
+ * cell p of a raster of single-direction (D8) flow codes,
+ *     A(p) = w(p) + sum of A(n) over the neighbours n whose one downstream cell is p,
+ * i.e. the count (w = 1) or weighted sum of all cells upslope of p, p included.
+ * The library computes it with the paper's tile decomposition (Section 3):
+ * a per-tile solve (Algorithm 1) that also links each perimeter cell to the
+ * tile exit its flow path reaches (Algorithm 2), a global solve over those
+ * perimeter links (Section 3.2), and a finalising per-tile pass that adds the
+ * flow entering each tile along its downstream paths (Algorithm 3, Section 3.3;
+ * EVICT strategy: the tile solve is recomputed, nothing per-cell is kept
+ * between passes).
+ *
+ * Raster conventions (all entry points):
+ *  - Row-major, row 0 = north; every raster argument has its own row pitch in
+ *    ELEMENTS (>= cols).  All raster pointers are DEVICE pointers owned by the
+ *    caller; the library never allocates device memory on these paths: all
+ *    scratch comes from the caller's workspace (size from *_workspace_size),
+ *    which must be 256-byte aligned.
+ *  - Codes, one byte per cell: 0 = NoData, 1..8 = E, NE, N, NW, W, SW, S, SE
+ *    (offsets (0,+1) (-1,+1) (-1,0) (-1,-1) (0,-1) (+1,-1) (+1,0) (+1,+1)),
+ *    9 = NoFlow.  Codes 10..255 are invalid: reported as FA_ERR_BAD_CODE in the
+ *    device status and treated as NoData.  The paper fixes one byte and ten
+ *    values per code (Section 4, Data Types) but no numbering; this is ours.
+ *  - Optional NoData mask (uint8, nonzero = NoData); a cell is NoData if its
+ *    code is 0 or invalid or its mask byte is nonzero.
+ *  - A cell has no downstream cell (its flow leaves the system) when it is
+ *    NoFlow, or its target is off the grid or NoData (Algorithm 1 skips such
+ *    targets; Algorithm 2 treats outside-of-data cells as NoData).  NoFlow
+ *    cells keep what they receive.  NoData cells get output 0.
+ *
+ * Asynchrony and errors:
+ *  - Every compute entry point enqueues work on `stream` (a cudaStream_t; NULL
+ *    = legacy default stream) and returns without synchronising.
+ *  - Host-detectable errors (NULL pointers, bad sizes or pitches, dtype
+ *    mismatch, workspace too small or misaligned) return synchronously with
+ *    nothing enqueued.
+ *  - Conditions found on the device (invalid codes, cycles, uint32 overflow,
+ *    non-finite weights, a bounded wait that ran out) are recorded in a device
+ *    status block of FA_STATUS_WORDS int32 words (8-byte aligned): d_status if
+ *    non-NULL, else a block inside the workspace.  fa_status_read() copies it
+ *    back.  The library never traps or asserts on the device.
+ *  - Results are bitwise reproducible run to run for a fixed tile shape and
+ *    input (no atomics-dependent floating-point ordering).
+ */
+#ifndef FA_H
+#define FA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FA_OK = 0,
+    FA_WARN_OVERFLOW = 1,     /* a uint32 count wrapped: outputs are mod 2^32 */
+    FA_ERR_INVALID_ARG = -1,  /* host-side argument check failed */
+    FA_ERR_BAD_CODE = -2,     /* a code in 10..255 was found (treated as NoData) */
+    FA_ERR_CYCLE = -3,        /* the flow graph has a cycle; cells on it are unspecified */
+    FA_ERR_WORKSPACE = -4,    /* workspace NULL, too small or misaligned */
+    FA_ERR_CUDA = -5,         /* a CUDA runtime call failed */
+    FA_ERR_TIMEOUT = -6,      /* a bounded device wait ran out */
+    FA_ERR_NONFINITE = -7     /* a weight or gradient was NaN or infinite */
+} fa_status;
+
+typedef enum { FA_OUT_U32 = 0, FA_OUT_F32 = 1 } fa_out_dtype;
+
+/* Device status block: word 0 = bitmask of FA_FLAG_*, word 1 = number of
+ * offending cells or perimeter-graph nodes, words 2-3 = smallest offending cell
+ * index r*cols + c as a little-endian int64 (INT64_MAX while none was found;
+ * fa_status_read reports that as -1).  Reset at the start of every call. */
+#define FA_STATUS_WORDS 4
+#define FA_FLAG_BAD_CODE 1
+#define FA_FLAG_CYCLE 2
+#define FA_FLAG_OVERFLOW 4
+#define FA_FLAG_TIMEOUT 8
+#define FA_FLAG_NONFINITE 16
+
+/* Tile shape: 0 = library default (64 x 64).  1 <= tile_h, tile_w and
+ * tile_h * tile_w <= 16384.  Results do not depend on the tile shape, except
+ * for the rounding of floating-point sums. */
+typedef struct {
+    int32_t tile_h, tile_w;
+    int32_t reserved0, reserved1;
+} fa_options;
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t fa_version(void);
+
+/* Workspace bytes that fa_accumulate needs for a rows x cols raster (any output
+ * dtype and weighting).  Returns 0 if the arguments are invalid. */
+size_t fa_workspace_size(int64_t rows, int64_t cols, const fa_options *opts);
+
+/*
+ * Flow accumulation of one raster (Eq. 1; Sections 3.1-3.3, Algorithms 1-3).
+ *   codes    [rows x pitch_codes] uint8 D8 codes (device).
+ *   weights  [rows x pitch_w] float32 per-cell weights w(p) (device), or NULL
+ *            for unit weights (upslope cell counts).
+ *   mask     [rows x pitch_mask] uint8 NoData mask (device) or NULL.
+ *   out      [rows x pitch_out] uint32 (FA_OUT_U32, counts mod 2^32; requires
+ *            weights == NULL) or float32 (FA_OUT_F32; sums kept as compensated
+ *            float pairs inside tiles and 128-bit fixed point across tiles, then
+ *            rounded once to float32).
+ *   workspace, ws_bytes: caller-owned device scratch, >= fa_workspace_size().
+ *   d_status: device int32[FA_STATUS_WORDS] or NULL (see above).
+ * rows or cols == 0 is valid and enqueues nothing but the status reset.
+ */
+fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t cols, int64_t pitch_codes,
+                        const float *weights, int64_t pitch_w, const uint8_t *mask,
+                        int64_t pitch_mask, void *out, fa_out_dtype out_dtype,
+                        int64_t pitch_out, void *workspace, size_t ws_bytes,
+                        const fa_options *opts, int32_t *d_status, void *stream);
+
+/*
+ * Copies the device status block back (synchronises `stream`) and maps it to
+ * the most severe fa_status: BAD_CODE, then CYCLE, NONFINITE, TIMEOUT, then
+ * FA_WARN_OVERFLOW, else FA_OK.  count / first_index may be NULL.
+ * d_status NULL means the block inside `workspace`.
+ */
+fa_status fa_status_read(const int32_t *d_status, const void *workspace, void *stream,
+                         int64_t *count, int64_t *first_index);
+
+/*
+ * Phase timing (a tracing aid, not part of the computation).  While enabled,
+ * each fa_accumulate call records CUDA events on its own stream at the
+ * boundaries of its phases: pass 1 (per-tile solve and perimeter links,
+ * Section 3.1), the perimeter-graph resolve (Section 3.2) and pass 2 (the
+ * finalising per-tile pass, Section 3.3).  fa_timing_read synchronises on the
+ * last event of the most recent call and writes up to n phase durations in
+ * milliseconds; it returns how many phases it wrote (0 if none was recorded,
+ * -1 on a CUDA error).  Events are created on first use; one thread and one
+ * device at a time.
+ */
+void fa_timing_enable(int32_t on);
+int32_t fa_timing_read(float *ms, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FA_H */

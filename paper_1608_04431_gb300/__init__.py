@@ -1,0 +1,142 @@
+"""GB300 (sm_103a) D8 flow accumulation.
+
+Thin binding over the C ABI of libfa.so (include/fa.h).  The ``fa_*``
+functions carry the C names and only marshal arguments: torch tensors supply
+device memory and the current CUDA stream; every step of the computation runs
+in the library's CUDA kernels.  ``accumulate`` is a convenience wrapper that
+also allocates the output and a cached workspace.
+
+Flow accumulation (the paper's Eq. 1 with alpha in {0,1}): for every valid
+cell p, A(p) = w(p) + sum of A(n) over neighbours n that drain into p.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (FA_ERR_BAD_CODE, FA_ERR_CUDA, FA_ERR_CYCLE, FA_ERR_INVALID_ARG,  # noqa: F401
+                   FA_ERR_NONFINITE, FA_ERR_TIMEOUT, FA_ERR_WORKSPACE, FA_OK, FA_OUT_F32,
+                   FA_OUT_U32, FA_STATUS_WORDS, FA_WARN_OVERFLOW, STATUS_NAMES, fa_options)
+
+__all__ = ["fa_version", "fa_workspace_size", "fa_accumulate", "fa_status_read",
+           "fa_timing_enable", "fa_timing_read", "accumulate",
+           "FlowAccError", "options"]
+
+
+class FlowAccError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
+
+
+def options(tile=None) -> fa_options:
+    o = fa_options()
+    if tile is not None:
+        o.tile_h, o.tile_w = int(tile[0]), int(tile[1])
+    return o
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _pitch(t):
+    if t is None:
+        return 0
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("rasters must be 2-D with unit column stride")
+    return t.stride(0)
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points
+# ---------------------------------------------------------------------------
+def fa_version() -> int:
+    return _lib.load().fa_version()
+
+
+def fa_workspace_size(rows: int, cols: int, opts: fa_options | None = None) -> int:
+    return _lib.load().fa_workspace_size(rows, cols, ctypes.byref(opts or fa_options()))
+
+
+def fa_accumulate(codes, weights, mask, out, out_dtype, workspace, opts=None, d_status=None,
+                  stream=None) -> int:
+    """Enqueue fa_accumulate on the current (or given) stream; returns the
+    host-side status code.  All tensors are CUDA tensors."""
+    rows, cols = codes.shape
+    return _lib.load().fa_accumulate(
+        _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(mask),
+        _pitch(mask), _ptr(out), out_dtype, _pitch(out), _ptr(workspace), workspace.numel(),
+        ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_status_read(d_status=None, workspace=None, stream=None):
+    """Synchronise the stream and read the device status block back:
+    returns (status, count, first_index)."""
+    cnt, first = ctypes.c_int64(0), ctypes.c_int64(-1)
+    st = _lib.load().fa_status_read(_ptr(d_status), _ptr(workspace), _stream_ptr(stream),
+                                    ctypes.byref(cnt), ctypes.byref(first))
+    return st, cnt.value, first.value
+
+
+def fa_timing_enable(on: bool) -> None:
+    _lib.load().fa_timing_enable(1 if on else 0)
+
+
+def fa_timing_read(n: int = 8):
+    """Phase durations (ms) of the most recent call made while timing was on."""
+    buf = (ctypes.c_float * n)()
+    m = _lib.load().fa_timing_read(buf, n)
+    if m < 0:
+        raise FlowAccError(FA_ERR_CUDA, "fa_timing_read")
+    return [float(buf[i]) for i in range(m)]
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    """A cached uint8 workspace of at least nbytes on `device` (torch memory)."""
+    key = torch.device(device)
+    ws = _ws_cache.get(key)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=key)
+        _ws_cache[key] = ws
+    return ws
+
+
+def accumulate(codes: torch.Tensor, weights: torch.Tensor | None = None,
+               mask: torch.Tensor | None = None, out_dtype=None, tile=None,
+               out: torch.Tensor | None = None, check: bool = False, stream=None):
+    """Flow accumulation of one raster.  codes: uint8 [R, C] CUDA tensor;
+    weights: float32 [R, C] or None (counts); mask: uint8 [R, C] or None.
+    Returns uint32 counts (no weights, default) or float32 sums.  check=True
+    synchronises and raises FlowAccError on any device-reported error."""
+    if codes.dtype != torch.uint8 or not codes.is_cuda:
+        raise TypeError("codes must be a uint8 CUDA tensor")
+    if out_dtype is None:
+        out_dtype = FA_OUT_U32 if weights is None else FA_OUT_F32
+    R, C = codes.shape
+    if out is None:
+        out = torch.empty((R, C), dtype=torch.uint32 if out_dtype == FA_OUT_U32 else torch.float32,
+                          device=codes.device)
+    opts = options(tile)
+    ws = workspace(fa_workspace_size(R, C, opts), codes.device)
+    st = fa_accumulate(codes, weights, mask, out, out_dtype, ws, opts, None, stream)
+    if st != FA_OK:
+        raise FlowAccError(st, "fa_accumulate")
+    if check:
+        st, _, _ = fa_status_read(None, ws, stream)
+        if st < 0:
+            raise FlowAccError(st, "fa_accumulate (device)")
+    return out

@@ -1,0 +1,73 @@
+"""ctypes loader for libfa.so (the in-tree CUDA library built from csrc/)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+_lib = None
+
+# keep in sync with include/fa.h
+FA_OK = 0
+FA_WARN_OVERFLOW = 1
+FA_ERR_INVALID_ARG = -1
+FA_ERR_BAD_CODE = -2
+FA_ERR_CYCLE = -3
+FA_ERR_WORKSPACE = -4
+FA_ERR_CUDA = -5
+FA_ERR_TIMEOUT = -6
+FA_ERR_NONFINITE = -7
+FA_OUT_U32 = 0
+FA_OUT_F32 = 1
+FA_STATUS_WORDS = 4
+
+STATUS_NAMES = {
+    FA_OK: "FA_OK", FA_WARN_OVERFLOW: "FA_WARN_OVERFLOW", FA_ERR_INVALID_ARG: "FA_ERR_INVALID_ARG",
+    FA_ERR_BAD_CODE: "FA_ERR_BAD_CODE", FA_ERR_CYCLE: "FA_ERR_CYCLE",
+    FA_ERR_WORKSPACE: "FA_ERR_WORKSPACE", FA_ERR_CUDA: "FA_ERR_CUDA",
+    FA_ERR_TIMEOUT: "FA_ERR_TIMEOUT", FA_ERR_NONFINITE: "FA_ERR_NONFINITE",
+}
+
+
+class fa_options(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes)
+_P, _I64, _I32, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+_OPT = ctypes.POINTER(fa_options)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "fa_version": (_I32, []),
+    "fa_workspace_size": (_SZ, [_I64, _I64, _OPT]),
+    "fa_accumulate": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I32, _I64, _P, _SZ,
+                             _OPT, _P, _P]),
+    "fa_status_read": (_I32, [_P, _P, _P, _PI64, _PI64]),
+    "fa_timing_enable": (None, [_I32]),
+    "fa_timing_read": (_I32, [ctypes.POINTER(ctypes.c_float), _I32]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libfa.so, building it first if it is missing or stale.  There is no
+    fallback: without the library every entry point raises."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libfa.so is not built ({_build.LIB}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

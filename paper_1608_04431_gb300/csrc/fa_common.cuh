@@ -1,0 +1,164 @@
+// Device-side building blocks shared by the flow-accumulation kernels.
+//
+// Code encoding (one byte per cell): 0 NoData, 1..8 = E, NE, N, NW, W, SW, S,
+// SE, 9 NoFlow, 10..255 invalid.  Row 0 is north.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fa {
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+// ---------------------------------------------------------------------------
+// direction decoding without memory lookups: (dr+1) and (dc+1) for codes 0..9
+// packed two bits per code into one 32-bit constant each.
+// ---------------------------------------------------------------------------
+constexpr uint32_t pack2(const int (&v)[10]) {
+    uint32_t p = 0;
+    for (int k = 0; k < 10; ++k) p |= uint32_t(v[k] + 1) << (2 * k);
+    return p;
+}
+constexpr int kDRtab[10] = {0, 0, -1, -1, -1, 0, 1, 1, 1, 0};
+constexpr int kDCtab[10] = {0, 1, 1, 0, -1, -1, -1, 0, 1, 0};
+constexpr uint32_t kDRP = pack2(kDRtab);
+constexpr uint32_t kDCP = pack2(kDCtab);
+
+__host__ __device__ __forceinline__ int dir_dr(int k) { return int((kDRP >> (2 * k)) & 3u) - 1; }
+__host__ __device__ __forceinline__ int dir_dc(int k) { return int((kDCP >> (2 * k)) & 3u) - 1; }
+// the direction that points back: E<->W, NE<->SW, N<->S, NW<->SE
+__host__ __device__ __forceinline__ int dir_rev(int k) { return ((k + 3) & 7) + 1; }
+
+// Effective code byte kept in shared memory for the tile and its one-cell halo:
+// 0 = NoData / off-grid / masked / invalid; otherwise the code 1..9, with
+// HALO set for a valid cell that lies outside the tile.
+constexpr uint8_t HALO = 0x10;
+
+// ---------------------------------------------------------------------------
+// perimeter slots of an h x w tile: top row west->east, right column north->
+// south, bottom row east->west, left column south->north; each perimeter cell
+// exactly once.  P = w (h == 1), h (w == 1), else 2w + 2h - 4.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int perim_count(int h, int w) {
+    if (h == 1) return w;
+    if (w == 1) return h;
+    return 2 * w + 2 * h - 4;
+}
+
+__host__ __device__ __forceinline__ int slot_of(int r, int c, int h, int w) {
+    if (h == 1) return c;
+    if (w == 1) return r;
+    if (r == 0) return c;
+    if (c == w - 1) return w - 1 + r;
+    if (r == h - 1) return (w + h - 2) + (w - 1 - c);
+    return (2 * w + h - 3) + (h - 1 - r);  // c == 0, 1 <= r <= h-2
+}
+
+__host__ __device__ __forceinline__ void cell_of(int s, int h, int w, int &r, int &c) {
+    if (h == 1) { r = 0; c = s; return; }
+    if (w == 1) { r = s; c = 0; return; }
+    if (s < w) { r = 0; c = s; return; }
+    s -= w;
+    if (s < h - 1) { r = 1 + s; c = w - 1; return; }
+    s -= h - 1;
+    if (s < w - 1) { r = h - 1; c = w - 2 - s; return; }
+    s -= w - 1;
+    r = h - 2 - s;
+    c = 0;
+}
+
+// ---------------------------------------------------------------------------
+// compensated float pair (hi + lo, |lo| <= ulp(hi)/2): ~48-bit sums from FP32
+// arithmetic (Knuth TwoSum, then a Fast2Sum renormalisation).  The _rn
+// intrinsics keep the compiler from contracting or reordering the steps.
+// ---------------------------------------------------------------------------
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    float s = __fadd_rn(a.hi, b.hi);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    float hi = __fadd_rn(s, e);
+    float lo = __fsub_rn(e, __fsub_rn(hi, s));
+    return FF{hi, lo};
+}
+
+__device__ __forceinline__ float ff_round(FF a) { return __fadd_rn(a.hi, a.lo); }
+
+// ---------------------------------------------------------------------------
+// 128-bit two's-complement fixed point with 2^-q resolution, used for the
+// cross-tile (perimeter graph) sums: integer addition is associative, so the
+// order in which atomics land cannot change a single bit of the result.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int clz128(u128 a) {
+    uint64_t hi = uint64_t(a >> 64), lo = uint64_t(a);
+    return hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+}
+
+__device__ __forceinline__ u128 shl_s(u128 v, int sh) {
+    if (sh >= 128 || sh <= -128) return 0;
+    return sh >= 0 ? (v << sh) : (v >> (-sh));
+}
+
+// exact for any double whose bits at and above 2^-q fit; lower bits truncated
+// toward zero.
+__device__ __forceinline__ u128 d2fix(double x, int q) {
+    if (x == 0.0) return 0;
+    int e;
+    double m = frexp(x, &e);  // x = m * 2^e, 0.5 <= |m| < 1
+    long long mi = (long long)ldexp(m, 53);
+    bool neg = mi < 0;
+    u128 v = (u128)(unsigned long long)(neg ? -mi : mi);
+    v = shl_s(v, e - 53 + q);
+    return neg ? (u128)(-(i128)v) : v;
+}
+
+// nearest-ish double of a fixed-point value (top 64 bits rounded to 53)
+__device__ __forceinline__ double fix2d(u128 v, int q) {
+    bool neg = (int64_t)(uint64_t)(v >> 64) < 0;
+    u128 a = neg ? (u128)(-(i128)v) : v;
+    if (a == 0) return 0.0;
+    int top = 127 - clz128(a);
+    int sh = top - 63;
+    uint64_t t = sh >= 0 ? uint64_t(a >> sh) : uint64_t(a << (-sh));
+    double d = ldexp((double)t, sh - q);
+    return neg ? -d : d;
+}
+
+__device__ __forceinline__ FF fix2ff(u128 v, int q) {
+    double d = fix2d(v, q);
+    float hi = (float)d;
+    u128 r = v - d2fix((double)hi, q);  // exact residual in fixed point
+    float lo = (float)fix2d(r, q);
+    return FF{hi, lo};
+}
+
+__device__ __forceinline__ void atomic_add_u128(u128 *addr, u128 v) {
+    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    unsigned long long *p = reinterpret_cast<unsigned long long *>(addr);
+    unsigned long long old = atomicAdd(p, lo);
+    if (old + lo < old) hi += 1ull;  // carry out of the low word
+    if (hi) atomicAdd(p + 1, hi);
+}
+
+// ---------------------------------------------------------------------------
+// device status block (see fa.h): flags, count, smallest offending index
+// ---------------------------------------------------------------------------
+struct StatusBlock {
+    int32_t flags;
+    int32_t count;
+    long long first;  // smallest offending cell index, LLONG_MAX when none
+};
+
+__device__ __forceinline__ void status_report(StatusBlock *st, int flag, int n, long long first) {
+    atomicOr(&st->flags, flag);
+    if (n) atomicAdd(&st->count, n);
+    if (first != 0x7fffffffffffffffll) atomicMin(&st->first, first);
+}
+
+}  // namespace fa

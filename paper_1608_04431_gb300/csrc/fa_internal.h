@@ -1,0 +1,68 @@
+// Host-side declarations shared by the translation units of libfa.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fa.h"
+
+namespace fa {
+
+// Geometry of the tile decomposition of one raster (Section 3: the raster is
+// subdivided into equal rectangular tiles; the last row/column may be ragged).
+struct Geom {
+    int64_t rows, cols;
+    int th, tw;          // nominal tile shape
+    int tiles_x, tiles_y;
+    int pmax;            // per-tile slot capacity: 2*th + 2*tw >= perimeter cells
+    int64_t tiles() const { return (int64_t)tiles_x * tiles_y; }
+};
+
+bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g);
+
+// Workspace carving: every region 256-byte aligned.
+struct Carver {
+    uintptr_t base, cur, end;
+    explicit Carver(void *p, size_t n) : base((uintptr_t)p), cur((uintptr_t)p), end((uintptr_t)p + n) {}
+    template <class T>
+    T *take(size_t count) {
+        cur = (cur + 255) & ~uintptr_t(255);
+        T *p = (T *)cur;
+        cur += count * sizeof(T);
+        return p;
+    }
+    size_t used() const { return cur - base; }
+    bool fits() const { return cur <= end; }
+};
+
+// Forward workspace regions (device pointers).
+struct FwdWork {
+    void *status;          // StatusBlock (16 bytes)
+    uint32_t *misc;        // [0] max |w| bits, [1..] per-round active counts
+    uint32_t *nexit;       // [T] exits per tile
+    uint16_t *link;        // [T*pmax] perimeter slot -> exit rank, 0xFFFF = terminates
+    uint32_t *node_dst;    // [T*pmax] exit rank -> global slot id of its target cell
+    double *node_val;      // [T*pmax] exit rank -> tile-local accumulation A_loc
+    void *x;               // [T*pmax] u128 forest values (G after resolve)
+    void *dl0, *dl1;       // [T*pmax] u128 pending scatter buffers
+    uint32_t *J0, *J1;     // [T*pmax] jump pointers
+    int kmax;              // number of jump rounds
+};
+
+size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry);
+
+// Phase timing: records an event on `s` at phase boundary `i` (0..kMaxPhase)
+// when enabled; no-op otherwise.
+constexpr int kMaxPhase = 8;
+void timing_mark(int i, cudaStream_t s);
+void timing_set_count(int n);
+
+// Launch the whole forward pipeline on `stream`.  val_mode 0: uint32 counts
+// (weights must be NULL); 1: float32 output (weights or unit).
+cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,
+                           int64_t pm, const float *w, int64_t pw, void *out, int64_t po,
+                           int val_mode, const FwdWork &ws, void *status, cudaStream_t s);
+
+}  // namespace fa
