@@ -185,7 +185,7 @@ def run_reference(args, ws, rank):
     import synth
 
     codes = synth.dem_codes(ROWS, COLS, SEED)
-    steps = max(1, args.steps if args.steps <= 3 else 1)
+    steps = max(1, min(args.steps, 3))
     rows = ROWS // 4  # each step: a 4096-row band (~6.7e7 cells, a few seconds on one core)
     vals = []
     for _ in range(max(0, min(args.warmup, 1))):
@@ -219,7 +219,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the f32 and e2e legs")
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up and timed steps (for ncu): no clock sampling, phase "
+                         "timing, extra legs or CPU baseline")
     args = ap.parse_args()
+    if args.profile:
+        args.no_extra = args.no_cpu_baseline = True
     if args.warmup < 3:
         args.warmup = 3
 
@@ -258,10 +263,11 @@ def main():
         raise fa.FlowAccError(st[0], "device status")
 
     sampler = ClockSampler(local)
-    sampler.start()
-    t_pre = time.time()
-    while time.time() - t_pre < 0.4:  # keep the GPU busy while the sampler starts
-        step_counts()
+    if not args.profile:
+        sampler.start()
+        t_pre = time.time()
+        while time.time() - t_pre < 0.4:  # keep the GPU busy while the sampler starts
+            step_counts()
     barrier(ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -277,8 +283,11 @@ def main():
     value = ws * cells / (ms_max / 1e3)
 
     # per-phase durations, live, on the launching stream
-    fa.fa_timing_enable(True)
     phases = []
+    if args.profile:
+        print(json.dumps({"profile_run": True, "ms_per_step": ms_max}), flush=True)
+        return
+    fa.fa_timing_enable(True)
     for _ in range(5):
         step_counts()
         phases.append(fa.fa_timing_read())
@@ -312,8 +321,7 @@ def main():
         "phases_ms": dict(zip(names, ph)),
         "clocks": clocks,
     }
-    kmax = int(np.ceil(np.log2((ROWS // TILE[0]) * (COLS // TILE[1]) * (2 * sum(TILE)) + 1))) + 2
-    line["gpu_launches"] = args.steps * (5 + kmax)
+    line["gpu_launches"] = args.steps * fa.fa_kernel_launches(ROWS, COLS, opts)
 
     if not args.no_extra:
         # float32 weighted form on the same raster

@@ -91,8 +91,14 @@ typedef struct {
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t fa_version(void);
 
-/* Workspace bytes that fa_accumulate needs for a rows x cols raster (any output
- * dtype and weighting).  Returns 0 if the arguments are invalid. */
+/* Number of kernel launches one fa_accumulate call enqueues for this shape
+ * (useful for graph capture and launch accounting); -1 if arguments are
+ * invalid. */
+int32_t fa_kernel_launches(int64_t rows, int64_t cols, const fa_options *opts);
+
+/* Workspace bytes that fa_accumulate and fa_accumulate_adjoint need for a
+ * rows x cols raster (any output dtype and weighting).  Returns 0 if the
+ * arguments are invalid. */
 size_t fa_workspace_size(int64_t rows, int64_t cols, const fa_options *opts);
 
 /*
@@ -114,6 +120,30 @@ fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t cols, int64_
                         int64_t pitch_mask, void *out, fa_out_dtype out_dtype,
                         int64_t pitch_out, void *workspace, size_t ws_bytes,
                         const fa_options *opts, int32_t *d_status, void *stream);
+
+/*
+ * Adjoint (transpose) of fa_accumulate with respect to the weights.  Eq. 1 with
+ * alpha in {0,1} is linear in w: A = (I - P)^-1 w, P the one-successor flow
+ * matrix (Section 2).  Given grad_out = dL/dA this writes
+ *     grad_w = dL/dw = (I - P)^-T grad_out,  i.e.  grad_w(c) = sum of grad_out
+ * over c's downstream path, c included (the cells whose accumulation w(c)
+ * feeds).  Same tile decomposition as fa_accumulate (Sections 3.1-3.3), with
+ * pointer jumping over each tile's flow forest and over the exit forest.
+ *   codes, mask      as in fa_accumulate.
+ *   grad_out         [rows x pitch_g] float32 (device).
+ *   grad_w           [rows x pitch_gw] float32 (device); 0 at NoData cells.
+ *   workspace        >= fa_workspace_size() bytes.
+ * Cells on a cycle, or whose downstream path enters one, are unspecified and
+ * FA_ERR_CYCLE is recorded.  The jump tables live in shared memory, so the
+ * tile must satisfy 25*(tile_h+2)*(tile_w+2) + 4*(tile_h+tile_w) <= 232448
+ * bytes (64x64 and 64x128 fit; 128x128 does not); other shapes return
+ * FA_ERR_INVALID_ARG.  Sums are compensated float pairs, rounded once.
+ */
+fa_status fa_accumulate_adjoint(const uint8_t *codes, int64_t rows, int64_t cols,
+                                int64_t pitch_codes, const uint8_t *mask, int64_t pitch_mask,
+                                const float *grad_out, int64_t pitch_g, float *grad_w,
+                                int64_t pitch_gw, void *workspace, size_t ws_bytes,
+                                const fa_options *opts, int32_t *d_status, void *stream);
 
 /*
  * Copies the device status block back (synchronises `stream`) and maps it to

@@ -20,7 +20,8 @@ from ._lib import (FA_ERR_BAD_CODE, FA_ERR_CUDA, FA_ERR_CYCLE, FA_ERR_INVALID_AR
                    FA_ERR_NONFINITE, FA_ERR_TIMEOUT, FA_ERR_WORKSPACE, FA_OK, FA_OUT_F32,
                    FA_OUT_U32, FA_STATUS_WORDS, FA_WARN_OVERFLOW, STATUS_NAMES, fa_options)
 
-__all__ = ["fa_version", "fa_workspace_size", "fa_accumulate", "fa_status_read",
+__all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumulate",
+           "fa_accumulate_adjoint", "fa_status_read", "adjoint", "FlowAccumulate",
            "fa_timing_enable", "fa_timing_read", "accumulate",
            "FlowAccError", "options"]
 
@@ -66,6 +67,10 @@ def fa_workspace_size(rows: int, cols: int, opts: fa_options | None = None) -> i
     return _lib.load().fa_workspace_size(rows, cols, ctypes.byref(opts or fa_options()))
 
 
+def fa_kernel_launches(rows: int, cols: int, opts: fa_options | None = None) -> int:
+    return _lib.load().fa_kernel_launches(rows, cols, ctypes.byref(opts or fa_options()))
+
+
 def fa_accumulate(codes, weights, mask, out, out_dtype, workspace, opts=None, d_status=None,
                   stream=None) -> int:
     """Enqueue fa_accumulate on the current (or given) stream; returns the
@@ -74,6 +79,16 @@ def fa_accumulate(codes, weights, mask, out, out_dtype, workspace, opts=None, d_
     return _lib.load().fa_accumulate(
         _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(mask),
         _pitch(mask), _ptr(out), out_dtype, _pitch(out), _ptr(workspace), workspace.numel(),
+        ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_accumulate_adjoint(codes, mask, grad_out, grad_w, workspace, opts=None, d_status=None,
+                          stream=None) -> int:
+    """Enqueue fa_accumulate_adjoint: grad_w = (I - P)^-T grad_out."""
+    rows, cols = codes.shape
+    return _lib.load().fa_accumulate_adjoint(
+        _ptr(codes), rows, cols, _pitch(codes), _ptr(mask), _pitch(mask), _ptr(grad_out),
+        _pitch(grad_out), _ptr(grad_w), _pitch(grad_w), _ptr(workspace), workspace.numel(),
         ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
 
 
@@ -140,3 +155,44 @@ def accumulate(codes: torch.Tensor, weights: torch.Tensor | None = None,
         if st < 0:
             raise FlowAccError(st, "fa_accumulate (device)")
     return out
+
+
+def adjoint(codes: torch.Tensor, grad_out: torch.Tensor, mask: torch.Tensor | None = None,
+            tile=None, out: torch.Tensor | None = None, check: bool = False, stream=None):
+    """dL/dw for dL/dA = grad_out: the sum of grad_out along each cell's
+    downstream path (float32)."""
+    if grad_out.dtype != torch.float32:
+        raise TypeError("grad_out must be float32")
+    R, C = codes.shape
+    if out is None:
+        out = torch.empty((R, C), dtype=torch.float32, device=codes.device)
+    opts = options(tile)
+    ws = workspace(fa_workspace_size(R, C, opts), codes.device)
+    st = fa_accumulate_adjoint(codes, mask, grad_out, out, ws, opts, None, stream)
+    if st != FA_OK:
+        raise FlowAccError(st, "fa_accumulate_adjoint")
+    if check:
+        st, _, _ = fa_status_read(None, ws, stream)
+        if st < 0:
+            raise FlowAccError(st, "fa_accumulate_adjoint (device)")
+    return out
+
+
+class FlowAccumulate(torch.autograd.Function):
+    """A = accumulation of weights w over the D8 codes; differentiable in w.
+    forward: fa_accumulate (float32); backward: fa_accumulate_adjoint."""
+
+    @staticmethod
+    def forward(ctx, weights, codes, mask=None, tile=None):
+        ctx.save_for_backward(codes, mask) if mask is not None else ctx.save_for_backward(codes)
+        ctx.has_mask = mask is not None
+        ctx.tile = tile
+        return accumulate(codes, weights.contiguous(), mask, out_dtype=FA_OUT_F32, tile=tile)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        saved = ctx.saved_tensors
+        codes = saved[0]
+        mask = saved[1] if ctx.has_mask else None
+        gw = adjoint(codes, grad_out.contiguous().float(), mask, tile=ctx.tile)
+        return gw, None, None, None

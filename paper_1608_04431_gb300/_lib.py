@@ -42,8 +42,11 @@ _PI64 = ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "fa_version": (_I32, []),
     "fa_workspace_size": (_SZ, [_I64, _I64, _OPT]),
+    "fa_kernel_launches": (_I32, [_I64, _I64, _OPT]),
     "fa_accumulate": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I32, _I64, _P, _SZ,
                              _OPT, _P, _P]),
+    "fa_accumulate_adjoint": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ,
+                                     _OPT, _P, _P]),
     "fa_status_read": (_I32, [_P, _P, _P, _PI64, _PI64]),
     "fa_timing_enable": (None, [_I32]),
     "fa_timing_read": (_I32, [ctypes.POINTER(ctypes.c_float), _I32]),

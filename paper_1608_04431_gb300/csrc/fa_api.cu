@@ -51,11 +51,23 @@ extern "C" int32_t fa_timing_read(float *ms, int32_t n) {
     return m;
 }
 
+extern "C" int32_t fa_kernel_launches(int64_t rows, int64_t cols, const fa_options *opts) {
+    Geom g;
+    if (!make_geom(rows, cols, opts, g)) return -1;
+    if (rows == 0 || cols == 0) return 1;  // the status reset only
+    FwdWork w;
+    carve_forward(nullptr, 0, g, w, true);
+    return 5 + w.kmax;  // status reset, pass 1, forest init, kmax rounds, forest final, pass 2
+}
+
 extern "C" size_t fa_workspace_size(int64_t rows, int64_t cols, const fa_options *opts) {
     Geom g;
     if (!make_geom(rows, cols, opts, g)) return 0;
     FwdWork w;
-    return carve_forward(nullptr, 0, g, w, true);
+    AdjWork a;
+    const size_t f = carve_forward(nullptr, 0, g, w, true);
+    const size_t b = carve_adjoint(nullptr, 0, g, a);
+    return f > b ? f : b;
 }
 
 extern "C" fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t cols,
@@ -68,6 +80,7 @@ extern "C" fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t c
     if (!make_geom(rows, cols, opts, g)) return FA_ERR_INVALID_ARG;
     if (out_dtype != FA_OUT_U32 && out_dtype != FA_OUT_F32) return FA_ERR_INVALID_ARG;
     if (out_dtype == FA_OUT_U32 && weights) return FA_ERR_INVALID_ARG;
+    if (!forward_tile_ok(g, out_dtype == FA_OUT_F32 ? 1 : 0)) return FA_ERR_INVALID_ARG;
     const bool empty = rows == 0 || cols == 0;
     if (!empty) {
         if (!codes || !out) return FA_ERR_INVALID_ARG;
@@ -107,4 +120,30 @@ extern "C" fa_status fa_status_read(const int32_t *d_status, const void *workspa
     if (f & FA_FLAG_TIMEOUT) return FA_ERR_TIMEOUT;
     if (f & FA_FLAG_OVERFLOW) return FA_WARN_OVERFLOW;
     return FA_OK;
+}
+
+extern "C" fa_status fa_accumulate_adjoint(const uint8_t *codes, int64_t rows, int64_t cols,
+                                           int64_t pitch_codes, const uint8_t *mask,
+                                           int64_t pitch_mask, const float *grad_out,
+                                           int64_t pitch_g, float *grad_w, int64_t pitch_gw,
+                                           void *workspace, size_t ws_bytes,
+                                           const fa_options *opts, int32_t *d_status,
+                                           void *stream) {
+    Geom g;
+    if (!make_geom(rows, cols, opts, g) || !adjoint_fits(g)) return FA_ERR_INVALID_ARG;
+    const bool empty = rows == 0 || cols == 0;
+    if (!empty) {
+        if (!codes || !grad_out || !grad_w) return FA_ERR_INVALID_ARG;
+        if (pitch_codes < cols || pitch_g < cols || pitch_gw < cols) return FA_ERR_INVALID_ARG;
+        if (mask && pitch_mask < cols) return FA_ERR_INVALID_ARG;
+        if (!aligned(grad_out, 4) || !aligned(grad_w, 4)) return FA_ERR_INVALID_ARG;
+    }
+    if (d_status && !aligned(d_status, 8)) return FA_ERR_INVALID_ARG;
+    if (!workspace || !aligned(workspace, 256)) return FA_ERR_WORKSPACE;
+    AdjWork w;
+    const size_t need = carve_adjoint(workspace, ws_bytes, g, w);
+    if (ws_bytes < need) return FA_ERR_WORKSPACE;
+    cudaError_t e = launch_adjoint(g, codes, pitch_codes, mask, pitch_mask, grad_out, pitch_g,
+                                   grad_w, pitch_gw, w, d_status, (cudaStream_t)stream);
+    return e == cudaSuccess ? FA_OK : FA_ERR_CUDA;
 }

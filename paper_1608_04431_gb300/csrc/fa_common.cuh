@@ -4,6 +4,7 @@
 // SE, 9 NoFlow, 10..255 invalid.  Row 0 is north.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -159,6 +160,58 @@ __device__ __forceinline__ void status_report(StatusBlock *st, int flag, int n, 
     atomicOr(&st->flags, flag);
     if (n) atomicAdd(&st->count, n);
     if (first != 0x7fffffffffffffffll) atomicMin(&st->first, first);
+}
+
+// ---------------------------------------------------------------------------
+// shared constants and block/warp helpers
+// ---------------------------------------------------------------------------
+constexpr uint16_t LINK_TERM = 0xFFFF;   // flow path ends inside the tile
+constexpr uint32_t NODE_NONE = 0xFFFFFFFFu;
+constexpr long long NO_INDEX = LLONG_MAX;
+
+__device__ __forceinline__ int off_of(int k, int W2) { return dir_dr(k) * W2 + dir_dc(k); }
+
+// block-wide sum / min helpers (blockDim.x <= 1024, multiple of 32)
+__device__ __forceinline__ int warp_sum(int v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ long long warp_min_ll(long long v) {
+    for (int o = 16; o; o >>= 1) {
+        long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+__device__ __forceinline__ uint32_t warp_max_u(uint32_t v) {
+    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Exclusive scan of one int per thread over the block; returns the prefix and
+// writes the total to *total.  Uses s_warp (>= 32 ints of shared memory).
+static __device__ int block_exclusive_scan(int v, int *s_warp, int *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < nw ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        s_warp[lane] = t;  // inclusive warp-total prefix
+    }
+    __syncthreads();
+    int before = wid ? s_warp[wid - 1] : 0;
+    *total = s_warp[nw - 1];
+    __syncthreads();
+    return before + x - v;
 }
 
 }  // namespace fa

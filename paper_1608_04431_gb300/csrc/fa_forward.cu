@@ -1,22 +1,25 @@
 // Forward D8 flow accumulation: tile passes and perimeter-graph resolve.
 //
-// Pipeline for one raster (Section 3 of the paper, EVICT strategy):
-//   pass 1  k_tile<.., 1>   per tile: Algorithm 1 (dependency counts, then the
-//                           queue-free equivalent of its Kahn loop) and
-//                           Algorithm 2 (each perimeter cell's exit link);
-//                           emits the tile-local accumulation at every exit
-//                           cell and the target of its flow (Section 3.2).
+// Pipeline for one raster (Section 3 of the paper; the tile-local result is
+// retained in the output raster between the passes):
+//   pass 1  k_solve<V>      per tile: Algorithm 1 (dependency counts, then a
+//                           queue-free Kahn loop) writing the tile-local
+//                           accumulation A_loc into the output; Algorithm 2
+//                           for the cells that receive flow from other tiles;
+//                           emits A_loc at every exit cell and the target of
+//                           its flow (the perimeter data of Section 3.2).
 //   resolve k_forest_*      the global flow graph over exit cells
 //                           (Section 3.2): G(e) = A_loc(e) + sum of G over the
 //                           exits whose flow enters the tile at a cell linked
 //                           to e, by pointer-jumping rounds.
-//   pass 2  k_tile<.., 2>   per tile: recompute the tile (EVICT, Section 3.3)
-//                           with w'(p) = w(p) + in(p), where in(p) is the flow
-//                           entering at perimeter cell p from neighbouring
-//                           tiles, and write A.  Adding in(p) to the weight of
-//                           p carries it along p's whole downstream path, which
-//                           is what Algorithm 3 does when it adds the offset
-//                           to every cell downstream of the entry.
+//   pass 2  k_offsets<V>    per tile: the flow in(p) entering each perimeter
+//                           cell p from other tiles is added to every cell on
+//                           p's downstream path inside the tile (Algorithm 3,
+//                           Section 3.3), read-modify-writing only those cells
+//                           of the output.
+// Inside a tile all sums are integers: uint32 counts, or 64-bit fixed point
+// with a per-tile scale for float weights, so the order in which atomics land
+// cannot change any bit of the result.
 #include <climits>
 #include <type_traits>
 
@@ -24,10 +27,6 @@
 #include "fa_internal.h"
 
 namespace fa {
-
-constexpr uint16_t LINK_TERM = 0xFFFF;   // flow path ends inside the tile
-constexpr uint32_t NODE_NONE = 0xFFFFFFFFu;
-constexpr long long NO_INDEX = LLONG_MAX;
 
 struct TileArgs {
     int64_t rows, cols;
@@ -49,7 +48,7 @@ struct TileArgs {
     uint32_t *maxw;
 };
 
-// fixed-point scale: |sum| <= cells * max|w| < 2^124 * 2^-q
+// global fixed-point scale for the perimeter graph: |sum| <= cells * max|w| < 2^(124 - q)
 __device__ __forceinline__ int fix_scale(int64_t cells, uint32_t maxw_bits) {
     float mw = __uint_as_float(maxw_bits);
     if (!(mw > 0.0f) || maxw_bits >= 0x7f800000u) return 0;
@@ -58,114 +57,154 @@ __device__ __forceinline__ int fix_scale(int64_t cells, uint32_t maxw_bits) {
     return 124 - e;
 }
 
-template <class V>
-struct ValOps;
-
-template <>
-struct ValOps<uint32_t> {
-    __device__ static uint32_t zero() { return 0u; }
-};
-template <>
-struct ValOps<FF> {
-    __device__ static FF zero() { return FF{0.0f, 0.0f}; }
-};
-
-__device__ __forceinline__ int off_of(int k, int W2) { return dir_dr(k) * W2 + dir_dc(k); }
-
-// block-wide sum / min helpers (blockDim.x <= 1024, multiple of 32)
-__device__ __forceinline__ int warp_sum(int v) {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ long long warp_min_ll(long long v) {
-    for (int o = 16; o; o >>= 1) {
-        long long u = __shfl_xor_sync(0xffffffffu, v, o);
-        v = u < v ? u : v;
-    }
-    return v;
-}
-__device__ __forceinline__ uint32_t warp_max_u(uint32_t v) {
-    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+// per-tile 64-bit scale: |sum| <= bound < 2^(62 - q)
+__device__ __forceinline__ int tile_scale(double bound) {
+    if (!(bound > 0.0) || !(bound < 1e300)) return 0;
+    int e;
+    frexp(bound, &e);
+    return 62 - e;
 }
 
-// Exclusive scan of one int per thread over the block; returns the prefix and
-// writes the total to *total.  Uses s_warp (>= 32 ints of shared memory).
-__device__ int block_exclusive_scan(int v, int *s_warp, int *total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int t = lane < nw ? s_warp[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
+__device__ __forceinline__ long long f2fix64(float x, int q) { return (long long)ldexp((double)x, q); }
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of a tile.  Codes and every per-cell array share one
+// byte-index space: halo row hr (0 .. h+1, tile row r = hr - 1) starts at
+// hr * S; tile column c sits at byte c + 4 (halo columns at bytes 3 and w + 4),
+// so each group of 4 interior cells is one aligned 32-bit word and the
+// in-degree can be computed four cells at a time.  S is a multiple of 16 with
+// at least 8 spare bytes after the east halo column.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int tile_stride(int tw) { return ((tw + 12 + 15) / 16) * 16; }
+
+__host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm) {
+    const size_t nb = (size_t)(th + 2) * tile_stride(tw);
+    size_t b = valm ? nb * 8 : 0;             // 64-bit fixed-point sums
+    b += nb * 4;                              // packed word per cell
+    b += nb;                                  // effective codes
+    b += (size_t)th * tw * 2;                 // source queue (u16 cell indices)
+    b += (size_t)(2 * th + 2 * tw) * 2;       // exit rank per perimeter slot
+    return (b + 15) & ~size_t(15);
+}
+
+__host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
+    const size_t nb = (size_t)(th + 2) * tile_stride(tw);
+    size_t b = nb * 8;                        // per-cell offset
+    b += (size_t)(2 * th + 2 * tw) * 16;      // inflow per perimeter slot
+    b += nb;                                  // effective codes
+    return (b + 15) & ~size_t(15);
+}
+
+__host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
+    return (int64_t)(th + 2) * tile_stride(tw) <= 65535 && (int64_t)th * tw <= 16384 &&
+           solve_smem_bytes(th, tw, valm) <= 227 * 1024 && offsets_smem_bytes(th, tw) <= 227 * 1024;
+}
+
+constexpr uint16_t LAB_UNKNOWN = 0xFFFE;
+
+// effective code byte of grid cell (gr, gc): 0 for NoData / masked / invalid /
+// off-grid, else the code with HALO set when the cell lies outside the tile
+__device__ __forceinline__ uint8_t eff_code(const TileArgs &a, int64_t gr, int64_t gc, bool halo,
+                                            int &nbad, long long &fbad, bool count_bad) {
+    if (gr < 0 || gr >= a.rows || gc < 0 || gc >= a.cols) return 0;
+    const uint8_t k = a.codes[gr * a.pc + gc];
+    if (k > 9) {
+        if (count_bad) {
+            ++nbad;
+            fbad = min(fbad, (long long)(gr * a.cols + gc));
         }
-        s_warp[lane] = t;  // inclusive warp-total prefix
+        return 0;
     }
-    __syncthreads();
-    int before = wid ? s_warp[wid - 1] : 0;
-    *total = s_warp[nw - 1];
-    __syncthreads();
-    return before + x - v;
+    if (k == 0 || (a.mask && a.mask[gr * a.pm + gc])) return 0;
+    return halo ? (uint8_t)(k | HALO) : k;
 }
 
+// Load a tile's effective codes with a one-cell halo (Algorithm 1's F) into
+// ec, one 32-bit word per lane; counts invalid codes inside the tile.
+__device__ __forceinline__ void load_codes(const TileArgs &a, uint8_t *ec, int64_t R0, int64_t C0,
+                                           int h, int w, int S, bool count_bad, int &nbad,
+                                           long long &fbad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool fast =
+        ((reinterpret_cast<uintptr_t>(a.codes) | (uintptr_t)a.pc | (uintptr_t)C0) & 3) == 0 &&
+        a.mask == nullptr;
+    const int words = S >> 2;
+    for (int hr = warp; hr < h + 2; hr += nw) {
+        const int64_t gr = R0 - 1 + hr;
+        const bool hrow = hr == 0 || hr == h + 1;
+        uint32_t *row = reinterpret_cast<uint32_t *>(ec + hr * S);
+        for (int wd = lane; wd < words; wd += 32) {
+            const int c0 = 4 * wd - 4;  // tile column of the word's first byte
+            uint32_t v = 0;
+            if (!hrow && c0 >= 0 && c0 + 3 < w && fast && gr >= 0 && gr < a.rows) {
+                const uint32_t raw =
+                    *reinterpret_cast<const uint32_t *>(a.codes + gr * a.pc + C0 + c0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t k = (raw >> (8 * j)) & 0xffu;
+                    if (k > 9) {
+                        if (count_bad) {
+                            ++nbad;
+                            fbad = min(fbad, (long long)(gr * a.cols + C0 + c0 + j));
+                        }
+                    } else {
+                        v |= k << (8 * j);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = c0 + j;
+                    if (c < -1 || c > w) continue;
+                    const bool hcell = hrow || c == -1 || c == w;
+                    v |= (uint32_t)eff_code(a, gr, C0 + c, hcell, nbad, fbad, count_bad && !hcell)
+                         << (8 * j);
+                }
+            }
+            row[wd] = v;
+        }
+    }
+}
+
+// The in-tile successor direction of an interior cell: its code when the
+// target is a valid cell inside the tile, else 0.
+__device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
+    const int k = ec[i];
+    if (k < 1 || k > 8) return 0;
+    const uint8_t et = ec[i + off_of(k, S)];
+    return (et && !(et & HALO)) ? (uint32_t)k : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// pass 1: tile solve
+// ---------------------------------------------------------------------------
 template <int VALM>
-struct ValType {
-    typedef uint32_t type;
-};
-template <>
-struct ValType<1> {
-    typedef FF type;
-};
-
-// shared-memory bytes for a tile pass
-__host__ __device__ inline size_t tile_smem_bytes(int th, int tw, int valm) {
-    size_t nh = (size_t)(th + 2) * (tw + 2);
-    size_t vb = valm ? 8 : 4;
-    size_t b = nh * vb;                  // val
-    b += ((nh + 3) / 4) * 4;             // packed counters
-    b += nh;                             // effective codes
-    b += nh;                             // predecessor masks
-    b = (b + 1) & ~size_t(1);
-    b += (size_t)(2 * th + 2 * tw) * 2;  // exit ranks per perimeter slot
-    return b;
-}
-
-// ---------------------------------------------------------------------------
-// per-tile pass (PASS 1 or 2)
-// ---------------------------------------------------------------------------
-template <int VALM, int PASS>
-__global__ void __launch_bounds__(256) k_tile(TileArgs a) {
-    typedef typename ValType<VALM>::type V;
+__global__ void __launch_bounds__(256) k_solve(TileArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_cnt_bad, s_cnt_cyc, s_flags;
+    __shared__ int s_cnt_bad, s_cnt_cyc, s_flags, s_nsrc, s_qhead;
     __shared__ long long s_first;
     __shared__ uint32_t s_maxw;
 
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int t = blockIdx.x;
     const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
     const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
     const int h = (int)min((int64_t)a.th, a.rows - R0);
     const int w = (int)min((int64_t)a.tw, a.cols - C0);
-    const int W2 = w + 2, NH = (h + 2) * W2;
-    const int NHmax = (a.th + 2) * (a.tw + 2);
+    const int S = tile_stride(a.tw);
+    const int NB = (a.th + 2) * S;
     const int n_in = h * w;
 
-    V *val = reinterpret_cast<V *>(smem);
-    uint32_t *cnt4 = reinterpret_cast<uint32_t *>(smem + sizeof(V) * NHmax);
-    uint8_t *cnt8 = reinterpret_cast<uint8_t *>(cnt4);
-    uint8_t *ec = reinterpret_cast<uint8_t *>(cnt4 + (NHmax + 3) / 4);
-    uint8_t *pmk = ec + NHmax;
-    uint16_t *rank = reinterpret_cast<uint16_t *>(
-        (reinterpret_cast<uintptr_t>(pmk + NHmax) + 1) & ~uintptr_t(1));
+    // counts: word = [step:4 | pending:4 | sum:24]
+    // weights: word = [step:4 | pending:4] and a separate 64-bit fixed-point sum
+    long long *fsum = reinterpret_cast<long long *>(smem);
+    uint32_t *word = reinterpret_cast<uint32_t *>(smem + (VALM ? 8 * (size_t)NB : 0));
+    uint8_t *ec = reinterpret_cast<uint8_t *>(word + NB);
+    uint16_t *srcq = reinterpret_cast<uint16_t *>(ec + NB);
+    uint16_t *rank = srcq + a.th * a.tw;
+    uint16_t *lab = reinterpret_cast<uint16_t *>(word);  // after the solve
 
     if (tid == 0) {
         s_cnt_bad = 0;
@@ -173,77 +212,356 @@ __global__ void __launch_bounds__(256) k_tile(TileArgs a) {
         s_flags = 0;
         s_first = NO_INDEX;
         s_maxw = 0;
+        s_nsrc = 0;
+        s_qhead = 0;
     }
-
-    // ---- load the tile's codes with a one-cell halo (Algorithm 1's F) -------
     int nbad = 0;
     long long fbad = NO_INDEX;
-    for (int i = tid; i < NH; i += nt) {
-        const int hr = i / W2, hc = i - hr * W2;
-        const int64_t gr = R0 - 1 + hr, gc = C0 - 1 + hc;
-        uint8_t e = 0;
-        if (gr >= 0 && gr < a.rows && gc >= 0 && gc < a.cols) {
-            const uint8_t k = a.codes[gr * a.pc + gc];
-            const bool inside = hr >= 1 && hr <= h && hc >= 1 && hc <= w;
-            if (k > 9) {
-                if (PASS == 1 && inside) {
-                    ++nbad;
-                    fbad = min(fbad, (long long)(gr * a.cols + gc));
-                }
-            } else if (k != 0 && !(a.mask && a.mask[gr * a.pm + gc])) {
-                e = k | (inside ? 0 : HALO);
-            }
-        }
-        ec[i] = e;
-    }
+    load_codes(a, ec, R0, C0, h, w, S, true, nbad, fbad);
     __syncthreads();
 
-    // ---- dependency counts D from in-tile upstream neighbours (gather) ------
+    // ---- dependency counts D (Algorithm 1, first loop), four cells at a time:
+    // bit k-1 of pm is set when the neighbour at offset k holds the reverse code
     uint32_t maxw = 0;
     int nonfinite = 0;
-    for (int j = tid; j < n_in; j += nt) {
-        const int r = j / w, c = j - r * w;
-        const int i = (r + 1) * W2 + (c + 1);
-        const uint8_t e = ec[i];
-        uint8_t m = 0;
-        V v0 = ValOps<V>::zero();
-        if (e) {
+    const int groups = (w + 3) >> 2;
+    for (int r = warp; r < h; r += nw) {
+        for (int g0 = 0; g0 < groups; g0 += 32) {  // warp-uniform trip count
+            const int gq = g0 + lane;
+            int mysrc = 0;
+            uint16_t srcs[4];
+            if (gq < groups) {
+                const int c = 4 * gq;
+                const int base = (r + 1) * S + c + 4;
+                uint32_t L[3], Cw[3], Rw[3];
 #pragma unroll
-            for (int k = 1; k <= 8; ++k) {
-                const uint8_t en = ec[i + off_of(k, W2)];
-                if (en && !(en & HALO) && (en & 15) == dir_rev(k)) m |= uint8_t(1u << (k - 1));
+                for (int d = 0; d < 3; ++d) {
+                    const uint32_t *p = reinterpret_cast<const uint32_t *>(ec + base + (d - 1) * S);
+                    L[d] = p[-1];
+                    Cw[d] = p[0];
+                    Rw[d] = p[1];
+                }
+                uint32_t pm = 0;
+#pragma unroll
+                for (int k = 1; k <= 8; ++k) {
+                    const int d = dir_dr(k) + 1, dc = dir_dc(k);
+                    const uint32_t nbr = dc == 0 ? Cw[d]
+                                                 : (dc > 0 ? __funnelshift_r(Cw[d], Rw[d], 8)
+                                                           : __funnelshift_l(L[d], Cw[d], 8));
+                    pm |= __vcmpeq4(nbr, 0x01010101u * (uint32_t)dir_rev(k)) &
+                          (0x01010101u << (k - 1));
+                }
+                uint32_t x = pm - ((pm >> 1) & 0x55555555u);  // per-byte popcount
+                x = (x & 0x33333333u) + ((x >> 2) & 0x33333333u);
+                x = (x + (x >> 4)) & 0x0F0F0F0Fu;
+                const int nvalid = min(4, w - c);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j >= nvalid) break;
+                    const int i = base + j;
+                    if (!((Cw[1] >> (8 * j)) & 0xffu)) {
+                        word[i] = 0;
+                        continue;
+                    }
+                    const uint32_t pend = (x >> (8 * j)) & 0xffu;
+                    const uint32_t st = step_of(ec, i, S);
+                    if constexpr (VALM == 0) {
+                        word[i] = (st << 28) | (pend << 24) | 1u;
+                    } else {
+                        word[i] = (st << 4) | pend;
+                        const float wv = a.w ? a.w[(R0 + r) * a.pw + (C0 + c + j)] : 1.0f;
+                        const uint32_t b = __float_as_uint(wv) & 0x7fffffffu;
+                        if (b >= 0x7f800000u) nonfinite = 1;
+                        maxw = max(maxw, b);
+                        fsum[i] = (long long)__float_as_uint(wv);  // raw bits until the scale is known
+                    }
+                    if (pend == 0) srcs[mysrc++] = (uint16_t)i;
+                }
             }
-            if constexpr (VALM == 0) {
-                v0 = 1u;
-            } else {
-                const float wv = a.w ? a.w[(R0 + r) * a.pw + (C0 + c)] : 1.0f;
-                const uint32_t b = __float_as_uint(wv) & 0x7fffffffu;
-                if (b >= 0x7f800000u) nonfinite = 1;
-                maxw = max(maxw, b);
-                v0 = FF{wv, 0.0f};
+            // append the lanes' sources to the block queue (warp-aggregated)
+            int incl = mysrc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            int qbase = 0;
+            if (lane == 31 && tot) qbase = atomicAdd(&s_nsrc, tot);
+            qbase = __shfl_sync(0xffffffffu, qbase, 31);
+            for (int j = 0; j < mysrc; ++j) srcq[qbase + incl - mysrc + j] = srcs[j];
         }
-        pmk[i] = m;
-        cnt8[i] = (uint8_t)__popc(m);
-        val[i] = v0;
+    }
+    int qt = 0;
+    if constexpr (VALM == 1) {
+        maxw = warp_max_u(maxw);
+        if (lane == 0 && maxw) atomicMax(&s_maxw, maxw);
+        __syncthreads();
+        qt = (s_maxw >= 0x7f800000u) ? 0 : tile_scale((double)n_in * (double)__uint_as_float(s_maxw));
+        for (int r = warp; r < h; r += nw)
+            for (int c = lane; c < w; c += 32) {
+                const int i = (r + 1) * S + c + 4;
+                if (ec[i]) fsum[i] = f2fix64(__uint_as_float((uint32_t)fsum[i]), qt);
+            }
     }
     __syncthreads();
 
-    int ovf = 0;
-    // ---- pass 2: add the inflow from neighbouring tiles to entry cells -----
-    if constexpr (PASS == 2) {
-        const int P = perim_count(h, w);
-        const int q = VALM ? fix_scale(a.rows * a.cols, *a.maxw) : 0;
-        for (int s = tid; s < P; s += nt) {
-            int r, c;
-            cell_of(s, h, w, r, c);
-            const int i = (r + 1) * W2 + (c + 1);
-            if (!ec[i]) continue;
-            u128 inflow = 0;
-            bool any = false;
+    // ---- the Kahn loop without a ready queue: lanes take sources from the
+    // block queue and push their final value downstream; the lane whose
+    // delivery completes a cell (its last pending upstream neighbour) carries
+    // on from it.  Integer sums make the result independent of the order.
+    {
+        const int nsrc = s_nsrc;
+        int cur = -1;
+        uint32_t st = 0;
+        uint32_t v32 = 0;
+        long long v64 = 0;
+        bool drained = false;
+        for (int guard = 0; guard < 4 * n_in + 64; ++guard) {
+            const unsigned idle = __ballot_sync(0xffffffffu, cur < 0);
+            if (idle && !drained) {
+                const int leader = __ffs(idle) - 1;
+                int qb = 0;
+                if (lane == leader) qb = atomicAdd(&s_qhead, __popc(idle));
+                qb = __shfl_sync(0xffffffffu, qb, leader);
+                if (qb >= nsrc) drained = true;
+                if (cur < 0) {
+                    const int pos = qb + __popc(idle & ((1u << lane) - 1u));
+                    if (pos < nsrc) {
+                        cur = srcq[pos];
+                        const uint32_t wd = word[cur];
+                        if constexpr (VALM == 0) {
+                            st = wd >> 28;
+                            v32 = wd & 0xFFFFFFu;
+                        } else {
+                            st = wd >> 4;
+                            v64 = fsum[cur];
+                        }
+                    }
+                }
+            }
+            if (__ballot_sync(0xffffffffu, cur >= 0) == 0 && drained) break;
+            if (cur < 0) continue;
+            if (st == 0) {
+                cur = -1;
+                continue;
+            }
+            const int tgt = cur + off_of((int)st, S);
+            if constexpr (VALM == 0) {
+                const uint32_t old = atomicAdd(&word[tgt], v32 - (1u << 24));
+                if (((old >> 24) & 15u) == 1u) {
+                    v32 += old & 0xFFFFFFu;
+                    st = old >> 28;
+                    cur = tgt;
+                } else {
+                    cur = -1;
+                }
+            } else {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&fsum[tgt]),
+                          (unsigned long long)v64);
+                __threadfence_block();
+                const uint32_t old = atomicSub(&word[tgt], 1u);
+                if ((old & 15u) == 1u) {
+                    __threadfence_block();
+                    v64 = *reinterpret_cast<volatile long long *>(&fsum[tgt]);
+                    st = old >> 4;
+                    cur = tgt;
+                } else {
+                    cur = -1;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- write A_loc (0 for NoData and for cells on cycles: those never
+    // lose their last pending dependency) ---------------------------------
+    int ncyc = 0;
+    long long fcyc = NO_INDEX;
+    const double inv = ldexp(1.0, -qt);
+    for (int r = warp; r < h; r += nw) {
+        const size_t orow = (size_t)(R0 + r) * a.po + C0;
+        const int base = (r + 1) * S + 4;
+        for (int c = lane; c < w; c += 32) {
+            const int i = base + c;
+            const uint32_t wd = word[i];
+            bool fin = ec[i] != 0;
+            if constexpr (VALM == 0) {
+                if (fin && ((wd >> 24) & 15u)) fin = false;
+            } else {
+                if (fin && (wd & 15u)) fin = false;
+            }
+            if (ec[i] && !fin) {
+                ++ncyc;
+                fcyc = min(fcyc, (long long)((R0 + r) * a.cols + (C0 + c)));
+            }
+            if constexpr (VALM == 0) {
+                reinterpret_cast<uint32_t *>(a.out)[orow + c] = fin ? (wd & 0xFFFFFFu) : 0u;
+            } else {
+                reinterpret_cast<float *>(a.out)[orow + c] = fin ? (float)((double)fsum[i] * inv) : 0.0f;
+            }
+        }
+    }
+
+    // ---- exit cells (flow leaves the tile into a valid cell) get ranks ----
+    const int P = perim_count(h, w);
+    const int chunk = (P + nt - 1) / nt;
+    const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
+    int mine = 0;
+    for (int s = s0; s < s1; ++s) {
+        int r, c;
+        cell_of(s, h, w, r, c);
+        const int i = (r + 1) * S + c + 4;
+        const int k = ec[i];
+        if (k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO)) ++mine;
+    }
+    int total;
+    int rk = block_exclusive_scan(mine, s_warp, &total);
+    const size_t tbase = (size_t)t * a.pmax;
+    for (int s = s0; s < s1; ++s) {
+        int r, c;
+        cell_of(s, h, w, r, c);
+        const int i = (r + 1) * S + c + 4;
+        const int k = ec[i];
+        const bool ex = k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO);
+        rank[s] = ex ? (uint16_t)rk : LINK_TERM;
+        if (ex) {
+            // perimeter record: A_loc at the exit and the target of its flow
+            const int64_t gr = R0 + r + dir_dr(k), gc = C0 + c + dir_dc(k);
+            const int tyd = (int)(gr / a.th), txd = (int)(gc / a.tw);
+            const int hd = (int)min((int64_t)a.th, a.rows - (int64_t)tyd * a.th);
+            const int wd = (int)min((int64_t)a.tw, a.cols - (int64_t)txd * a.tw);
+            const int sd = slot_of((int)(gr - (int64_t)tyd * a.th), (int)(gc - (int64_t)txd * a.tw),
+                                   hd, wd);
+            a.node_dst[tbase + rk] = (uint32_t)(((size_t)tyd * a.tiles_x + txd) * a.pmax + sd);
+            double v;
+            if constexpr (VALM == 0) v = (double)(word[i] & 0xFFFFFFu);
+            else v = (double)fsum[i] * inv;
+            a.node_val[tbase + rk] = v;
+            ++rk;
+        }
+    }
+    __syncthreads();
+    // labels (exit rank reached, or terminates) replace the packed words
+    for (int i = tid; i < NB; i += nt) lab[i] = LAB_UNKNOWN;
+    __syncthreads();
+
+    // ---- Algorithm 2 for the cells that receive flow from other tiles (and
+    // for exits, which link to themselves); walks stop at the first cell an
+    // earlier walk labelled ------------------------------------------------
+    for (int s = tid; s < P; s += nt) {
+        int r, c;
+        cell_of(s, h, w, r, c);
+        const int i0 = (r + 1) * S + c + 4;
+        uint16_t lk = LINK_TERM;
+        const uint16_t myrank = rank[s];
+        bool entry = false;
+        if (ec[i0]) {
 #pragma unroll
             for (int k = 1; k <= 8; ++k) {
-                const uint8_t en = ec[i + off_of(k, W2)];
+                const uint8_t en = ec[i0 + off_of(k, S)];
+                entry |= (en & HALO) && (en & 15) == dir_rev(k);
+            }
+        }
+        if (myrank != LINK_TERM) {
+            lk = myrank;
+        } else if (entry) {
+            int cur = i0, steps = 0;
+            for (; steps <= n_in; ++steps) {
+                const uint16_t L0 = lab[cur];
+                if (L0 != LAB_UNKNOWN) {
+                    lk = L0;
+                    break;
+                }
+                const int k = ec[cur];
+                if (k < 1 || k > 8) break;
+                const int nxt = cur + off_of(k, S);
+                const uint8_t et = ec[nxt];
+                if (!et) break;
+                if (et & HALO) {
+                    const int cr = cur / S - 1, cc = cur - (cur / S) * S - 4;
+                    lk = rank[slot_of(cr, cc, h, w)];
+                    break;
+                }
+                cur = nxt;
+            }
+            // label the walked cells so later walks stop early (benign races:
+            // every writer stores the same value)
+            int c2 = i0;
+            for (int st2 = 0; st2 < steps; ++st2) {
+                lab[c2] = lk;
+                c2 += off_of(ec[c2], S);
+            }
+        }
+        a.link[tbase + s] = lk;
+    }
+    if (tid == 0) a.nexit[t] = (uint32_t)total;
+
+    // ---- status -------------------------------------------------------------
+    nbad = warp_sum(nbad);
+    ncyc = warp_sum(ncyc);
+    fbad = warp_min_ll(min(fbad, fcyc));
+    maxw = warp_max_u(maxw);
+    nonfinite = warp_sum(nonfinite);
+    if (lane == 0) {
+        if (nbad) atomicAdd(&s_cnt_bad, nbad);
+        if (ncyc) atomicAdd(&s_cnt_cyc, ncyc);
+        if (fbad != NO_INDEX) atomicMin(&s_first, fbad);
+        if (maxw) atomicMax(&s_maxw, maxw);
+        if (nonfinite) atomicOr(&s_flags, FA_FLAG_NONFINITE);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int fl = s_flags;
+        if (s_cnt_bad) fl |= FA_FLAG_BAD_CODE;
+        if (s_cnt_cyc) fl |= FA_FLAG_CYCLE;
+        if (fl) status_report(a.st, fl, s_cnt_bad + s_cnt_cyc, s_first);
+        if (s_maxw) atomicMax(a.maxw, s_maxw);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: add the flow entering each perimeter cell to its downstream path
+// ---------------------------------------------------------------------------
+template <int VALM>
+__global__ void __launch_bounds__(256) k_offsets(TileArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int s_emax;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int t = blockIdx.x;
+    const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+    const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
+    const int h = (int)min((int64_t)a.th, a.rows - R0);
+    const int w = (int)min((int64_t)a.tw, a.cols - C0);
+    const int S = tile_stride(a.tw);
+    const int NB = (a.th + 2) * S;
+    const int n_in = h * w;
+    const int P = perim_count(h, w);
+
+    unsigned long long *off = reinterpret_cast<unsigned long long *>(smem);
+    u128 *inf = reinterpret_cast<u128 *>(off + NB);
+    uint8_t *ec = reinterpret_cast<uint8_t *>(inf + 2 * a.th + 2 * a.tw);
+
+    if (tid == 0) s_emax = INT_MIN;
+    int nbad = 0;
+    long long fbad = NO_INDEX;
+    load_codes(a, ec, R0, C0, h, w, S, false, nbad, fbad);
+    for (int i = tid; i < NB; i += nt) off[i] = 0ull;
+    __syncthreads();
+
+    // ---- in(p) = sum of G over the exits of neighbouring tiles draining into p
+    const int qf = VALM ? fix_scale(a.rows * a.cols, *a.maxw) : 0;
+    int any = 0, emax = INT_MIN;
+    for (int s = tid; s < P; s += nt) {
+        int r, c;
+        cell_of(s, h, w, r, c);
+        const int i = (r + 1) * S + c + 4;
+        u128 inflow = 0;
+        if (ec[i]) {
+#pragma unroll
+            for (int k = 1; k <= 8; ++k) {
+                const uint8_t en = ec[i + off_of(k, S)];
                 if ((en & HALO) && (en & 15) == dir_rev(k)) {
                     const int64_t gr = R0 + r + dir_dr(k), gc = C0 + c + dir_dc(k);
                     const int tyh = (int)(gr / a.th), txh = (int)(gc / a.tw);
@@ -251,187 +569,85 @@ __global__ void __launch_bounds__(256) k_tile(TileArgs a) {
                     const int wh = (int)min((int64_t)a.tw, a.cols - (int64_t)txh * a.tw);
                     const int sh = slot_of((int)(gr - (int64_t)tyh * a.th),
                                            (int)(gc - (int64_t)txh * a.tw), hh, wh);
-                    const size_t tbase = ((size_t)tyh * a.tiles_x + txh) * a.pmax;
-                    const uint16_t l = a.link[tbase + sh];
-                    if (l != LINK_TERM) {  // always an exit rank: h drains out of its tile
-                        inflow += a.G[tbase + l];
-                        any = true;
-                    }
+                    const size_t tb = ((size_t)tyh * a.tiles_x + txh) * a.pmax;
+                    const uint16_t l = a.link[tb + sh];
+                    if (l != LINK_TERM) inflow += a.G[tb + l];  // h is an exit of its tile
                 }
-            }
-            if (!any) continue;
-            if constexpr (VALM == 0) {
-                const uint64_t s64 = (uint64_t)val[i] + (uint64_t)inflow;
-                if ((inflow >> 32) != 0 || (s64 >> 32) != 0) ovf = 1;
-                val[i] = (uint32_t)s64;
-            } else {
-                val[i] = ff_add(val[i], fix2ff(inflow, q));
             }
         }
-        __syncthreads();
+        inf[s] = inflow;
+        if (inflow != 0) {
+            any = 1;
+            if constexpr (VALM == 1) {
+                int e;
+                frexp(fabs(fix2d(inflow, qf)), &e);
+                emax = max(emax, e);
+            }
+        }
+    }
+    if constexpr (VALM == 1) {
+        if (emax != INT_MIN) atomicMax(&s_emax, emax);
+    }
+    any = __syncthreads_or(any);
+    if (!any) return;
+    // offsets of this tile stay below P * max|in(p)| < 2^(emax + log2 P)
+    int qo = 0;
+    if constexpr (VALM == 1) {
+        int lp = 0;
+        while ((1 << lp) < P) ++lp;
+        qo = 62 - (s_emax + lp + 1);
     }
 
-    // ---- Kahn loop without a queue: walk from every source; a cell is final
-    // once its last in-tile upstream neighbour is, and the thread that
-    // delivers that last dependency carries on downstream (pull-gather in
-    // fixed E..SE order keeps floating-point sums deterministic). -------------
-    for (int j = tid; j < n_in; j += nt) {
-        const int r = j / w, c = j - r * w;
-        const int i0 = (r + 1) * W2 + (c + 1);
-        if (!ec[i0] || pmk[i0]) continue;
-        int cur = i0;
+    // ---- walk each entry's downstream path inside the tile, adding in(p) ---
+    for (int s = tid; s < P; s += nt) {
+        const u128 inflow = inf[s];
+        if (inflow == 0) continue;
+        unsigned long long v;
+        if constexpr (VALM == 0) {
+            v = (unsigned long long)inflow;
+        } else {
+            const int sh = qf - qo;  // from the graph scale to this tile's scale
+            const i128 si = (i128)inflow;
+            v = (unsigned long long)(long long)(sh >= 0 ? (sh < 127 ? (si >> sh) : (si < 0 ? -1 : 0))
+                                                        : (si << (-sh)));
+        }
+        int r, c;
+        cell_of(s, h, w, r, c);
+        int cur = (r + 1) * S + c + 4;
         for (int step = 0; step < n_in; ++step) {
-            uint8_t m = pmk[cur];
-            if constexpr (VALM == 0) {
-                uint64_t s64 = val[cur];
-                while (m) {
-                    const int k = __ffs(m);
-                    m &= m - 1;
-                    s64 += val[cur + off_of(k, W2)];
-                }
-                if (s64 >> 32) ovf = 1;
-                val[cur] = (uint32_t)s64;
-            } else {
-                FF v = val[cur];
-                while (m) {
-                    const int k = __ffs(m);
-                    m &= m - 1;
-                    v = ff_add(v, val[cur + off_of(k, W2)]);
-                }
-                val[cur] = v;
-            }
-            const int k = ec[cur] & 15;
-            if (k == 9) break;
-            const int nxt = cur + off_of(k, W2);
+            atomicAdd(&off[cur], v);
+            const int k = ec[cur];
+            if (k < 1 || k > 8) break;
+            const int nxt = cur + off_of(k, S);
             const uint8_t et = ec[nxt];
             if (!et || (et & HALO)) break;
-            __threadfence_block();
-            const int sh = (nxt & 3) * 8;
-            const uint32_t old = atomicSub(&cnt4[nxt >> 2], 1u << sh);
-            if (((old >> sh) & 0xffu) != 1u) break;
-            __threadfence_block();
             cur = nxt;
         }
     }
     __syncthreads();
 
-    if constexpr (PASS == 1) {
-        // ---- cells never finalised lie on in-tile cycles ------------------
-        int ncyc = 0;
-        long long fcyc = NO_INDEX;
-        for (int j = tid; j < n_in; j += nt) {
-            const int r = j / w, c = j - r * w;
-            const int i = (r + 1) * W2 + (c + 1);
-            if (ec[i] && cnt8[i]) {
-                ++ncyc;
-                fcyc = min(fcyc, (long long)((R0 + r) * a.cols + (C0 + c)));
-            }
-        }
-        // ---- exit cells (flow leaves the tile into a valid cell) get ranks -
-        const int P = perim_count(h, w);
-        const int chunk = (P + nt - 1) / nt;
-        const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
-        int mine = 0;
-        for (int s = s0; s < s1; ++s) {
-            int r, c;
-            cell_of(s, h, w, r, c);
-            const int i = (r + 1) * W2 + (c + 1);
-            const int k = ec[i] & 15;
-            bool ex = false;
-            if (k >= 1 && k <= 8) ex = (ec[i + off_of(k, W2)] & HALO) != 0;
-            mine += ex;
-        }
-        int total;
-        int rk = block_exclusive_scan(mine, s_warp, &total);
-        for (int s = s0; s < s1; ++s) {
-            int r, c;
-            cell_of(s, h, w, r, c);
-            const int i = (r + 1) * W2 + (c + 1);
-            const int k = ec[i] & 15;
-            bool ex = false;
-            if (k >= 1 && k <= 8) ex = (ec[i + off_of(k, W2)] & HALO) != 0;
-            rank[s] = ex ? (uint16_t)rk++ : LINK_TERM;
-        }
-        __syncthreads();
-        // ---- Algorithm 2 for every perimeter cell; exit records -----------
-        const size_t tbase = (size_t)t * a.pmax;
-        for (int s = tid; s < P; s += nt) {
-            int r, c;
-            cell_of(s, h, w, r, c);
-            int cur = (r + 1) * W2 + (c + 1);
-            uint16_t lk = LINK_TERM;
-            if (ec[cur]) {
-                for (int step = 0; step <= n_in; ++step) {
-                    const int k = ec[cur] & 15;
-                    if (k == 9) break;
-                    const int nxt = cur + off_of(k, W2);
-                    const uint8_t et = ec[nxt];
-                    if (!et) break;
-                    if (et & HALO) {
-                        const int cr = cur / W2 - 1, cc = cur - (cur / W2) * W2 - 1;
-                        lk = rank[slot_of(cr, cc, h, w)];
-                        break;
-                    }
-                    cur = nxt;
-                }
-            }
-            a.link[tbase + s] = lk;
-            const uint16_t myrank = rank[s];
-            if (myrank != LINK_TERM) {
-                const int i = (r + 1) * W2 + (c + 1);
-                const int k = ec[i] & 15;
-                const int64_t gr = R0 + r + dir_dr(k), gc = C0 + c + dir_dc(k);
-                const int tyd = (int)(gr / a.th), txd = (int)(gc / a.tw);
-                const int hd = (int)min((int64_t)a.th, a.rows - (int64_t)tyd * a.th);
-                const int wd = (int)min((int64_t)a.tw, a.cols - (int64_t)txd * a.tw);
-                const int sd = slot_of((int)(gr - (int64_t)tyd * a.th),
-                                       (int)(gc - (int64_t)txd * a.tw), hd, wd);
-                a.node_dst[tbase + myrank] =
-                    (uint32_t)(((size_t)tyd * a.tiles_x + txd) * a.pmax + sd);
-                double v;
-                if constexpr (VALM == 0) v = (double)val[i];
-                else v = (double)val[i].hi + (double)val[i].lo;
-                a.node_val[tbase + myrank] = v;
-            }
-        }
-        if (tid == 0) a.nexit[t] = (uint32_t)total;
-        // ---- status -------------------------------------------------------
-        nbad = warp_sum(nbad);
-        ncyc = warp_sum(ncyc);
-        fbad = warp_min_ll(min(fbad, fcyc));
-        maxw = warp_max_u(maxw);
-        nonfinite = warp_sum(nonfinite);
-        if ((tid & 31) == 0) {
-            if (nbad) atomicAdd(&s_cnt_bad, nbad);
-            if (ncyc) atomicAdd(&s_cnt_cyc, ncyc);
-            if (fbad != NO_INDEX) atomicMin(&s_first, fbad);
-            if (maxw) atomicMax(&s_maxw, maxw);
-            if (nonfinite) atomicOr(&s_flags, FA_FLAG_NONFINITE);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int fl = s_flags;
-            if (s_cnt_bad) fl |= FA_FLAG_BAD_CODE;
-            if (s_cnt_cyc) fl |= FA_FLAG_CYCLE;
-            if (fl) status_report(a.st, fl, s_cnt_bad + s_cnt_cyc, s_first);
-            if (s_maxw) atomicMax(a.maxw, s_maxw);
-        }
-    } else {
-        // ---- pass 2: write A (0 for NoData and for cells on cycles) --------
-        for (int j = tid; j < n_in; j += nt) {
-            const int r = j / w, c = j - r * w;
-            const int i = (r + 1) * W2 + (c + 1);
-            const bool fin = ec[i] && !cnt8[i];
-            const size_t o = (size_t)(R0 + r) * a.po + (C0 + c);
+    // ---- read-modify-write the output where an offset arrived -------------
+    int ovf = 0;
+    const double inv = ldexp(1.0, -qo);
+    for (int r = warp; r < h; r += nw) {
+        const size_t orow = (size_t)(R0 + r) * a.po + C0;
+        const int base = (r + 1) * S + 4;
+        for (int c = lane; c < w; c += 32) {
+            const unsigned long long o = off[base + c];
+            if (!o) continue;
             if constexpr (VALM == 0) {
-                reinterpret_cast<uint32_t *>(a.out)[o] = fin ? val[i] : 0u;
+                uint32_t *p = reinterpret_cast<uint32_t *>(a.out) + orow + c;
+                const unsigned long long s64 = (unsigned long long)*p + o;
+                if (s64 >> 32) ovf = 1;
+                *p = (uint32_t)s64;
             } else {
-                reinterpret_cast<float *>(a.out)[o] = fin ? ff_round(val[i]) : 0.0f;
+                float *p = reinterpret_cast<float *>(a.out) + orow + c;
+                *p = (float)((double)*p + (double)(long long)o * inv);
             }
         }
-        ovf = __syncthreads_or(ovf);
-        if (tid == 0 && ovf) status_report(a.st, FA_FLAG_OVERFLOW, 0, NO_INDEX);
     }
+    ovf = __syncthreads_or(ovf);
+    if (tid == 0 && ovf) status_report(a.st, FA_FLAG_OVERFLOW, 0, NO_INDEX);
 }
 
 // ---------------------------------------------------------------------------
@@ -564,6 +780,8 @@ bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g) {
     return true;
 }
 
+bool forward_tile_ok(const Geom &g, int valm) { return tile_shape_ok(g.th, g.tw, valm); }
+
 static int jump_rounds(int64_t max_nodes) {
     int k = 1;
     while (k < 40 && ((int64_t)1 << k) <= max_nodes) ++k;
@@ -589,20 +807,39 @@ size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry
     return c.used() + 256;
 }
 
-template <int VALM, int PASS>
-static cudaError_t launch_tile(const Geom &g, const TileArgs &ta, cudaStream_t s) {
-    const size_t smem = tile_smem_bytes(g.th, g.tw, VALM);
-    static int configured = 0;
+template <class K>
+static cudaError_t set_smem(K kern, size_t smem, int &configured) {
     if (smem > 48 * 1024 && configured < (int)smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile<VALM, PASS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = (int)smem;
     }
+    return cudaSuccess;
+}
+
+static int tile_threads(const Geom &g) {
     const int cells = g.th * g.tw;
-    int nt = cells >= 256 ? 256 : ((cells + 31) / 32) * 32;
-    k_tile<VALM, PASS><<<(unsigned)g.tiles(), nt, smem, s>>>(ta);
+    return cells >= 256 ? 256 : ((cells + 31) / 32) * 32;
+}
+
+template <int VALM>
+static cudaError_t launch_solve(const Geom &g, const TileArgs &ta, cudaStream_t s) {
+    static int configured = 0;
+    const size_t smem = solve_smem_bytes(g.th, g.tw, VALM);
+    cudaError_t e = set_smem(k_solve<VALM>, smem, configured);
+    if (e != cudaSuccess) return e;
+    k_solve<VALM><<<(unsigned)g.tiles(), tile_threads(g), smem, s>>>(ta);
+    return cudaGetLastError();
+}
+
+template <int VALM>
+static cudaError_t launch_offsets(const Geom &g, const TileArgs &ta, cudaStream_t s) {
+    static int configured = 0;
+    const size_t smem = offsets_smem_bytes(g.th, g.tw);
+    cudaError_t e = set_smem(k_offsets<VALM>, smem, configured);
+    if (e != cudaSuccess) return e;
+    k_offsets<VALM><<<(unsigned)g.tiles(), tile_threads(g), smem, s>>>(ta);
     return cudaGetLastError();
 }
 
@@ -639,7 +876,7 @@ cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, cons
     ta.maxw = ws.misc;
 
     timing_mark(0, s);
-    e = val_mode ? launch_tile<1, 1>(g, ta, s) : launch_tile<0, 1>(g, ta, s);
+    e = val_mode ? launch_solve<1>(g, ta, s) : launch_solve<0>(g, ta, s);
     if (e != cudaSuccess) return e;
     timing_mark(1, s);
 
@@ -666,7 +903,7 @@ cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, cons
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     timing_mark(2, s);
-    e = val_mode ? launch_tile<1, 2>(g, ta, s) : launch_tile<0, 2>(g, ta, s);
+    e = val_mode ? launch_offsets<1>(g, ta, s) : launch_offsets<0>(g, ta, s);
     timing_mark(3, s);
     timing_set_count(3);
     return e;

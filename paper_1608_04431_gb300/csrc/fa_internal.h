@@ -21,6 +21,9 @@ struct Geom {
 };
 
 bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g);
+// whether the forward tile kernel supports this tile shape (shared memory and
+// 16-bit cell indices); valm 0 = uint32 counts, 1 = float32
+bool forward_tile_ok(const Geom &g, int valm);
 
 // Workspace carving: every region 256-byte aligned.
 struct Carver {
@@ -64,5 +67,25 @@ void timing_set_count(int n);
 cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,
                            int64_t pm, const float *w, int64_t pw, void *out, int64_t po,
                            int val_mode, const FwdWork &ws, void *status, cudaStream_t s);
+
+// Adjoint workspace regions (device pointers); FF values stored as 8 bytes.
+struct AdjWork {
+    void *status;
+    uint32_t *misc;       // [1 + k] exit nodes still jumping after round k
+    uint32_t *nexit;      // [T]
+    uint16_t *link;       // [T*pmax] perimeter slot -> exit rank, 0xFFFF = terminates
+    uint32_t *node_dst;   // [T*pmax] exit rank -> global slot id of its target
+    uint64_t *lam_slot;   // [T*pmax] in-tile path sums on perimeter slots
+    uint64_t *v0, *v1;    // [T*pmax] forest jump values
+    uint64_t *outv;       // [T*pmax] out(e) per exit
+    uint32_t *J0, *J1;    // [T*pmax] forest jump pointers
+    int kmax;
+};
+
+size_t carve_adjoint(void *ws, size_t bytes, const Geom &g, AdjWork &w);
+bool adjoint_fits(const Geom &g);
+cudaError_t launch_adjoint(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,
+                           int64_t pm, const float *gin, int64_t pg, float *out, int64_t po,
+                           const AdjWork &ws, void *status, cudaStream_t s);
 
 }  // namespace fa
