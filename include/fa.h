@@ -64,7 +64,8 @@ typedef enum {
     FA_ERR_WORKSPACE = -4,    /* workspace NULL, too small or misaligned */
     FA_ERR_CUDA = -5,         /* a CUDA runtime call failed */
     FA_ERR_TIMEOUT = -6,      /* a bounded device wait ran out */
-    FA_ERR_NONFINITE = -7     /* a weight or gradient was NaN or infinite */
+    FA_ERR_NONFINITE = -7,    /* a weight or gradient was NaN or infinite */
+    FA_ERR_TOO_LARGE = -8     /* fa_accumulate_noalloc: raster needs more than its fixed scratch */
 } fa_status;
 
 typedef enum { FA_OUT_U32 = 0, FA_OUT_F32 = 1 } fa_out_dtype;
@@ -120,6 +121,36 @@ fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t cols, int64_
                         int64_t pitch_mask, void *out, fa_out_dtype out_dtype,
                         int64_t pitch_out, void *workspace, size_t ws_bytes,
                         const fa_options *opts, int32_t *d_status, void *stream);
+
+/*
+ * fa_accumulate for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this exists for programs that can pass their own input and
+ * output rasters but cannot supply scratch -- plugin hosts that expose only the
+ * caller's buffers, pipelines that reserve all device memory at start-up and
+ * forbid allocation afterwards, or programs whose memory is owned by another
+ * framework's allocator.  Arguments and results are those of fa_accumulate
+ * without the workspace: the scratch is one buffer of FA_NOALLOC_SCRATCH_BYTES
+ * compiled into the library (every GPU that loads its module keeps it until
+ * the process exits), and the call allocates nothing.
+ *  - Size limit: rasters whose fa_workspace_size() exceeds
+ *    FA_NOALLOC_SCRATCH_BYTES return FA_ERR_TOO_LARGE with nothing enqueued
+ *    (with the default 64 x 64 tiles that is roughly 15 million cells, e.g.
+ *    3800 x 3800).
+ *  - The first call on each device looks up the buffer's device address
+ *    (cudaGetSymbolAddress, which may load the library's module); make that
+ *    first call outside any stream capture.
+ *  - All calls on a device share the buffer: calls that can overlap on the GPU
+ *    race and give wrong results; order them on one stream or synchronise.
+ *  - d_status may be NULL, in which case device-detected conditions are
+ *    recorded only inside the shared buffer and cannot be read back.
+ *  - Phase timing is not recorded for these calls.
+ */
+#define FA_NOALLOC_SCRATCH_BYTES (64u << 20)
+fa_status fa_accumulate_noalloc(const uint8_t *codes, int64_t rows, int64_t cols,
+                                int64_t pitch_codes, const float *weights, int64_t pitch_w,
+                                const uint8_t *mask, int64_t pitch_mask, void *out,
+                                fa_out_dtype out_dtype, int64_t pitch_out, const fa_options *opts,
+                                int32_t *d_status, void *stream);
 
 /*
  * Adjoint (transpose) of fa_accumulate with respect to the weights.  Eq. 1 with

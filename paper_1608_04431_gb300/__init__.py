@@ -17,11 +17,12 @@ import torch
 
 from . import _lib
 from ._lib import (FA_ERR_BAD_CODE, FA_ERR_CUDA, FA_ERR_CYCLE, FA_ERR_INVALID_ARG,  # noqa: F401
-                   FA_ERR_NONFINITE, FA_ERR_TIMEOUT, FA_ERR_WORKSPACE, FA_OK, FA_OUT_F32,
-                   FA_OUT_U32, FA_STATUS_WORDS, FA_WARN_OVERFLOW, STATUS_NAMES, fa_options)
+                   FA_ERR_NONFINITE, FA_ERR_TIMEOUT, FA_ERR_TOO_LARGE, FA_ERR_WORKSPACE,
+                   FA_NOALLOC_SCRATCH_BYTES, FA_OK, FA_OUT_F32, FA_OUT_U32, FA_STATUS_WORDS,
+                   FA_WARN_OVERFLOW, STATUS_NAMES, fa_options)
 
 __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumulate",
-           "fa_accumulate_adjoint", "fa_status_read", "adjoint", "FlowAccumulate",
+           "fa_accumulate_noalloc", "fa_accumulate_adjoint", "fa_status_read", "adjoint", "FlowAccumulate",
            "fa_timing_enable", "fa_timing_read", "accumulate",
            "FlowAccError", "options"]
 
@@ -80,6 +81,19 @@ def fa_accumulate(codes, weights, mask, out, out_dtype, workspace, opts=None, d_
         _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(mask),
         _pitch(mask), _ptr(out), out_dtype, _pitch(out), _ptr(workspace), workspace.numel(),
         ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_accumulate_noalloc(codes, weights, mask, out, out_dtype, opts=None, d_status=None,
+                          stream=None) -> int:
+    """Enqueue fa_accumulate_noalloc: fa_accumulate without a workspace, for
+    callers that cannot allocate device memory; scratch comes from a fixed
+    buffer inside the library (FA_NOALLOC_SCRATCH_BYTES), shared by all calls
+    on a device, so overlapping calls race.  Returns the host-side status."""
+    rows, cols = codes.shape
+    return _lib.load().fa_accumulate_noalloc(
+        _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(mask),
+        _pitch(mask), _ptr(out), out_dtype, _pitch(out), ctypes.byref(opts or fa_options()),
+        _ptr(d_status), _stream_ptr(stream))
 
 
 def fa_accumulate_adjoint(codes, mask, grad_out, grad_w, workspace, opts=None, d_status=None,

@@ -18,6 +18,8 @@ FA_ERR_WORKSPACE = -4
 FA_ERR_CUDA = -5
 FA_ERR_TIMEOUT = -6
 FA_ERR_NONFINITE = -7
+FA_ERR_TOO_LARGE = -8
+FA_NOALLOC_SCRATCH_BYTES = 64 << 20
 FA_OUT_U32 = 0
 FA_OUT_F32 = 1
 FA_STATUS_WORDS = 4
@@ -27,6 +29,7 @@ STATUS_NAMES = {
     FA_ERR_BAD_CODE: "FA_ERR_BAD_CODE", FA_ERR_CYCLE: "FA_ERR_CYCLE",
     FA_ERR_WORKSPACE: "FA_ERR_WORKSPACE", FA_ERR_CUDA: "FA_ERR_CUDA",
     FA_ERR_TIMEOUT: "FA_ERR_TIMEOUT", FA_ERR_NONFINITE: "FA_ERR_NONFINITE",
+    FA_ERR_TOO_LARGE: "FA_ERR_TOO_LARGE",
 }
 
 
@@ -45,6 +48,8 @@ SIGNATURES = {
     "fa_kernel_launches": (_I32, [_I64, _I64, _OPT]),
     "fa_accumulate": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I32, _I64, _P, _SZ,
                              _OPT, _P, _P]),
+    "fa_accumulate_noalloc": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I32, _I64,
+                                     _OPT, _P, _P]),
     "fa_accumulate_adjoint": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ,
                                      _OPT, _P, _P]),
     "fa_status_read": (_I32, [_P, _P, _P, _PI64, _PI64]),

@@ -35,6 +35,11 @@ void timing_mark(int i, cudaStream_t s) {
 void timing_set_count(int n) {
     if (g_timing) g_phases = n;
 }
+bool timing_swap(bool on) {
+    const bool was = g_timing;
+    g_timing = on;
+    return was;
+}
 }  // namespace fa
 
 extern "C" void fa_timing_enable(int32_t on) {

@@ -61,6 +61,8 @@ size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry
 constexpr int kMaxPhase = 8;
 void timing_mark(int i, cudaStream_t s);
 void timing_set_count(int n);
+// sets whether phase timing records events; returns the previous setting
+bool timing_swap(bool on);
 
 // Launch the whole forward pipeline on `stream`.  val_mode 0: uint32 counts
 // (weights must be NULL); 1: float32 output (weights or unit).
