@@ -84,13 +84,14 @@ __host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm) {
     b += nb;                                  // effective codes
     b += (size_t)th * tw * 2;                 // source queue (u16 cell indices)
     b += (size_t)(2 * th + 2 * tw) * 2;       // exit rank per perimeter slot
+    b += (size_t)(2 * th + 2 * tw) * 2;       // entry-cell list
     return (b + 15) & ~size_t(15);
 }
 
 __host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
     const size_t nb = (size_t)(th + 2) * tile_stride(tw);
     size_t b = nb * 8;                        // per-cell offset
-    b += (size_t)(2 * th + 2 * tw) * 16;      // inflow per perimeter slot
+    b += (size_t)(2 * th + 2 * tw) * 18;      // inflow and slot per listed entry
     b += nb;                                  // effective codes
     return (b + 15) & ~size_t(15);
 }
@@ -102,66 +103,80 @@ __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
 
 constexpr uint16_t LAB_UNKNOWN = 0xFFFE;
 
-// effective code byte of grid cell (gr, gc): 0 for NoData / masked / invalid /
-// off-grid, else the code with HALO set when the cell lies outside the tile
-__device__ __forceinline__ uint8_t eff_code(const TileArgs &a, int64_t gr, int64_t gc, bool halo,
-                                            int &nbad, long long &fbad, bool count_bad) {
-    if (gr < 0 || gr >= a.rows || gc < 0 || gc >= a.cols) return 0;
-    const uint8_t k = a.codes[gr * a.pc + gc];
-    if (k > 9) {
-        if (count_bad) {
-            ++nbad;
-            fbad = min(fbad, (long long)(gr * a.cols + gc));
-        }
-        return 0;
-    }
-    if (k == 0 || (a.mask && a.mask[gr * a.pm + gc])) return 0;
-    return halo ? (uint8_t)(k | HALO) : k;
-}
-
 // Load a tile's effective codes with a one-cell halo (Algorithm 1's F) into
-// ec, one 32-bit word per lane; counts invalid codes inside the tile.
+// ec.  Each lane first issues the loads for up to four rows (one 32-bit word of
+// interior codes, or the single halo byte its word holds), then converts and
+// stores them, so several global loads are in flight per lane.  Invalid codes
+// inside the tile are counted.
 __device__ __forceinline__ void load_codes(const TileArgs &a, uint8_t *ec, int64_t R0, int64_t C0,
                                            int h, int w, int S, bool count_bad, int &nbad,
                                            long long &fbad) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool fast =
-        ((reinterpret_cast<uintptr_t>(a.codes) | (uintptr_t)a.pc | (uintptr_t)C0) & 3) == 0 &&
-        a.mask == nullptr;
+        ((reinterpret_cast<uintptr_t>(a.codes) | (uintptr_t)a.pc | (uintptr_t)C0) & 3) == 0;
     const int words = S >> 2;
-    for (int hr = warp; hr < h + 2; hr += nw) {
-        const int64_t gr = R0 - 1 + hr;
-        const bool hrow = hr == 0 || hr == h + 1;
-        uint32_t *row = reinterpret_cast<uint32_t *>(ec + hr * S);
-        for (int wd = lane; wd < words; wd += 32) {
+    constexpr int U = 4;
+    for (int hr0 = warp; hr0 < h + 2; hr0 += U * nw) {
+        for (int wd0 = 0; wd0 < words; wd0 += 32) {
+            const int wd = wd0 + lane;
             const int c0 = 4 * wd - 4;  // tile column of the word's first byte
-            uint32_t v = 0;
-            if (!hrow && c0 >= 0 && c0 + 3 < w && fast && gr >= 0 && gr < a.rows) {
-                const uint32_t raw =
-                    *reinterpret_cast<const uint32_t *>(a.codes + gr * a.pc + C0 + c0);
+            uint32_t raw[U], mraw[U];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t k = (raw >> (8 * j)) & 0xffu;
-                    if (k > 9) {
-                        if (count_bad) {
-                            ++nbad;
-                            fbad = min(fbad, (long long)(gr * a.cols + C0 + c0 + j));
-                        }
+            for (int u = 0; u < U; ++u) {  // issue every load first
+                const int hr = hr0 + u * nw;
+                raw[u] = 0;
+                mraw[u] = 0;
+                if (hr >= h + 2 || wd >= words) continue;
+                const int64_t gr = R0 - 1 + hr;
+                if (gr < 0 || gr >= a.rows) continue;
+                const uint8_t *row = a.codes + gr * a.pc + C0;
+                const uint8_t *mrow = a.mask ? a.mask + gr * a.pm + C0 : nullptr;
+                if (c0 >= 0 && c0 + 3 < w) {
+                    if (fast) {
+                        raw[u] = *reinterpret_cast<const uint32_t *>(row + c0);
                     } else {
-                        v |= k << (8 * j);
+                        raw[u] = (uint32_t)row[c0] | ((uint32_t)row[c0 + 1] << 8) |
+                                 ((uint32_t)row[c0 + 2] << 16) | ((uint32_t)row[c0 + 3] << 24);
+                    }
+                    if (mrow)
+                        mraw[u] = (uint32_t)mrow[c0] | ((uint32_t)mrow[c0 + 1] << 8) |
+                                  ((uint32_t)mrow[c0 + 2] << 16) | ((uint32_t)mrow[c0 + 3] << 24);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int c = c0 + j;
+                        if (c < -1 || c > w) continue;
+                        if (C0 + c < 0 || C0 + c >= a.cols) continue;
+                        raw[u] |= (uint32_t)row[c] << (8 * j);
+                        if (mrow) mraw[u] |= (uint32_t)(mrow[c] ? 1 : 0) << (8 * j);
                     }
                 }
-            } else {
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {  // then convert and store
+                const int hr = hr0 + u * nw;
+                if (hr >= h + 2 || wd >= words) continue;
+                const int64_t gr = R0 - 1 + hr;
+                const bool hrow = hr == 0 || hr == h + 1;
+                uint32_t v = 0;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int c = c0 + j;
                     if (c < -1 || c > w) continue;
+                    const uint32_t k = (raw[u] >> (8 * j)) & 0xffu;
                     const bool hcell = hrow || c == -1 || c == w;
-                    v |= (uint32_t)eff_code(a, gr, C0 + c, hcell, nbad, fbad, count_bad && !hcell)
-                         << (8 * j);
+                    if (k > 9) {
+                        if (count_bad && !hcell) {
+                            ++nbad;
+                            fbad = min(fbad, (long long)(gr * a.cols + C0 + c));
+                        }
+                        continue;
+                    }
+                    if (k == 0 || ((mraw[u] >> (8 * j)) & 0xffu)) continue;
+                    v |= (k | (hcell ? HALO : 0u)) << (8 * j);
                 }
+                reinterpret_cast<uint32_t *>(ec + hr * S)[wd] = v;
             }
-            row[wd] = v;
         }
     }
 }
@@ -178,11 +193,13 @@ __device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
 // ---------------------------------------------------------------------------
 // pass 1: tile solve
 // ---------------------------------------------------------------------------
+
 template <int VALM>
-__global__ void __launch_bounds__(256) k_solve(TileArgs a) {
+__global__ void __launch_bounds__(256, 5) k_solve(TileArgs a) {
+    typedef typename std::conditional<VALM == 0, uint32_t, long long>::type PV;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_cnt_bad, s_cnt_cyc, s_flags, s_nsrc, s_qhead;
+    __shared__ int s_cnt_bad, s_cnt_cyc, s_flags, s_nsrc, s_nent;
     __shared__ long long s_first;
     __shared__ uint32_t s_maxw;
 
@@ -196,6 +213,8 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
     const int S = tile_stride(a.tw);
     const int NB = (a.th + 2) * S;
     const int n_in = h * w;
+    const int P = perim_count(h, w);
+    const size_t tbase = (size_t)t * a.pmax;
 
     // counts: word = [step:4 | pending:4 | sum:24]
     // weights: word = [step:4 | pending:4] and a separate 64-bit fixed-point sum
@@ -204,7 +223,7 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
     uint8_t *ec = reinterpret_cast<uint8_t *>(word + NB);
     uint16_t *srcq = reinterpret_cast<uint16_t *>(ec + NB);
     uint16_t *rank = srcq + a.th * a.tw;
-    uint16_t *lab = reinterpret_cast<uint16_t *>(word);  // after the solve
+    uint16_t *entq = rank + a.pmax;
 
     if (tid == 0) {
         s_cnt_bad = 0;
@@ -213,24 +232,33 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
         s_first = NO_INDEX;
         s_maxw = 0;
         s_nsrc = 0;
-        s_qhead = 0;
+        s_nent = 0;
     }
     int nbad = 0;
     long long fbad = NO_INDEX;
+    // [phase] load
     load_codes(a, ec, R0, C0, h, w, S, true, nbad, fbad);
     __syncthreads();
 
-    // ---- dependency counts D (Algorithm 1, first loop), four cells at a time:
-    // bit k-1 of pm is set when the neighbour at offset k holds the reverse code
+    // [phase] init
+    // ---- dependency counts D (Algorithm 1, first loop) and the in-tile
+    // successor of every cell, four cells per lane from the same neighbour
+    // words: byte j of nbr_k is the code of cell j's neighbour in direction k.
+    // A row of g groups uses the next power of two >= g lanes, so one warp
+    // iteration covers 32 / lanes-per-row rows.
     uint32_t maxw = 0;
     int nonfinite = 0;
     const int groups = (w + 3) >> 2;
-    for (int r = warp; r < h; r += nw) {
-        for (int g0 = 0; g0 < groups; g0 += 32) {  // warp-uniform trip count
-            const int gq = g0 + lane;
+    int lpr_log = 0;
+    while ((1 << lpr_log) < groups && lpr_log < 5) ++lpr_log;
+    const int rows_per_it = 32 >> lpr_log;
+    const int sub = lane >> lpr_log, gl = lane & ((1 << lpr_log) - 1);
+    for (int r0 = warp * rows_per_it; r0 < h; r0 += nw * rows_per_it) {
+        for (int g0 = 0; g0 < groups; g0 += (1 << lpr_log)) {  // warp-uniform trip counts
+            const int r = r0 + sub, gq = g0 + gl;
             int mysrc = 0;
             uint16_t srcs[4];
-            if (gq < groups) {
+            if (r < h && gq < groups) {
                 const int c = 4 * gq;
                 const int base = (r + 1) * S + c + 4;
                 uint32_t L[3], Cw[3], Rw[3];
@@ -241,41 +269,48 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
                     Cw[d] = p[0];
                     Rw[d] = p[1];
                 }
-                uint32_t pm = 0;
+                const uint32_t me = Cw[1];
+                uint32_t pm = 0, stepw = 0;
 #pragma unroll
                 for (int k = 1; k <= 8; ++k) {
                     const int d = dir_dr(k) + 1, dc = dir_dc(k);
                     const uint32_t nbr = dc == 0 ? Cw[d]
                                                  : (dc > 0 ? __funnelshift_r(Cw[d], Rw[d], 8)
                                                            : __funnelshift_l(L[d], Cw[d], 8));
+                    const uint32_t kk = 0x01010101u * (uint32_t)k;
+                    // the neighbour drains into this cell
                     pm |= __vcmpeq4(nbr, 0x01010101u * (uint32_t)dir_rev(k)) &
                           (0x01010101u << (k - 1));
+                    // this cell drains into the neighbour, a valid cell of the tile
+                    const uint32_t inside = __vcmpne4(nbr, 0u) & __vcmpeq4(nbr & 0x10101010u, 0u);
+                    stepw |= __vcmpeq4(me, kk) & inside & kk;
                 }
                 uint32_t x = pm - ((pm >> 1) & 0x55555555u);  // per-byte popcount
                 x = (x & 0x33333333u) + ((x >> 2) & 0x33333333u);
                 x = (x + (x >> 4)) & 0x0F0F0F0Fu;
                 const int nvalid = min(4, w - c);
+                const uint32_t colmask = nvalid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nvalid)) - 1u);
+                const uint32_t valid = __vcmpne4(me, 0u) & colmask;
+                const uint32_t src = valid & __vcmpeq4(x, 0u);
+                uint32_t wv4[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (j >= nvalid) break;
-                    const int i = base + j;
-                    if (!((Cw[1] >> (8 * j)) & 0xffu)) {
-                        word[i] = 0;
-                        continue;
-                    }
-                    const uint32_t pend = (x >> (8 * j)) & 0xffu;
-                    const uint32_t st = step_of(ec, i, S);
-                    if constexpr (VALM == 0) {
-                        word[i] = (st << 28) | (pend << 24) | 1u;
-                    } else {
-                        word[i] = (st << 4) | pend;
-                        const float wv = a.w ? a.w[(R0 + r) * a.pw + (C0 + c + j)] : 1.0f;
-                        const uint32_t b = __float_as_uint(wv) & 0x7fffffffu;
+                    const uint32_t sj = (stepw >> (8 * j)) & 15u, pj = (x >> (8 * j)) & 15u;
+                    const bool vj = (valid >> (8 * j)) & 1u;
+                    if constexpr (VALM == 0) wv4[j] = vj ? ((sj << 28) | (pj << 24) | 1u) : 0u;
+                    else wv4[j] = vj ? ((sj << 4) | pj) : 0u;
+                    if ((src >> (8 * j)) & 1u) srcs[mysrc++] = (uint16_t)(base + j);
+                }
+                *reinterpret_cast<uint4 *>(word + base) = make_uint4(wv4[0], wv4[1], wv4[2], wv4[3]);
+                if constexpr (VALM == 1) {
+                    for (int j = 0; j < nvalid; ++j) {
+                        if (!((valid >> (8 * j)) & 1u)) continue;
+                        const float wf = a.w ? a.w[(R0 + r) * a.pw + (C0 + c + j)] : 1.0f;
+                        const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
                         if (b >= 0x7f800000u) nonfinite = 1;
                         maxw = max(maxw, b);
-                        fsum[i] = (long long)__float_as_uint(wv);  // raw bits until the scale is known
+                        fsum[base + j] = (long long)__float_as_uint(wf);  // raw bits until scaled
                     }
-                    if (pend == 0) srcs[mysrc++] = (uint16_t)i;
                 }
             }
             // append the lanes' sources to the block queue (warp-aggregated)
@@ -292,6 +327,55 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
             for (int j = 0; j < mysrc; ++j) srcq[qbase + incl - mysrc + j] = srcs[j];
         }
     }
+
+    // ---- exit cells (flow leaves the tile into a valid cell) get ranks in
+    // slot order; entry cells (flow arrives from a valid cell outside) are
+    // listed for Algorithm 2 ------------------------------------------------
+    const int chunk = (P + nt - 1) / nt;
+    const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
+    int mine = 0;
+    for (int s = s0; s < s1; ++s) {
+        int r, c;
+        cell_of(s, h, w, r, c);
+        const int i = (r + 1) * S + c + 4;
+        const int k = ec[i];
+        if (k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO)) ++mine;
+    }
+    int total;
+    int rk = block_exclusive_scan(mine, s_warp, &total);
+    for (int s = s0; s < s1; ++s) {
+        int r, c;
+        cell_of(s, h, w, r, c);
+        const int i = (r + 1) * S + c + 4;
+        const int k = ec[i];
+        const bool ex = k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO);
+        rank[s] = ex ? (uint16_t)rk : LINK_TERM;
+        bool entry = false;
+        if (ec[i]) {
+#pragma unroll
+            for (int kk = 1; kk <= 8; ++kk) {
+                const uint8_t en = ec[i + off_of(kk, S)];
+                entry |= (en & HALO) && (en & 15) == dir_rev(kk);
+            }
+        }
+        if (ex) {
+            // where the exit's flow goes: a perimeter slot of a neighbouring tile
+            const int rr = r + dir_dr(k), cc = c + dir_dc(k);  // tile-local, one step outside
+            const int tyd = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
+            const int txd = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
+            const int64_t R0d = (int64_t)tyd * a.th, C0d = (int64_t)txd * a.tw;
+            const int hd = (int)min((int64_t)a.th, a.rows - R0d);
+            const int wd = (int)min((int64_t)a.tw, a.cols - C0d);
+            const int sd = slot_of((int)(R0 + rr - R0d), (int)(C0 + cc - C0d), hd, wd);
+            a.node_dst[tbase + rk] = (uint32_t)(((size_t)tyd * a.tiles_x + txd) * a.pmax + sd);
+            a.link[tbase + s] = (uint16_t)rk;  // an exit links to itself
+            ++rk;
+        } else if (entry) {
+            entq[atomicAdd(&s_nent, 1)] = (uint16_t)s;
+        } else {
+            a.link[tbase + s] = LINK_TERM;
+        }
+    }
     int qt = 0;
     if constexpr (VALM == 1) {
         maxw = warp_max_u(maxw);
@@ -306,64 +390,56 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
     }
     __syncthreads();
 
-    // ---- the Kahn loop without a ready queue: lanes take sources from the
-    // block queue and push their final value downstream; the lane whose
-    // delivery completes a cell (its last pending upstream neighbour) carries
-    // on from it.  Integer sums make the result independent of the order.
-    {
+    // [phase] walk
+    // ---- the Kahn loop without a ready queue: every lane walks its static
+    // slice of the source queue, pushing final values downstream; the lane
+    // whose delivery completes a cell (its last pending upstream neighbour)
+    // carries on from it.  Integer sums make the order irrelevant, and the
+    // lanes need no coordination.  Meanwhile the last two warps run
+    // Algorithm 2 for the entry cells (it reads only the codes).
+    const int lwn = nw >= 4 ? 2 : 0;          // warps walking entry links alongside
+    const int mww = nw - lwn;                 // warps running the solve
+    if (warp < mww) {
         const int nsrc = s_nsrc;
-        int cur = -1;
+        const int stride = mww * 32;
+        int qi = tid, cur = -1;
         uint32_t st = 0;
-        uint32_t v32 = 0;
-        long long v64 = 0;
-        bool drained = false;
-        for (int guard = 0; guard < 4 * n_in + 64; ++guard) {
-            const unsigned idle = __ballot_sync(0xffffffffu, cur < 0);
-            if (idle && !drained) {
-                const int leader = __ffs(idle) - 1;
-                int qb = 0;
-                if (lane == leader) qb = atomicAdd(&s_qhead, __popc(idle));
-                qb = __shfl_sync(0xffffffffu, qb, leader);
-                if (qb >= nsrc) drained = true;
-                if (cur < 0) {
-                    const int pos = qb + __popc(idle & ((1u << lane) - 1u));
-                    if (pos < nsrc) {
-                        cur = srcq[pos];
-                        const uint32_t wd = word[cur];
-                        if constexpr (VALM == 0) {
-                            st = wd >> 28;
-                            v32 = wd & 0xFFFFFFu;
-                        } else {
-                            st = wd >> 4;
-                            v64 = fsum[cur];
-                        }
-                    }
+        PV v = 0;
+        for (int guard = 0; guard < 2 * n_in + 2; ++guard) {
+            if (cur < 0) {
+                if (qi >= nsrc) break;
+                cur = srcq[qi];
+                qi += stride;
+                const uint32_t wd = word[cur];
+                if constexpr (VALM == 0) {
+                    st = wd >> 28;
+                    v = wd & 0xFFFFFFu;
+                } else {
+                    st = wd >> 4;
+                    v = fsum[cur];
                 }
             }
-            if (__ballot_sync(0xffffffffu, cur >= 0) == 0 && drained) break;
-            if (cur < 0) continue;
             if (st == 0) {
                 cur = -1;
                 continue;
             }
             const int tgt = cur + off_of((int)st, S);
             if constexpr (VALM == 0) {
-                const uint32_t old = atomicAdd(&word[tgt], v32 - (1u << 24));
+                const uint32_t old = atomicAdd(&word[tgt], v - (1u << 24));
                 if (((old >> 24) & 15u) == 1u) {
-                    v32 += old & 0xFFFFFFu;
+                    v += old & 0xFFFFFFu;
                     st = old >> 28;
                     cur = tgt;
                 } else {
                     cur = -1;
                 }
             } else {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&fsum[tgt]),
-                          (unsigned long long)v64);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&fsum[tgt]), (unsigned long long)v);
                 __threadfence_block();
                 const uint32_t old = atomicSub(&word[tgt], 1u);
                 if ((old & 15u) == 1u) {
                     __threadfence_block();
-                    v64 = *reinterpret_cast<volatile long long *>(&fsum[tgt]);
+                    v = *reinterpret_cast<volatile long long *>(&fsum[tgt]);
                     st = old >> 4;
                     cur = tgt;
                 } else {
@@ -372,10 +448,38 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
             }
         }
     }
+    if (warp >= mww || lwn == 0) {
+        if (lwn == 0) __syncthreads();  // one- to three-warp blocks: links after the solve
+        // Algorithm 2 for the entry cells: follow the in-tile path to the exit
+        const int nent = s_nent;
+        const int lt = lwn ? tid - mww * 32 : tid, stride = lwn ? lwn * 32 : nt;
+        for (int q = lt; q < nent; q += stride) {
+            const int s = entq[q];
+            int r, c;
+            cell_of(s, h, w, r, c);
+            int c2 = (r + 1) * S + c + 4;
+            uint16_t lk = LINK_TERM;
+            for (int steps = 0; steps <= n_in; ++steps) {
+                const int k = ec[c2];
+                if (k < 1 || k > 8) break;
+                const int nxt = c2 + off_of(k, S);
+                const uint8_t et = ec[nxt];
+                if (!et) break;
+                if (et & HALO) {
+                    const int cr = c2 / S - 1, cc = c2 - (c2 / S) * S - 4;
+                    lk = rank[slot_of(cr, cc, h, w)];
+                    break;
+                }
+                c2 = nxt;
+            }
+            a.link[tbase + s] = lk;
+        }
+    }
     __syncthreads();
 
+    // [phase] output
     // ---- write A_loc (0 for NoData and for cells on cycles: those never
-    // lose their last pending dependency) ---------------------------------
+    // lose their last pending dependency); exit records --------------------
     int ncyc = 0;
     long long fcyc = NO_INDEX;
     const double inv = ldexp(1.0, -qt);
@@ -398,102 +502,21 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
             if constexpr (VALM == 0) {
                 reinterpret_cast<uint32_t *>(a.out)[orow + c] = fin ? (wd & 0xFFFFFFu) : 0u;
             } else {
-                reinterpret_cast<float *>(a.out)[orow + c] = fin ? (float)((double)fsum[i] * inv) : 0.0f;
+                reinterpret_cast<float *>(a.out)[orow + c] =
+                    fin ? (float)((double)fsum[i] * inv) : 0.0f;
             }
         }
     }
-
-    // ---- exit cells (flow leaves the tile into a valid cell) get ranks ----
-    const int P = perim_count(h, w);
-    const int chunk = (P + nt - 1) / nt;
-    const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
-    int mine = 0;
-    for (int s = s0; s < s1; ++s) {
-        int r, c;
-        cell_of(s, h, w, r, c);
-        const int i = (r + 1) * S + c + 4;
-        const int k = ec[i];
-        if (k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO)) ++mine;
-    }
-    int total;
-    int rk = block_exclusive_scan(mine, s_warp, &total);
-    const size_t tbase = (size_t)t * a.pmax;
-    for (int s = s0; s < s1; ++s) {
-        int r, c;
-        cell_of(s, h, w, r, c);
-        const int i = (r + 1) * S + c + 4;
-        const int k = ec[i];
-        const bool ex = k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO);
-        rank[s] = ex ? (uint16_t)rk : LINK_TERM;
-        if (ex) {
-            // perimeter record: A_loc at the exit and the target of its flow
-            const int64_t gr = R0 + r + dir_dr(k), gc = C0 + c + dir_dc(k);
-            const int tyd = (int)(gr / a.th), txd = (int)(gc / a.tw);
-            const int hd = (int)min((int64_t)a.th, a.rows - (int64_t)tyd * a.th);
-            const int wd = (int)min((int64_t)a.tw, a.cols - (int64_t)txd * a.tw);
-            const int sd = slot_of((int)(gr - (int64_t)tyd * a.th), (int)(gc - (int64_t)txd * a.tw),
-                                   hd, wd);
-            a.node_dst[tbase + rk] = (uint32_t)(((size_t)tyd * a.tiles_x + txd) * a.pmax + sd);
-            double v;
-            if constexpr (VALM == 0) v = (double)(word[i] & 0xFFFFFFu);
-            else v = (double)fsum[i] * inv;
-            a.node_val[tbase + rk] = v;
-            ++rk;
-        }
-    }
-    __syncthreads();
-    // labels (exit rank reached, or terminates) replace the packed words
-    for (int i = tid; i < NB; i += nt) lab[i] = LAB_UNKNOWN;
-    __syncthreads();
-
-    // ---- Algorithm 2 for the cells that receive flow from other tiles (and
-    // for exits, which link to themselves); walks stop at the first cell an
-    // earlier walk labelled ------------------------------------------------
     for (int s = tid; s < P; s += nt) {
+        const uint16_t rks = rank[s];
+        if (rks == LINK_TERM) continue;
         int r, c;
         cell_of(s, h, w, r, c);
-        const int i0 = (r + 1) * S + c + 4;
-        uint16_t lk = LINK_TERM;
-        const uint16_t myrank = rank[s];
-        bool entry = false;
-        if (ec[i0]) {
-#pragma unroll
-            for (int k = 1; k <= 8; ++k) {
-                const uint8_t en = ec[i0 + off_of(k, S)];
-                entry |= (en & HALO) && (en & 15) == dir_rev(k);
-            }
-        }
-        if (myrank != LINK_TERM) {
-            lk = myrank;
-        } else if (entry) {
-            int cur = i0, steps = 0;
-            for (; steps <= n_in; ++steps) {
-                const uint16_t L0 = lab[cur];
-                if (L0 != LAB_UNKNOWN) {
-                    lk = L0;
-                    break;
-                }
-                const int k = ec[cur];
-                if (k < 1 || k > 8) break;
-                const int nxt = cur + off_of(k, S);
-                const uint8_t et = ec[nxt];
-                if (!et) break;
-                if (et & HALO) {
-                    const int cr = cur / S - 1, cc = cur - (cur / S) * S - 4;
-                    lk = rank[slot_of(cr, cc, h, w)];
-                    break;
-                }
-                cur = nxt;
-            }
-            // label the walked cells so later walks stop early (benign races:
-            // every writer stores the same value)
-            int c2 = i0;
-            for (int st2 = 0; st2 < steps; ++st2) {
-                lab[c2] = lk;
-                c2 += off_of(ec[c2], S);
-            }
-        }
-        a.link[tbase + s] = lk;
+        const int i = (r + 1) * S + c + 4;
+        double vv;
+        if constexpr (VALM == 0) vv = (double)(word[i] & 0xFFFFFFu);
+        else vv = (double)fsum[i] * inv;
+        a.node_val[tbase + rks] = vv;  // A_loc at the exit (the perimeter data's A)
     }
     if (tid == 0) a.nexit[t] = (uint32_t)total;
 
@@ -518,15 +541,16 @@ __global__ void __launch_bounds__(256) k_solve(TileArgs a) {
         if (fl) status_report(a.st, fl, s_cnt_bad + s_cnt_cyc, s_first);
         if (s_maxw) atomicMax(a.maxw, s_maxw);
     }
+    // [phase] end
 }
 
 // ---------------------------------------------------------------------------
 // pass 2: add the flow entering each perimeter cell to its downstream path
 // ---------------------------------------------------------------------------
 template <int VALM>
-__global__ void __launch_bounds__(256) k_offsets(TileArgs a) {
+__global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_emax;
+    __shared__ int s_emax, s_nent;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int t = blockIdx.x;
@@ -540,10 +564,14 @@ __global__ void __launch_bounds__(256) k_offsets(TileArgs a) {
     const int P = perim_count(h, w);
 
     unsigned long long *off = reinterpret_cast<unsigned long long *>(smem);
-    u128 *inf = reinterpret_cast<u128 *>(off + NB);
-    uint8_t *ec = reinterpret_cast<uint8_t *>(inf + 2 * a.th + 2 * a.tw);
+    u128 *einf = reinterpret_cast<u128 *>(off + NB);  // inflow per listed entry
+    uint16_t *eslot = reinterpret_cast<uint16_t *>(einf + a.pmax);
+    uint8_t *ec = reinterpret_cast<uint8_t *>(eslot + a.pmax);
 
-    if (tid == 0) s_emax = INT_MIN;
+    if (tid == 0) {
+        s_emax = INT_MIN;
+        s_nent = 0;
+    }
     int nbad = 0;
     long long fbad = NO_INDEX;
     load_codes(a, ec, R0, C0, h, w, S, false, nbad, fbad);
@@ -552,44 +580,51 @@ __global__ void __launch_bounds__(256) k_offsets(TileArgs a) {
 
     // ---- in(p) = sum of G over the exits of neighbouring tiles draining into p
     const int qf = VALM ? fix_scale(a.rows * a.cols, *a.maxw) : 0;
-    int any = 0, emax = INT_MIN;
+    int emax = INT_MIN;
     for (int s = tid; s < P; s += nt) {
         int r, c;
         cell_of(s, h, w, r, c);
         const int i = (r + 1) * S + c + 4;
-        u128 inflow = 0;
-        if (ec[i]) {
+        if (!ec[i]) continue;
+        size_t gidx[8];
+        int ng = 0;
 #pragma unroll
-            for (int k = 1; k <= 8; ++k) {
-                const uint8_t en = ec[i + off_of(k, S)];
-                if ((en & HALO) && (en & 15) == dir_rev(k)) {
-                    const int64_t gr = R0 + r + dir_dr(k), gc = C0 + c + dir_dc(k);
-                    const int tyh = (int)(gr / a.th), txh = (int)(gc / a.tw);
-                    const int hh = (int)min((int64_t)a.th, a.rows - (int64_t)tyh * a.th);
-                    const int wh = (int)min((int64_t)a.tw, a.cols - (int64_t)txh * a.tw);
-                    const int sh = slot_of((int)(gr - (int64_t)tyh * a.th),
-                                           (int)(gc - (int64_t)txh * a.tw), hh, wh);
-                    const size_t tb = ((size_t)tyh * a.tiles_x + txh) * a.pmax;
-                    const uint16_t l = a.link[tb + sh];
-                    if (l != LINK_TERM) inflow += a.G[tb + l];  // h is an exit of its tile
-                }
+        for (int k = 1; k <= 8; ++k) {
+            const uint8_t en = ec[i + off_of(k, S)];
+            if ((en & HALO) && (en & 15) == dir_rev(k)) {
+                const int rr = r + dir_dr(k), cc = c + dir_dc(k);  // one step outside the tile
+                const int tyh = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
+                const int txh = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
+                const int64_t R0h = (int64_t)tyh * a.th, C0h = (int64_t)txh * a.tw;
+                const int hh = (int)min((int64_t)a.th, a.rows - R0h);
+                const int wh = (int)min((int64_t)a.tw, a.cols - C0h);
+                const int sh = slot_of((int)(R0 + rr - R0h), (int)(C0 + cc - C0h), hh, wh);
+                gidx[ng++] = ((size_t)tyh * a.tiles_x + txh) * a.pmax + sh;
             }
         }
-        inf[s] = inflow;
-        if (inflow != 0) {
-            any = 1;
-            if constexpr (VALM == 1) {
-                int e;
-                frexp(fabs(fix2d(inflow, qf)), &e);
-                emax = max(emax, e);
-            }
+        if (!ng) continue;
+        uint16_t lk[8];
+        for (int j = 0; j < ng; ++j) lk[j] = a.link[gidx[j]];  // independent loads first
+        u128 inflow = 0;
+        for (int j = 0; j < ng; ++j)
+            if (lk[j] != LINK_TERM)  // always an exit rank: the neighbour drains out of its tile
+                inflow += a.G[gidx[j] - (gidx[j] % a.pmax) + lk[j]];
+        if (inflow == 0) continue;
+        const int e = atomicAdd(&s_nent, 1);
+        eslot[e] = (uint16_t)s;
+        einf[e] = inflow;
+        if constexpr (VALM == 1) {
+            int ex;
+            frexp(fabs(fix2d(inflow, qf)), &ex);
+            emax = max(emax, ex);
         }
     }
     if constexpr (VALM == 1) {
         if (emax != INT_MIN) atomicMax(&s_emax, emax);
     }
-    any = __syncthreads_or(any);
-    if (!any) return;
+    __syncthreads();
+    const int nent = s_nent;
+    if (nent == 0) return;
     // offsets of this tile stay below P * max|in(p)| < 2^(emax + log2 P)
     int qo = 0;
     if constexpr (VALM == 1) {
@@ -598,10 +633,10 @@ __global__ void __launch_bounds__(256) k_offsets(TileArgs a) {
         qo = 62 - (s_emax + lp + 1);
     }
 
-    // ---- walk each entry's downstream path inside the tile, adding in(p) ---
-    for (int s = tid; s < P; s += nt) {
-        const u128 inflow = inf[s];
-        if (inflow == 0) continue;
+    // ---- walk each entry's downstream path inside the tile, adding in(p);
+    // every lane takes its own entries, with no coordination ----------------
+    for (int q = tid; q < nent; q += nt) {
+        const u128 inflow = einf[q];
         unsigned long long v;
         if constexpr (VALM == 0) {
             v = (unsigned long long)inflow;
@@ -612,16 +647,16 @@ __global__ void __launch_bounds__(256) k_offsets(TileArgs a) {
                                                         : (si << (-sh)));
         }
         int r, c;
-        cell_of(s, h, w, r, c);
+        cell_of(eslot[q], h, w, r, c);
         int cur = (r + 1) * S + c + 4;
-        for (int step = 0; step < n_in; ++step) {
+        for (int steps = 0; steps < n_in; ++steps) {
             atomicAdd(&off[cur], v);
             const int k = ec[cur];
             if (k < 1 || k > 8) break;
-            const int nxt = cur + off_of(k, S);
-            const uint8_t et = ec[nxt];
+            const int tg = cur + off_of(k, S);
+            const uint8_t et = ec[tg];
             if (!et || (et & HALO)) break;
-            cur = nxt;
+            cur = tg;
         }
     }
     __syncthreads();
