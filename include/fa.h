@@ -83,10 +83,15 @@ typedef enum { FA_OUT_U32 = 0, FA_OUT_F32 = 1 } fa_out_dtype;
 
 /* Tile shape: 0 = library default (64 x 64).  1 <= tile_h, tile_w and
  * tile_h * tile_w <= 16384.  Results do not depend on the tile shape, except
- * for the rounding of floating-point sums. */
+ * for the rounding of floating-point sums.
+ * flags: FA_OPT_NO_TMA disables staging code tiles into shared memory with the
+ * Tensor Memory Accelerator (used when the raster allows it: 16-byte aligned
+ * codes and pitch, tile width a multiple of 16, no mask raster); results are
+ * identical either way. */
+#define FA_OPT_NO_TMA 1
 typedef struct {
     int32_t tile_h, tile_w;
-    int32_t reserved0, reserved1;
+    int32_t flags, reserved;
 } fa_options;
 
 /* Library version as major*10000 + minor*100 + patch. */

@@ -18,7 +18,8 @@ import torch
 from . import _lib
 from ._lib import (FA_ERR_BAD_CODE, FA_ERR_CUDA, FA_ERR_CYCLE, FA_ERR_INVALID_ARG,  # noqa: F401
                    FA_ERR_NONFINITE, FA_ERR_TIMEOUT, FA_ERR_TOO_LARGE, FA_ERR_WORKSPACE,
-                   FA_NOALLOC_SCRATCH_BYTES, FA_OK, FA_OUT_F32, FA_OUT_U32, FA_STATUS_WORDS,
+                   FA_NOALLOC_SCRATCH_BYTES, FA_OK, FA_OPT_NO_TMA, FA_OUT_F32, FA_OUT_U32,
+                   FA_STATUS_WORDS,
                    FA_WARN_OVERFLOW, STATUS_NAMES, fa_options)
 
 __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumulate",
@@ -33,10 +34,11 @@ class FlowAccError(RuntimeError):
         super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
 
 
-def options(tile=None) -> fa_options:
+def options(tile=None, flags: int = 0) -> fa_options:
     o = fa_options()
     if tile is not None:
         o.tile_h, o.tile_w = int(tile[0]), int(tile[1])
+    o.flags = int(flags)
     return o
 
 
@@ -146,7 +148,7 @@ def workspace(nbytes: int, device) -> torch.Tensor:
 
 def accumulate(codes: torch.Tensor, weights: torch.Tensor | None = None,
                mask: torch.Tensor | None = None, out_dtype=None, tile=None,
-               out: torch.Tensor | None = None, check: bool = False, stream=None):
+               out: torch.Tensor | None = None, check: bool = False, stream=None, flags: int = 0):
     """Flow accumulation of one raster.  codes: uint8 [R, C] CUDA tensor;
     weights: float32 [R, C] or None (counts); mask: uint8 [R, C] or None.
     Returns uint32 counts (no weights, default) or float32 sums.  check=True
@@ -159,7 +161,7 @@ def accumulate(codes: torch.Tensor, weights: torch.Tensor | None = None,
     if out is None:
         out = torch.empty((R, C), dtype=torch.uint32 if out_dtype == FA_OUT_U32 else torch.float32,
                           device=codes.device)
-    opts = options(tile)
+    opts = options(tile, flags)
     ws = workspace(fa_workspace_size(R, C, opts), codes.device)
     st = fa_accumulate(codes, weights, mask, out, out_dtype, ws, opts, None, stream)
     if st != FA_OK:

@@ -23,6 +23,7 @@ FA_NOALLOC_SCRATCH_BYTES = 64 << 20
 FA_OUT_U32 = 0
 FA_OUT_F32 = 1
 FA_STATUS_WORDS = 4
+FA_OPT_NO_TMA = 1
 
 STATUS_NAMES = {
     FA_OK: "FA_OK", FA_WARN_OVERFLOW: "FA_WARN_OVERFLOW", FA_ERR_INVALID_ARG: "FA_ERR_INVALID_ARG",
@@ -35,7 +36,7 @@ STATUS_NAMES = {
 
 class fa_options(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes)

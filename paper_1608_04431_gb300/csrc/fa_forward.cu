@@ -20,8 +20,12 @@
 // Inside a tile all sums are integers: uint32 counts, or 64-bit fixed point
 // with a per-tile scale for float weights, so the order in which atomics land
 // cannot change any bit of the result.
+#include <algorithm>
 #include <climits>
+#include <cstring>
 #include <type_traits>
+
+#include <cudaTypedefs.h>
 
 #include "fa_common.cuh"
 #include "fa_internal.h"
@@ -30,7 +34,7 @@ namespace fa {
 
 struct TileArgs {
     int64_t rows, cols;
-    int th, tw, tiles_x, pmax;
+    int th, tw, tiles_x, tiles_y, pmax;
     const uint8_t *codes;
     int64_t pc;
     const uint8_t *mask;
@@ -70,18 +74,26 @@ __device__ __forceinline__ long long f2fix64(float x, int q) { return (long long
 // ---------------------------------------------------------------------------
 // Shared-memory layout of a tile.  Codes and every per-cell array share one
 // byte-index space: halo row hr (0 .. h+1, tile row r = hr - 1) starts at
-// hr * S; tile column c sits at byte c + 4 (halo columns at bytes 3 and w + 4),
-// so each group of 4 interior cells is one aligned 32-bit word and the
-// in-degree can be computed four cells at a time.  S is a multiple of 16 with
-// at least 8 spare bytes after the east halo column.
+// hr * S; tile column c sits at byte c + X0 (halo columns at bytes X0 - 1 and
+// X0 + w).  Each group of 4 interior cells is one aligned 32-bit word, so the
+// in-degree is computed four cells at a time, and a row is exactly the TMA box
+// that starts X0 bytes left of the tile (a 16-byte aligned column when the
+// tile width is a multiple of 16).  S >= X0 + tw + 16.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int tile_stride(int tw) { return ((tw + 12 + 15) / 16) * 16; }
+constexpr int X0 = 16;
+__host__ __device__ inline int tile_stride(int tw) { return ((tw + 32 + 15) / 16) * 16; }
 
-__host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm) {
+// bytes of one staged code tile, rounded so a second stage stays 128-aligned
+__host__ __device__ inline size_t code_buf_bytes(int th, int tw) {
+    return (((size_t)(th + 2) * tile_stride(tw)) + 127) & ~size_t(127);
+}
+
+__host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm, bool tma) {
     const size_t nb = (size_t)(th + 2) * tile_stride(tw);
-    size_t b = valm ? nb * 8 : 0;             // 64-bit fixed-point sums
+    size_t b = 128;                           // alignment slack of the dynamic window
+    b += code_buf_bytes(th, tw) * (tma ? 2 : 1);  // effective codes (two TMA stages)
+    b += valm ? nb * 8 : 0;                   // 64-bit fixed-point sums
     b += nb * 4;                              // packed word per cell
-    b += nb;                                  // effective codes
     b += (size_t)th * tw * 2;                 // source queue (u16 cell indices)
     b += (size_t)(2 * th + 2 * tw) * 2;       // exit rank per perimeter slot
     b += (size_t)(2 * th + 2 * tw) * 2;       // entry-cell list
@@ -90,7 +102,7 @@ __host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm) {
 
 __host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
     const size_t nb = (size_t)(th + 2) * tile_stride(tw);
-    size_t b = nb * 8;                        // per-cell offset
+    size_t b = (((size_t)th * tw + 1) & ~size_t(1)) * 8;  // per-cell offset, padded to 16 B
     b += (size_t)(2 * th + 2 * tw) * 18;      // inflow and slot per listed entry
     b += nb;                                  // effective codes
     return (b + 15) & ~size_t(15);
@@ -98,10 +110,10 @@ __host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
 
 __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
     return (int64_t)(th + 2) * tile_stride(tw) <= 65535 && (int64_t)th * tw <= 16384 &&
-           solve_smem_bytes(th, tw, valm) <= 227 * 1024 && offsets_smem_bytes(th, tw) <= 227 * 1024;
+           solve_smem_bytes(th, tw, valm, false) <= 227 * 1024 &&
+           offsets_smem_bytes(th, tw) <= 227 * 1024;
 }
 
-constexpr uint16_t LAB_UNKNOWN = 0xFFFE;
 
 // Load a tile's effective codes with a one-cell halo (Algorithm 1's F) into
 // ec.  Each lane first issues the loads for up to four rows (one 32-bit word of
@@ -119,7 +131,7 @@ __device__ __forceinline__ void load_codes(const TileArgs &a, uint8_t *ec, int64
     for (int hr0 = warp; hr0 < h + 2; hr0 += U * nw) {
         for (int wd0 = 0; wd0 < words; wd0 += 32) {
             const int wd = wd0 + lane;
-            const int c0 = 4 * wd - 4;  // tile column of the word's first byte
+            const int c0 = 4 * wd - X0;  // tile column of the word's first byte
             uint32_t raw[U], mraw[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {  // issue every load first
@@ -181,6 +193,53 @@ __device__ __forceinline__ void load_codes(const TileArgs &a, uint8_t *ec, int64
     }
 }
 
+// In-place conversion of a TMA-staged box (raw codes; row hr = tile row
+// hr - 1; tile column c at byte X0 + c) into effective codes: interior cells
+// keep valid codes (invalid ones become NoData and are counted); the one-cell
+// ring around the tile keeps valid codes with HALO set; everything else in the
+// box (neighbouring tiles' cells beyond the ring) is zeroed.
+__device__ __forceinline__ void transform_box(uint8_t *ec, int h, int w, int S, int64_t R0,
+                                              int64_t C0, int64_t cols, int &nbad,
+                                              long long &fbad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int words = S >> 2;
+    for (int hr = warp; hr < h + 2; hr += nw) {
+        const bool irow = hr >= 1 && hr <= h;
+        uint32_t *row = reinterpret_cast<uint32_t *>(ec + hr * S);
+        for (int wd = lane; wd < words; wd += 32) {
+            const int c0 = 4 * wd - X0;
+            const uint32_t raw = row[wd];
+            uint32_t v = 0;
+            if (irow && c0 >= 0 && c0 + 3 < w) {  // four interior cells
+                const uint32_t bad = __vcmpgtu4(raw, 0x09090909u);
+                if (bad) {
+                    nbad += __popc(bad) >> 3;
+                    const int j = (__ffs(bad) - 1) >> 3;
+                    fbad = min(fbad, (long long)((R0 + hr - 1) * cols + (C0 + c0 + j)));
+                }
+                v = raw & ~bad;
+            } else if (c0 + 3 >= -1 && c0 <= w) {  // touches the ring
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = c0 + j;
+                    if (c < -1 || c > w) continue;
+                    const uint32_t k = (raw >> (8 * j)) & 0xffu;
+                    const bool interior = irow && c >= 0 && c < w;
+                    if (k == 0 || k > 9) {
+                        if (interior && k > 9) {
+                            ++nbad;
+                            fbad = min(fbad, (long long)((R0 + hr - 1) * cols + (C0 + c)));
+                        }
+                        continue;
+                    }
+                    v |= (k | (interior ? 0u : (uint32_t)HALO)) << (8 * j);
+                }
+            }
+            row[wd] = v;
+        }
+    }
+}
+
 // The in-tile successor direction of an interior cell: its code when the
 // target is a valid cell inside the tile, else 0.
 __device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
@@ -193,344 +252,399 @@ __device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
 // ---------------------------------------------------------------------------
 // pass 1: tile solve
 // ---------------------------------------------------------------------------
-
-template <int VALM>
-__global__ void __launch_bounds__(256, 5) k_solve(TileArgs a) {
+// Persistent CTAs: each block solves tiles t = blockIdx.x, + gridDim.x, ...
+// With TMA the codes of tile t + gridDim.x (box of S x (th+2) bytes at column
+// C0 - X0, row R0 - 1; outside the raster reads as 0 = NoData) are staged into
+// the other shared buffer while tile t is solved.
+template <int VALM, bool TMA>
+__global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_constant__ CUtensorMap tmap) {
     typedef typename std::conditional<VALM == 0, uint32_t, long long>::type PV;
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_cnt_bad, s_cnt_cyc, s_flags, s_nsrc, s_nent;
-    __shared__ long long s_first;
+    __shared__ int s_nsrc, s_nent, s_flags;
     __shared__ uint32_t s_maxw;
+    __shared__ __align__(8) uint64_t s_bar[2];
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int t = blockIdx.x;
-    const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
-    const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
-    const int h = (int)min((int64_t)a.th, a.rows - R0);
-    const int w = (int)min((int64_t)a.tw, a.cols - C0);
     const int S = tile_stride(a.tw);
     const int NB = (a.th + 2) * S;
-    const int n_in = h * w;
-    const int P = perim_count(h, w);
-    const size_t tbase = (size_t)t * a.pmax;
+    const int T = a.tiles_x * a.tiles_y;
 
-    // counts: word = [step:4 | pending:4 | sum:24]
-    // weights: word = [step:4 | pending:4] and a separate 64-bit fixed-point sum
-    long long *fsum = reinterpret_cast<long long *>(smem);
-    uint32_t *word = reinterpret_cast<uint32_t *>(smem + (VALM ? 8 * (size_t)NB : 0));
-    uint8_t *ec = reinterpret_cast<uint8_t *>(word + NB);
-    uint16_t *srcq = reinterpret_cast<uint16_t *>(ec + NB);
+    // shared layout: code buffers (two with TMA, each 128-byte aligned for the
+    // bulk copies), then the per-cell arrays
+    const size_t CB = code_buf_bytes(a.th, a.tw);
+    uint8_t *base128 = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem) + 127) &
+                                                   ~uintptr_t(127));
+    uint8_t *cbuf0 = base128;
+    uint8_t *cbuf1 = base128 + (TMA ? CB : 0);
+    long long *fsum = reinterpret_cast<long long *>(base128 + (TMA ? 2 : 1) * CB);
+    uint32_t *word = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(fsum) +
+                                                  (VALM ? 8 * (size_t)NB : 0));
+    uint16_t *srcq = reinterpret_cast<uint16_t *>(word + NB);
     uint16_t *rank = srcq + a.th * a.tw;
     uint16_t *entq = rank + a.pmax;
 
-    if (tid == 0) {
-        s_cnt_bad = 0;
-        s_cnt_cyc = 0;
-        s_flags = 0;
-        s_first = NO_INDEX;
-        s_maxw = 0;
-        s_nsrc = 0;
-        s_nent = 0;
-    }
-    int nbad = 0;
+    // status, accumulated over this block's tiles
+    int nbad = 0, ncyc = 0, nonfinite = 0;
     long long fbad = NO_INDEX;
-    // [phase] load
-    load_codes(a, ec, R0, C0, h, w, S, true, nbad, fbad);
-    __syncthreads();
+    uint32_t gmaxw = 0;
 
-    // [phase] init
-    // ---- dependency counts D (Algorithm 1, first loop) and the in-tile
-    // successor of every cell, four cells per lane from the same neighbour
-    // words: byte j of nbr_k is the code of cell j's neighbour in direction k.
-    // A row of g groups uses the next power of two >= g lanes, so one warp
-    // iteration covers 32 / lanes-per-row rows.
-    uint32_t maxw = 0;
-    int nonfinite = 0;
-    const int groups = (w + 3) >> 2;
-    int lpr_log = 0;
-    while ((1 << lpr_log) < groups && lpr_log < 5) ++lpr_log;
-    const int rows_per_it = 32 >> lpr_log;
-    const int sub = lane >> lpr_log, gl = lane & ((1 << lpr_log) - 1);
-    for (int r0 = warp * rows_per_it; r0 < h; r0 += nw * rows_per_it) {
-        for (int g0 = 0; g0 < groups; g0 += (1 << lpr_log)) {  // warp-uniform trip counts
-            const int r = r0 + sub, gq = g0 + gl;
-            int mysrc = 0;
-            uint16_t srcs[4];
-            if (r < h && gq < groups) {
-                const int c = 4 * gq;
-                const int base = (r + 1) * S + c + 4;
-                uint32_t L[3], Cw[3], Rw[3];
+    if (tid == 0) {
+        s_flags = 0;
+        if (TMA) {
+            mbar_init(&s_bar[0], 1);
+            mbar_init(&s_bar[1], 1);
+            mbar_fence_init();
+        }
+    }
+    __syncthreads();
+    auto issue = [&](int tn, int bb) {  // one thread: stage tile tn's codes into buffer bb
+        const int tyn = tn / a.tiles_x, txn = tn - tyn * a.tiles_x;
+        mbar_expect_tx(&s_bar[bb], (uint32_t)NB);
+        tma_load_2d(bb ? cbuf1 : cbuf0, &tmap, txn * a.tw - X0, tyn * a.th - 1, &s_bar[bb]);
+    };
+    if (TMA && tid == 0 && blockIdx.x < T) issue(blockIdx.x, 0);
+
+    int it = 0, to_it = -1;
+    for (int t = blockIdx.x; t < T; t += gridDim.x, ++it) {
+        const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+        const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
+        const int h = (int)min((int64_t)a.th, a.rows - R0);
+        const int w = (int)min((int64_t)a.tw, a.cols - C0);
+        const int n_in = h * w;
+        const int P = perim_count(h, w);
+        const size_t tbase = (size_t)t * a.pmax;
+        uint8_t *ec = (TMA && (it & 1)) ? cbuf1 : cbuf0;
+        if (tid == 0) {
+            s_nsrc = 0;
+            s_nent = 0;
+            s_maxw = 0;
+        }
+
+        // [phase] load
+        if constexpr (TMA) {
+            const int tn = t + gridDim.x;
+            if (tid == 0 && tn < T) issue(tn, (it & 1) ^ 1);
+            if (!mbar_wait(&s_bar[it & 1], (uint32_t)((it >> 1) & 1))) atomicOr(&s_flags, FA_FLAG_TIMEOUT);
+            __syncthreads();
+            if (s_flags & FA_FLAG_TIMEOUT) {
+                to_it = (t + (int)gridDim.x < T) ? -2 - it : it;  // -2-it: the next stage was issued too
+                break;
+            }
+            transform_box(ec, h, w, S, R0, C0, a.cols, nbad, fbad);
+        } else {
+            load_codes(a, ec, R0, C0, h, w, S, true, nbad, fbad);
+        }
+        __syncthreads();
+
+        // [phase] init
+        // ---- dependency counts D (Algorithm 1, first loop) and the in-tile
+        // successor of every cell, four cells per lane from the same neighbour
+        // words: byte j of nbr_k is the code of cell j's neighbour in
+        // direction k.  A row of g groups uses the next power of two >= g
+        // lanes, so one warp iteration covers 32 / lanes-per-row rows.
+        uint32_t maxw = 0;
+        const int groups = (w + 3) >> 2;
+        int lpr_log = 0;
+        while ((1 << lpr_log) < groups && lpr_log < 5) ++lpr_log;
+        const int rows_per_it = 32 >> lpr_log;
+        const int sub = lane >> lpr_log, gl = lane & ((1 << lpr_log) - 1);
+        for (int r0 = warp * rows_per_it; r0 < h; r0 += nw * rows_per_it) {
+            for (int g0 = 0; g0 < groups; g0 += (1 << lpr_log)) {  // warp-uniform trip counts
+                const int r = r0 + sub, gq = g0 + gl;
+                int mysrc = 0;
+                uint16_t srcs[4];
+                if (r < h && gq < groups) {
+                    const int c = 4 * gq;
+                    const int base = (r + 1) * S + c + X0;
+                    uint32_t L[3], Cw[3], Rw[3];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const uint32_t *p = reinterpret_cast<const uint32_t *>(ec + base + (d - 1) * S);
-                    L[d] = p[-1];
-                    Cw[d] = p[0];
-                    Rw[d] = p[1];
-                }
-                const uint32_t me = Cw[1];
-                uint32_t pm = 0, stepw = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        const uint32_t *p =
+                            reinterpret_cast<const uint32_t *>(ec + base + (d - 1) * S);
+                        L[d] = p[-1];
+                        Cw[d] = p[0];
+                        Rw[d] = p[1];
+                    }
+                    const uint32_t me = Cw[1];
+                    uint32_t pm = 0, stepw = 0;
 #pragma unroll
-                for (int k = 1; k <= 8; ++k) {
-                    const int d = dir_dr(k) + 1, dc = dir_dc(k);
-                    const uint32_t nbr = dc == 0 ? Cw[d]
-                                                 : (dc > 0 ? __funnelshift_r(Cw[d], Rw[d], 8)
-                                                           : __funnelshift_l(L[d], Cw[d], 8));
-                    const uint32_t kk = 0x01010101u * (uint32_t)k;
-                    // the neighbour drains into this cell
-                    pm |= __vcmpeq4(nbr, 0x01010101u * (uint32_t)dir_rev(k)) &
-                          (0x01010101u << (k - 1));
-                    // this cell drains into the neighbour, a valid cell of the tile
-                    const uint32_t inside = __vcmpne4(nbr, 0u) & __vcmpeq4(nbr & 0x10101010u, 0u);
-                    stepw |= __vcmpeq4(me, kk) & inside & kk;
-                }
-                uint32_t x = pm - ((pm >> 1) & 0x55555555u);  // per-byte popcount
-                x = (x & 0x33333333u) + ((x >> 2) & 0x33333333u);
-                x = (x + (x >> 4)) & 0x0F0F0F0Fu;
-                const int nvalid = min(4, w - c);
-                const uint32_t colmask = nvalid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nvalid)) - 1u);
-                const uint32_t valid = __vcmpne4(me, 0u) & colmask;
-                const uint32_t src = valid & __vcmpeq4(x, 0u);
-                uint32_t wv4[4];
+                    for (int k = 1; k <= 8; ++k) {
+                        const int d = dir_dr(k) + 1, dc = dir_dc(k);
+                        const uint32_t nbr = dc == 0 ? Cw[d]
+                                                     : (dc > 0 ? __funnelshift_r(Cw[d], Rw[d], 8)
+                                                               : __funnelshift_l(L[d], Cw[d], 8));
+                        const uint32_t kk = 0x01010101u * (uint32_t)k;
+                        // the neighbour drains into this cell
+                        pm |= __vcmpeq4(nbr, 0x01010101u * (uint32_t)dir_rev(k)) &
+                              (0x01010101u << (k - 1));
+                        // this cell drains into the neighbour, a valid cell of the tile
+                        const uint32_t inside =
+                            __vcmpne4(nbr, 0u) & __vcmpeq4(nbr & 0x10101010u, 0u);
+                        stepw |= __vcmpeq4(me, kk) & inside & kk;
+                    }
+                    uint32_t x = pm - ((pm >> 1) & 0x55555555u);  // per-byte popcount
+                    x = (x & 0x33333333u) + ((x >> 2) & 0x33333333u);
+                    x = (x + (x >> 4)) & 0x0F0F0F0Fu;
+                    const int nvalid = min(4, w - c);
+                    const uint32_t colmask = nvalid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nvalid)) - 1u);
+                    const uint32_t valid = __vcmpne4(me, 0u) & colmask;
+                    const uint32_t src = valid & __vcmpeq4(x, 0u);
+                    uint32_t wv4[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t sj = (stepw >> (8 * j)) & 15u, pj = (x >> (8 * j)) & 15u;
-                    const bool vj = (valid >> (8 * j)) & 1u;
-                    if constexpr (VALM == 0) wv4[j] = vj ? ((sj << 28) | (pj << 24) | 1u) : 0u;
-                    else wv4[j] = vj ? ((sj << 4) | pj) : 0u;
-                    if ((src >> (8 * j)) & 1u) srcs[mysrc++] = (uint16_t)(base + j);
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t sj = (stepw >> (8 * j)) & 15u, pj = (x >> (8 * j)) & 15u;
+                        const bool vj = (valid >> (8 * j)) & 1u;
+                        if constexpr (VALM == 0) wv4[j] = vj ? ((sj << 28) | (pj << 24) | 1u) : 0u;
+                        else wv4[j] = vj ? ((sj << 4) | pj) : 0u;
+                        if ((src >> (8 * j)) & 1u) srcs[mysrc++] = (uint16_t)(base + j);
+                    }
+                    *reinterpret_cast<uint4 *>(word + base) =
+                        make_uint4(wv4[0], wv4[1], wv4[2], wv4[3]);
+                    if constexpr (VALM == 1) {
+                        for (int j = 0; j < nvalid; ++j) {
+                            if (!((valid >> (8 * j)) & 1u)) continue;
+                            const float wf = a.w ? a.w[(R0 + r) * a.pw + (C0 + c + j)] : 1.0f;
+                            const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
+                            if (b >= 0x7f800000u) nonfinite = 1;
+                            maxw = max(maxw, b);
+                            fsum[base + j] = (long long)__float_as_uint(wf);  // raw bits until scaled
+                        }
+                    }
                 }
-                *reinterpret_cast<uint4 *>(word + base) = make_uint4(wv4[0], wv4[1], wv4[2], wv4[3]);
-                if constexpr (VALM == 1) {
-                    for (int j = 0; j < nvalid; ++j) {
-                        if (!((valid >> (8 * j)) & 1u)) continue;
-                        const float wf = a.w ? a.w[(R0 + r) * a.pw + (C0 + c + j)] : 1.0f;
-                        const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
-                        if (b >= 0x7f800000u) nonfinite = 1;
-                        maxw = max(maxw, b);
-                        fsum[base + j] = (long long)__float_as_uint(wf);  // raw bits until scaled
+                // append the lanes' sources to the block queue (warp-aggregated)
+                int incl = mysrc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                int qbase = 0;
+                if (lane == 31 && tot) qbase = atomicAdd(&s_nsrc, tot);
+                qbase = __shfl_sync(0xffffffffu, qbase, 31);
+                for (int j = 0; j < mysrc; ++j) srcq[qbase + incl - mysrc + j] = srcs[j];
+            }
+        }
+
+        // ---- exit cells (flow leaves the tile into a valid cell) get ranks in
+        // slot order; entry cells (flow arrives from a valid cell outside) are
+        // listed for Algorithm 2 ------------------------------------------------
+        const int chunk = (P + nt - 1) / nt;
+        const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
+        int mine = 0;
+        for (int s = s0; s < s1; ++s) {
+            int r, c;
+            cell_of(s, h, w, r, c);
+            const int i = (r + 1) * S + c + X0;
+            const int k = ec[i];
+            if (k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO)) ++mine;
+        }
+        int total;
+        int rk = block_exclusive_scan(mine, s_warp, &total);
+        for (int s = s0; s < s1; ++s) {
+            int r, c;
+            cell_of(s, h, w, r, c);
+            const int i = (r + 1) * S + c + X0;
+            const int k = ec[i];
+            const bool ex = k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO);
+            rank[s] = ex ? (uint16_t)rk : LINK_TERM;
+            bool entry = false;
+            if (ec[i]) {
+#pragma unroll
+                for (int kk = 1; kk <= 8; ++kk) {
+                    const uint8_t en = ec[i + off_of(kk, S)];
+                    entry |= (en & HALO) && (en & 15) == dir_rev(kk);
+                }
+            }
+            if (ex) {
+                // where the exit's flow goes: a perimeter slot of a neighbouring tile
+                const int rr = r + dir_dr(k), cc = c + dir_dc(k);  // tile-local, one step outside
+                const int tyd = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
+                const int txd = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
+                const int64_t R0d = (int64_t)tyd * a.th, C0d = (int64_t)txd * a.tw;
+                const int hd = (int)min((int64_t)a.th, a.rows - R0d);
+                const int wd = (int)min((int64_t)a.tw, a.cols - C0d);
+                const int sd = slot_of((int)(R0 + rr - R0d), (int)(C0 + cc - C0d), hd, wd);
+                a.node_dst[tbase + rk] = (uint32_t)(((size_t)tyd * a.tiles_x + txd) * a.pmax + sd);
+                a.link[tbase + s] = (uint16_t)rk;  // an exit links to itself
+                ++rk;
+            } else if (entry) {
+                entq[atomicAdd(&s_nent, 1)] = (uint16_t)s;
+            } else {
+                a.link[tbase + s] = LINK_TERM;
+            }
+        }
+        int qt = 0;
+        if constexpr (VALM == 1) {
+            gmaxw = max(gmaxw, maxw);
+            maxw = warp_max_u(maxw);
+            if (lane == 0 && maxw) atomicMax(&s_maxw, maxw);
+            __syncthreads();
+            qt = (s_maxw >= 0x7f800000u) ? 0
+                                         : tile_scale((double)n_in * (double)__uint_as_float(s_maxw));
+            for (int r = warp; r < h; r += nw)
+                for (int c = lane; c < w; c += 32) {
+                    const int i = (r + 1) * S + c + X0;
+                    if (ec[i]) fsum[i] = f2fix64(__uint_as_float((uint32_t)fsum[i]), qt);
+                }
+        }
+        __syncthreads();
+
+        // [phase] walk
+        // ---- the Kahn loop without a ready queue: every lane walks its static
+        // slice of the source queue, pushing final values downstream; the lane
+        // whose delivery completes a cell (its last pending upstream
+        // neighbour) carries on from it.  Integer sums make the order
+        // irrelevant, and the lanes need no coordination.  Meanwhile the last
+        // two warps run Algorithm 2 for the entry cells (it reads only codes).
+        const int lwn = nw >= 4 ? 2 : 0;  // warps walking entry links alongside
+        const int mww = nw - lwn;         // warps running the solve
+        if (warp < mww) {
+            const int nsrc = s_nsrc;
+            const int stride = mww * 32;
+            int qi = tid, cur = -1;
+            uint32_t st = 0;
+            PV v = 0;
+            for (int guard = 0; guard < 2 * n_in + 2; ++guard) {
+                if (cur < 0) {
+                    if (qi >= nsrc) break;
+                    cur = srcq[qi];
+                    qi += stride;
+                    const uint32_t wd = word[cur];
+                    if constexpr (VALM == 0) {
+                        st = wd >> 28;
+                        v = wd & 0xFFFFFFu;
+                    } else {
+                        st = wd >> 4;
+                        v = fsum[cur];
+                    }
+                }
+                if (st == 0) {
+                    cur = -1;
+                    continue;
+                }
+                const int tgt = cur + off_of((int)st, S);
+                if constexpr (VALM == 0) {
+                    const uint32_t old = atomicAdd(&word[tgt], v - (1u << 24));
+                    if (((old >> 24) & 15u) == 1u) {
+                        v += old & 0xFFFFFFu;
+                        st = old >> 28;
+                        cur = tgt;
+                    } else {
+                        cur = -1;
+                    }
+                } else {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&fsum[tgt]),
+                              (unsigned long long)v);
+                    __threadfence_block();
+                    const uint32_t old = atomicSub(&word[tgt], 1u);
+                    if ((old & 15u) == 1u) {
+                        __threadfence_block();
+                        v = *reinterpret_cast<volatile long long *>(&fsum[tgt]);
+                        st = old >> 4;
+                        cur = tgt;
+                    } else {
+                        cur = -1;
                     }
                 }
             }
-            // append the lanes' sources to the block queue (warp-aggregated)
-            int incl = mysrc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
-            int qbase = 0;
-            if (lane == 31 && tot) qbase = atomicAdd(&s_nsrc, tot);
-            qbase = __shfl_sync(0xffffffffu, qbase, 31);
-            for (int j = 0; j < mysrc; ++j) srcq[qbase + incl - mysrc + j] = srcs[j];
         }
-    }
-
-    // ---- exit cells (flow leaves the tile into a valid cell) get ranks in
-    // slot order; entry cells (flow arrives from a valid cell outside) are
-    // listed for Algorithm 2 ------------------------------------------------
-    const int chunk = (P + nt - 1) / nt;
-    const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
-    int mine = 0;
-    for (int s = s0; s < s1; ++s) {
-        int r, c;
-        cell_of(s, h, w, r, c);
-        const int i = (r + 1) * S + c + 4;
-        const int k = ec[i];
-        if (k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO)) ++mine;
-    }
-    int total;
-    int rk = block_exclusive_scan(mine, s_warp, &total);
-    for (int s = s0; s < s1; ++s) {
-        int r, c;
-        cell_of(s, h, w, r, c);
-        const int i = (r + 1) * S + c + 4;
-        const int k = ec[i];
-        const bool ex = k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO);
-        rank[s] = ex ? (uint16_t)rk : LINK_TERM;
-        bool entry = false;
-        if (ec[i]) {
-#pragma unroll
-            for (int kk = 1; kk <= 8; ++kk) {
-                const uint8_t en = ec[i + off_of(kk, S)];
-                entry |= (en & HALO) && (en & 15) == dir_rev(kk);
+        if (warp >= mww || lwn == 0) {
+            if (lwn == 0) __syncthreads();  // one- to three-warp blocks: links after the solve
+            // Algorithm 2 for the entry cells: follow the in-tile path to the exit
+            const int nent = s_nent;
+            const int lt = lwn ? tid - mww * 32 : tid, stride = lwn ? lwn * 32 : nt;
+            for (int q = lt; q < nent; q += stride) {
+                const int s = entq[q];
+                int r, c;
+                cell_of(s, h, w, r, c);
+                int c2 = (r + 1) * S + c + X0;
+                uint16_t lk = LINK_TERM;
+                for (int steps = 0; steps <= n_in; ++steps) {
+                    const int k = ec[c2];
+                    if (k < 1 || k > 8) break;
+                    const int nxt = c2 + off_of(k, S);
+                    const uint8_t et = ec[nxt];
+                    if (!et) break;
+                    if (et & HALO) {
+                        const int cr = c2 / S - 1, cc = c2 - (c2 / S) * S - X0;
+                        lk = rank[slot_of(cr, cc, h, w)];
+                        break;
+                    }
+                    c2 = nxt;
+                }
+                a.link[tbase + s] = lk;
             }
         }
-        if (ex) {
-            // where the exit's flow goes: a perimeter slot of a neighbouring tile
-            const int rr = r + dir_dr(k), cc = c + dir_dc(k);  // tile-local, one step outside
-            const int tyd = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
-            const int txd = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
-            const int64_t R0d = (int64_t)tyd * a.th, C0d = (int64_t)txd * a.tw;
-            const int hd = (int)min((int64_t)a.th, a.rows - R0d);
-            const int wd = (int)min((int64_t)a.tw, a.cols - C0d);
-            const int sd = slot_of((int)(R0 + rr - R0d), (int)(C0 + cc - C0d), hd, wd);
-            a.node_dst[tbase + rk] = (uint32_t)(((size_t)tyd * a.tiles_x + txd) * a.pmax + sd);
-            a.link[tbase + s] = (uint16_t)rk;  // an exit links to itself
-            ++rk;
-        } else if (entry) {
-            entq[atomicAdd(&s_nent, 1)] = (uint16_t)s;
-        } else {
-            a.link[tbase + s] = LINK_TERM;
-        }
-    }
-    int qt = 0;
-    if constexpr (VALM == 1) {
-        maxw = warp_max_u(maxw);
-        if (lane == 0 && maxw) atomicMax(&s_maxw, maxw);
         __syncthreads();
-        qt = (s_maxw >= 0x7f800000u) ? 0 : tile_scale((double)n_in * (double)__uint_as_float(s_maxw));
-        for (int r = warp; r < h; r += nw)
-            for (int c = lane; c < w; c += 32) {
-                const int i = (r + 1) * S + c + 4;
-                if (ec[i]) fsum[i] = f2fix64(__uint_as_float((uint32_t)fsum[i]), qt);
-            }
-    }
-    __syncthreads();
 
-    // [phase] walk
-    // ---- the Kahn loop without a ready queue: every lane walks its static
-    // slice of the source queue, pushing final values downstream; the lane
-    // whose delivery completes a cell (its last pending upstream neighbour)
-    // carries on from it.  Integer sums make the order irrelevant, and the
-    // lanes need no coordination.  Meanwhile the last two warps run
-    // Algorithm 2 for the entry cells (it reads only the codes).
-    const int lwn = nw >= 4 ? 2 : 0;          // warps walking entry links alongside
-    const int mww = nw - lwn;                 // warps running the solve
-    if (warp < mww) {
-        const int nsrc = s_nsrc;
-        const int stride = mww * 32;
-        int qi = tid, cur = -1;
-        uint32_t st = 0;
-        PV v = 0;
-        for (int guard = 0; guard < 2 * n_in + 2; ++guard) {
-            if (cur < 0) {
-                if (qi >= nsrc) break;
-                cur = srcq[qi];
-                qi += stride;
-                const uint32_t wd = word[cur];
+        // [phase] output
+        // ---- write A_loc (0 for NoData and for cells on cycles: those never
+        // lose their last pending dependency); exit records ------------------
+        const double inv = ldexp(1.0, -qt);
+        for (int r = warp; r < h; r += nw) {
+            const size_t orow = (size_t)(R0 + r) * a.po + C0;
+            const int base = (r + 1) * S + X0;
+            for (int c = lane; c < w; c += 32) {
+                const int i = base + c;
+                const uint32_t wd = word[i];
+                bool fin = ec[i] != 0;
                 if constexpr (VALM == 0) {
-                    st = wd >> 28;
-                    v = wd & 0xFFFFFFu;
+                    if (fin && ((wd >> 24) & 15u)) fin = false;
                 } else {
-                    st = wd >> 4;
-                    v = fsum[cur];
+                    if (fin && (wd & 15u)) fin = false;
                 }
-            }
-            if (st == 0) {
-                cur = -1;
-                continue;
-            }
-            const int tgt = cur + off_of((int)st, S);
-            if constexpr (VALM == 0) {
-                const uint32_t old = atomicAdd(&word[tgt], v - (1u << 24));
-                if (((old >> 24) & 15u) == 1u) {
-                    v += old & 0xFFFFFFu;
-                    st = old >> 28;
-                    cur = tgt;
-                } else {
-                    cur = -1;
+                if (ec[i] && !fin) {
+                    ++ncyc;
+                    fbad = min(fbad, (long long)((R0 + r) * a.cols + (C0 + c)));
                 }
-            } else {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&fsum[tgt]), (unsigned long long)v);
-                __threadfence_block();
-                const uint32_t old = atomicSub(&word[tgt], 1u);
-                if ((old & 15u) == 1u) {
-                    __threadfence_block();
-                    v = *reinterpret_cast<volatile long long *>(&fsum[tgt]);
-                    st = old >> 4;
-                    cur = tgt;
+                if constexpr (VALM == 0) {
+                    reinterpret_cast<uint32_t *>(a.out)[orow + c] = fin ? (wd & 0xFFFFFFu) : 0u;
                 } else {
-                    cur = -1;
+                    reinterpret_cast<float *>(a.out)[orow + c] =
+                        fin ? (float)((double)fsum[i] * inv) : 0.0f;
                 }
             }
         }
-    }
-    if (warp >= mww || lwn == 0) {
-        if (lwn == 0) __syncthreads();  // one- to three-warp blocks: links after the solve
-        // Algorithm 2 for the entry cells: follow the in-tile path to the exit
-        const int nent = s_nent;
-        const int lt = lwn ? tid - mww * 32 : tid, stride = lwn ? lwn * 32 : nt;
-        for (int q = lt; q < nent; q += stride) {
-            const int s = entq[q];
+        for (int s = tid; s < P; s += nt) {
+            const uint16_t rks = rank[s];
+            if (rks == LINK_TERM) continue;
             int r, c;
             cell_of(s, h, w, r, c);
-            int c2 = (r + 1) * S + c + 4;
-            uint16_t lk = LINK_TERM;
-            for (int steps = 0; steps <= n_in; ++steps) {
-                const int k = ec[c2];
-                if (k < 1 || k > 8) break;
-                const int nxt = c2 + off_of(k, S);
-                const uint8_t et = ec[nxt];
-                if (!et) break;
-                if (et & HALO) {
-                    const int cr = c2 / S - 1, cc = c2 - (c2 / S) * S - 4;
-                    lk = rank[slot_of(cr, cc, h, w)];
-                    break;
-                }
-                c2 = nxt;
-            }
-            a.link[tbase + s] = lk;
+            const int i = (r + 1) * S + c + X0;
+            double vv;
+            if constexpr (VALM == 0) vv = (double)(word[i] & 0xFFFFFFu);
+            else vv = (double)fsum[i] * inv;
+            a.node_val[tbase + rks] = vv;  // A_loc at the exit (the perimeter data's A)
         }
+        if (tid == 0) a.nexit[t] = (uint32_t)total;
+        if constexpr (TMA) fence_proxy_async();  // this buffer is refilled by TMA later
+        __syncthreads();
+        // [phase] end
     }
-    __syncthreads();
-
-    // [phase] output
-    // ---- write A_loc (0 for NoData and for cells on cycles: those never
-    // lose their last pending dependency); exit records --------------------
-    int ncyc = 0;
-    long long fcyc = NO_INDEX;
-    const double inv = ldexp(1.0, -qt);
-    for (int r = warp; r < h; r += nw) {
-        const size_t orow = (size_t)(R0 + r) * a.po + C0;
-        const int base = (r + 1) * S + 4;
-        for (int c = lane; c < w; c += 32) {
-            const int i = base + c;
-            const uint32_t wd = word[i];
-            bool fin = ec[i] != 0;
-            if constexpr (VALM == 0) {
-                if (fin && ((wd >> 24) & 15u)) fin = false;
-            } else {
-                if (fin && (wd & 15u)) fin = false;
-            }
-            if (ec[i] && !fin) {
-                ++ncyc;
-                fcyc = min(fcyc, (long long)((R0 + r) * a.cols + (C0 + c)));
-            }
-            if constexpr (VALM == 0) {
-                reinterpret_cast<uint32_t *>(a.out)[orow + c] = fin ? (wd & 0xFFFFFFu) : 0u;
-            } else {
-                reinterpret_cast<float *>(a.out)[orow + c] =
-                    fin ? (float)((double)fsum[i] * inv) : 0.0f;
-            }
-        }
-    }
-    for (int s = tid; s < P; s += nt) {
-        const uint16_t rks = rank[s];
-        if (rks == LINK_TERM) continue;
-        int r, c;
-        cell_of(s, h, w, r, c);
-        const int i = (r + 1) * S + c + 4;
-        double vv;
-        if constexpr (VALM == 0) vv = (double)(word[i] & 0xFFFFFFu);
-        else vv = (double)fsum[i] * inv;
-        a.node_val[tbase + rks] = vv;  // A_loc at the exit (the perimeter data's A)
-    }
-    if (tid == 0) a.nexit[t] = (uint32_t)total;
 
     // ---- status -------------------------------------------------------------
+    __shared__ int s_cnt_bad, s_cnt_cyc;
+    __shared__ long long s_first;
+    if (tid == 0) {
+        s_cnt_bad = 0;
+        s_cnt_cyc = 0;
+        s_first = NO_INDEX;
+        s_maxw = 0;
+    }
+    __syncthreads();
     nbad = warp_sum(nbad);
     ncyc = warp_sum(ncyc);
-    fbad = warp_min_ll(min(fbad, fcyc));
-    maxw = warp_max_u(maxw);
+    fbad = warp_min_ll(fbad);
+    gmaxw = warp_max_u(gmaxw);
     nonfinite = warp_sum(nonfinite);
     if (lane == 0) {
         if (nbad) atomicAdd(&s_cnt_bad, nbad);
         if (ncyc) atomicAdd(&s_cnt_cyc, ncyc);
         if (fbad != NO_INDEX) atomicMin(&s_first, fbad);
-        if (maxw) atomicMax(&s_maxw, maxw);
+        if (gmaxw) atomicMax(&s_maxw, gmaxw);
         if (nonfinite) atomicOr(&s_flags, FA_FLAG_NONFINITE);
     }
     __syncthreads();
@@ -541,7 +655,15 @@ __global__ void __launch_bounds__(256, 5) k_solve(TileArgs a) {
         if (fl) status_report(a.st, fl, s_cnt_bad + s_cnt_cyc, s_first);
         if (s_maxw) atomicMax(a.maxw, s_maxw);
     }
-    // [phase] end
+    if constexpr (TMA) {
+        // a timed-out wait may leave copies in flight into this block's
+        // shared memory: wait again (bounded) for the stages still pending
+        if (to_it != -1 && tid == 0) {
+            const int i0 = to_it >= 0 ? to_it : -2 - to_it;
+            mbar_wait(&s_bar[i0 & 1], (uint32_t)((i0 >> 1) & 1));
+            if (to_it < -1) mbar_wait(&s_bar[(i0 + 1) & 1], (uint32_t)(((i0 + 1) >> 1) & 1));
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -549,7 +671,7 @@ __global__ void __launch_bounds__(256, 5) k_solve(TileArgs a) {
 // ---------------------------------------------------------------------------
 template <int VALM>
 __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_emax, s_nent;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -559,12 +681,12 @@ __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
     const int h = (int)min((int64_t)a.th, a.rows - R0);
     const int w = (int)min((int64_t)a.tw, a.cols - C0);
     const int S = tile_stride(a.tw);
-    const int NB = (a.th + 2) * S;
     const int n_in = h * w;
     const int P = perim_count(h, w);
 
-    unsigned long long *off = reinterpret_cast<unsigned long long *>(smem);
-    u128 *einf = reinterpret_cast<u128 *>(off + NB);  // inflow per listed entry
+    unsigned long long *off = reinterpret_cast<unsigned long long *>(smem);  // r * w + c
+    // inflow per listed entry; the offset array is padded to keep it 16-byte aligned
+    u128 *einf = reinterpret_cast<u128 *>(off + (((size_t)a.th * a.tw + 1) & ~size_t(1)));
     uint16_t *eslot = reinterpret_cast<uint16_t *>(einf + a.pmax);
     uint8_t *ec = reinterpret_cast<uint8_t *>(eslot + a.pmax);
 
@@ -575,7 +697,7 @@ __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
     int nbad = 0;
     long long fbad = NO_INDEX;
     load_codes(a, ec, R0, C0, h, w, S, false, nbad, fbad);
-    for (int i = tid; i < NB; i += nt) off[i] = 0ull;
+    for (int i = tid; i < n_in; i += nt) off[i] = 0ull;
     __syncthreads();
 
     // ---- in(p) = sum of G over the exits of neighbouring tiles draining into p
@@ -584,7 +706,7 @@ __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
     for (int s = tid; s < P; s += nt) {
         int r, c;
         cell_of(s, h, w, r, c);
-        const int i = (r + 1) * S + c + 4;
+        const int i = (r + 1) * S + c + X0;
         if (!ec[i]) continue;
         size_t gidx[8];
         int ng = 0;
@@ -648,15 +770,17 @@ __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
         }
         int r, c;
         cell_of(eslot[q], h, w, r, c);
-        int cur = (r + 1) * S + c + 4;
+        int cur = (r + 1) * S + c + X0;
         for (int steps = 0; steps < n_in; ++steps) {
-            atomicAdd(&off[cur], v);
+            atomicAdd(&off[r * w + c], v);
             const int k = ec[cur];
             if (k < 1 || k > 8) break;
             const int tg = cur + off_of(k, S);
             const uint8_t et = ec[tg];
             if (!et || (et & HALO)) break;
             cur = tg;
+            r += dir_dr(k);
+            c += dir_dc(k);
         }
     }
     __syncthreads();
@@ -666,9 +790,8 @@ __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
     const double inv = ldexp(1.0, -qo);
     for (int r = warp; r < h; r += nw) {
         const size_t orow = (size_t)(R0 + r) * a.po + C0;
-        const int base = (r + 1) * S + 4;
         for (int c = lane; c < w; c += 32) {
-            const unsigned long long o = off[base + c];
+            const unsigned long long o = off[r * w + c];
             if (!o) continue;
             if constexpr (VALM == 0) {
                 uint32_t *p = reinterpret_cast<uint32_t *>(a.out) + orow + c;
@@ -810,6 +933,7 @@ bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g) {
     g.tiles_y = (int)((rows + th - 1) / th);
     g.tiles_x = (int)((cols + tw - 1) / tw);
     g.pmax = 2 * th + 2 * tw;
+    g.flags = opts ? opts->flags : 0;
     // node ids are tile * pmax + rank in 32 bits
     if ((double)g.tiles() * g.pmax >= 4.0e9) return false;
     return true;
@@ -858,14 +982,89 @@ static int tile_threads(const Geom &g) {
     return cells >= 256 ? 256 : ((cells + 31) / 32) * 32;
 }
 
-template <int VALM>
-static cudaError_t launch_solve(const Geom &g, const TileArgs &ta, cudaStream_t s) {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against libcuda); nullptr when unavailable
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// TMA staging of code tiles: a 2-D uint8 map over the raster with a box of
+// tile_stride(tw) x (th + 2) bytes.  Needs a 16-byte aligned base and pitch,
+// a tile width that is a multiple of 16 (so every box starts on a 16-byte
+// column), box sides <= 256 and no separate mask raster.
+static bool make_code_map(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,
+                          CUtensorMap *m) {
+    if (mask || !codes) return false;
+    if (((uintptr_t)codes & 15) || (pc & 15) || (g.tw & 15)) return false;
+    const int S = tile_stride(g.tw);
+    if (S > 256 || g.th + 2 > 256) return false;
+    if (g.cols >= (int64_t(1) << 31) || g.rows >= (int64_t(1) << 31)) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)g.cols, (cuuint64_t)g.rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pc};
+    cuuint32_t box[2] = {(cuuint32_t)S, (cuuint32_t)(g.th + 2)};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(codes), dims, strides,
+               box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+    }
+    return n;
+}
+
+template <int VALM, bool TMA>
+static cudaError_t launch_solve_k(const Geom &g, const TileArgs &ta, const CUtensorMap &m,
+                                  cudaStream_t s) {
     static int configured = 0;
-    const size_t smem = solve_smem_bytes(g.th, g.tw, VALM);
-    cudaError_t e = set_smem(k_solve<VALM>, smem, configured);
+    static int per_sm = 0, per_sm_smem = -1, per_sm_nt = -1;
+    const size_t smem = solve_smem_bytes(g.th, g.tw, VALM, TMA);
+    cudaError_t e = set_smem(k_solve<VALM, TMA>, smem, configured);
     if (e != cudaSuccess) return e;
-    k_solve<VALM><<<(unsigned)g.tiles(), tile_threads(g), smem, s>>>(ta);
+    const int nt = tile_threads(g);
+    if (per_sm_smem != (int)smem || per_sm_nt != nt) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<VALM, TMA>, nt, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        per_sm_smem = (int)smem;
+        per_sm_nt = nt;
+    }
+    const int64_t T = g.tiles();
+    const unsigned grid = (unsigned)std::min<int64_t>(T, (int64_t)per_sm * sm_count());
+    k_solve<VALM, TMA><<<grid, nt, smem, s>>>(ta, m);
     return cudaGetLastError();
+}
+
+template <int VALM>
+static cudaError_t launch_solve(const Geom &g, const TileArgs &ta, const uint8_t *codes,
+                                int64_t pc, const uint8_t *mask, bool allow_tma, cudaStream_t s) {
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    if (allow_tma && solve_smem_bytes(g.th, g.tw, VALM, true) <= 227 * 1024 &&
+        make_code_map(g, codes, pc, mask, &m))
+        return launch_solve_k<VALM, true>(g, ta, m, s);
+    return launch_solve_k<VALM, false>(g, ta, m, s);
 }
 
 template <int VALM>
@@ -893,6 +1092,7 @@ cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, cons
     ta.th = g.th;
     ta.tw = g.tw;
     ta.tiles_x = g.tiles_x;
+    ta.tiles_y = g.tiles_y;
     ta.pmax = g.pmax;
     ta.codes = codes;
     ta.pc = pc;
@@ -911,7 +1111,9 @@ cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, cons
     ta.maxw = ws.misc;
 
     timing_mark(0, s);
-    e = val_mode ? launch_solve<1>(g, ta, s) : launch_solve<0>(g, ta, s);
+    const bool tma = !(g.flags & FA_OPT_NO_TMA);
+    e = val_mode ? launch_solve<1>(g, ta, codes, pc, mask, tma, s)
+                 : launch_solve<0>(g, ta, codes, pc, mask, tma, s);
     if (e != cudaSuccess) return e;
     timing_mark(1, s);
 

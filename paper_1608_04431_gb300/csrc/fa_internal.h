@@ -17,6 +17,7 @@ struct Geom {
     int th, tw;          // nominal tile shape
     int tiles_x, tiles_y;
     int pmax;            // per-tile slot capacity: 2*th + 2*tw >= perimeter cells
+    int flags;           // FA_OPT_* from fa_options
     int64_t tiles() const { return (int64_t)tiles_x * tiles_y; }
 };
 
