@@ -128,6 +128,73 @@ fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t cols, int64_
                         const fa_options *opts, int32_t *d_status, void *stream);
 
 /*
+ * Batches.  Many rasters, each with its own shape, and up to FA_MAX_FIELDS
+ * weight fields sharing one raster's codes, accumulated in one pass of the
+ * tile pipeline (Sections 3.1-3.3 applied to every (raster, field) pair): the
+ * tiles of all pairs form one tile sequence for the persistent tile solve,
+ * one perimeter-graph resolve covers all of them (its nodes are (tile, exit),
+ * so no flow crosses from one pair to another), and one offset pass finishes
+ * them.  Each result equals fa_accumulate on that raster and field with the
+ * same tile shape: bit for bit for uint32 counts; float32 sums may differ in
+ * the last place, since the perimeter graph's fixed-point scale is set by the
+ * largest raster of the batch.  Every raster uses opts' tile shape; batches
+ * never stage codes by TMA.
+ *
+ * Errors (returned before anything is enqueued): FA_ERR_INVALID_ARG for
+ * n_rasters < 0, n_fields outside 0..FA_MAX_FIELDS, a bad tile shape, and, for
+ * a non-empty raster, NULL codes, NULL or 4-byte-misaligned out[k] or
+ * weights[k] (k < max(n_fields, 1)), or a pitch below cols; FA_ERR_WORKSPACE
+ * for a NULL, not 256-byte-aligned or too small workspace; FA_ERR_CUDA if a
+ * launch or copy fails.  Rasters with rows == 0 or cols == 0 are skipped.
+ * Device-side findings (bad codes, cycles, non-finite weights) go to the
+ * status block as for fa_accumulate; first_index is then a cell index within
+ * the raster where it was found, not a batch position.
+ */
+#define FA_MAX_FIELDS 16
+typedef struct {
+    const uint8_t *codes;               /* device, row-major [rows x pitch_codes] bytes */
+    int64_t rows, cols, pitch_codes;
+    const uint8_t *mask;                /* device NoData mask [rows x pitch_mask], or NULL */
+    int64_t pitch_mask;
+    const float *weights[FA_MAX_FIELDS];/* device float32 [rows x pitch_w] (first n_fields) */
+    int64_t pitch_w;
+    void *out[FA_MAX_FIELDS];           /* device outputs [rows x pitch_out] (first max(n_fields,1)) */
+    int64_t pitch_out;
+} fa_raster;
+
+/* Workspace bytes for a batch (0 if it is invalid).  n_fields == 0 means unit
+ * weights: uint32 counts into out[0]; 1..FA_MAX_FIELDS means float32 sums,
+ * weights[k] -> out[k] (float32). */
+size_t fa_batched_workspace_size(const fa_raster *rasters, int32_t n_rasters, int32_t n_fields,
+                                 const fa_options *opts);
+
+/* Accumulate a batch, asynchronously on `stream`.  `rasters` is a host array
+ * of n_rasters descriptors; the descriptor table is copied into the workspace
+ * on `stream`, so the host array may be reused once the call returns.  The
+ * caller owns every buffer; the library keeps nothing after the call. */
+fa_status fa_accumulate_batched(const fa_raster *rasters, int32_t n_rasters, int32_t n_fields,
+                                void *workspace, size_t ws_bytes, const fa_options *opts,
+                                int32_t *d_status, void *stream);
+
+/* A batch captured once in a CUDA graph and replayed by fa_plan_launch: the
+ * same launches as fa_accumulate_batched, without their host-side cost.  The
+ * plan reads the batch's buffers at replay time (new weights written in place
+ * give new results) and keeps using `workspace`, which holds its descriptor
+ * table: keep all of them allocated at the same addresses until
+ * fa_plan_destroy, and do not overlap two replays of one plan.  Creation
+ * uploads the table and synchronises `stream` once; capture runs on a private
+ * stream, so `stream` is never left in capture mode.  Errors as for
+ * fa_accumulate_batched; *plan is NULL on failure (FA_ERR_INVALID_ARG if plan
+ * itself is NULL).  fa_plan_launch returns FA_ERR_INVALID_ARG for a NULL plan
+ * and FA_ERR_CUDA if the graph launch fails; fa_plan_destroy(NULL) is a no-op. */
+typedef struct fa_plan_s *fa_plan;
+fa_status fa_batched_plan_create(const fa_raster *rasters, int32_t n_rasters, int32_t n_fields,
+                                 void *workspace, size_t ws_bytes, const fa_options *opts,
+                                 int32_t *d_status, void *stream, fa_plan *plan);
+fa_status fa_plan_launch(fa_plan plan, void *stream);
+void fa_plan_destroy(fa_plan plan);
+
+/*
  * fa_accumulate for callers that cannot allocate device memory.  The paper has
  * no counterpart: this exists for programs that can pass their own input and
  * output rasters but cannot supply scratch -- plugin hosts that expose only the

@@ -20,9 +20,11 @@ from ._lib import (FA_ERR_BAD_CODE, FA_ERR_CUDA, FA_ERR_CYCLE, FA_ERR_INVALID_AR
                    FA_ERR_NONFINITE, FA_ERR_TIMEOUT, FA_ERR_TOO_LARGE, FA_ERR_WORKSPACE,
                    FA_NOALLOC_SCRATCH_BYTES, FA_OK, FA_OPT_NO_TMA, FA_OUT_F32, FA_OUT_U32,
                    FA_STATUS_WORDS,
-                   FA_WARN_OVERFLOW, STATUS_NAMES, fa_options)
+                   FA_WARN_OVERFLOW, STATUS_NAMES, fa_options, fa_raster, FA_MAX_FIELDS)
 
 __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumulate",
+           "fa_batched_workspace_size", "fa_accumulate_batched", "fa_batched_plan_create",
+           "fa_plan_launch", "fa_plan_destroy", "accumulate_batched", "BatchPlan",
            "fa_accumulate_noalloc", "fa_accumulate_adjoint", "fa_status_read", "adjoint", "FlowAccumulate",
            "fa_timing_enable", "fa_timing_read", "accumulate",
            "FlowAccError", "options"]
@@ -108,6 +110,40 @@ def fa_accumulate_adjoint(codes, mask, grad_out, grad_w, workspace, opts=None, d
         ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
 
 
+def fa_batched_workspace_size(rasters, n_fields: int, opts: fa_options | None = None) -> int:
+    arr = (fa_raster * max(1, len(rasters)))(*rasters)
+    return _lib.load().fa_batched_workspace_size(arr, len(rasters), n_fields,
+                                                 ctypes.byref(opts or fa_options()))
+
+
+def fa_accumulate_batched(rasters, n_fields: int, workspace, opts=None, d_status=None,
+                          stream=None) -> int:
+    """Enqueue fa_accumulate_batched over a list of fa_raster descriptors."""
+    arr = (fa_raster * max(1, len(rasters)))(*rasters)
+    return _lib.load().fa_accumulate_batched(arr, len(rasters), n_fields, _ptr(workspace),
+                                             workspace.numel(), ctypes.byref(opts or fa_options()),
+                                             _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_batched_plan_create(rasters, n_fields: int, workspace, opts=None, d_status=None,
+                           stream=None):
+    """Capture a batch in a CUDA graph; returns (status, plan handle)."""
+    arr = (fa_raster * max(1, len(rasters)))(*rasters)
+    h = ctypes.c_void_p()
+    st = _lib.load().fa_batched_plan_create(arr, len(rasters), n_fields, _ptr(workspace),
+                                            workspace.numel(), ctypes.byref(opts or fa_options()),
+                                            _ptr(d_status), _stream_ptr(stream), ctypes.byref(h))
+    return st, h
+
+
+def fa_plan_launch(plan, stream=None) -> int:
+    return _lib.load().fa_plan_launch(plan, _stream_ptr(stream))
+
+
+def fa_plan_destroy(plan) -> None:
+    _lib.load().fa_plan_destroy(plan)
+
+
 def fa_status_read(d_status=None, workspace=None, stream=None):
     """Synchronise the stream and read the device status block back:
     returns (status, count, first_index)."""
@@ -139,6 +175,8 @@ _ws_cache: dict = {}
 def workspace(nbytes: int, device) -> torch.Tensor:
     """A cached uint8 workspace of at least nbytes on `device` (torch memory)."""
     key = torch.device(device)
+    if key.type == "cuda" and key.index is None:  # "cuda" and "cuda:N" share one buffer
+        key = torch.device("cuda", torch.cuda.current_device())
     ws = _ws_cache.get(key)
     if ws is None or ws.numel() < nbytes:
         ws = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=key)
@@ -212,3 +250,100 @@ class FlowAccumulate(torch.autograd.Function):
         mask = saved[1] if ctx.has_mask else None
         gw = adjoint(codes, grad_out.contiguous().float(), mask, tile=ctx.tile)
         return gw, None, None, None
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+def make_raster(codes: torch.Tensor, weights=None, outs=None, mask: torch.Tensor | None = None):
+    """fa_raster for one raster: codes uint8 [R, C]; weights: list of float32
+    [R, C] fields (or None for counts); outs: matching output tensors."""
+    r = fa_raster()
+    R, C = codes.shape
+    r.codes, r.rows, r.cols, r.pitch_codes = codes.data_ptr(), R, C, _pitch(codes)
+    if mask is not None:
+        r.mask, r.pitch_mask = mask.data_ptr(), _pitch(mask)
+    if weights:
+        if len(weights) > FA_MAX_FIELDS:
+            raise ValueError("too many fields")
+        for k, w in enumerate(weights):
+            r.weights[k] = w.data_ptr()
+        r.pitch_w = _pitch(weights[0])
+    for k, o in enumerate(outs):
+        r.out[k] = o.data_ptr()
+    r.pitch_out = _pitch(outs[0])
+    return r
+
+
+def _batch_outputs(items, n_fields):
+    outs = []
+    for it in items:
+        codes = it["codes"]
+        R, C = codes.shape
+        if n_fields == 0:
+            outs.append([torch.empty((R, C), dtype=torch.uint32, device=codes.device)])
+        else:
+            outs.append([torch.empty((R, C), dtype=torch.float32, device=codes.device)
+                         for _ in range(n_fields)])
+    return outs
+
+
+def accumulate_batched(items, n_fields: int = 0, tile=None, check: bool = False, stream=None):
+    """Flow accumulation of many rasters in one pass.  items: list of dicts with
+    'codes' (uint8 [R, C]), optional 'weights' (list of n_fields float32 [R, C])
+    and optional 'mask'.  Returns a list of output lists (uint32 counts when
+    n_fields == 0, else n_fields float32 sums per raster)."""
+    outs = _batch_outputs(items, n_fields)
+    rasters = [make_raster(it["codes"], it.get("weights"), o, it.get("mask"))
+               for it, o in zip(items, outs)]
+    opts = options(tile)
+    dev = items[0]["codes"].device if items else torch.device("cuda")
+    ws = workspace(fa_batched_workspace_size(rasters, n_fields, opts), dev)
+    st = fa_accumulate_batched(rasters, n_fields, ws, opts, None, stream)
+    if st != FA_OK:
+        raise FlowAccError(st, "fa_accumulate_batched")
+    if check:
+        st, _, _ = fa_status_read(None, ws, stream)
+        if st < 0:
+            raise FlowAccError(st, "fa_accumulate_batched (device)")
+    return outs
+
+
+class BatchPlan:
+    """A batch captured once in a CUDA graph; run() replays it.  Holds its
+    own workspace, status block and output tensors."""
+
+    def __init__(self, items, n_fields: int = 0, tile=None, stream=None):
+        self.items = items  # keep inputs alive
+        self.outs = _batch_outputs(items, n_fields)
+        rasters = [make_raster(it["codes"], it.get("weights"), o, it.get("mask"))
+                   for it, o in zip(items, self.outs)]
+        opts = options(tile)
+        dev = items[0]["codes"].device
+        self.ws = torch.empty(max(fa_batched_workspace_size(rasters, n_fields, opts), 1 << 20),
+                              dtype=torch.uint8, device=dev)
+        self.status = torch.zeros(FA_STATUS_WORDS, dtype=torch.int32, device=dev)
+        st, self.handle = fa_batched_plan_create(rasters, n_fields, self.ws, opts, self.status,
+                                                 stream)
+        if st != FA_OK:
+            raise FlowAccError(st, "fa_batched_plan_create")
+
+    def run(self, stream=None):
+        st = fa_plan_launch(self.handle, stream)
+        if st != FA_OK:
+            raise FlowAccError(st, "fa_plan_launch")
+        return self.outs
+
+    def status_read(self, stream=None):
+        return fa_status_read(self.status, None, stream)
+
+    def close(self):
+        if self.handle:
+            fa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -39,6 +39,17 @@ class fa_options(ctypes.Structure):
                 ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+FA_MAX_FIELDS = 16
+
+
+class fa_raster(ctypes.Structure):
+    _fields_ = [("codes", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("pitch_codes", ctypes.c_int64), ("mask", ctypes.c_void_p),
+                ("pitch_mask", ctypes.c_int64), ("weights", ctypes.c_void_p * FA_MAX_FIELDS),
+                ("pitch_w", ctypes.c_int64), ("out", ctypes.c_void_p * FA_MAX_FIELDS),
+                ("pitch_out", ctypes.c_int64)]
+
+
 # name -> (restype, argtypes)
 _P, _I64, _I32, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
 _OPT = ctypes.POINTER(fa_options)
@@ -54,6 +65,13 @@ SIGNATURES = {
     "fa_accumulate_adjoint": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ,
                                      _OPT, _P, _P]),
     "fa_status_read": (_I32, [_P, _P, _P, _PI64, _PI64]),
+    "fa_batched_workspace_size": (_SZ, [ctypes.POINTER(fa_raster), _I32, _I32, _OPT]),
+    "fa_accumulate_batched": (_I32, [ctypes.POINTER(fa_raster), _I32, _I32, _P, _SZ, _OPT, _P,
+                                     _P]),
+    "fa_batched_plan_create": (_I32, [ctypes.POINTER(fa_raster), _I32, _I32, _P, _SZ, _OPT, _P,
+                                      _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "fa_plan_launch": (_I32, [_P, _P]),
+    "fa_plan_destroy": (None, [_P]),
     "fa_timing_enable": (None, [_I32]),
     "fa_timing_read": (_I32, [ctypes.POINTER(ctypes.c_float), _I32]),
 }

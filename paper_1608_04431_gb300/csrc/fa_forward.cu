@@ -33,16 +33,8 @@
 namespace fa {
 
 struct TileArgs {
-    int64_t rows, cols;
-    int th, tw, tiles_x, tiles_y, pmax;
-    const uint8_t *codes;
-    int64_t pc;
-    const uint8_t *mask;
-    int64_t pm;
-    const float *w;
-    int64_t pw;
-    void *out;
-    int64_t po;
+    RasterDesc one;  // the raster of a single-raster call
+    int th, tw, pmax;
     uint32_t *nexit;
     uint16_t *link;
     uint32_t *node_dst;
@@ -50,7 +42,25 @@ struct TileArgs {
     const u128 *G;
     StatusBlock *st;
     uint32_t *maxw;
+    // batches: a table of rasters (nullptr for one raster), each with its
+    // tiles numbered from its tile_base in one global tile sequence
+    const RasterDesc *rtab;
+    int nr;
+    int64_t T;            // tiles in all
+    int64_t fcells;       // cell bound of the perimeter-graph fixed-point scale
 };
+
+// Points the raster fields of `a` at the raster owning global tile t.
+__device__ __forceinline__ RasterDesc raster_of(const TileArgs &a, int64_t t) {
+    if (!a.rtab) return a.one;
+    int lo = 0, hi = a.nr - 1;  // last raster with tile_base <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.rtab[mid].tile_base <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return a.rtab[lo];
+}
 
 // global fixed-point scale for the perimeter graph: |sum| <= cells * max|w| < 2^(124 - q)
 __device__ __forceinline__ int fix_scale(int64_t cells, uint32_t maxw_bits) {
@@ -120,12 +130,12 @@ __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
 // interior codes, or the single halo byte its word holds), then converts and
 // stores them, so several global loads are in flight per lane.  Invalid codes
 // inside the tile are counted.
-__device__ __forceinline__ void load_codes(const TileArgs &a, uint8_t *ec, int64_t R0, int64_t C0,
+__device__ __forceinline__ void load_codes(const RasterDesc &ras, uint8_t *ec, int64_t R0, int64_t C0,
                                            int h, int w, int S, bool count_bad, int &nbad,
                                            long long &fbad) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool fast =
-        ((reinterpret_cast<uintptr_t>(a.codes) | (uintptr_t)a.pc | (uintptr_t)C0) & 3) == 0;
+        ((reinterpret_cast<uintptr_t>(ras.codes) | (uintptr_t)ras.pc | (uintptr_t)C0) & 3) == 0;
     const int words = S >> 2;
     constexpr int U = 4;
     for (int hr0 = warp; hr0 < h + 2; hr0 += U * nw) {
@@ -140,9 +150,9 @@ __device__ __forceinline__ void load_codes(const TileArgs &a, uint8_t *ec, int64
                 mraw[u] = 0;
                 if (hr >= h + 2 || wd >= words) continue;
                 const int64_t gr = R0 - 1 + hr;
-                if (gr < 0 || gr >= a.rows) continue;
-                const uint8_t *row = a.codes + gr * a.pc + C0;
-                const uint8_t *mrow = a.mask ? a.mask + gr * a.pm + C0 : nullptr;
+                if (gr < 0 || gr >= ras.rows) continue;
+                const uint8_t *row = ras.codes + gr * ras.pc + C0;
+                const uint8_t *mrow = ras.mask ? ras.mask + gr * ras.pm + C0 : nullptr;
                 if (c0 >= 0 && c0 + 3 < w) {
                     if (fast) {
                         raw[u] = *reinterpret_cast<const uint32_t *>(row + c0);
@@ -158,7 +168,7 @@ __device__ __forceinline__ void load_codes(const TileArgs &a, uint8_t *ec, int64
                     for (int j = 0; j < 4; ++j) {
                         const int c = c0 + j;
                         if (c < -1 || c > w) continue;
-                        if (C0 + c < 0 || C0 + c >= a.cols) continue;
+                        if (C0 + c < 0 || C0 + c >= ras.cols) continue;
                         raw[u] |= (uint32_t)row[c] << (8 * j);
                         if (mrow) mraw[u] |= (uint32_t)(mrow[c] ? 1 : 0) << (8 * j);
                     }
@@ -180,7 +190,7 @@ __device__ __forceinline__ void load_codes(const TileArgs &a, uint8_t *ec, int64
                     if (k > 9) {
                         if (count_bad && !hcell) {
                             ++nbad;
-                            fbad = min(fbad, (long long)(gr * a.cols + C0 + c));
+                            fbad = min(fbad, (long long)(gr * ras.cols + C0 + c));
                         }
                         continue;
                     }
@@ -257,8 +267,9 @@ __device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
 // C0 - X0, row R0 - 1; outside the raster reads as 0 = NoData) are staged into
 // the other shared buffer while tile t is solved.
 template <int VALM, bool TMA>
-__global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_constant__ CUtensorMap tmap) {
     typedef typename std::conditional<VALM == 0, uint32_t, long long>::type PV;
+    const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_warp[33];
     __shared__ int s_nsrc, s_nent, s_flags;
@@ -269,7 +280,7 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int S = tile_stride(a.tw);
     const int NB = (a.th + 2) * S;
-    const int T = a.tiles_x * a.tiles_y;
+    const int64_t T = a.T;
 
     // shared layout: code buffers (two with TMA, each 128-byte aligned for the
     // bulk copies), then the per-cell arrays
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
     }
     __syncthreads();
     auto issue = [&](int tn, int bb) {  // one thread: stage tile tn's codes into buffer bb
-        const int tyn = tn / a.tiles_x, txn = tn - tyn * a.tiles_x;
+        const int tyn = tn / A.one.tiles_x, txn = tn - tyn * A.one.tiles_x;  // TMA: one raster only
         mbar_expect_tx(&s_bar[bb], (uint32_t)NB);
         tma_load_2d(bb ? cbuf1 : cbuf0, &tmap, txn * a.tw - X0, tyn * a.th - 1, &s_bar[bb]);
     };
@@ -308,10 +319,12 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
 
     int it = 0, to_it = -1;
     for (int t = blockIdx.x; t < T; t += gridDim.x, ++it) {
-        const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+        const RasterDesc ras = raster_of(a, t);
+        const int lt = (int)(t - ras.tile_base);
+        const int ty = lt / ras.tiles_x, tx = lt - ty * ras.tiles_x;
         const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
-        const int h = (int)min((int64_t)a.th, a.rows - R0);
-        const int w = (int)min((int64_t)a.tw, a.cols - C0);
+        const int h = (int)min((int64_t)a.th, ras.rows - R0);
+        const int w = (int)min((int64_t)a.tw, ras.cols - C0);
         const int n_in = h * w;
         const int P = perim_count(h, w);
         const size_t tbase = (size_t)t * a.pmax;
@@ -324,17 +337,17 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
 
         // [phase] load
         if constexpr (TMA) {
-            const int tn = t + gridDim.x;
-            if (tid == 0 && tn < T) issue(tn, (it & 1) ^ 1);
+            const int64_t tn = t + gridDim.x;
+            if (tid == 0 && tn < T) issue((int)tn, (it & 1) ^ 1);
             if (!mbar_wait(&s_bar[it & 1], (uint32_t)((it >> 1) & 1))) atomicOr(&s_flags, FA_FLAG_TIMEOUT);
             __syncthreads();
             if (s_flags & FA_FLAG_TIMEOUT) {
-                to_it = (t + (int)gridDim.x < T) ? -2 - it : it;  // -2-it: the next stage was issued too
+                to_it = (t + (int64_t)gridDim.x < T) ? -2 - it : it;  // -2-it: the next stage was issued too
                 break;
             }
-            transform_box(ec, h, w, S, R0, C0, a.cols, nbad, fbad);
+            transform_box(ec, h, w, S, R0, C0, ras.cols, nbad, fbad);
         } else {
-            load_codes(a, ec, R0, C0, h, w, S, true, nbad, fbad);
+            load_codes(ras, ec, R0, C0, h, w, S, true, nbad, fbad);
         }
         __syncthreads();
 
@@ -405,7 +418,7 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
                     if constexpr (VALM == 1) {
                         for (int j = 0; j < nvalid; ++j) {
                             if (!((valid >> (8 * j)) & 1u)) continue;
-                            const float wf = a.w ? a.w[(R0 + r) * a.pw + (C0 + c + j)] : 1.0f;
+                            const float wf = ras.w ? ras.w[(R0 + r) * ras.pw + (C0 + c + j)] : 1.0f;
                             const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
                             if (b >= 0x7f800000u) nonfinite = 1;
                             maxw = max(maxw, b);
@@ -464,10 +477,11 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
                 const int tyd = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
                 const int txd = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
                 const int64_t R0d = (int64_t)tyd * a.th, C0d = (int64_t)txd * a.tw;
-                const int hd = (int)min((int64_t)a.th, a.rows - R0d);
-                const int wd = (int)min((int64_t)a.tw, a.cols - C0d);
+                const int hd = (int)min((int64_t)a.th, ras.rows - R0d);
+                const int wd = (int)min((int64_t)a.tw, ras.cols - C0d);
                 const int sd = slot_of((int)(R0 + rr - R0d), (int)(C0 + cc - C0d), hd, wd);
-                a.node_dst[tbase + rk] = (uint32_t)(((size_t)tyd * a.tiles_x + txd) * a.pmax + sd);
+                a.node_dst[tbase + rk] =
+                    (uint32_t)(((size_t)ras.tile_base + (size_t)tyd * ras.tiles_x + txd) * a.pmax + sd);
                 a.link[tbase + s] = (uint16_t)rk;  // an exit links to itself
                 ++rk;
             } else if (entry) {
@@ -585,7 +599,7 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
         // lose their last pending dependency); exit records ------------------
         const double inv = ldexp(1.0, -qt);
         for (int r = warp; r < h; r += nw) {
-            const size_t orow = (size_t)(R0 + r) * a.po + C0;
+            const size_t orow = (size_t)(R0 + r) * ras.po + C0;
             const int base = (r + 1) * S + X0;
             for (int c = lane; c < w; c += 32) {
                 const int i = base + c;
@@ -598,12 +612,12 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
                 }
                 if (ec[i] && !fin) {
                     ++ncyc;
-                    fbad = min(fbad, (long long)((R0 + r) * a.cols + (C0 + c)));
+                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
                 }
                 if constexpr (VALM == 0) {
-                    reinterpret_cast<uint32_t *>(a.out)[orow + c] = fin ? (wd & 0xFFFFFFu) : 0u;
+                    reinterpret_cast<uint32_t *>(ras.out)[orow + c] = fin ? (wd & 0xFFFFFFu) : 0u;
                 } else {
-                    reinterpret_cast<float *>(a.out)[orow + c] =
+                    reinterpret_cast<float *>(ras.out)[orow + c] =
                         fin ? (float)((double)fsum[i] * inv) : 0.0f;
                 }
             }
@@ -670,16 +684,19 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs a, const __grid_const
 // pass 2: add the flow entering each perimeter cell to its downstream path
 // ---------------------------------------------------------------------------
 template <int VALM>
-__global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
+__global__ void __launch_bounds__(256, 4) k_offsets(TileArgs A) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_emax, s_nent;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int t = blockIdx.x;
-    const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+    const int64_t t = blockIdx.x;
+    const TileArgs &a = A;
+    const RasterDesc ras = raster_of(a, t);
+    const int lt = (int)(t - ras.tile_base);
+    const int ty = lt / ras.tiles_x, tx = lt - ty * ras.tiles_x;
     const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
-    const int h = (int)min((int64_t)a.th, a.rows - R0);
-    const int w = (int)min((int64_t)a.tw, a.cols - C0);
+    const int h = (int)min((int64_t)a.th, ras.rows - R0);
+    const int w = (int)min((int64_t)a.tw, ras.cols - C0);
     const int S = tile_stride(a.tw);
     const int n_in = h * w;
     const int P = perim_count(h, w);
@@ -696,12 +713,12 @@ __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
     }
     int nbad = 0;
     long long fbad = NO_INDEX;
-    load_codes(a, ec, R0, C0, h, w, S, false, nbad, fbad);
+    load_codes(ras, ec, R0, C0, h, w, S, false, nbad, fbad);
     for (int i = tid; i < n_in; i += nt) off[i] = 0ull;
     __syncthreads();
 
     // ---- in(p) = sum of G over the exits of neighbouring tiles draining into p
-    const int qf = VALM ? fix_scale(a.rows * a.cols, *a.maxw) : 0;
+    const int qf = VALM ? fix_scale(a.fcells, *a.maxw) : 0;
     int emax = INT_MIN;
     for (int s = tid; s < P; s += nt) {
         int r, c;
@@ -718,10 +735,10 @@ __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
                 const int tyh = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
                 const int txh = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
                 const int64_t R0h = (int64_t)tyh * a.th, C0h = (int64_t)txh * a.tw;
-                const int hh = (int)min((int64_t)a.th, a.rows - R0h);
-                const int wh = (int)min((int64_t)a.tw, a.cols - C0h);
+                const int hh = (int)min((int64_t)a.th, ras.rows - R0h);
+                const int wh = (int)min((int64_t)a.tw, ras.cols - C0h);
                 const int sh = slot_of((int)(R0 + rr - R0h), (int)(C0 + cc - C0h), hh, wh);
-                gidx[ng++] = ((size_t)tyh * a.tiles_x + txh) * a.pmax + sh;
+                gidx[ng++] = ((size_t)ras.tile_base + (size_t)tyh * ras.tiles_x + txh) * a.pmax + sh;
             }
         }
         if (!ng) continue;
@@ -789,17 +806,17 @@ __global__ void __launch_bounds__(256, 4) k_offsets(TileArgs a) {
     int ovf = 0;
     const double inv = ldexp(1.0, -qo);
     for (int r = warp; r < h; r += nw) {
-        const size_t orow = (size_t)(R0 + r) * a.po + C0;
+        const size_t orow = (size_t)(R0 + r) * ras.po + C0;
         for (int c = lane; c < w; c += 32) {
             const unsigned long long o = off[r * w + c];
             if (!o) continue;
             if constexpr (VALM == 0) {
-                uint32_t *p = reinterpret_cast<uint32_t *>(a.out) + orow + c;
+                uint32_t *p = reinterpret_cast<uint32_t *>(ras.out) + orow + c;
                 const unsigned long long s64 = (unsigned long long)*p + o;
                 if (s64 >> 32) ovf = 1;
                 *p = (uint32_t)s64;
             } else {
-                float *p = reinterpret_cast<float *>(a.out) + orow + c;
+                float *p = reinterpret_cast<float *>(ras.out) + orow + c;
                 *p = (float)((double)*p + (double)(long long)o * inv);
             }
         }
@@ -1034,9 +1051,10 @@ static int sm_count() {
     return n;
 }
 
+// Shared-memory limit and blocks per SM of k_solve<VALM, TMA> for a tile shape
+// (set and queried once per shape).
 template <int VALM, bool TMA>
-static cudaError_t launch_solve_k(const Geom &g, const TileArgs &ta, const CUtensorMap &m,
-                                  cudaStream_t s) {
+static cudaError_t solve_config(const Geom &g, int &blocks_per_sm) {
     static int configured = 0;
     static int per_sm = 0, per_sm_smem = -1, per_sm_nt = -1;
     const size_t smem = solve_smem_bytes(g.th, g.tw, VALM, TMA);
@@ -1050,9 +1068,24 @@ static cudaError_t launch_solve_k(const Geom &g, const TileArgs &ta, const CUten
         per_sm_smem = (int)smem;
         per_sm_nt = nt;
     }
-    const int64_t T = g.tiles();
-    const unsigned grid = (unsigned)std::min<int64_t>(T, (int64_t)per_sm * sm_count());
-    k_solve<VALM, TMA><<<grid, nt, smem, s>>>(ta, m);
+    blocks_per_sm = per_sm;
+    return cudaSuccess;
+}
+
+template <int VALM>
+static cudaError_t offsets_config(const Geom &g) {
+    static int configured = 0;
+    return set_smem(k_offsets<VALM>, offsets_smem_bytes(g.th, g.tw), configured);
+}
+
+template <int VALM, bool TMA>
+static cudaError_t launch_solve_k(const Geom &g, const TileArgs &ta, const CUtensorMap &m,
+                                  cudaStream_t s) {
+    int per_sm = 1;
+    cudaError_t e = solve_config<VALM, TMA>(g, per_sm);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<int64_t>(ta.T, (int64_t)per_sm * sm_count());
+    k_solve<VALM, TMA><<<grid, tile_threads(g), solve_smem_bytes(g.th, g.tw, VALM, TMA), s>>>(ta, m);
     return cudaGetLastError();
 }
 
@@ -1069,39 +1102,37 @@ static cudaError_t launch_solve(const Geom &g, const TileArgs &ta, const uint8_t
 
 template <int VALM>
 static cudaError_t launch_offsets(const Geom &g, const TileArgs &ta, cudaStream_t s) {
-    static int configured = 0;
-    const size_t smem = offsets_smem_bytes(g.th, g.tw);
-    cudaError_t e = set_smem(k_offsets<VALM>, smem, configured);
+    cudaError_t e = offsets_config<VALM>(g);
     if (e != cudaSuccess) return e;
-    k_offsets<VALM><<<(unsigned)g.tiles(), tile_threads(g), smem, s>>>(ta);
+    k_offsets<VALM><<<(unsigned)ta.T, tile_threads(g), offsets_smem_bytes(g.th, g.tw), s>>>(ta);
     return cudaGetLastError();
 }
 
-cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,
-                           int64_t pm, const float *w, int64_t pw, void *out, int64_t po,
-                           int val_mode, const FwdWork &ws, void *status, cudaStream_t s) {
+// Sets the kernels' shared-memory limits and caches their occupancy and the SM
+// count ahead of a stream capture (done on first use otherwise).  Batches
+// never stage codes by TMA.
+cudaError_t prepare_forward(const Geom &g, int val_mode) {
+    int per_sm = 1;
+    cudaError_t e = val_mode ? solve_config<1, false>(g, per_sm) : solve_config<0, false>(g, per_sm);
+    if (e == cudaSuccess) e = val_mode ? offsets_config<1>(g) : offsets_config<0>(g);
+    sm_count();
+    return e;
+}
+
+// Status reset, pass 1, the perimeter-graph resolve and pass 2 for the tiles
+// described by `ta` (one raster, or a batch through ta.rtab).
+static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const FwdWork &ws,
+                                void *status, const uint8_t *tma_codes, int64_t tma_pc,
+                                const uint8_t *tma_mask, cudaStream_t s) {
     StatusBlock *st = reinterpret_cast<StatusBlock *>(status ? status : ws.status);
     k_init_status<<<1, 64, 0, s>>>(st, ws.misc, 2 + ws.kmax);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (g.rows == 0 || g.cols == 0) return cudaSuccess;
+    if (ta.T == 0) return cudaSuccess;
 
-    TileArgs ta;
-    ta.rows = g.rows;
-    ta.cols = g.cols;
     ta.th = g.th;
     ta.tw = g.tw;
-    ta.tiles_x = g.tiles_x;
-    ta.tiles_y = g.tiles_y;
     ta.pmax = g.pmax;
-    ta.codes = codes;
-    ta.pc = pc;
-    ta.mask = mask;
-    ta.pm = pm;
-    ta.w = w;
-    ta.pw = pw;
-    ta.out = out;
-    ta.po = po;
     ta.nexit = ws.nexit;
     ta.link = ws.link;
     ta.node_dst = ws.node_dst;
@@ -1111,16 +1142,16 @@ cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, cons
     ta.maxw = ws.misc;
 
     timing_mark(0, s);
-    const bool tma = !(g.flags & FA_OPT_NO_TMA);
-    e = val_mode ? launch_solve<1>(g, ta, codes, pc, mask, tma, s)
-                 : launch_solve<0>(g, ta, codes, pc, mask, tma, s);
+    const bool tma = !(g.flags & FA_OPT_NO_TMA) && ta.rtab == nullptr;
+    e = val_mode ? launch_solve<1>(g, ta, tma_codes, tma_pc, tma_mask, tma, s)
+                 : launch_solve<0>(g, ta, tma_codes, tma_pc, tma_mask, tma, s);
     if (e != cudaSuccess) return e;
     timing_mark(1, s);
 
     ForestArgs f;
-    f.tiles = g.tiles();
+    f.tiles = ta.T;
     f.pmax = g.pmax;
-    f.cells = g.rows * g.cols;
+    f.cells = ta.fcells;
     f.valm = val_mode;
     f.nexit = ws.nexit;
     f.link = ws.link;
@@ -1144,6 +1175,44 @@ cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, cons
     timing_mark(3, s);
     timing_set_count(3);
     return e;
+}
+
+cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,
+                           int64_t pm, const float *w, int64_t pw, void *out, int64_t po,
+                           int val_mode, const FwdWork &ws, void *status, cudaStream_t s) {
+    TileArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    RasterDesc &r = ta.one;
+    r.codes = codes;
+    r.pc = pc;
+    r.mask = mask;
+    r.pm = pm;
+    r.w = w;
+    r.pw = pw;
+    r.out = out;
+    r.po = po;
+    r.rows = g.rows;
+    r.cols = g.cols;
+    r.tiles_x = g.tiles_x;
+    r.tiles_y = g.tiles_y;
+    r.tile_base = 0;
+    ta.rtab = nullptr;
+    ta.nr = 1;
+    ta.T = (g.rows == 0 || g.cols == 0) ? 0 : g.tiles();
+    ta.fcells = g.rows * g.cols;
+    return run_pipeline(g, ta, val_mode, ws, status, codes, pc, mask, s);
+}
+
+cudaError_t launch_forward_batched(const Geom &g, const RasterDesc *d_tab, int nr, int64_t T,
+                                   int64_t cells_bound, int val_mode, const FwdWork &ws,
+                                   void *status, cudaStream_t s) {
+    TileArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    ta.rtab = d_tab;
+    ta.nr = nr;
+    ta.T = T;
+    ta.fcells = cells_bound;
+    return run_pipeline(g, ta, val_mode, ws, status, nullptr, 0, nullptr, s);
 }
 
 }  // namespace fa

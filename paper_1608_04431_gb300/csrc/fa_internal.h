@@ -22,6 +22,23 @@ struct Geom {
 };
 
 bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g);
+
+// One raster of a batch as the kernels see it (device-resident table).  All
+// rasters of a batch share the tile shape; their tiles are numbered globally,
+// raster after raster, starting at tile_base.
+struct RasterDesc {
+    const uint8_t *codes;
+    int64_t pc;
+    const uint8_t *mask;
+    int64_t pm;
+    const float *w;
+    int64_t pw;
+    void *out;
+    int64_t po;
+    int64_t rows, cols;
+    int32_t tiles_x, tiles_y;
+    int64_t tile_base;
+};
 // whether the forward tile kernel supports this tile shape (shared memory and
 // 16-bit cell indices); valm 0 = uint32 counts, 1 = float32
 bool forward_tile_ok(const Geom &g, int valm);
@@ -64,6 +81,18 @@ void timing_mark(int i, cudaStream_t s);
 void timing_set_count(int n);
 // sets whether phase timing records events; returns the previous setting
 bool timing_swap(bool on);
+
+// Configures the forward kernels (shared-memory limits, device queries) so
+// that a later stream capture makes no first-use attribute calls.
+cudaError_t prepare_forward(const Geom &g, int val_mode);
+
+// Launch the forward pipeline over a batch described by a device table of
+// `nr` rasters (tiles numbered globally, `T` in all; every raster's weights
+// NULL and uint32 outputs when val_mode is 0); the workspace is carved for T
+// tiles.  cells_bound bounds the cell count of any raster (fixed-point scale).
+cudaError_t launch_forward_batched(const Geom &g, const RasterDesc *d_tab, int nr, int64_t T,
+                                   int64_t cells_bound, int val_mode, const FwdWork &ws,
+                                   void *status, cudaStream_t s);
 
 // Launch the whole forward pipeline on `stream`.  val_mode 0: uint32 counts
 // (weights must be NULL); 1: float32 output (weights or unit).

@@ -79,3 +79,59 @@ def test_accumulate_rejects_bad_args_without_gpu(lib):
     st = lib.fa_accumulate(fake, 10, 10, 10, None, 0, None, 0, fake, 7, 10,
                            fake, 1 << 30, ctypes.byref(o), None, None)
     assert st == _lib.FA_ERR_INVALID_ARG  # unknown dtype
+
+
+def _raster(rows, cols, n_fields, fake, pitch=None):
+    r = _lib.fa_raster()
+    r.codes = fake
+    r.rows, r.cols = rows, cols
+    r.pitch_codes = r.pitch_w = r.pitch_out = cols if pitch is None else pitch
+    for f in range(max(n_fields, 1)):
+        r.out[f] = fake
+        if n_fields:
+            r.weights[f] = fake
+    return r
+
+
+def test_batched_host_logic_without_gpu(lib):
+    o = _lib.fa_options()
+    fake = 1 << 20  # never dereferenced: validation and sizing only
+    arr = (_lib.fa_raster * 3)(_raster(100, 100, 0, fake), _raster(0, 7, 0, fake),
+                               _raster(300, 500, 0, fake))
+    one = lib.fa_batched_workspace_size(arr, 1, 0, ctypes.byref(o))
+    three = lib.fa_batched_workspace_size(arr, 3, 0, ctypes.byref(o))
+    assert 0 < one < three
+    # an empty raster adds no tiles and no table entry
+    assert lib.fa_batched_workspace_size(arr, 2, 0, ctypes.byref(o)) == one
+    w3 = (_lib.fa_raster * 1)(_raster(100, 100, 3, fake))
+    w1 = (_lib.fa_raster * 1)(_raster(100, 100, 1, fake))
+    assert lib.fa_batched_workspace_size(w3, 1, 3, ctypes.byref(o)) > \
+        lib.fa_batched_workspace_size(w1, 1, 1, ctypes.byref(o)) > 0
+    # rejected: negative count, too many fields, pitch < cols, missing output
+    assert lib.fa_batched_workspace_size(arr, -1, 0, ctypes.byref(o)) == 0
+    assert lib.fa_batched_workspace_size(w3, 1, _lib.FA_MAX_FIELDS + 1, ctypes.byref(o)) == 0
+    bad = (_lib.fa_raster * 1)(_raster(100, 100, 0, fake, pitch=50))
+    assert lib.fa_batched_workspace_size(bad, 1, 0, ctypes.byref(o)) == 0
+    nout = (_lib.fa_raster * 1)(_raster(100, 100, 0, fake))
+    nout[0].out[0] = None
+    assert lib.fa_batched_workspace_size(nout, 1, 0, ctypes.byref(o)) == 0
+    nw = (_lib.fa_raster * 1)(_raster(100, 100, 2, fake))
+    nw[0].weights[1] = None
+    assert lib.fa_batched_workspace_size(nw, 1, 2, ctypes.byref(o)) == 0
+    # workspace missing, misaligned or too small: refused before any CUDA call
+    st = lib.fa_accumulate_batched(arr, 3, 0, None, 1 << 30, ctypes.byref(o), None, None)
+    assert st == _lib.FA_ERR_WORKSPACE
+    st = lib.fa_accumulate_batched(arr, 3, 0, fake + 8, 1 << 30, ctypes.byref(o), None, None)
+    assert st == _lib.FA_ERR_WORKSPACE
+    st = lib.fa_accumulate_batched(arr, 3, 0, fake, three - 1, ctypes.byref(o), None, None)
+    assert st == _lib.FA_ERR_WORKSPACE
+    st = lib.fa_accumulate_batched(bad, 1, 0, fake, 1 << 30, ctypes.byref(o), None, None)
+    assert st == _lib.FA_ERR_INVALID_ARG
+    plan = ctypes.c_void_p(123)
+    st = lib.fa_batched_plan_create(arr, 3, 0, fake, three - 1, ctypes.byref(o), None, None,
+                                    ctypes.byref(plan))
+    assert st == _lib.FA_ERR_WORKSPACE and not plan.value
+    st = lib.fa_batched_plan_create(arr, 3, 0, fake, three, ctypes.byref(o), None, None, None)
+    assert st == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_plan_launch(None, None) == _lib.FA_ERR_INVALID_ARG
+    lib.fa_plan_destroy(None)
