@@ -11,7 +11,14 @@ Printed JSON line: cells/s over all ranks (max-over-ranks time), the roofline
 of the dominant kernel (algorithmic bytes / live CUDA-event duration), the
 float32 weighted form, an end-to-end number through the public API with host
 buffers, the oracle timed on host cores, and SM clocks sampled during the
-timed region.
+timed region.  Two more forms are timed on the same GPU against the plain
+kernel (their per-cell time over the plain kernel's):
+  batched: 64 spectral-DEM rasters, rows U{257..4096} x cols U{311..6000}
+    (seeds 301..364), 8 float32 fields each (4 uniform [0,1), 4 lognormal
+    sigma=1), one CUDA-graph replay of fa_accumulate_batched, against the same
+    512 (raster, field) pairs run one fa_accumulate call each;
+  adjoint: an 8192 x 8192 DEM raster (seed 401), dL/dA nonzero at 256 gauge
+    cells, fa_accumulate_adjoint against the float32 forward on that raster.
 
 --impl reference: times the CPU oracle (test infrastructure, a deliberately
 slow reference) on the same workload and metric on host cores.
@@ -40,6 +47,8 @@ TILE = (64, 64)
 BYTES_PER_CELL_COUNTS = 5  # 1 B code read + 4 B uint32 written (algorithmic minimum)
 BYTES_PER_CELL_F32 = 9     # + 4 B float32 weight read
 WORKLOAD = "d8_dem_16384x16384"
+BATCH_N, BATCH_FIELDS, BATCH_SEED, BATCH_SHAPE_SEED = 64, 8, 301, 300
+ADJ_N, ADJ_SEED, ADJ_GAUGES = 8192, 401, 256
 
 
 def peaks():
@@ -211,7 +220,134 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def _time(fn, stream, n):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def leg_batched(fa, dev, stream, opts, warmup, reps):
+    """64 rasters x 8 fields: one graph replay against the per-pair loop."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    import synth
+
+    shapes = synth.batch_shapes(BATCH_N, BATCH_SHAPE_SEED)
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        codes = list(ex.map(lambda i: synth.dem_codes(*shapes[i], BATCH_SEED + i), range(BATCH_N)))
+    items = []
+    for i, c in enumerate(codes):
+        g = torch.Generator(device=dev)
+        g.manual_seed(BATCH_SEED * 1000 + i)
+        ws = []
+        for k in range(BATCH_FIELDS):
+            t = torch.empty(c.shape, dtype=torch.float32, device=dev)
+            if k < BATCH_FIELDS // 2:
+                t.uniform_(0.0, 1.0, generator=g)
+            else:
+                t.log_normal_(0.0, 1.0, generator=g)
+            ws.append(t)
+        items.append({"codes": torch.from_numpy(c).to(dev), "weights": ws})
+    cells = int(sum(c.size for c in codes))
+    pairs = cells * BATCH_FIELDS
+    plan = fa.BatchPlan(items, BATCH_FIELDS, tile=(opts.tile_h, opts.tile_w), stream=stream)
+    for _ in range(warmup):
+        plan.run(stream)
+    ms_b = _time(lambda: plan.run(stream), stream, reps)
+    st = plan.status_read(stream)[0]
+
+    # the same pairs, one fa_accumulate call each
+    rmax = max(r for r, _ in shapes)
+    cmax = max(c for _, c in shapes)
+    work = torch.empty(fa.fa_workspace_size(rmax, cmax, opts), dtype=torch.uint8, device=dev)
+    outs = [[torch.empty(it["codes"].shape, dtype=torch.float32, device=dev)
+             for _ in range(BATCH_FIELDS)] for it in items]
+
+    def loop():
+        for it, oo in zip(items, outs):
+            for k in range(BATCH_FIELDS):
+                e = fa.fa_accumulate(it["codes"], it["weights"][k], None, oo[k], fa.FA_OUT_F32,
+                                     work, opts, None, stream)
+                if e != fa.FA_OK:
+                    raise fa.FlowAccError(e, "fa_accumulate (batch loop)")
+
+    loop()
+    ms_l = _time(loop, stream, max(2, reps // 2))
+    worst = 0.0
+    for ob, ol in zip(plan.outs, outs):
+        for k in range(BATCH_FIELDS):
+            a, b = ob[k].double(), ol[k].double()
+            worst = max(worst, float(((a - b).abs() / b.abs().clamp_min(1e-30)).max()))
+    plan.close()
+    return {"rasters": BATCH_N, "fields": BATCH_FIELDS, "cells": cells, "cell_fields": pairs,
+            "ms_graph_replay": ms_b, "cell_fields_per_s": pairs / (ms_b / 1e3),
+            "ns_per_cell_field": ms_b * 1e6 / pairs,
+            "ms_plain_loop": ms_l, "plain_loop_cell_fields_per_s": pairs / (ms_l / 1e3),
+            "time_vs_plain_loop": ms_b / ms_l,
+            # algorithmic bytes: 1 B code per cell, 4 B weight + 4 B output per pair
+            "hbm_frac_step": (cells + 8 * pairs) / (ms_b / 1e3) / 1e9,  # divided by the peak below
+            "status": int(st), "max_rel_diff_vs_plain": worst}
+
+
+def leg_adjoint(fa, dev, stream, opts, warmup, reps):
+    """8192^2 DEM: fa_accumulate_adjoint (dL/dA nonzero at 256 gauges) against
+    the float32 forward on the same raster; checked by <A(w), g> = <w, grad_w>."""
+    import torch
+
+    import synth
+
+    codes = synth.dem_codes(ADJ_N, ADJ_N, ADJ_SEED)
+    cells = codes.size
+    cd = torch.from_numpy(codes).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(ADJ_SEED + 1)
+    w = torch.empty(codes.shape, dtype=torch.float32, device=dev).uniform_(0.0, 2.0, generator=g)
+    work = torch.empty(fa.fa_workspace_size(ADJ_N, ADJ_N, opts), dtype=torch.uint8, device=dev)
+    A = torch.empty(codes.shape, dtype=torch.float32, device=dev)
+    cnt = fa.accumulate(cd).view(torch.int32).cpu().numpy().view(np.uint32)
+    gidx = synth.gauges(codes != 0, cnt, ADJ_GAUGES, ADJ_SEED + 2)
+    gout = torch.zeros(cells, dtype=torch.float32, device=dev)
+    gout[torch.from_numpy(gidx).to(dev)] = torch.from_numpy(
+        synth.rng(ADJ_SEED + 3).standard_normal(gidx.size).astype(np.float32)).to(dev)
+    gout = gout.view(codes.shape)
+    gw = torch.empty_like(gout)
+
+    def fwd():
+        e = fa.fa_accumulate(cd, w, None, A, fa.FA_OUT_F32, work, opts, None, stream)
+        if e != fa.FA_OK:
+            raise fa.FlowAccError(e, "fa_accumulate (adjoint leg)")
+
+    def adj():
+        e = fa.fa_accumulate_adjoint(cd, None, gout, gw, work, opts, None, stream)
+        if e != fa.FA_OK:
+            raise fa.FlowAccError(e, "fa_accumulate_adjoint")
+
+    for _ in range(warmup):
+        fwd()
+        adj()
+    ms_f = _time(fwd, stream, reps)
+    ms_a = _time(adj, stream, reps)
+    st = fa.fa_status_read(None, work, stream)[0]
+    lhs = float((A.double() * gout.double()).sum())
+    rhs = float((w.double() * gw.double()).sum())
+    return {"rows": ADJ_N, "cols": ADJ_N, "cells": cells, "gauges": int(gidx.size),
+            "ms_adjoint": ms_a, "cells_per_s": cells / (ms_a / 1e3),
+            "ms_forward_f32_same_raster": ms_f, "time_vs_forward_f32": ms_a / ms_f,
+            # algorithmic bytes: 1 B code + 4 B dL/dA (dense) + 4 B dL/dw per cell
+            "hbm_frac_step": 9 * cells / (ms_a / 1e3) / 1e9,  # divided by the peak below
+            "status": int(st), "dot_identity_rel_err": abs(lhs - rhs) / max(abs(lhs), 1e-30)}
+
+
 def main():
+    global ROWS, COLS, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
@@ -222,7 +358,12 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up and timed steps (for ncu): no clock sampling, phase "
                          "timing, extra legs or CPU baseline")
+    ap.add_argument("--size", type=int, default=ROWS,
+                    help="raster side; smaller than the default only for profiler captures")
     args = ap.parse_args()
+    if args.size != ROWS:
+        ROWS = COLS = args.size
+        WORKLOAD = f"d8_dem_{ROWS}x{COLS}"
     if args.profile:
         args.no_extra = args.no_cpu_baseline = True
     if args.warmup < 3:
@@ -373,6 +514,21 @@ def main():
                        "d2h_bytes_per_step": int(cells * 4), "ms_per_step": mse}
         # the result of the last step must be exact
         got = h_out.view(torch.int32).numpy().view(np.uint32)
+        del h_codes
+
+        # batched and adjoint forms against the plain kernel, same GPU
+        if rank == 0:
+            b = leg_batched(fa, dev, stream, opts, 2, 5)
+            b["hbm_frac_step"] = b["hbm_frac_step"] / peak
+            b["ns_per_cell_plain_f32"] = msf * 1e6 / cells
+            b["time_per_cell_vs_plain_f32"] = b["ns_per_cell_field"] / b["ns_per_cell_plain_f32"]
+            line["forms"]["batched"] = b
+            torch.cuda.empty_cache()
+            a = leg_adjoint(fa, dev, stream, opts, 3, 20)
+            a["hbm_frac_step"] = a["hbm_frac_step"] / peak
+            a["time_per_cell_vs_plain_f32"] = (a["ms_adjoint"] / a["cells"]) / (msf / cells)
+            line["forms"]["adjoint"] = a
+            torch.cuda.empty_cache()
     else:
         got = out_d.view(torch.int32).cpu().numpy().view(np.uint32)
 
