@@ -42,6 +42,8 @@ struct TileArgs {
     const u128 *G;
     StatusBlock *st;
     uint32_t *maxw;
+    uint32_t *ef_hdr, *ef_cp, *seg_merge, *inf_src;
+    uint16_t *ef_seg, *inf_seg;
     // batches: a table of rasters (nullptr for one raster), each with its
     // tiles numbered from its tile_base in one global tile sequence
     const RasterDesc *rtab;
@@ -98,23 +100,31 @@ __host__ __device__ inline size_t code_buf_bytes(int th, int tw) {
     return (((size_t)(th + 2) * tile_stride(tw)) + 127) & ~size_t(127);
 }
 
+// Row stride of the compact per-cell arrays (word, sums, claim tags): a
+// multiple of four so that a four-cell group is one 16-byte store.
+__host__ __device__ inline int cell_stride(int tw) { return (tw + 3) & ~3; }
+
 __host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm, bool tma) {
-    const size_t nb = (size_t)(th + 2) * tile_stride(tw);
+    const size_t nc = (size_t)th * cell_stride(tw), pm = (size_t)(2 * th + 2 * tw);
     size_t b = 128;                           // alignment slack of the dynamic window
     b += code_buf_bytes(th, tw) * (tma ? 2 : 1);  // effective codes (two TMA stages)
-    b += valm ? nb * 8 : 0;                   // 64-bit fixed-point sums
-    b += nb * 4;                              // packed word per cell
-    b += (size_t)th * tw * 2;                 // source queue (u16 cell indices)
-    b += (size_t)(2 * th + 2 * tw) * 2;       // exit rank per perimeter slot
-    b += (size_t)(2 * th + 2 * tw) * 2;       // entry-cell list
+    b += valm ? nc * 8 : 0;                   // 64-bit fixed-point sums
+    b += nc * 4;                              // packed word per cell
+    b += nc * 2;                              // entry-forest claim tag per cell
+    b += pm * 4;                              // segment -> where it joins another
+    b += nc * 2;                              // source queue (u16 cell indices)
+    b += pm * 2 * 3;                          // exit rank per slot, entry list, segment ends
     return (b + 15) & ~size_t(15);
 }
 
 __host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
-    const size_t nb = (size_t)(th + 2) * tile_stride(tw);
-    size_t b = (((size_t)th * tw + 1) & ~size_t(1)) * 8;  // per-cell offset, padded to 16 B
-    b += (size_t)(2 * th + 2 * tw) * 18;      // inflow and slot per listed entry
-    b += nb;                                  // effective codes
+    // segments: at most one per perimeter cell
+    const size_t nc = (size_t)th * cell_stride(tw), pc = (size_t)perim_count(th, tw);
+    size_t b = pc * 16;                       // inflow per segment (graph scale), then prefix sums
+    b += pc * 8 * 2;                          // inflow at the tile scale, flow at the end
+    b += pc * 4 * 2 + (pc + 1) * 4;           // join target, pending joins / fill, bucket start
+    b += pc * 2 * 2;                          // join position, joins grouped by target
+    b += nc * 2;                              // position of every entry-forest cell
     return (b + 15) & ~size_t(15);
 }
 
@@ -266,13 +276,24 @@ __device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
 // With TMA the codes of tile t + gridDim.x (box of S x (th+2) bytes at column
 // C0 - X0, row R0 - 1; outside the raster reads as 0 = NoData) are staged into
 // the other shared buffer while tile t is solved.
+//
+// Besides A_loc and the perimeter records (Algorithms 1 and 2) a tile records
+// its entry forest for pass 2: the cells on the in-tile paths downstream of
+// its entry cells.  The path of every entry is walked once, claiming cells as
+// it goes; a walk that reaches a cell already claimed by another entry's walk
+// stops there and records the join.  Each walk's claimed run is a segment:
+// the cells of segment e at positions 0, 1, ... in path order.
+constexpr uint32_t NO_JOIN = 0xFFFFFFFFu;
+
+// Resident blocks per SM: four 64 x 64 tiles fit shared memory for counts,
+// two with the 64-bit sums of weighted runs (which then get more registers).
 template <int VALM, bool TMA>
-__global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const __grid_constant__ CUtensorMap tmap) {
     typedef typename std::conditional<VALM == 0, uint32_t, long long>::type PV;
     const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_nsrc, s_nent, s_flags;
+    __shared__ int s_nsrc, s_nent, s_flags, s_qhead, s_nef, s_ninf;
     __shared__ uint32_t s_maxw;
     __shared__ __align__(8) uint64_t s_bar[2];
 
@@ -280,6 +301,8 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int S = tile_stride(a.tw);
     const int NB = (a.th + 2) * S;
+    const int WS = cell_stride(a.tw);  // compact arrays: cell (r, c) at r * WS + c
+    const int NC = a.th * WS;
     const int64_t T = a.T;
 
     // shared layout: code buffers (two with TMA, each 128-byte aligned for the
@@ -291,10 +314,13 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
     uint8_t *cbuf1 = base128 + (TMA ? CB : 0);
     long long *fsum = reinterpret_cast<long long *>(base128 + (TMA ? 2 : 1) * CB);
     uint32_t *word = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(fsum) +
-                                                  (VALM ? 8 * (size_t)NB : 0));
-    uint16_t *srcq = reinterpret_cast<uint16_t *>(word + NB);
-    uint16_t *rank = srcq + a.th * a.tw;
+                                                  (VALM ? 8 * (size_t)NC : 0));
+    uint16_t *tag = reinterpret_cast<uint16_t *>(word + NC);  // claiming segment + 1, 0 = free
+    uint32_t *segjoin = reinterpret_cast<uint32_t *>(tag + NC);
+    uint16_t *srcq = reinterpret_cast<uint16_t *>(segjoin + a.pmax);
+    uint16_t *rank = srcq + NC;
     uint16_t *entq = rank + a.pmax;
+    uint16_t *segend = entq + a.pmax;
 
     // status, accumulated over this block's tiles
     int nbad = 0, ncyc = 0, nonfinite = 0;
@@ -328,11 +354,15 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
         const int n_in = h * w;
         const int P = perim_count(h, w);
         const size_t tbase = (size_t)t * a.pmax;
+        const size_t efb = (size_t)t * a.th * a.tw, infb = (size_t)t * (a.pmax + 8);
         uint8_t *ec = (TMA && (it & 1)) ? cbuf1 : cbuf0;
         if (tid == 0) {
             s_nsrc = 0;
             s_nent = 0;
             s_maxw = 0;
+            s_qhead = 0;
+            s_nef = 0;
+            s_ninf = 0;
         }
 
         // [phase] load
@@ -366,11 +396,12 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
         for (int r0 = warp * rows_per_it; r0 < h; r0 += nw * rows_per_it) {
             for (int g0 = 0; g0 < groups; g0 += (1 << lpr_log)) {  // warp-uniform trip counts
                 const int r = r0 + sub, gq = g0 + gl;
-                int mysrc = 0;
-                uint16_t srcs[4];
+                uint32_t srcbits = 0;
+                int wbase = 0;
                 if (r < h && gq < groups) {
                     const int c = 4 * gq;
                     const int base = (r + 1) * S + c + X0;
+                    wbase = r * WS + c;
                     uint32_t L[3], Cw[3], Rw[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
@@ -403,7 +434,8 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
                     const int nvalid = min(4, w - c);
                     const uint32_t colmask = nvalid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nvalid)) - 1u);
                     const uint32_t valid = __vcmpne4(me, 0u) & colmask;
-                    const uint32_t src = valid & __vcmpeq4(x, 0u);
+                    const uint32_t sm = valid & __vcmpeq4(x, 0u) & 0x01010101u;
+                    srcbits = (sm | (sm >> 7) | (sm >> 14) | (sm >> 21)) & 15u;
                     uint32_t wv4[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -411,10 +443,10 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
                         const bool vj = (valid >> (8 * j)) & 1u;
                         if constexpr (VALM == 0) wv4[j] = vj ? ((sj << 28) | (pj << 24) | 1u) : 0u;
                         else wv4[j] = vj ? ((sj << 4) | pj) : 0u;
-                        if ((src >> (8 * j)) & 1u) srcs[mysrc++] = (uint16_t)(base + j);
                     }
-                    *reinterpret_cast<uint4 *>(word + base) =
+                    *reinterpret_cast<uint4 *>(word + wbase) =
                         make_uint4(wv4[0], wv4[1], wv4[2], wv4[3]);
+                    *reinterpret_cast<uint2 *>(tag + wbase) = make_uint2(0u, 0u);
                     if constexpr (VALM == 1) {
                         for (int j = 0; j < nvalid; ++j) {
                             if (!((valid >> (8 * j)) & 1u)) continue;
@@ -422,11 +454,12 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
                             const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
                             if (b >= 0x7f800000u) nonfinite = 1;
                             maxw = max(maxw, b);
-                            fsum[base + j] = (long long)__float_as_uint(wf);  // raw bits until scaled
+                            fsum[wbase + j] = (long long)__float_as_uint(wf);  // raw bits until scaled
                         }
                     }
                 }
                 // append the lanes' sources to the block queue (warp-aggregated)
+                const int mysrc = __popc(srcbits);
                 int incl = mysrc;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -437,13 +470,17 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
                 int qbase = 0;
                 if (lane == 31 && tot) qbase = atomicAdd(&s_nsrc, tot);
                 qbase = __shfl_sync(0xffffffffu, qbase, 31);
-                for (int j = 0; j < mysrc; ++j) srcq[qbase + incl - mysrc + j] = srcs[j];
+                int qp = qbase + incl - mysrc;
+                while (srcbits) {
+                    srcq[qp++] = (uint16_t)(wbase + __ffs(srcbits) - 1);
+                    srcbits &= srcbits - 1;
+                }
             }
         }
 
         // ---- exit cells (flow leaves the tile into a valid cell) get ranks in
-        // slot order; entry cells (flow arrives from a valid cell outside) are
-        // listed for Algorithm 2 ------------------------------------------------
+        // slot order; entry cells (a valid cell outside drains into them) are
+        // listed with the exits outside that feed them -----------------------
         const int chunk = (P + nt - 1) / nt;
         const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
         int mine = 0;
@@ -463,14 +500,6 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
             const int k = ec[i];
             const bool ex = k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO);
             rank[s] = ex ? (uint16_t)rk : LINK_TERM;
-            bool entry = false;
-            if (ec[i]) {
-#pragma unroll
-                for (int kk = 1; kk <= 8; ++kk) {
-                    const uint8_t en = ec[i + off_of(kk, S)];
-                    entry |= (en & HALO) && (en & 15) == dir_rev(kk);
-                }
-            }
             if (ex) {
                 // where the exit's flow goes: a perimeter slot of a neighbouring tile
                 const int rr = r + dir_dr(k), cc = c + dir_dc(k);  // tile-local, one step outside
@@ -484,11 +513,34 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
                     (uint32_t)(((size_t)ras.tile_base + (size_t)tyd * ras.tiles_x + txd) * a.pmax + sd);
                 a.link[tbase + s] = (uint16_t)rk;  // an exit links to itself
                 ++rk;
-            } else if (entry) {
-                entq[atomicAdd(&s_nent, 1)] = (uint16_t)s;
-            } else {
-                a.link[tbase + s] = LINK_TERM;
             }
+            if (!k) {  // NoData
+                a.link[tbase + s] = LINK_TERM;
+                continue;
+            }
+            // inflow links: every valid halo neighbour draining into this cell
+            int e = -1;
+#pragma unroll
+            for (int kk = 1; kk <= 8; ++kk) {
+                const uint8_t en = ec[i + off_of(kk, S)];
+                if (!((en & HALO) && (en & 15) == dir_rev(kk))) continue;
+                if (e < 0) {
+                    e = atomicAdd(&s_nent, 1);
+                    entq[e] = (uint16_t)s;
+                }
+                const int rr = r + dir_dr(kk), cc = c + dir_dc(kk);  // the feeding cell, outside
+                const int tyh = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
+                const int txh = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
+                const int64_t R0h = (int64_t)tyh * a.th, C0h = (int64_t)txh * a.tw;
+                const int hh = (int)min((int64_t)a.th, ras.rows - R0h);
+                const int wh = (int)min((int64_t)a.tw, ras.cols - C0h);
+                const int sh = slot_of((int)(R0 + rr - R0h), (int)(C0 + cc - C0h), hh, wh);
+                const int j = atomicAdd(&s_ninf, 1);
+                a.inf_src[infb + j] =
+                    (uint32_t)(((size_t)ras.tile_base + (size_t)tyh * ras.tiles_x + txh) * a.pmax + sh);
+                a.inf_seg[infb + j] = (uint16_t)e;
+            }
+            if (!ex && e < 0) a.link[tbase + s] = LINK_TERM;
         }
         int qt = 0;
         if constexpr (VALM == 1) {
@@ -501,45 +553,54 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
             for (int r = warp; r < h; r += nw)
                 for (int c = lane; c < w; c += 32) {
                     const int i = (r + 1) * S + c + X0;
-                    if (ec[i]) fsum[i] = f2fix64(__uint_as_float((uint32_t)fsum[i]), qt);
+                    if (ec[i]) fsum[r * WS + c] = f2fix64(__uint_as_float((uint32_t)fsum[r * WS + c]), qt);
                 }
         }
         __syncthreads();
 
         // [phase] walk
-        // ---- the Kahn loop without a ready queue: every lane walks its static
-        // slice of the source queue, pushing final values downstream; the lane
-        // whose delivery completes a cell (its last pending upstream
-        // neighbour) carries on from it.  Integer sums make the order
-        // irrelevant, and the lanes need no coordination.  Meanwhile the last
-        // two warps run Algorithm 2 for the entry cells (it reads only codes).
-        const int lwn = nw >= 4 ? 2 : 0;  // warps walking entry links alongside
+        // ---- the Kahn loop without a ready queue: a lane takes the next
+        // source from the shared queue, pushes its final value downstream,
+        // and carries on from the cell its delivery completes (the last
+        // pending upstream neighbour); otherwise it takes another source.
+        // Integer sums make the order irrelevant.  Meanwhile the last two
+        // warps walk the entry paths (Algorithm 2), which reads only codes.
+        const int lwn = nw >= 4 ? 2 : 0;  // warps walking entry paths alongside
         const int mww = nw - lwn;         // warps running the solve
         if (warp < mww) {
             const int nsrc = s_nsrc;
-            const int stride = mww * 32;
-            int qi = tid, cur = -1;
+            int cur = -1;
             uint32_t st = 0;
             PV v = 0;
-            for (int guard = 0; guard < 2 * n_in + 2; ++guard) {
-                if (cur < 0) {
-                    if (qi >= nsrc) break;
-                    cur = srcq[qi];
-                    qi += stride;
-                    const uint32_t wd = word[cur];
-                    if constexpr (VALM == 0) {
-                        st = wd >> 28;
-                        v = wd & 0xFFFFFFu;
-                    } else {
-                        st = wd >> 4;
-                        v = fsum[cur];
+            for (int guard = 0; guard < 2 * n_in + 64; ++guard) {
+                const unsigned need = __ballot_sync(0xffffffffu, cur < 0);
+                if (need) {
+                    const int leader = __ffs(need) - 1;
+                    int qb = 0;
+                    if (lane == leader) qb = atomicAdd(&s_qhead, __popc(need));
+                    qb = __shfl_sync(0xffffffffu, qb, leader);
+                    if (cur < 0) {
+                        const int qi = qb + __popc(need & ((1u << lane) - 1u));
+                        if (qi < nsrc) {
+                            cur = srcq[qi];
+                            const uint32_t wd = word[cur];
+                            if constexpr (VALM == 0) {
+                                st = wd >> 28;
+                                v = wd & 0xFFFFFFu;
+                            } else {
+                                st = wd >> 4;
+                                v = fsum[cur];
+                            }
+                        }
                     }
                 }
-                if (st == 0) {
+                if (!__any_sync(0xffffffffu, cur >= 0)) break;  // queue drained, no walk left
+                if (cur < 0) continue;
+                if (st == 0) {  // no successor in the tile
                     cur = -1;
                     continue;
                 }
-                const int tgt = cur + off_of((int)st, S);
+                const int tgt = cur + dir_dr((int)st) * WS + dir_dc((int)st);
                 if constexpr (VALM == 0) {
                     const uint32_t old = atomicAdd(&word[tgt], v - (1u << 24));
                     if (((old >> 24) & 15u) == 1u) {
@@ -566,44 +627,58 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
             }
         }
         if (warp >= mww || lwn == 0) {
-            if (lwn == 0) __syncthreads();  // one- to three-warp blocks: links after the solve
-            // Algorithm 2 for the entry cells: follow the in-tile path to the exit
+            if (lwn == 0) __syncthreads();  // one- to three-warp blocks: entry paths after the solve
+            // Algorithm 2 for the entry cells, one segment per entry: claim
+            // cells along the path until it leaves the tile, ends, or reaches
+            // a cell another segment claimed
             const int nent = s_nent;
-            const int lt = lwn ? tid - mww * 32 : tid, stride = lwn ? lwn * 32 : nt;
-            for (int q = lt; q < nent; q += stride) {
-                const int s = entq[q];
+            const int lt2 = lwn ? tid - mww * 32 : tid, stride = lwn ? lwn * 32 : nt;
+            for (int q = lt2; q < nent; q += stride) {
                 int r, c;
-                cell_of(s, h, w, r, c);
-                int c2 = (r + 1) * S + c + X0;
-                uint16_t lk = LINK_TERM;
-                for (int steps = 0; steps <= n_in; ++steps) {
-                    const int k = ec[c2];
-                    if (k < 1 || k > 8) break;
-                    const int nxt = c2 + off_of(k, S);
-                    const uint8_t et = ec[nxt];
-                    if (!et) break;
-                    if (et & HALO) {
-                        const int cr = c2 / S - 1, cc = c2 - (c2 / S) * S - X0;
-                        lk = rank[slot_of(cr, cc, h, w)];
+                cell_of(entq[q], h, w, r, c);
+                int pi = (r + 1) * S + c + X0, ci = r * WS + c;
+                uint16_t end = LINK_TERM;
+                uint32_t join = NO_JOIN;
+                for (int pos = 0; pos < n_in; ++pos) {
+                    const uint16_t old = atomicCAS(&tag[ci], (uint16_t)0, (uint16_t)(q + 1));
+                    if (old != 0) {  // joins segment old - 1 at cell ci
+                        join = ((uint32_t)(old - 1) << 16) | (uint32_t)ci;
                         break;
                     }
-                    c2 = nxt;
+                    const int idx = atomicAdd(&s_nef, 1);
+                    a.ef_cp[efb + idx] = ((uint32_t)ci << 16) | (uint32_t)pos;
+                    a.ef_seg[efb + idx] = (uint16_t)q;
+                    const int k = ec[pi];
+                    if (k < 1 || k > 8) break;  // NoFlow: the path ends here
+                    const int np = pi + off_of(k, S);
+                    const uint8_t et = ec[np];
+                    if (!et) break;  // into NoData or off the raster
+                    if (et & HALO) {  // leaves the tile: this cell is an exit
+                        end = rank[slot_of(r, c, h, w)];
+                        break;
+                    }
+                    pi = np;
+                    ci += dir_dr(k) * WS + dir_dc(k);
+                    r += dir_dr(k);
+                    c += dir_dc(k);
                 }
-                a.link[tbase + s] = lk;
+                segend[q] = end;
+                segjoin[q] = join;
             }
         }
         __syncthreads();
 
         // [phase] output
         // ---- write A_loc (0 for NoData and for cells on cycles: those never
-        // lose their last pending dependency); exit records ------------------
+        // lose their last pending dependency); exit records; links of the
+        // entry cells; the entry forest's segment joins ----------------------
         const double inv = ldexp(1.0, -qt);
         for (int r = warp; r < h; r += nw) {
             const size_t orow = (size_t)(R0 + r) * ras.po + C0;
             const int base = (r + 1) * S + X0;
             for (int c = lane; c < w; c += 32) {
-                const int i = base + c;
-                const uint32_t wd = word[i];
+                const int i = base + c, ci = r * WS + c;
+                const uint32_t wd = word[ci];
                 bool fin = ec[i] != 0;
                 if constexpr (VALM == 0) {
                     if (fin && ((wd >> 24) & 15u)) fin = false;
@@ -618,7 +693,7 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
                     reinterpret_cast<uint32_t *>(ras.out)[orow + c] = fin ? (wd & 0xFFFFFFu) : 0u;
                 } else {
                     reinterpret_cast<float *>(ras.out)[orow + c] =
-                        fin ? (float)((double)fsum[i] * inv) : 0.0f;
+                        fin ? (float)((double)fsum[ci] * inv) : 0.0f;
                 }
             }
         }
@@ -627,13 +702,25 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
             if (rks == LINK_TERM) continue;
             int r, c;
             cell_of(s, h, w, r, c);
-            const int i = (r + 1) * S + c + X0;
             double vv;
-            if constexpr (VALM == 0) vv = (double)(word[i] & 0xFFFFFFu);
-            else vv = (double)fsum[i] * inv;
+            if constexpr (VALM == 0) vv = (double)(word[r * WS + c] & 0xFFFFFFu);
+            else vv = (double)fsum[r * WS + c] * inv;
             a.node_val[tbase + rks] = vv;  // A_loc at the exit (the perimeter data's A)
         }
-        if (tid == 0) a.nexit[t] = (uint32_t)total;
+        const int nent = s_nent;
+        for (int e = tid; e < nent; e += nt) {
+            a.seg_merge[tbase + e] = segjoin[e];
+            const int s = entq[e];
+            if (rank[s] != LINK_TERM) continue;  // an exit links to itself
+            int x = e;
+            for (int hop = 0; hop < nent && segjoin[x] != NO_JOIN; ++hop) x = (int)(segjoin[x] >> 16);
+            a.link[tbase + s] = segjoin[x] == NO_JOIN ? segend[x] : LINK_TERM;
+        }
+        if (tid == 0) {
+            a.nexit[t] = (uint32_t)total;
+            reinterpret_cast<uint4 *>(a.ef_hdr)[t] =
+                make_uint4((uint32_t)s_nef, (uint32_t)nent, (uint32_t)s_ninf, 0u);
+        }
         if constexpr (TMA) fence_proxy_async();  // this buffer is refilled by TMA later
         __syncthreads();
         // [phase] end
@@ -681,144 +768,213 @@ __global__ void __launch_bounds__(256, 4) k_solve(TileArgs A, const __grid_const
 }
 
 // ---------------------------------------------------------------------------
-// pass 2: add the flow entering each perimeter cell to its downstream path
+// pass 2: add the flow entering each tile to the cells downstream of its entry
+// cells.  in(e), the flow arriving at entry e from outside, follows e's path:
+// every cell of segment e gets in(e), and from the cell where segment q joins
+// segment e onwards every cell also gets F(q), the flow at the end of q
+// (in(q) plus the F of every segment joining q).  So the offset of the cell at
+// position j of segment e is in(e) + sum of F(q) over the segments q joining e
+// at positions <= j.  Codes are not needed: pass 1 recorded the segments.
 // ---------------------------------------------------------------------------
 template <int VALM>
-__global__ void __launch_bounds__(256, 4) k_offsets(TileArgs A) {
+__global__ void __launch_bounds__(128) k_offsets(TileArgs A) {
+    typedef typename std::conditional<VALM == 0, unsigned long long, long long>::type OV;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int s_emax, s_nent;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int64_t t = blockIdx.x;
+    __shared__ int s_emax;
     const TileArgs &a = A;
+    const int64_t t = blockIdx.x;
+    const uint4 hd = reinterpret_cast<const uint4 *>(a.ef_hdr)[t];
+    const int nef = (int)hd.x, nseg = (int)hd.y, ninf = (int)hd.z;
+    if (nseg == 0 || nef == 0) return;  // no flow enters this tile
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const RasterDesc ras = raster_of(a, t);
     const int lt = (int)(t - ras.tile_base);
     const int ty = lt / ras.tiles_x, tx = lt - ty * ras.tiles_x;
     const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
     const int h = (int)min((int64_t)a.th, ras.rows - R0);
     const int w = (int)min((int64_t)a.tw, ras.cols - C0);
-    const int S = tile_stride(a.tw);
-    const int n_in = h * w;
+    const int WS = cell_stride(a.tw);
     const int P = perim_count(h, w);
+    const int pm = a.pmax;
+    const size_t tb = (size_t)t * pm, eb = (size_t)t * a.th * a.tw, ib = (size_t)t * (pm + 8);
 
-    unsigned long long *off = reinterpret_cast<unsigned long long *>(smem);  // r * w + c
-    // inflow per listed entry; the offset array is padded to keep it 16-byte aligned
-    u128 *einf = reinterpret_cast<u128 *>(off + (((size_t)a.th * a.tw + 1) & ~size_t(1)));
-    uint16_t *eslot = reinterpret_cast<uint16_t *>(einf + a.pmax);
-    uint8_t *ec = reinterpret_cast<uint8_t *>(eslot + a.pmax);
+    // one segment per entry cell: nseg <= perimeter cells of the nominal tile
+    const int pc = perim_count(a.th, a.tw);
+    u128 *inS = reinterpret_cast<u128 *>(smem);  // [pc] in(e), perimeter-graph scale
+    OV *pre = reinterpret_cast<OV *>(inS);       //   later: prefix sums of F over grouped joins
+    OV *inT = reinterpret_cast<OV *>(inS + pc);  // [pc] in(e), this tile's scale
+    OV *F = inT + pc;                            // [pc] flow at the end of segment e
+    int *par = reinterpret_cast<int *>(F + pc);  // [pc] segment e joins, or -1
+    int *pend = par + pc;                        // [pc] joins into e not yet summed
+    int *mfill = pend;                           //   later: fill counts of the groups
+    int *moff = pend + pc;                       // [pc + 1] start of e's joins in mlist
+    uint16_t *mpos = reinterpret_cast<uint16_t *>(moff + pc + 1);  // [pc] position e joins at
+    uint16_t *mlist = mpos + pc;                 // [pc] joining segments grouped by target
+    uint16_t *posmap = mlist + pc;               // [th * WS] position of every forest cell
 
-    if (tid == 0) {
-        s_emax = INT_MIN;
-        s_nent = 0;
+    if (tid == 0) s_emax = INT_MIN;
+    for (int e = tid; e < nseg; e += nt) {
+        inS[e] = 0;
+        pend[e] = 0;
+        moff[e] = 0;
     }
-    int nbad = 0;
-    long long fbad = NO_INDEX;
-    load_codes(ras, ec, R0, C0, h, w, S, false, nbad, fbad);
-    for (int i = tid; i < n_in; i += nt) off[i] = 0ull;
+    for (int j = tid; j < nef; j += nt) {
+        const uint32_t cp = a.ef_cp[eb + j];
+        posmap[cp >> 16] = (uint16_t)(cp & 0xFFFFu);
+    }
     __syncthreads();
 
-    // ---- in(p) = sum of G over the exits of neighbouring tiles draining into p
-    const int qf = VALM ? fix_scale(a.fcells, *a.maxw) : 0;
-    int emax = INT_MIN;
-    for (int s = tid; s < P; s += nt) {
-        int r, c;
-        cell_of(s, h, w, r, c);
-        const int i = (r + 1) * S + c + X0;
-        if (!ec[i]) continue;
-        size_t gidx[8];
-        int ng = 0;
-#pragma unroll
-        for (int k = 1; k <= 8; ++k) {
-            const uint8_t en = ec[i + off_of(k, S)];
-            if ((en & HALO) && (en & 15) == dir_rev(k)) {
-                const int rr = r + dir_dr(k), cc = c + dir_dc(k);  // one step outside the tile
-                const int tyh = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
-                const int txh = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
-                const int64_t R0h = (int64_t)tyh * a.th, C0h = (int64_t)txh * a.tw;
-                const int hh = (int)min((int64_t)a.th, ras.rows - R0h);
-                const int wh = (int)min((int64_t)a.tw, ras.cols - C0h);
-                const int sh = slot_of((int)(R0 + rr - R0h), (int)(C0 + cc - C0h), hh, wh);
-                gidx[ng++] = ((size_t)ras.tile_base + (size_t)tyh * ras.tiles_x + txh) * a.pmax + sh;
-            }
+    // ---- in(e) = sum of G over the exits outside draining into entry e
+    for (int j = tid; j < ninf; j += nt) {
+        const uint32_t src = a.inf_src[ib + j];
+        const uint16_t lk = a.link[src];
+        if (lk == LINK_TERM) continue;  // never: a cell draining into this tile is an exit
+        atomic_add_u128(&inS[a.inf_seg[ib + j]], a.G[src - src % (uint32_t)pm + lk]);
+    }
+    // ---- the join tree of the segments
+    for (int e = tid; e < nseg; e += nt) {
+        const uint32_t m = a.seg_merge[tb + e];
+        if (m == NO_JOIN) {
+            par[e] = -1;
+            continue;
         }
-        if (!ng) continue;
-        uint16_t lk[8];
-        for (int j = 0; j < ng; ++j) lk[j] = a.link[gidx[j]];  // independent loads first
-        u128 inflow = 0;
-        for (int j = 0; j < ng; ++j)
-            if (lk[j] != LINK_TERM)  // always an exit rank: the neighbour drains out of its tile
-                inflow += a.G[gidx[j] - (gidx[j] % a.pmax) + lk[j]];
-        if (inflow == 0) continue;
-        const int e = atomicAdd(&s_nent, 1);
-        eslot[e] = (uint16_t)s;
-        einf[e] = inflow;
-        if constexpr (VALM == 1) {
+        const int p = (int)(m >> 16);
+        par[e] = p;
+        mpos[e] = posmap[m & 0xFFFFu];
+        atomicAdd(&pend[p], 1);
+        atomicAdd(&moff[p], 1);
+    }
+    __syncthreads();
+    const int qf = VALM ? fix_scale(a.fcells, *a.maxw) : 0;
+    if constexpr (VALM == 1) {
+        int emax = INT_MIN;
+        for (int e = tid; e < nseg; e += nt) {
+            if (inS[e] == 0) continue;
             int ex;
-            frexp(fabs(fix2d(inflow, qf)), &ex);
+            frexp(fabs(fix2d(inS[e], qf)), &ex);
             emax = max(emax, ex);
         }
-    }
-    if constexpr (VALM == 1) {
         if (emax != INT_MIN) atomicMax(&s_emax, emax);
+        __syncthreads();
+        if (s_emax == INT_MIN) return;  // no inflow at all
     }
-    __syncthreads();
-    const int nent = s_nent;
-    if (nent == 0) return;
-    // offsets of this tile stay below P * max|in(p)| < 2^(emax + log2 P)
+    // offsets of this tile stay below P * max|in(e)| < 2^(emax + log2 P)
     int qo = 0;
     if constexpr (VALM == 1) {
         int lp = 0;
         while ((1 << lp) < P) ++lp;
         qo = 62 - (s_emax + lp + 1);
     }
-
-    // ---- walk each entry's downstream path inside the tile, adding in(p);
-    // every lane takes its own entries, with no coordination ----------------
-    for (int q = tid; q < nent; q += nt) {
-        const u128 inflow = einf[q];
-        unsigned long long v;
+    for (int e = tid; e < nseg; e += nt) {
+        OV v;
         if constexpr (VALM == 0) {
-            v = (unsigned long long)inflow;
+            v = (OV)inS[e];
         } else {
             const int sh = qf - qo;  // from the graph scale to this tile's scale
-            const i128 si = (i128)inflow;
-            v = (unsigned long long)(long long)(sh >= 0 ? (sh < 127 ? (si >> sh) : (si < 0 ? -1 : 0))
-                                                        : (si << (-sh)));
+            const i128 si = (i128)inS[e];
+            v = (OV)(sh >= 0 ? (sh < 127 ? (si >> sh) : (si < 0 ? -1 : 0)) : (si << (-sh)));
         }
-        int r, c;
-        cell_of(eslot[q], h, w, r, c);
-        int cur = (r + 1) * S + c + X0;
-        for (int steps = 0; steps < n_in; ++steps) {
-            atomicAdd(&off[r * w + c], v);
-            const int k = ec[cur];
-            if (k < 1 || k > 8) break;
-            const int tg = cur + off_of(k, S);
-            const uint8_t et = ec[tg];
-            if (!et || (et & HALO)) break;
-            cur = tg;
-            r += dir_dr(k);
-            c += dir_dc(k);
+        inT[e] = v;
+        F[e] = v;
+    }
+    __syncthreads();
+
+    // ---- F over the join tree, leaves first (one warp; the rounds end when
+    // no segment became ready, at the latest after nseg rounds)
+    if (warp == 0) {
+        for (int round = 0; round <= nseg; ++round) {
+            bool any = false;
+            for (int e = lane; e < nseg; e += 32)
+                if (pend[e] == 0) {
+                    pend[e] = -2;  // ready: every join into e is summed
+                    any = true;
+                }
+            if (!__any_sync(0xffffffffu, any)) break;
+            __syncwarp();
+            for (int e = lane; e < nseg; e += 32) {
+                if (pend[e] != -2) continue;
+                pend[e] = -1;
+                const int p = par[e];
+                if (p >= 0) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&F[p]),
+                              (unsigned long long)F[e]);
+                    atomicSub(&pend[p], 1);
+                }
+            }
+            __syncwarp();
+        }
+        // group the joins by target: exclusive scan of the counts
+        int run = 0;
+        for (int b0 = 0; b0 < nseg; b0 += 32) {
+            const int e = b0 + lane;
+            const int cnt = e < nseg ? moff[e] : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (e < nseg) moff[e] = run + incl - cnt;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) moff[nseg] = run;
+    }
+    __syncthreads();
+    for (int e = tid; e < nseg; e += nt) mfill[e] = 0;
+    __syncthreads();
+    for (int e = tid; e < nseg; e += nt) {
+        const int p = par[e];
+        if (p >= 0) mlist[moff[p] + atomicAdd(&mfill[p], 1)] = (uint16_t)e;
+    }
+    __syncthreads();
+    // each target: its joins by position, then running sums of their F
+    for (int p = tid; p < nseg; p += nt) {
+        const int b = moff[p], n = moff[p + 1] - b;
+        for (int i = 1; i < n; ++i) {  // insertion sort (join lists are short)
+            const uint16_t x = mlist[b + i];
+            int j = i - 1;
+            while (j >= 0 && mpos[mlist[b + j]] > mpos[x]) {
+                mlist[b + j + 1] = mlist[b + j];
+                --j;
+            }
+            mlist[b + j + 1] = x;
+        }
+        OV run = 0;
+        for (int i = 0; i < n; ++i) {
+            run += F[mlist[b + i]];
+            pre[b + i] = run;
         }
     }
     __syncthreads();
 
-    // ---- read-modify-write the output where an offset arrived -------------
+    // ---- every forest cell: read-modify-write its output
     int ovf = 0;
     const double inv = ldexp(1.0, -qo);
-    for (int r = warp; r < h; r += nw) {
-        const size_t orow = (size_t)(R0 + r) * ras.po + C0;
-        for (int c = lane; c < w; c += 32) {
-            const unsigned long long o = off[r * w + c];
-            if (!o) continue;
-            if constexpr (VALM == 0) {
-                uint32_t *p = reinterpret_cast<uint32_t *>(ras.out) + orow + c;
-                const unsigned long long s64 = (unsigned long long)*p + o;
-                if (s64 >> 32) ovf = 1;
-                *p = (uint32_t)s64;
-            } else {
-                float *p = reinterpret_cast<float *>(ras.out) + orow + c;
-                *p = (float)((double)*p + (double)(long long)o * inv);
-            }
+    for (int j = tid; j < nef; j += nt) {
+        const uint32_t cp = a.ef_cp[eb + j];
+        const int e = a.ef_seg[eb + j];
+        const int ci = (int)(cp >> 16), pos = (int)(cp & 0xFFFFu);
+        OV o = inT[e];
+        int lo = moff[e], hi = moff[e + 1];  // joins into e at positions <= pos
+        const int b = lo;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((int)mpos[mlist[mid]] <= pos) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo > b) o += pre[lo - 1];
+        if (!o) continue;
+        const int r = ci / WS, c = ci - r * WS;
+        const size_t oi = (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
+        if constexpr (VALM == 0) {
+            uint32_t *p = reinterpret_cast<uint32_t *>(ras.out) + oi;
+            const unsigned long long s64 = (unsigned long long)*p + o;
+            if (s64 >> 32) ovf = 1;
+            *p = (uint32_t)s64;
+        } else {
+            float *p = reinterpret_cast<float *>(ras.out) + oi;
+            *p = (float)((double)*p + (double)o * inv);
         }
     }
     ovf = __syncthreads_or(ovf);
@@ -979,6 +1135,13 @@ size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry
     w.dl1 = c.take<u128>(S);
     w.J0 = c.take<uint32_t>(S);
     w.J1 = c.take<uint32_t>(S);
+    const size_t cells = T * (size_t)g.th * g.tw, inf = T * (size_t)(g.pmax + 8);
+    w.ef_hdr = c.take<uint32_t>(T * 4);
+    w.ef_cp = c.take<uint32_t>(cells);
+    w.ef_seg = c.take<uint16_t>(cells);
+    w.seg_merge = c.take<uint32_t>(S);
+    w.inf_src = c.take<uint32_t>(inf);
+    w.inf_seg = c.take<uint16_t>(inf);
     (void)dry;
     return c.used() + 256;
 }
@@ -1104,7 +1267,7 @@ template <int VALM>
 static cudaError_t launch_offsets(const Geom &g, const TileArgs &ta, cudaStream_t s) {
     cudaError_t e = offsets_config<VALM>(g);
     if (e != cudaSuccess) return e;
-    k_offsets<VALM><<<(unsigned)ta.T, tile_threads(g), offsets_smem_bytes(g.th, g.tw), s>>>(ta);
+    k_offsets<VALM><<<(unsigned)ta.T, 128, offsets_smem_bytes(g.th, g.tw), s>>>(ta);
     return cudaGetLastError();
 }
 
@@ -1140,6 +1303,12 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     ta.G = reinterpret_cast<const u128 *>(ws.x);
     ta.st = st;
     ta.maxw = ws.misc;
+    ta.ef_hdr = ws.ef_hdr;
+    ta.ef_cp = ws.ef_cp;
+    ta.ef_seg = ws.ef_seg;
+    ta.seg_merge = ws.seg_merge;
+    ta.inf_src = ws.inf_src;
+    ta.inf_seg = ws.inf_seg;
 
     timing_mark(0, s);
     const bool tma = !(g.flags & FA_OPT_NO_TMA) && ta.rtab == nullptr;
