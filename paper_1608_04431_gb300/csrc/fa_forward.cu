@@ -114,6 +114,7 @@ __host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm, boo
     b += pm * 4;                              // segment -> where it joins another
     b += nc * 2;                              // source queue (u16 cell indices)
     b += pm * 2 * 3;                          // exit rank per slot, entry list, segment ends
+    b += pm * 2 + (pm + 8) * 2;               // entry number per slot, inflow link -> slot
     return (b + 15) & ~size_t(15);
 }
 
@@ -213,11 +214,19 @@ __device__ __forceinline__ void load_codes(const RasterDesc &ras, uint8_t *ec, i
     }
 }
 
+// Bytes j = 0..3 of a word whose byte 0 is tile column c0 that lie in columns
+// lo..hi, as 0xFF bytes.
+__device__ __forceinline__ uint32_t col_mask(int c0, int lo, int hi) {
+    const int a = min(max(lo - c0, 0), 4), b = min(max(hi - c0 + 1, 0), 4);
+    return (uint32_t)(((1ull << (8 * b)) - 1ull) & ~((1ull << (8 * a)) - 1ull));
+}
+
 // In-place conversion of a TMA-staged box (raw codes; row hr = tile row
 // hr - 1; tile column c at byte X0 + c) into effective codes: interior cells
 // keep valid codes (invalid ones become NoData and are counted); the one-cell
 // ring around the tile keeps valid codes with HALO set; everything else in the
-// box (neighbouring tiles' cells beyond the ring) is zeroed.
+// box (neighbouring tiles' cells beyond the ring) is zeroed.  Four bytes per
+// lane, without branches except for the rare invalid code.
 __device__ __forceinline__ void transform_box(uint8_t *ec, int h, int w, int S, int64_t R0,
                                               int64_t C0, int64_t cols, int &nbad,
                                               long long &fbad) {
@@ -228,33 +237,18 @@ __device__ __forceinline__ void transform_box(uint8_t *ec, int h, int w, int S, 
         uint32_t *row = reinterpret_cast<uint32_t *>(ec + hr * S);
         for (int wd = lane; wd < words; wd += 32) {
             const int c0 = 4 * wd - X0;
-            const uint32_t raw = row[wd];
-            uint32_t v = 0;
-            if (irow && c0 >= 0 && c0 + 3 < w) {  // four interior cells
-                const uint32_t bad = __vcmpgtu4(raw, 0x09090909u);
-                if (bad) {
-                    nbad += __popc(bad) >> 3;
-                    const int j = (__ffs(bad) - 1) >> 3;
-                    fbad = min(fbad, (long long)((R0 + hr - 1) * cols + (C0 + c0 + j)));
-                }
-                v = raw & ~bad;
-            } else if (c0 + 3 >= -1 && c0 <= w) {  // touches the ring
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = c0 + j;
-                    if (c < -1 || c > w) continue;
-                    const uint32_t k = (raw >> (8 * j)) & 0xffu;
-                    const bool interior = irow && c >= 0 && c < w;
-                    if (k == 0 || k > 9) {
-                        if (interior && k > 9) {
-                            ++nbad;
-                            fbad = min(fbad, (long long)((R0 + hr - 1) * cols + (C0 + c)));
-                        }
-                        continue;
-                    }
-                    v |= (k | (interior ? 0u : (uint32_t)HALO)) << (8 * j);
-                }
+            const uint32_t keep = col_mask(c0, -1, w);
+            const uint32_t inter = irow ? col_mask(c0, 0, w - 1) : 0u;
+            uint32_t v = row[wd] & keep;
+            const uint32_t bad = __vcmpgtu4(v, 0x09090909u);
+            const uint32_t badin = bad & inter;
+            if (badin) {
+                nbad += __popc(badin) >> 3;
+                const int j = (__ffs(badin) - 1) >> 3;
+                fbad = min(fbad, (long long)((R0 + hr - 1) * cols + (C0 + c0 + j)));
             }
+            v &= ~bad;
+            v |= __vcmpne4(v, 0u) & (keep & ~inter) & 0x10101010u;
             row[wd] = v;
         }
     }
@@ -284,6 +278,7 @@ __device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
 // stops there and records the join.  Each walk's claimed run is a segment:
 // the cells of segment e at positions 0, 1, ... in path order.
 constexpr uint32_t NO_JOIN = 0xFFFFFFFFu;
+constexpr uint16_t NO_ENTRY = 0xFFFFu;
 
 // Resident blocks per SM: four 64 x 64 tiles fit shared memory for counts,
 // two with the 64-bit sums of weighted runs (which then get more registers).
@@ -321,6 +316,8 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
     uint16_t *rank = srcq + NC;
     uint16_t *entq = rank + a.pmax;
     uint16_t *segend = entq + a.pmax;
+    uint16_t *eidx = segend + a.pmax;     // slot -> entry number, NO_ENTRY if not an entry
+    uint16_t *lslot = eidx + a.pmax;      // inflow link -> the slot it feeds
 
     // status, accumulated over this block's tiles
     int nbad = 0, ncyc = 0, nonfinite = 0;
@@ -364,12 +361,15 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
             s_nef = 0;
             s_ninf = 0;
         }
+        for (int q = tid; q < a.pmax; q += nt) eidx[q] = NO_ENTRY;
 
         // [phase] load
         if constexpr (TMA) {
             const int64_t tn = t + gridDim.x;
-            if (tid == 0 && tn < T) issue((int)tn, (it & 1) ^ 1);
-            if (!mbar_wait(&s_bar[it & 1], (uint32_t)((it >> 1) & 1))) atomicOr(&s_flags, FA_FLAG_TIMEOUT);
+            if (tid == 0) {  // one thread waits for the stage; the barrier publishes it
+                if (tn < T) issue((int)tn, (it & 1) ^ 1);
+                if (!mbar_wait(&s_bar[it & 1], (uint32_t)((it >> 1) & 1))) s_flags |= FA_FLAG_TIMEOUT;
+            }
             __syncthreads();
             if (s_flags & FA_FLAG_TIMEOUT) {
                 to_it = (t + (int64_t)gridDim.x < T) ? -2 - it : it;  // -2-it: the next stage was issued too
@@ -478,9 +478,48 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
             }
         }
 
+        // ---- inflow links: every valid cell of the halo ring draining into the
+        // tile (an exit of its own tile) feeds a perimeter cell, which is then
+        // an entry cell.  Ring positions: the row above (w + 2 cells, west to
+        // east), the row below, then the columns west and east of the tile.
+        const int ring = 2 * (h + w) + 4;
+        for (int q = tid; q < ring; q += nt) {
+            int rr, cc;
+            if (q < w + 2) {
+                rr = -1;
+                cc = q - 1;
+            } else if (q < 2 * w + 4) {
+                rr = h;
+                cc = q - (w + 2) - 1;
+            } else if (q < 2 * w + 4 + h) {
+                rr = q - (2 * w + 4);
+                cc = -1;
+            } else {
+                rr = q - (2 * w + 4 + h);
+                cc = w;
+            }
+            const uint8_t en = ec[(rr + 1) * S + cc + X0];
+            const int k = en & 15;
+            if (!(en & HALO) || k < 1 || k > 8) continue;  // NoData, off the raster, NoFlow
+            const int tr = rr + dir_dr(k), tc = cc + dir_dc(k);
+            if (tr < 0 || tr >= h || tc < 0 || tc >= w) continue;  // drains elsewhere
+            if (!ec[(tr + 1) * S + tc + X0]) continue;             // into NoData
+            const int st = slot_of(tr, tc, h, w);
+            eidx[st] = 0;  // an entry cell
+            const int tyh = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
+            const int txh = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
+            const int64_t R0h = (int64_t)tyh * a.th, C0h = (int64_t)txh * a.tw;
+            const int hh = (int)min((int64_t)a.th, ras.rows - R0h);
+            const int wh = (int)min((int64_t)a.tw, ras.cols - C0h);
+            const int sh = slot_of((int)(R0 + rr - R0h), (int)(C0 + cc - C0h), hh, wh);
+            const int jl = atomicAdd(&s_ninf, 1);
+            a.inf_src[infb + jl] =
+                (uint32_t)(((size_t)ras.tile_base + (size_t)tyh * ras.tiles_x + txh) * a.pmax + sh);
+            lslot[jl] = (uint16_t)st;
+        }
+
         // ---- exit cells (flow leaves the tile into a valid cell) get ranks in
-        // slot order; entry cells (a valid cell outside drains into them) are
-        // listed with the exits outside that feed them -----------------------
+        // slot order; entry cells are numbered (one entry-forest segment each)
         const int chunk = (P + nt - 1) / nt;
         const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
         int mine = 0;
@@ -492,7 +531,7 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
             if (k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO)) ++mine;
         }
         int total;
-        int rk = block_exclusive_scan(mine, s_warp, &total);
+        int rk = block_exclusive_scan(mine, s_warp, &total);  // (its barriers publish eidx)
         for (int s = s0; s < s1; ++s) {
             int r, c;
             cell_of(s, h, w, r, c);
@@ -514,33 +553,13 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
                 a.link[tbase + s] = (uint16_t)rk;  // an exit links to itself
                 ++rk;
             }
-            if (!k) {  // NoData
+            if (eidx[s] != NO_ENTRY) {
+                const int e = atomicAdd(&s_nent, 1);
+                entq[e] = (uint16_t)s;
+                eidx[s] = (uint16_t)e;
+            } else if (!ex) {
                 a.link[tbase + s] = LINK_TERM;
-                continue;
             }
-            // inflow links: every valid halo neighbour draining into this cell
-            int e = -1;
-#pragma unroll
-            for (int kk = 1; kk <= 8; ++kk) {
-                const uint8_t en = ec[i + off_of(kk, S)];
-                if (!((en & HALO) && (en & 15) == dir_rev(kk))) continue;
-                if (e < 0) {
-                    e = atomicAdd(&s_nent, 1);
-                    entq[e] = (uint16_t)s;
-                }
-                const int rr = r + dir_dr(kk), cc = c + dir_dc(kk);  // the feeding cell, outside
-                const int tyh = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
-                const int txh = tx + (cc < 0 ? -1 : (cc >= w ? 1 : 0));
-                const int64_t R0h = (int64_t)tyh * a.th, C0h = (int64_t)txh * a.tw;
-                const int hh = (int)min((int64_t)a.th, ras.rows - R0h);
-                const int wh = (int)min((int64_t)a.tw, ras.cols - C0h);
-                const int sh = slot_of((int)(R0 + rr - R0h), (int)(C0 + cc - C0h), hh, wh);
-                const int j = atomicAdd(&s_ninf, 1);
-                a.inf_src[infb + j] =
-                    (uint32_t)(((size_t)ras.tile_base + (size_t)tyh * ras.tiles_x + txh) * a.pmax + sh);
-                a.inf_seg[infb + j] = (uint16_t)e;
-            }
-            if (!ex && e < 0) a.link[tbase + s] = LINK_TERM;
         }
         int qt = 0;
         if constexpr (VALM == 1) {
@@ -569,9 +588,10 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
         const int mww = nw - lwn;         // warps running the solve
         if (warp < mww) {
             const int nsrc = s_nsrc;
-            int cur = -1;
-            uint32_t st = 0;
-            PV v = 0;
+            const unsigned below = (1u << lane) - 1u;
+            int cur = -1;     // the cell this lane carries on from, -1 = idle
+            uint32_t wv = 0;  // its word, final: successor step | 0 pending | A_loc (counts)
+            long long fv = 0; // its final fixed-point sum (weights)
             for (int guard = 0; guard < 2 * n_in + 64; ++guard) {
                 const unsigned need = __ballot_sync(0xffffffffu, cur < 0);
                 if (need) {
@@ -579,46 +599,39 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
                     int qb = 0;
                     if (lane == leader) qb = atomicAdd(&s_qhead, __popc(need));
                     qb = __shfl_sync(0xffffffffu, qb, leader);
-                    if (cur < 0) {
-                        const int qi = qb + __popc(need & ((1u << lane) - 1u));
-                        if (qi < nsrc) {
-                            cur = srcq[qi];
-                            const uint32_t wd = word[cur];
-                            if constexpr (VALM == 0) {
-                                st = wd >> 28;
-                                v = wd & 0xFFFFFFu;
-                            } else {
-                                st = wd >> 4;
-                                v = fsum[cur];
-                            }
-                        }
+                    const int qi = qb + __popc(need & below);
+                    if (cur < 0 && qi < nsrc) {
+                        cur = srcq[qi];
+                        wv = word[cur];
+                        if constexpr (VALM == 1) fv = fsum[cur];
                     }
+                    if (!__any_sync(0xffffffffu, cur >= 0)) break;  // queue drained, no walk left
                 }
-                if (!__any_sync(0xffffffffu, cur >= 0)) break;  // queue drained, no walk left
                 if (cur < 0) continue;
+                const int st = VALM == 0 ? (int)(wv >> 28) : (int)((wv >> 4) & 15u);
                 if (st == 0) {  // no successor in the tile
                     cur = -1;
                     continue;
                 }
-                const int tgt = cur + dir_dr((int)st) * WS + dir_dc((int)st);
+                const int tgt = cur + dir_dr(st) * WS + dir_dc(st);
                 if constexpr (VALM == 0) {
-                    const uint32_t old = atomicAdd(&word[tgt], v - (1u << 24));
-                    if (((old >> 24) & 15u) == 1u) {
-                        v += old & 0xFFFFFFu;
-                        st = old >> 28;
+                    const uint32_t delta = (wv & 0xFFFFFFu) - (1u << 24);
+                    const uint32_t old = atomicAdd(&word[tgt], delta);
+                    if (((old >> 24) & 15u) == 1u) {  // the last pending inflow: tgt is final
+                        wv = old + delta;
                         cur = tgt;
                     } else {
                         cur = -1;
                     }
                 } else {
                     atomicAdd(reinterpret_cast<unsigned long long *>(&fsum[tgt]),
-                              (unsigned long long)v);
+                              (unsigned long long)fv);
                     __threadfence_block();
                     const uint32_t old = atomicSub(&word[tgt], 1u);
                     if ((old & 15u) == 1u) {
                         __threadfence_block();
-                        v = *reinterpret_cast<volatile long long *>(&fsum[tgt]);
-                        st = old >> 4;
+                        fv = *reinterpret_cast<volatile long long *>(&fsum[tgt]);
+                        wv = old - 1u;
                         cur = tgt;
                     } else {
                         cur = -1;
@@ -630,13 +643,16 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
             if (lwn == 0) __syncthreads();  // one- to three-warp blocks: entry paths after the solve
             // Algorithm 2 for the entry cells, one segment per entry: claim
             // cells along the path until it leaves the tile, ends, or reaches
-            // a cell another segment claimed
+            // a cell another segment claimed.  The in-tile successor is the
+            // step packed into the word (the solve never changes those bits).
             const int nent = s_nent;
+            uint32_t *efc = a.ef_cp + efb;
+            uint16_t *efs = a.ef_seg + efb;
             const int lt2 = lwn ? tid - mww * 32 : tid, stride = lwn ? lwn * 32 : nt;
             for (int q = lt2; q < nent; q += stride) {
                 int r, c;
                 cell_of(entq[q], h, w, r, c);
-                int pi = (r + 1) * S + c + X0, ci = r * WS + c;
+                int ci = r * WS + c;
                 uint16_t end = LINK_TERM;
                 uint32_t join = NO_JOIN;
                 for (int pos = 0; pos < n_in; ++pos) {
@@ -646,21 +662,19 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
                         break;
                     }
                     const int idx = atomicAdd(&s_nef, 1);
-                    a.ef_cp[efb + idx] = ((uint32_t)ci << 16) | (uint32_t)pos;
-                    a.ef_seg[efb + idx] = (uint16_t)q;
-                    const int k = ec[pi];
-                    if (k < 1 || k > 8) break;  // NoFlow: the path ends here
-                    const int np = pi + off_of(k, S);
-                    const uint8_t et = ec[np];
-                    if (!et) break;  // into NoData or off the raster
-                    if (et & HALO) {  // leaves the tile: this cell is an exit
-                        end = rank[slot_of(r, c, h, w)];
+                    efc[idx] = ((uint32_t)ci << 16) | (uint32_t)pos;
+                    efs[idx] = (uint16_t)q;
+                    const uint32_t wd = word[ci];
+                    const int k = VALM == 0 ? (int)(wd >> 28) : (int)((wd >> 4) & 15u);
+                    if (k == 0) {  // no successor in the tile: an exit, or the path ends
+                        const int rr = ci / WS, cc = ci - rr * WS;
+                        const int i = (rr + 1) * S + cc + X0;
+                        const int kc = ec[i];
+                        if (kc >= 1 && kc <= 8 && (ec[i + off_of(kc, S)] & HALO))
+                            end = rank[slot_of(rr, cc, h, w)];
                         break;
                     }
-                    pi = np;
                     ci += dir_dr(k) * WS + dir_dc(k);
-                    r += dir_dr(k);
-                    c += dir_dc(k);
                 }
                 segend[q] = end;
                 segjoin[q] = join;
@@ -673,27 +687,36 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
         // lose their last pending dependency); exit records; links of the
         // entry cells; the entry forest's segment joins ----------------------
         const double inv = ldexp(1.0, -qt);
-        for (int r = warp; r < h; r += nw) {
-            const size_t orow = (size_t)(R0 + r) * ras.po + C0;
-            const int base = (r + 1) * S + X0;
-            for (int c = lane; c < w; c += 32) {
-                const int i = base + c, ci = r * WS + c;
-                const uint32_t wd = word[ci];
-                bool fin = ec[i] != 0;
-                if constexpr (VALM == 0) {
-                    if (fin && ((wd >> 24) & 15u)) fin = false;
-                } else {
-                    if (fin && (wd & 15u)) fin = false;
+        // four cells per lane, as in the init loop; whole 16-byte stores when
+        // the output row allows them
+        const bool vec = ((reinterpret_cast<uintptr_t>(ras.out) |
+                           ((uintptr_t)ras.po << 2) | ((uintptr_t)C0 << 2)) & 15) == 0;
+        for (int r0 = warp * rows_per_it; r0 < h; r0 += nw * rows_per_it) {
+            for (int g0 = 0; g0 < groups; g0 += (1 << lpr_log)) {
+                const int r = r0 + sub, gq = g0 + gl;
+                if (r >= h || gq >= groups) continue;
+                const int c = 4 * gq, wb = r * WS + c;
+                const int nvalid = min(4, w - c);
+                const uint32_t codes4 = *reinterpret_cast<const uint32_t *>(ec + (r + 1) * S + c + X0);
+                const uint4 w4 = *reinterpret_cast<const uint4 *>(word + wb);
+                const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                uint32_t ov[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const bool valid = jj < nvalid && ((codes4 >> (8 * jj)) & 0xFFu) != 0;
+                    const bool fin = valid && (VALM == 0 ? ((wv[jj] >> 24) & 15u) == 0 : (wv[jj] & 15u) == 0);
+                    if (valid && !fin) {
+                        ++ncyc;
+                        fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c + jj)));
+                    }
+                    if constexpr (VALM == 0) ov[jj] = fin ? (wv[jj] & 0xFFFFFFu) : 0u;
+                    else ov[jj] = fin ? __float_as_uint((float)((double)fsum[wb + jj] * inv)) : 0u;
                 }
-                if (ec[i] && !fin) {
-                    ++ncyc;
-                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
-                }
-                if constexpr (VALM == 0) {
-                    reinterpret_cast<uint32_t *>(ras.out)[orow + c] = fin ? (wd & 0xFFFFFFu) : 0u;
+                uint32_t *orow = reinterpret_cast<uint32_t *>(ras.out) + (size_t)(R0 + r) * ras.po + C0 + c;
+                if (vec && nvalid == 4) {
+                    *reinterpret_cast<uint4 *>(orow) = make_uint4(ov[0], ov[1], ov[2], ov[3]);
                 } else {
-                    reinterpret_cast<float *>(ras.out)[orow + c] =
-                        fin ? (float)((double)fsum[ci] * inv) : 0.0f;
+                    for (int jj = 0; jj < nvalid; ++jj) orow[jj] = ov[jj];
                 }
             }
         }
@@ -708,6 +731,7 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
             a.node_val[tbase + rks] = vv;  // A_loc at the exit (the perimeter data's A)
         }
         const int nent = s_nent;
+        for (int j = tid; j < s_ninf; j += nt) a.inf_seg[infb + j] = eidx[lslot[j]];
         for (int e = tid; e < nent; e += nt) {
             a.seg_merge[tbase + e] = segjoin[e];
             const int s = entq[e];
