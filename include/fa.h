@@ -81,9 +81,14 @@ typedef enum { FA_OUT_U32 = 0, FA_OUT_F32 = 1 } fa_out_dtype;
 #define FA_FLAG_TIMEOUT 8
 #define FA_FLAG_NONFINITE 16
 
-/* Tile shape: 0 = library default (64 x 64).  1 <= tile_h, tile_w and
- * tile_h * tile_w <= 16384.  Results do not depend on the tile shape, except
- * for the rounding of floating-point sums.
+/* Tile shape: 0 = library default (64 x 64).  1 <= tile_h, tile_w,
+ * tile_h * tile_w <= 16384 and tile_h * (tile_w rounded up to a multiple of
+ * 4) <= 16384; the per-tile shared memory must also fit (all such shapes for
+ * counts; up to about 11000 cells with weights, e.g. 96 x 96 or 64 x 128).
+ * The tile's halo rows must also keep (tile_h + 2) * (tile_w + 32 rounded up
+ * to a multiple of 16) <= 65535.  Other shapes return
+ * FA_ERR_INVALID_ARG.  Results do not depend on the tile shape, except for
+ * the rounding of floating-point sums.
  * flags: FA_OPT_NO_TMA disables staging code tiles into shared memory with the
  * Tensor Memory Accelerator (used when the raster allows it: 16-byte aligned
  * codes and pitch, tile width a multiple of 16, no mask raster); results are

@@ -173,6 +173,24 @@ constexpr long long NO_INDEX = LLONG_MAX;
 __device__ __forceinline__ int off_of(int k, int W2) { return dir_dr(k) * W2 + dir_dc(k); }
 
 // block-wide sum / min helpers (blockDim.x <= 1024, multiple of 32)
+// Named barrier `id` (1..15) over the first n threads of the block (n a
+// multiple of 32); the block-wide barrier is id 0.
+__device__ __forceinline__ void bar_sync_n(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// Named barrier that also returns whether any participating thread passed
+// a nonzero `pred`.
+__device__ __forceinline__ int bar_or_n(int id, int n, int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %3, 0;\n\t"
+        "bar.red.or.pred q, %1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(id), "r"(n), "r"(pred)
+        : "memory");
+    return r;
+}
+
 __device__ __forceinline__ int warp_sum(int v) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;

@@ -39,7 +39,7 @@ struct TileArgs {
     uint16_t *link;
     uint32_t *node_dst;
     double *node_val;
-    const u128 *G;
+    const void *G;  // resolved perimeter graph: u64 counts or u128 fixed-point sums
     StatusBlock *st;
     uint32_t *maxw;
     uint32_t *ef_hdr, *ef_cp, *seg_merge, *inf_src;
@@ -104,17 +104,29 @@ __host__ __device__ inline size_t code_buf_bytes(int th, int tw) {
 // multiple of four so that a four-cell group is one 16-byte store.
 __host__ __device__ inline int cell_stride(int tw) { return (tw + 3) & ~3; }
 
+// Four-cell groups of the compact arrays owned by one jump thread (their
+// pointers live in registers during the rounds).
+constexpr int KG = 4;
+// Threads of a tile-solve block: one per KG groups of the compact arrays
+// (th x cell_stride(tw) cells <= 16384), at least a warp, at most 1024.  All
+// of them run the jump rounds, then walk the entry paths.
+__host__ __device__ inline int jump_threads(int th, int tw) {
+    const int ng = th * cell_stride(tw) / 4;
+    const int need = (ng + KG - 1) / KG;
+    return min(1024, max(32, ((need + 31) / 32) * 32));
+}
+__host__ __device__ inline int solve_threads(int th, int tw) { return jump_threads(th, tw); }
+
 __host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm, bool tma) {
     const size_t nc = (size_t)th * cell_stride(tw), pm = (size_t)(2 * th + 2 * tw);
     size_t b = 128;                           // alignment slack of the dynamic window
     b += code_buf_bytes(th, tw) * (tma ? 2 : 1);  // effective codes (two TMA stages)
-    b += valm ? nc * 8 : 0;                   // 64-bit fixed-point sums
-    b += nc * 4;                              // packed word per cell
+    b += nc * (valm ? 16 : 4);                // value and round inflow per cell
+    b += nc * 2;                              // successor (jump pointer) per cell
     b += nc * 2;                              // entry-forest claim tag per cell
     b += pm * 4;                              // segment -> where it joins another
-    b += nc * 2;                              // source queue (u16 cell indices)
-    b += pm * 2 * 3;                          // exit rank per slot, entry list, segment ends
-    b += pm * 2 + (pm + 8) * 2;               // entry number per slot, inflow link -> slot
+    b += pm * 2 * 4;                          // exit rank per slot, entry list, segment ends, entry number
+    b += (pm + 8) * 2;                        // inflow link -> slot
     return (b + 15) & ~size_t(15);
 }
 
@@ -131,6 +143,7 @@ __host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
 
 __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
     return (int64_t)(th + 2) * tile_stride(tw) <= 65535 && (int64_t)th * tw <= 16384 &&
+           (int64_t)th * cell_stride(tw) <= 16384 &&
            solve_smem_bytes(th, tw, valm, false) <= 227 * 1024 &&
            offsets_smem_bytes(th, tw) <= 227 * 1024;
 }
@@ -232,13 +245,16 @@ __device__ __forceinline__ void transform_box(uint8_t *ec, int h, int w, int S, 
                                               long long &fbad) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int words = S >> 2;
+    // the byte masks of the lane's first word column (the common case of one
+    // word per lane: S <= 128)
+    const uint32_t keep0 = col_mask(4 * lane - X0, -1, w), inter0 = col_mask(4 * lane - X0, 0, w - 1);
     for (int hr = warp; hr < h + 2; hr += nw) {
         const bool irow = hr >= 1 && hr <= h;
         uint32_t *row = reinterpret_cast<uint32_t *>(ec + hr * S);
         for (int wd = lane; wd < words; wd += 32) {
             const int c0 = 4 * wd - X0;
-            const uint32_t keep = col_mask(c0, -1, w);
-            const uint32_t inter = irow ? col_mask(c0, 0, w - 1) : 0u;
+            const uint32_t keep = wd == lane ? keep0 : col_mask(c0, -1, w);
+            const uint32_t inter = irow ? (wd == lane ? inter0 : col_mask(c0, 0, w - 1)) : 0u;
             uint32_t v = row[wd] & keep;
             const uint32_t bad = __vcmpgtu4(v, 0x09090909u);
             const uint32_t badin = bad & inter;
@@ -280,15 +296,15 @@ __device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
 constexpr uint32_t NO_JOIN = 0xFFFFFFFFu;
 constexpr uint16_t NO_ENTRY = 0xFFFFu;
 
-// Resident blocks per SM: four 64 x 64 tiles fit shared memory for counts,
-// two with the 64-bit sums of weighted runs (which then get more registers).
+// A block of solve_threads(tile) threads (up to 1024), each owning at most KG
+// four-cell groups of the compact arrays during the jump rounds.
 template <int VALM, bool TMA>
-__global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constant__ CUtensorMap tmap) {
     typedef typename std::conditional<VALM == 0, uint32_t, long long>::type PV;
     const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_nsrc, s_nent, s_flags, s_qhead, s_nef, s_ninf;
+    __shared__ int s_nent, s_flags, s_nef, s_ninf;
     __shared__ uint32_t s_maxw;
     __shared__ __align__(8) uint64_t s_bar[2];
 
@@ -307,13 +323,16 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
                                                    ~uintptr_t(127));
     uint8_t *cbuf0 = base128;
     uint8_t *cbuf1 = base128 + (TMA ? CB : 0);
-    long long *fsum = reinterpret_cast<long long *>(base128 + (TMA ? 2 : 1) * CB);
-    uint32_t *word = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(fsum) +
-                                                  (VALM ? 8 * (size_t)NC : 0));
-    uint16_t *tag = reinterpret_cast<uint16_t *>(word + NC);  // claiming segment + 1, 0 = free
+    uint8_t *cells = base128 + (TMA ? 2 : 1) * CB;
+    // counts: per cell its value x (low 16 bits) and the inflow of the current
+    // jump round (high 16 bits); weights: 64-bit fixed-point x and inflow
+    uint32_t *xd = reinterpret_cast<uint32_t *>(cells);
+    long long *x64 = reinterpret_cast<long long *>(cells);
+    long long *d64 = x64 + NC;
+    uint16_t *J = reinterpret_cast<uint16_t *>(cells + (VALM ? 16 : 4) * (size_t)NC);
+    uint16_t *tag = J + NC;  // claiming segment + 1, 0 = free
     uint32_t *segjoin = reinterpret_cast<uint32_t *>(tag + NC);
-    uint16_t *srcq = reinterpret_cast<uint16_t *>(segjoin + a.pmax);
-    uint16_t *rank = srcq + NC;
+    uint16_t *rank = reinterpret_cast<uint16_t *>(segjoin + a.pmax);
     uint16_t *entq = rank + a.pmax;
     uint16_t *segend = entq + a.pmax;
     uint16_t *eidx = segend + a.pmax;     // slot -> entry number, NO_ENTRY if not an entry
@@ -354,10 +373,8 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
         const size_t efb = (size_t)t * a.th * a.tw, infb = (size_t)t * (a.pmax + 8);
         uint8_t *ec = (TMA && (it & 1)) ? cbuf1 : cbuf0;
         if (tid == 0) {
-            s_nsrc = 0;
             s_nent = 0;
             s_maxw = 0;
-            s_qhead = 0;
             s_nef = 0;
             s_ninf = 0;
         }
@@ -382,26 +399,28 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
         __syncthreads();
 
         // [phase] init
-        // ---- dependency counts D (Algorithm 1, first loop) and the in-tile
-        // successor of every cell, four cells per lane from the same neighbour
+        // ---- the in-tile successor of every cell (Algorithm 1's D, as the
+        // jump pointer J_0), four cells per lane from the same neighbour
         // words: byte j of nbr_k is the code of cell j's neighbour in
         // direction k.  A row of g groups uses the next power of two >= g
-        // lanes, so one warp iteration covers 32 / lanes-per-row rows.
+        // lanes, so one warp iteration covers 32 / lanes-per-row rows.  Cells
+        // outside the tile (edge tiles) get no successor and value 0.
         uint32_t maxw = 0;
-        const int groups = (w + 3) >> 2;
+        const int groups = (w + 3) >> 2;  // groups holding tile cells
+        const int gall = WS >> 2;         // groups per row of the compact arrays
         int lpr_log = 0;
-        while ((1 << lpr_log) < groups && lpr_log < 5) ++lpr_log;
+        while ((1 << lpr_log) < gall && lpr_log < 5) ++lpr_log;
         const int rows_per_it = 32 >> lpr_log;
         const int sub = lane >> lpr_log, gl = lane & ((1 << lpr_log) - 1);
-        for (int r0 = warp * rows_per_it; r0 < h; r0 += nw * rows_per_it) {
-            for (int g0 = 0; g0 < groups; g0 += (1 << lpr_log)) {  // warp-uniform trip counts
+        for (int r0 = warp * rows_per_it; r0 < a.th; r0 += nw * rows_per_it) {
+            for (int g0 = 0; g0 < gall; g0 += (1 << lpr_log)) {
                 const int r = r0 + sub, gq = g0 + gl;
-                uint32_t srcbits = 0;
-                int wbase = 0;
+                if (r >= a.th || gq >= gall) continue;
+                const int c = 4 * gq, wbase = r * WS + c;
+                uint32_t jw0 = 0xFFFFFFFFu, jw1 = 0xFFFFFFFFu, valid = 0;
+                uint32_t wbits[4] = {0u, 0u, 0u, 0u};  // raw weight bits (weights)
                 if (r < h && gq < groups) {
-                    const int c = 4 * gq;
                     const int base = (r + 1) * S + c + X0;
-                    wbase = r * WS + c;
                     uint32_t L[3], Cw[3], Rw[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
@@ -412,7 +431,7 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
                         Rw[d] = p[1];
                     }
                     const uint32_t me = Cw[1];
-                    uint32_t pm = 0, stepw = 0;
+                    uint32_t stepw = 0;
 #pragma unroll
                     for (int k = 1; k <= 8; ++k) {
                         const int d = dir_dr(k) + 1, dc = dir_dc(k);
@@ -420,60 +439,45 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
                                                      : (dc > 0 ? __funnelshift_r(Cw[d], Rw[d], 8)
                                                                : __funnelshift_l(L[d], Cw[d], 8));
                         const uint32_t kk = 0x01010101u * (uint32_t)k;
-                        // the neighbour drains into this cell
-                        pm |= __vcmpeq4(nbr, 0x01010101u * (uint32_t)dir_rev(k)) &
-                              (0x01010101u << (k - 1));
                         // this cell drains into the neighbour, a valid cell of the tile
                         const uint32_t inside =
                             __vcmpne4(nbr, 0u) & __vcmpeq4(nbr & 0x10101010u, 0u);
                         stepw |= __vcmpeq4(me, kk) & inside & kk;
                     }
-                    uint32_t x = pm - ((pm >> 1) & 0x55555555u);  // per-byte popcount
-                    x = (x & 0x33333333u) + ((x >> 2) & 0x33333333u);
-                    x = (x + (x >> 4)) & 0x0F0F0F0Fu;
                     const int nvalid = min(4, w - c);
                     const uint32_t colmask = nvalid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nvalid)) - 1u);
-                    const uint32_t valid = __vcmpne4(me, 0u) & colmask;
-                    const uint32_t sm = valid & __vcmpeq4(x, 0u) & 0x01010101u;
-                    srcbits = (sm | (sm >> 7) | (sm >> 14) | (sm >> 21)) & 15u;
-                    uint32_t wv4[4];
+                    valid = __vcmpne4(me, 0u) & colmask;
+                    uint32_t sc[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint32_t sj = (stepw >> (8 * j)) & 15u, pj = (x >> (8 * j)) & 15u;
-                        const bool vj = (valid >> (8 * j)) & 1u;
-                        if constexpr (VALM == 0) wv4[j] = vj ? ((sj << 28) | (pj << 24) | 1u) : 0u;
-                        else wv4[j] = vj ? ((sj << 4) | pj) : 0u;
+                    for (int q = 0; q < 4; ++q) {
+                        const int st = (int)((stepw >> (8 * q)) & 15u);
+                        sc[q] = st ? (uint32_t)(wbase + q + dir_dr(st) * WS + dir_dc(st)) : 0xFFFFu;
                     }
-                    *reinterpret_cast<uint4 *>(word + wbase) =
-                        make_uint4(wv4[0], wv4[1], wv4[2], wv4[3]);
-                    *reinterpret_cast<uint2 *>(tag + wbase) = make_uint2(0u, 0u);
+                    jw0 = sc[0] | (sc[1] << 16);
+                    jw1 = sc[2] | (sc[3] << 16);
                     if constexpr (VALM == 1) {
-                        for (int j = 0; j < nvalid; ++j) {
-                            if (!((valid >> (8 * j)) & 1u)) continue;
-                            const float wf = ras.w ? ras.w[(R0 + r) * ras.pw + (C0 + c + j)] : 1.0f;
-                            const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (!((valid >> (8 * q)) & 1u)) continue;
+                            const float wf = ras.w ? ras.w[(R0 + r) * ras.pw + (C0 + c + q)] : 1.0f;
+                            wbits[q] = __float_as_uint(wf);
+                            const uint32_t b = wbits[q] & 0x7fffffffu;
                             if (b >= 0x7f800000u) nonfinite = 1;
                             maxw = max(maxw, b);
-                            fsum[wbase + j] = (long long)__float_as_uint(wf);  // raw bits until scaled
                         }
                     }
                 }
-                // append the lanes' sources to the block queue (warp-aggregated)
-                const int mysrc = __popc(srcbits);
-                int incl = mysrc;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                int qbase = 0;
-                if (lane == 31 && tot) qbase = atomicAdd(&s_nsrc, tot);
-                qbase = __shfl_sync(0xffffffffu, qbase, 31);
-                int qp = qbase + incl - mysrc;
-                while (srcbits) {
-                    srcq[qp++] = (uint16_t)(wbase + __ffs(srcbits) - 1);
-                    srcbits &= srcbits - 1;
+                *reinterpret_cast<uint2 *>(J + wbase) = make_uint2(jw0, jw1);
+                *reinterpret_cast<uint2 *>(tag + wbase) = make_uint2(0u, 0u);
+                if constexpr (VALM == 0) {
+                    *reinterpret_cast<uint4 *>(xd + wbase) =
+                        make_uint4(valid & 1u, (valid >> 8) & 1u, (valid >> 16) & 1u, valid >> 24 & 1u);
+                } else {
+                    // raw weight bits until the tile's scale is known
+                    *reinterpret_cast<longlong2 *>(x64 + wbase) = make_longlong2(wbits[0], wbits[1]);
+                    *reinterpret_cast<longlong2 *>(x64 + wbase + 2) = make_longlong2(wbits[2], wbits[3]);
+                    *reinterpret_cast<longlong2 *>(d64 + wbase) = make_longlong2(0, 0);
+                    *reinterpret_cast<longlong2 *>(d64 + wbase + 2) = make_longlong2(0, 0);
                 }
             }
         }
@@ -572,87 +576,131 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
             for (int r = warp; r < h; r += nw)
                 for (int c = lane; c < w; c += 32) {
                     const int i = (r + 1) * S + c + X0;
-                    if (ec[i]) fsum[r * WS + c] = f2fix64(__uint_as_float((uint32_t)fsum[r * WS + c]), qt);
+                    if (ec[i]) x64[r * WS + c] = f2fix64(__uint_as_float((uint32_t)x64[r * WS + c]), qt);
                 }
         }
         __syncthreads();
 
         // [phase] walk
-        // ---- the Kahn loop without a ready queue: a lane takes the next
-        // source from the shared queue, pushes its final value downstream,
-        // and carries on from the cell its delivery completes (the last
-        // pending upstream neighbour); otherwise it takes another source.
-        // Integer sums make the order irrelevant.  Meanwhile the last two
-        // warps walk the entry paths (Algorithm 2), which reads only codes.
-        const int lwn = nw >= 4 ? 2 : 0;  // warps walking entry paths alongside
-        const int mww = nw - lwn;         // warps running the solve
-        if (warp < mww) {
-            const int nsrc = s_nsrc;
-            const unsigned below = (1u << lane) - 1u;
-            int cur = -1;     // the cell this lane carries on from, -1 = idle
-            uint32_t wv = 0;  // its word, final: successor step | 0 pending | A_loc (counts)
-            long long fv = 0; // its final fixed-point sum (weights)
-            for (int guard = 0; guard < 2 * n_in + 64; ++guard) {
-                const unsigned need = __ballot_sync(0xffffffffu, cur < 0);
-                if (need) {
-                    const int leader = __ffs(need) - 1;
-                    int qb = 0;
-                    if (lane == leader) qb = atomicAdd(&s_qhead, __popc(need));
-                    qb = __shfl_sync(0xffffffffu, qb, leader);
-                    const int qi = qb + __popc(need & below);
-                    if (cur < 0 && qi < nsrc) {
-                        cur = srcq[qi];
-                        wv = word[cur];
-                        if constexpr (VALM == 1) fv = fsum[cur];
-                    }
-                    if (!__any_sync(0xffffffffu, cur >= 0)) break;  // queue drained, no walk left
-                }
-                if (cur < 0) continue;
-                const int st = VALM == 0 ? (int)(wv >> 28) : (int)((wv >> 4) & 15u);
-                if (st == 0) {  // no successor in the tile
-                    cur = -1;
-                    continue;
-                }
-                const int tgt = cur + dir_dr(st) * WS + dir_dc(st);
-                if constexpr (VALM == 0) {
-                    const uint32_t delta = (wv & 0xFFFFFFu) - (1u << 24);
-                    const uint32_t old = atomicAdd(&word[tgt], delta);
-                    if (((old >> 24) & 15u) == 1u) {  // the last pending inflow: tgt is final
-                        wv = old + delta;
-                        cur = tgt;
+        // ---- A_loc by pointer jumping on the tile's flow forest (Eq. 1 with
+        // the tile as the whole raster).  In round k every cell u adds its
+        // value to J_k(u), the cell 2^k steps downstream (while the in-tile
+        // path is that long), and J_{k+1}(u) = J_k(J_k(u)).  After rounds
+        // 0..m-1 a cell holds the sum over the cells at most 2^m - 1 steps
+        // upstream of it, which is A_loc once 2^m exceeds the longest path.
+        // A round scatters into the inflow half (counts) or array (weights)
+        // and gathers J_k o J_k; after a barrier every cell folds its inflow
+        // into its value and publishes its new pointer.  Each thread keeps
+        // the pointers of its four-cell groups in registers.  Integer sums:
+        // the result does not depend on the order of the atomic adds.
+        const int NG = NC >> 2;
+        const int njt = jump_threads(a.th, a.tw);
+        const bool sep = nt > njt;
+        if (tid < njt) {
+            uint2 jg[KG];
+#pragma unroll
+            for (int i = 0; i < KG; ++i) {
+                const int g = tid + i * njt;
+                jg[i] = g < NG ? *reinterpret_cast<const uint2 *>(J + 4 * g)
+                               : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+            }
+            for (int round = 0; round < 16; ++round) {  // 2^15 > any in-tile path
+                uint2 jn[KG];
+#pragma unroll
+                for (int i = 0; i < KG; ++i) {
+                    jn[i] = jg[i];
+                    const int g = tid + i * njt;
+                    if (g >= NG || (jg[i].x & jg[i].y) == 0xFFFFFFFFu) continue;  // no pointer left
+                    const uint32_t jv[4] = {jg[i].x & 0xFFFFu, jg[i].x >> 16, jg[i].y & 0xFFFFu,
+                                            jg[i].y >> 16};
+                    uint32_t jj[4];
+                    if constexpr (VALM == 0) {
+                        const uint4 x4 = *reinterpret_cast<const uint4 *>(xd + 4 * g);
+                        const uint32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            jj[q] = 0xFFFFu;
+                            if (jv[q] != 0xFFFFu) {
+                                jj[q] = J[jv[q]];
+                                atomicAdd(&xd[jv[q]], xs[q] << 16);  // into the inflow half
+                            }
+                        }
                     } else {
-                        cur = -1;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            jj[q] = 0xFFFFu;
+                            if (jv[q] != 0xFFFFu) {
+                                jj[q] = J[jv[q]];
+                                atomicAdd(reinterpret_cast<unsigned long long *>(&d64[jv[q]]),
+                                          (unsigned long long)x64[4 * g + q]);
+                            }
+                        }
                     }
-                } else {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&fsum[tgt]),
-                              (unsigned long long)fv);
-                    __threadfence_block();
-                    const uint32_t old = atomicSub(&word[tgt], 1u);
-                    if ((old & 15u) == 1u) {
-                        __threadfence_block();
-                        fv = *reinterpret_cast<volatile long long *>(&fsum[tgt]);
-                        wv = old - 1u;
-                        cur = tgt;
+                    jn[i] = make_uint2(jj[0] | (jj[1] << 16), jj[2] | (jj[3] << 16));
+                }
+                bar_sync_n(1, njt);
+                int act = 0;
+#pragma unroll
+                for (int i = 0; i < KG; ++i) {
+                    const int g = tid + i * njt;
+                    if (g >= NG) continue;
+                    if (jn[i].x != jg[i].x || jn[i].y != jg[i].y) {
+                        *reinterpret_cast<uint2 *>(J + 4 * g) = jn[i];
+                        jg[i] = jn[i];
+                    }
+                    act |= (jg[i].x & jg[i].y) != 0xFFFFFFFFu;
+                    if constexpr (VALM == 0) {
+                        uint4 v = *reinterpret_cast<const uint4 *>(xd + 4 * g);
+                        if ((v.x | v.y | v.z | v.w) >> 16) {
+                            v.x = (v.x & 0xFFFFu) + (v.x >> 16);
+                            v.y = (v.y & 0xFFFFu) + (v.y >> 16);
+                            v.z = (v.z & 0xFFFFu) + (v.z >> 16);
+                            v.w = (v.w & 0xFFFFu) + (v.w >> 16);
+                            *reinterpret_cast<uint4 *>(xd + 4 * g) = v;
+                        }
                     } else {
-                        cur = -1;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const long long dv = d64[4 * g + q];
+                            if (dv) {
+                                x64[4 * g + q] += dv;
+                                d64[4 * g + q] = 0;
+                            }
+                        }
                     }
+                }
+                if (!bar_or_n(1, njt, act)) break;
+            }
+            // cells whose path never ended lie on a cycle inside the tile or drain
+            // into one
+#pragma unroll
+            for (int i = 0; i < KG; ++i) {
+                const int g = tid + i * njt;
+                if (g >= NG || (jg[i].x & jg[i].y) == 0xFFFFFFFFu) continue;
+                const uint32_t jv[4] = {jg[i].x & 0xFFFFu, jg[i].x >> 16, jg[i].y & 0xFFFFu, jg[i].y >> 16};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (jv[q] == 0xFFFFu) continue;
+                    ++ncyc;
+                    const int ci = 4 * g + q, rr = ci / WS, cc = ci - rr * WS;
+                    fbad = min(fbad, (long long)((R0 + rr) * ras.cols + (C0 + cc)));
                 }
             }
-        }
-        if (warp >= mww || lwn == 0) {
-            if (lwn == 0) __syncthreads();  // one- to three-warp blocks: entry paths after the solve
-            // Algorithm 2 for the entry cells, one segment per entry: claim
-            // cells along the path until it leaves the tile, ends, or reaches
-            // a cell another segment claimed.  The in-tile successor is the
-            // step packed into the word (the solve never changes those bits).
+
+        }  // jump threads
+
+        // ---- Algorithm 2 for the entry cells, one segment per entry: claim
+        // cells along the path until it leaves the tile, ends, or reaches a
+        // cell another segment claimed (the extra warp, during the rounds)
+        if (!sep || tid >= njt) {
             const int nent = s_nent;
             uint32_t *efc = a.ef_cp + efb;
             uint16_t *efs = a.ef_seg + efb;
-            const int lt2 = lwn ? tid - mww * 32 : tid, stride = lwn ? lwn * 32 : nt;
-            for (int q = lt2; q < nent; q += stride) {
+            const int q0 = sep ? tid - njt : tid, qs = sep ? nt - njt : nt;
+            for (int q = q0; q < nent; q += qs) {
                 int r, c;
                 cell_of(entq[q], h, w, r, c);
-                int ci = r * WS + c;
+                int pi = (r + 1) * S + c + X0, ci = r * WS + c;
                 uint16_t end = LINK_TERM;
                 uint32_t join = NO_JOIN;
                 for (int pos = 0; pos < n_in; ++pos) {
@@ -664,17 +712,19 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
                     const int idx = atomicAdd(&s_nef, 1);
                     efc[idx] = ((uint32_t)ci << 16) | (uint32_t)pos;
                     efs[idx] = (uint16_t)q;
-                    const uint32_t wd = word[ci];
-                    const int k = VALM == 0 ? (int)(wd >> 28) : (int)((wd >> 4) & 15u);
-                    if (k == 0) {  // no successor in the tile: an exit, or the path ends
-                        const int rr = ci / WS, cc = ci - rr * WS;
-                        const int i = (rr + 1) * S + cc + X0;
-                        const int kc = ec[i];
-                        if (kc >= 1 && kc <= 8 && (ec[i + off_of(kc, S)] & HALO))
-                            end = rank[slot_of(rr, cc, h, w)];
+                    const int k = ec[pi];
+                    if (k < 1 || k > 8) break;  // NoFlow: the path ends here
+                    const int np = pi + off_of(k, S);
+                    const uint8_t et = ec[np];
+                    if (!et) break;  // into NoData or off the raster
+                    if (et & HALO) {  // leaves the tile: this cell is an exit
+                        end = rank[slot_of(r, c, h, w)];
                         break;
                     }
+                    pi = np;
                     ci += dir_dr(k) * WS + dir_dc(k);
+                    r += dir_dr(k);
+                    c += dir_dc(k);
                 }
                 segend[q] = end;
                 segjoin[q] = join;
@@ -683,9 +733,8 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
         __syncthreads();
 
         // [phase] output
-        // ---- write A_loc (0 for NoData and for cells on cycles: those never
-        // lose their last pending dependency); exit records; links of the
-        // entry cells; the entry forest's segment joins ----------------------
+        // ---- write A_loc (0 for NoData; unspecified on cycles); exit records;
+        // links of the entry cells; the entry forest's segment joins --------
         const double inv = ldexp(1.0, -qt);
         // four cells per lane, as in the init loop; whole 16-byte stores when
         // the output row allows them
@@ -698,19 +747,18 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
                 const int c = 4 * gq, wb = r * WS + c;
                 const int nvalid = min(4, w - c);
                 const uint32_t codes4 = *reinterpret_cast<const uint32_t *>(ec + (r + 1) * S + c + X0);
-                const uint4 w4 = *reinterpret_cast<const uint4 *>(word + wb);
-                const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
                 uint32_t ov[4];
+                if constexpr (VALM == 0) {
+                    const uint4 x4 = *reinterpret_cast<const uint4 *>(xd + wb);
+                    const uint32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const bool valid = jj < nvalid && ((codes4 >> (8 * jj)) & 0xFFu) != 0;
-                    const bool fin = valid && (VALM == 0 ? ((wv[jj] >> 24) & 15u) == 0 : (wv[jj] & 15u) == 0);
-                    if (valid && !fin) {
-                        ++ncyc;
-                        fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c + jj)));
+                    for (int jj = 0; jj < 4; ++jj) ov[jj] = xs[jj] & 0xFFFFu;  // NoData holds 0
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const bool valid = jj < nvalid && ((codes4 >> (8 * jj)) & 0xFFu) != 0;
+                        ov[jj] = valid ? __float_as_uint((float)((double)x64[wb + jj] * inv)) : 0u;
                     }
-                    if constexpr (VALM == 0) ov[jj] = fin ? (wv[jj] & 0xFFFFFFu) : 0u;
-                    else ov[jj] = fin ? __float_as_uint((float)((double)fsum[wb + jj] * inv)) : 0u;
                 }
                 uint32_t *orow = reinterpret_cast<uint32_t *>(ras.out) + (size_t)(R0 + r) * ras.po + C0 + c;
                 if (vec && nvalid == 4) {
@@ -726,8 +774,8 @@ __global__ void __launch_bounds__(256, VALM ? 2 : 4) k_solve(TileArgs A, const _
             int r, c;
             cell_of(s, h, w, r, c);
             double vv;
-            if constexpr (VALM == 0) vv = (double)(word[r * WS + c] & 0xFFFFFFu);
-            else vv = (double)fsum[r * WS + c] * inv;
+            if constexpr (VALM == 0) vv = (double)(xd[r * WS + c] & 0xFFFFu);
+            else vv = (double)x64[r * WS + c] * inv;
             a.node_val[tbase + rks] = vv;  // A_loc at the exit (the perimeter data's A)
         }
         const int nent = s_nent;
@@ -854,7 +902,12 @@ __global__ void __launch_bounds__(128) k_offsets(TileArgs A) {
         const uint32_t src = a.inf_src[ib + j];
         const uint16_t lk = a.link[src];
         if (lk == LINK_TERM) continue;  // never: a cell draining into this tile is an exit
-        atomic_add_u128(&inS[a.inf_seg[ib + j]], a.G[src - src % (uint32_t)pm + lk]);
+        const size_t gi = src - src % (uint32_t)pm + lk;
+        if constexpr (VALM == 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&inS[a.inf_seg[ib + j]]),
+                      reinterpret_cast<const unsigned long long *>(a.G)[gi]);
+        else
+            atomic_add_u128(&inS[a.inf_seg[ib + j]], reinterpret_cast<const u128 *>(a.G)[gi]);
     }
     // ---- the join tree of the segments
     for (int e = tid; e < nseg; e += nt) {
@@ -1017,25 +1070,35 @@ struct ForestArgs {
     const uint16_t *link;
     const uint32_t *node_dst;
     const double *node_val;
-    u128 *x, *dl0, *dl1;
+    void *x, *dl0, *dl1;  // u64 (counts) or u128 (fixed-point sums) per node
     uint32_t *J0, *J1;
     uint32_t *misc;  // [0] max|w| bits, [1 + k] active nodes in round k
     StatusBlock *st;
 };
 
+// Node values: uint64 counts (unit weights) or 128-bit fixed-point sums.
+__device__ __forceinline__ void atomic_add_v(unsigned long long *p, unsigned long long v) {
+    atomicAdd(p, v);
+}
+__device__ __forceinline__ void atomic_add_v(u128 *p, u128 v) { atomic_add_u128(p, v); }
+
+template <class V>
 __global__ void k_forest_init(ForestArgs f) {
     const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (tile >= f.tiles) return;
+    V *x = reinterpret_cast<V *>(f.x), *dl0 = reinterpret_cast<V *>(f.dl0),
+      *dl1 = reinterpret_cast<V *>(f.dl1);
     const uint32_t n = f.nexit[tile];
     const int q = f.valm ? fix_scale(f.cells, f.misc[0]) : 0;
     const size_t base = (size_t)tile * f.pmax;
     for (uint32_t j = lane; j < n; j += 32) {
         const size_t node = base + j;
         const double v = f.node_val[node];
-        f.x[node] = f.valm ? d2fix(v, q) : (u128)(unsigned long long)v;
-        f.dl0[node] = 0;
-        f.dl1[node] = 0;
+        if constexpr (sizeof(V) == 8) x[node] = (V)v;  // an exact integer count
+        else x[node] = f.valm ? d2fix(v, q) : (u128)(unsigned long long)v;
+        dl0[node] = 0;
+        dl1[node] = 0;
         const uint32_t dst = f.node_dst[node];
         const uint16_t l = f.link[dst];
         f.J0[node] = l == LINK_TERM ? NODE_NONE : (dst / f.pmax) * f.pmax + l;
@@ -1047,13 +1110,15 @@ __global__ void k_forest_init(ForestArgs f) {
 // of A_loc over all nodes at most 2^m - 1 links upstream, i.e. the product
 // (I + P)(I + P^2)...(I + P^(2^(m-1))) applied to A_loc, which equals
 // (I - P)^-1 A_loc once 2^m exceeds the longest path.
+template <class V>
 __global__ void k_forest_round(ForestArgs f, int k) {
     if (k > 0 && f.misc[k] == 0) return;  // round k-1 moved nothing: done
     const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (tile >= f.tiles) return;
-    u128 *dprev = (k & 1) ? f.dl0 : f.dl1;
-    u128 *dcur = (k & 1) ? f.dl1 : f.dl0;
+    V *x = reinterpret_cast<V *>(f.x);
+    V *dprev = reinterpret_cast<V *>((k & 1) ? f.dl0 : f.dl1);
+    V *dcur = reinterpret_cast<V *>((k & 1) ? f.dl1 : f.dl0);
     const uint32_t *Jc = (k & 1) ? f.J1 : f.J0;
     uint32_t *Jn = (k & 1) ? f.J0 : f.J1;
     const uint32_t n = f.nexit[tile];
@@ -1061,18 +1126,18 @@ __global__ void k_forest_round(ForestArgs f, int k) {
     int nact = 0;
     for (uint32_t j = lane; j < n; j += 32) {
         const size_t node = base + j;
-        u128 xv = f.x[node];
+        V xv = x[node];
         if (k > 0) {
-            const u128 d = dprev[node];
+            const V d = dprev[node];
             if (d) {
                 xv += d;
-                f.x[node] = xv;
+                x[node] = xv;
                 dprev[node] = 0;
             }
         }
         const uint32_t jj = Jc[node];
         if (jj != NODE_NONE) {
-            atomic_add_u128(&dcur[jj], xv);
+            atomic_add_v(&dcur[jj], xv);
             Jn[node] = Jc[jj];
             ++nact;
         } else {
@@ -1085,10 +1150,13 @@ __global__ void k_forest_round(ForestArgs f, int k) {
 
 // Absorb whatever is still pending and flag nodes whose paths never ended
 // (a cross-tile cycle).
+template <class V>
 __global__ void k_forest_final(ForestArgs f, int kmax) {
     const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (tile >= f.tiles) return;
+    V *x = reinterpret_cast<V *>(f.x), *dl0 = reinterpret_cast<V *>(f.dl0),
+      *dl1 = reinterpret_cast<V *>(f.dl1);
     const bool live = f.misc[kmax] != 0;
     const uint32_t *Jl = (kmax & 1) ? f.J1 : f.J0;
     const uint32_t n = f.nexit[tile];
@@ -1096,8 +1164,8 @@ __global__ void k_forest_final(ForestArgs f, int kmax) {
     int ncyc = 0;
     for (uint32_t j = lane; j < n; j += 32) {
         const size_t node = base + j;
-        const u128 d = f.dl0[node] + f.dl1[node];
-        if (d) f.x[node] += d;
+        const V d = dl0[node] + dl1[node];
+        if (d) x[node] += d;
         if (live && Jl[node] != NODE_NONE) ++ncyc;
     }
     ncyc = warp_sum(ncyc);
@@ -1181,10 +1249,6 @@ static cudaError_t set_smem(K kern, size_t smem, int &configured) {
     return cudaSuccess;
 }
 
-static int tile_threads(const Geom &g) {
-    const int cells = g.th * g.tw;
-    return cells >= 256 ? 256 : ((cells + 31) / 32) * 32;
-}
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against libcuda); nullptr when unavailable
@@ -1247,7 +1311,7 @@ static cudaError_t solve_config(const Geom &g, int &blocks_per_sm) {
     const size_t smem = solve_smem_bytes(g.th, g.tw, VALM, TMA);
     cudaError_t e = set_smem(k_solve<VALM, TMA>, smem, configured);
     if (e != cudaSuccess) return e;
-    const int nt = tile_threads(g);
+    const int nt = solve_threads(g.th, g.tw);
     if (per_sm_smem != (int)smem || per_sm_nt != nt) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<VALM, TMA>, nt, smem);
         if (e != cudaSuccess) return e;
@@ -1272,7 +1336,7 @@ static cudaError_t launch_solve_k(const Geom &g, const TileArgs &ta, const CUten
     cudaError_t e = solve_config<VALM, TMA>(g, per_sm);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<int64_t>(ta.T, (int64_t)per_sm * sm_count());
-    k_solve<VALM, TMA><<<grid, tile_threads(g), solve_smem_bytes(g.th, g.tw, VALM, TMA), s>>>(ta, m);
+    k_solve<VALM, TMA><<<grid, solve_threads(g.th, g.tw), solve_smem_bytes(g.th, g.tw, VALM, TMA), s>>>(ta, m);
     return cudaGetLastError();
 }
 
@@ -1324,7 +1388,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     ta.link = ws.link;
     ta.node_dst = ws.node_dst;
     ta.node_val = ws.node_val;
-    ta.G = reinterpret_cast<const u128 *>(ws.x);
+    ta.G = ws.x;
     ta.st = st;
     ta.maxw = ws.misc;
     ta.ef_hdr = ws.ef_hdr;
@@ -1350,17 +1414,23 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     f.link = ws.link;
     f.node_dst = ws.node_dst;
     f.node_val = ws.node_val;
-    f.x = reinterpret_cast<u128 *>(ws.x);
-    f.dl0 = reinterpret_cast<u128 *>(ws.dl0);
-    f.dl1 = reinterpret_cast<u128 *>(ws.dl1);
+    f.x = ws.x;
+    f.dl0 = ws.dl0;
+    f.dl1 = ws.dl1;
     f.J0 = ws.J0;
     f.J1 = ws.J1;
     f.misc = ws.misc;
     f.st = st;
     const unsigned fb = (unsigned)((f.tiles * 32 + 255) / 256);
-    k_forest_init<<<fb, 256, 0, s>>>(f);
-    for (int k = 0; k < ws.kmax; ++k) k_forest_round<<<fb, 256, 0, s>>>(f, k);
-    k_forest_final<<<fb, 256, 0, s>>>(f, ws.kmax);
+    if (val_mode) {
+        k_forest_init<u128><<<fb, 256, 0, s>>>(f);
+        for (int k = 0; k < ws.kmax; ++k) k_forest_round<u128><<<fb, 256, 0, s>>>(f, k);
+        k_forest_final<u128><<<fb, 256, 0, s>>>(f, ws.kmax);
+    } else {
+        k_forest_init<unsigned long long><<<fb, 256, 0, s>>>(f);
+        for (int k = 0; k < ws.kmax; ++k) k_forest_round<unsigned long long><<<fb, 256, 0, s>>>(f, k);
+        k_forest_final<unsigned long long><<<fb, 256, 0, s>>>(f, ws.kmax);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     timing_mark(2, s);

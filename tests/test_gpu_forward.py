@@ -152,7 +152,7 @@ def test_tile_shape_invariance():
     """Integer results are identical for every tile shape (the paper's own
     correctness check compares the tiled run with the untiled one)."""
     codes = synth.dem_codes(257, 311, 99)
-    base, _ = run(codes, tile=(257, 63))
+    base, _ = run(codes, tile=(255, 63))
     for tile in [(1, 1), (2, 5), (8, 8), (16, 64), (64, 64), (128, 128), (32, 512), (1, 2048),
                  (512, 1), (256, 64)]:
         got, st = run(codes, tile=tile)
@@ -164,6 +164,8 @@ def test_unsupported_tile_shapes_rejected():
     w = torch.zeros((10, 10), dtype=torch.float32, device="cuda")
     with pytest.raises(fa.FlowAccError):
         fa.accumulate(c, tile=(4096, 1))  # 16-bit cell index space exceeded
+    with pytest.raises(fa.FlowAccError):
+        fa.accumulate(c, tile=(257, 63))  # 257 x 64 compact cells > 16384
     with pytest.raises(fa.FlowAccError):
         fa.accumulate(c, w, tile=(128, 128))  # float pairs exceed shared memory
 
