@@ -4,8 +4,10 @@ Workload (one step = the whole hot path over one raster: pass 1, the
 perimeter-graph resolve and pass 2): a 16384 x 16384 raster (2.7e8 cells) of
 uint8 D8 codes from the seeded spectral-DEM generator (1/f^2 spectrum,
 priority-flood eps fill, 1% NoData disk; seed 201), unit weights, uint32
-counts, 64 x 64 tiles.  Inputs are resident in HBM; they (268 MB codes +
-1.07 GB output) exceed the 129 MB L2, so no explicit flush runs between steps.
+counts, with the tile shape picked by the library's autotuner (fa_autotune,
+run before the timed region).  Inputs are resident in HBM; they (268 MB codes
++ 1.07 GB output) exceed the 129 MB L2, so no explicit flush runs between
+steps.
 
 Printed JSON line: cells/s over all ranks (max-over-ranks time), the roofline
 of the dominant kernel (algorithmic bytes / live CUDA-event duration), the
@@ -15,8 +17,9 @@ timed region.  Two more forms are timed on the same GPU against the plain
 kernel (their per-cell time over the plain kernel's):
   batched: 64 spectral-DEM rasters, rows U{257..4096} x cols U{311..6000}
     (seeds 301..364), 8 float32 fields each (4 uniform [0,1), 4 lognormal
-    sigma=1), one CUDA-graph replay of fa_accumulate_batched, against the same
-    512 (raster, field) pairs run one fa_accumulate call each;
+    sigma=1), one CUDA-graph replay of fa_accumulate_batched with the tile
+    shape fa_autotune_batched picks, against the same 512 (raster, field)
+    pairs run one fa_accumulate call each with that shape;
   adjoint: an 8192 x 8192 DEM raster (seed 401), dL/dA nonzero at 256 gauge
     cells, fa_accumulate_adjoint against the float32 forward on that raster.
 
@@ -258,7 +261,8 @@ def leg_batched(fa, dev, stream, opts, warmup, reps):
         items.append({"codes": torch.from_numpy(c).to(dev), "weights": ws})
     cells = int(sum(c.size for c in codes))
     pairs = cells * BATCH_FIELDS
-    plan = fa.BatchPlan(items, BATCH_FIELDS, tile=(opts.tile_h, opts.tile_w), stream=stream)
+    plan = fa.BatchPlan(items, BATCH_FIELDS, tile="auto", stream=stream)
+    opts = fa.options(plan.tile)
     for _ in range(warmup):
         plan.run(stream)
     ms_b = _time(lambda: plan.run(stream), stream, reps)
@@ -294,7 +298,7 @@ def leg_batched(fa, dev, stream, opts, warmup, reps):
             "time_vs_plain_loop": ms_b / ms_l,
             # algorithmic bytes: 1 B code per cell, 4 B weight + 4 B output per pair
             "hbm_frac_step": (cells + 8 * pairs) / (ms_b / 1e3) / 1e9,  # divided by the peak below
-            "status": int(st), "max_rel_diff_vs_plain": worst}
+            "tile": list(plan.tile), "status": int(st), "max_rel_diff_vs_plain": worst}
 
 
 def leg_adjoint(fa, dev, stream, opts, warmup, reps):
@@ -358,6 +362,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up and timed steps (for ncu): no clock sampling, phase "
                          "timing, extra legs or CPU baseline")
+    ap.add_argument("--tile", default="auto",
+                    help="tile shape HxW for the plain leg, or 'auto' (fa_autotune; default)")
     ap.add_argument("--size", type=int, default=ROWS,
                     help="raster side; smaller than the default only for profiler captures")
     args = ap.parse_args()
@@ -386,7 +392,11 @@ def main():
     cells = codes.size
     codes_d = torch.from_numpy(codes).to(dev)
     out_d = torch.empty((ROWS, COLS), dtype=torch.uint32, device=dev)
-    opts = fa.options(TILE)
+    if args.tile == "auto":
+        tile = fa.autotune(codes_d)  # before the timed region
+    else:
+        tile = tuple(int(v) for v in args.tile.lower().split("x"))
+    opts = fa.options(tile)
     wsz = fa.fa_workspace_size(ROWS, COLS, opts)
     work = torch.empty(wsz, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -455,7 +465,10 @@ def main():
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "rows": ROWS, "cols": COLS, "seed": SEED,
-                   "tile": list(TILE), "weights": "unit", "out": "uint32",
+                   "tile": list(tile),
+                   "tile_choice": "fa_autotune" if args.tile == "auto" else "fixed",
+                   "weights": "unit",
+                   "out": "uint32",
                    "l2": "inputs+outputs 1.34 GB > 129 MB L2, no flush",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": roof, "roofline_step": roof_step,
@@ -468,9 +481,14 @@ def main():
         # float32 weighted form on the same raster
         w_d = torch.from_numpy(synth.uniform_weights(codes.shape, WSEED)).to(dev)
         outf = torch.empty((ROWS, COLS), dtype=torch.float32, device=dev)
+        tile_f = fa.autotune(codes_d, w_d)
+        opts_f = fa.options(tile_f)
+        work_f = torch.empty(fa.fa_workspace_size(ROWS, COLS, opts_f), dtype=torch.uint8,
+                             device=dev)
 
         def step_f32():
-            s = fa.fa_accumulate(codes_d, w_d, None, outf, fa.FA_OUT_F32, work, opts, None, stream)
+            s = fa.fa_accumulate(codes_d, w_d, None, outf, fa.FA_OUT_F32, work_f, opts_f, None,
+                                 stream)
             if s != fa.FA_OK:
                 raise fa.FlowAccError(s, "fa_accumulate f32")
 
@@ -486,9 +504,10 @@ def main():
         msf = e0.elapsed_time(e1) / k2
         line["forms"] = {"plain_u32": {"cells_per_s": cells / (ms / 1e3), "ms": ms},
                          "plain_f32": {"cells_per_s": cells / (msf / 1e3), "ms": msf,
+                                       "tile": list(tile_f),
                                        "hbm_frac_step": cells * BYTES_PER_CELL_F32 / (msf / 1e3)
                                        / 1e9 / peak}}
-        del w_d, outf
+        del w_d, outf, work_f
 
         # end to end through the public API from pinned host buffers
         h_codes = torch.from_numpy(codes).pin_memory()
@@ -524,7 +543,7 @@ def main():
             b["time_per_cell_vs_plain_f32"] = b["ns_per_cell_field"] / b["ns_per_cell_plain_f32"]
             line["forms"]["batched"] = b
             torch.cuda.empty_cache()
-            a = leg_adjoint(fa, dev, stream, opts, 3, 20)
+            a = leg_adjoint(fa, dev, stream, fa.options(TILE), 3, 20)
             a["hbm_frac_step"] = a["hbm_frac_step"] / peak
             a["time_per_cell_vs_plain_f32"] = (a["ms_adjoint"] / a["cells"]) / (msf / cells)
             line["forms"]["adjoint"] = a

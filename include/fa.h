@@ -119,8 +119,8 @@ size_t fa_workspace_size(int64_t rows, int64_t cols, const fa_options *opts);
  *            for unit weights (upslope cell counts).
  *   mask     [rows x pitch_mask] uint8 NoData mask (device) or NULL.
  *   out      [rows x pitch_out] uint32 (FA_OUT_U32, counts mod 2^32; requires
- *            weights == NULL) or float32 (FA_OUT_F32; sums kept as compensated
- *            float pairs inside tiles and 128-bit fixed point across tiles, then
+ *            weights == NULL) or float32 (FA_OUT_F32; sums kept in 64-bit fixed
+ *            point inside tiles and 128-bit fixed point across tiles, then
  *            rounded once to float32).
  *   workspace, ws_bytes: caller-owned device scratch, >= fa_workspace_size().
  *   d_status: device int32[FA_STATUS_WORDS] or NULL (see above).
@@ -198,6 +198,38 @@ fa_status fa_batched_plan_create(const fa_raster *rasters, int32_t n_rasters, in
                                  int32_t *d_status, void *stream, fa_plan *plan);
 fa_status fa_plan_launch(fa_plan plan, void *stream);
 void fa_plan_destroy(fa_plan plan);
+
+/*
+ * Tile-shape autotuner.  The tile shape trades work inside a tile against the
+ * size of the perimeter graph (Section 3.2 grows with the number of tiles),
+ * and the best trade depends on the raster, so it is measured: fa_autotune
+ * runs fa_accumulate on the caller's own inputs with each candidate shape
+ * (64x64, 64x128, 128x64, 96x64, 64x96, 32x128, 128x32, 48x64, 32x64, 64x32,
+ * 96x96, 128x128, skipping those the weighting or the workspace does not
+ * allow), times each on `stream` with CUDA events (one untimed and two timed
+ * calls; the call synchronises `stream`), writes the fastest shape to *best
+ * (other fields copied from opts, which may be NULL) and leaves that shape's
+ * result in `out`.  Every shape gives the same counts, and float sums that
+ * differ only by rounding.  Arguments as for fa_accumulate; the workspace
+ * must hold fa_autotune_workspace_size() bytes (shapes that do not fit are
+ * skipped).  Returns the first error fa_accumulate reports for an argument
+ * problem, FA_ERR_WORKSPACE if no candidate fits, FA_ERR_INVALID_ARG if no
+ * candidate is allowed or best is NULL.  Nothing is cached: pass *best as
+ * `opts` to later calls.
+ * fa_autotune_batched does the same for a batch (fa_accumulate_batched; one
+ * shape for the whole batch), with fa_autotune_batched_workspace_size().
+ */
+size_t fa_autotune_workspace_size(int64_t rows, int64_t cols, const fa_options *opts);
+fa_status fa_autotune(const uint8_t *codes, int64_t rows, int64_t cols, int64_t pitch_codes,
+                      const float *weights, int64_t pitch_w, const uint8_t *mask,
+                      int64_t pitch_mask, void *out, fa_out_dtype out_dtype, int64_t pitch_out,
+                      void *workspace, size_t ws_bytes, const fa_options *opts, void *stream,
+                      fa_options *best);
+size_t fa_autotune_batched_workspace_size(const fa_raster *rasters, int32_t n_rasters,
+                                          int32_t n_fields, const fa_options *opts);
+fa_status fa_autotune_batched(const fa_raster *rasters, int32_t n_rasters, int32_t n_fields,
+                              void *workspace, size_t ws_bytes, const fa_options *opts,
+                              void *stream, fa_options *best);
 
 /*
  * fa_accumulate for callers that cannot allocate device memory.  The paper has

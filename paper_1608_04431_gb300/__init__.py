@@ -27,6 +27,8 @@ __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumula
            "fa_plan_launch", "fa_plan_destroy", "accumulate_batched", "BatchPlan",
            "fa_accumulate_noalloc", "fa_accumulate_adjoint", "fa_status_read", "adjoint", "FlowAccumulate",
            "fa_timing_enable", "fa_timing_read", "accumulate",
+           "fa_autotune_workspace_size", "fa_autotune", "fa_autotune_batched_workspace_size",
+           "fa_autotune_batched", "autotune", "autotune_batched",
            "FlowAccError", "options"]
 
 
@@ -110,6 +112,37 @@ def fa_accumulate_adjoint(codes, mask, grad_out, grad_w, workspace, opts=None, d
         ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
 
 
+def fa_autotune_workspace_size(rows: int, cols: int, opts: fa_options | None = None) -> int:
+    return _lib.load().fa_autotune_workspace_size(rows, cols, ctypes.byref(opts or fa_options()))
+
+
+def fa_autotune(codes, weights, mask, out, out_dtype, workspace, opts=None, stream=None):
+    """Run fa_autotune; returns (status, fa_options of the fastest shape)."""
+    rows, cols = codes.shape
+    best = fa_options()
+    st = _lib.load().fa_autotune(
+        _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(mask),
+        _pitch(mask), _ptr(out), out_dtype, _pitch(out), _ptr(workspace), workspace.numel(),
+        ctypes.byref(opts or fa_options()), _stream_ptr(stream), ctypes.byref(best))
+    return st, best
+
+
+def fa_autotune_batched_workspace_size(rasters, n_fields: int, opts=None) -> int:
+    arr = (fa_raster * max(1, len(rasters)))(*rasters)
+    return _lib.load().fa_autotune_batched_workspace_size(arr, len(rasters), n_fields,
+                                                          ctypes.byref(opts or fa_options()))
+
+
+def fa_autotune_batched(rasters, n_fields: int, workspace, opts=None, stream=None):
+    """Run fa_autotune_batched; returns (status, fa_options of the fastest shape)."""
+    arr = (fa_raster * max(1, len(rasters)))(*rasters)
+    best = fa_options()
+    st = _lib.load().fa_autotune_batched(arr, len(rasters), n_fields, _ptr(workspace),
+                                         workspace.numel(), ctypes.byref(opts or fa_options()),
+                                         _stream_ptr(stream), ctypes.byref(best))
+    return st, best
+
+
 def fa_batched_workspace_size(rasters, n_fields: int, opts: fa_options | None = None) -> int:
     arr = (fa_raster * max(1, len(rasters)))(*rasters)
     return _lib.load().fa_batched_workspace_size(arr, len(rasters), n_fields,
@@ -184,15 +217,42 @@ def workspace(nbytes: int, device) -> torch.Tensor:
     return ws
 
 
+_tile_cache: dict = {}
+
+
+def autotune(codes: torch.Tensor, weights: torch.Tensor | None = None,
+             mask: torch.Tensor | None = None, stream=None):
+    """The fastest tile shape for this raster (fa_autotune on the given inputs),
+    remembered per (device, shape, weighted, masked) for tile="auto"."""
+    R, C = codes.shape
+    key = (codes.device, R, C, weights is not None, mask is not None)
+    if key not in _tile_cache:
+        out_dtype = FA_OUT_U32 if weights is None else FA_OUT_F32
+        out = torch.empty((R, C), dtype=torch.uint32 if weights is None else torch.float32,
+                          device=codes.device)
+        ws = workspace(fa_autotune_workspace_size(R, C), codes.device)
+        st, best = fa_autotune(codes, weights, mask, out, out_dtype, ws, None, stream)
+        if st != FA_OK:
+            raise FlowAccError(st, "fa_autotune")
+        _tile_cache[key] = (best.tile_h, best.tile_w)
+    return _tile_cache[key]
+
+
 def accumulate(codes: torch.Tensor, weights: torch.Tensor | None = None,
                mask: torch.Tensor | None = None, out_dtype=None, tile=None,
                out: torch.Tensor | None = None, check: bool = False, stream=None, flags: int = 0):
     """Flow accumulation of one raster.  codes: uint8 [R, C] CUDA tensor;
     weights: float32 [R, C] or None (counts); mask: uint8 [R, C] or None.
-    Returns uint32 counts (no weights, default) or float32 sums.  check=True
-    synchronises and raises FlowAccError on any device-reported error."""
+    Returns uint32 counts (no weights, default) or float32 sums.  tile: None
+    (64 x 64), (h, w), or "auto" (autotune() once per raster shape).
+    check=True synchronises and raises FlowAccError on any device-reported
+    error."""
     if codes.dtype != torch.uint8 or not codes.is_cuda:
         raise TypeError("codes must be a uint8 CUDA tensor")
+    if isinstance(tile, str):
+        if tile != "auto":
+            raise ValueError("tile must be None, (h, w) or 'auto'")
+        tile = autotune(codes, weights, mask, stream)
     if out_dtype is None:
         out_dtype = FA_OUT_U32 if weights is None else FA_OUT_F32
     R, C = codes.shape
@@ -296,8 +356,10 @@ def accumulate_batched(items, n_fields: int = 0, tile=None, check: bool = False,
     outs = _batch_outputs(items, n_fields)
     rasters = [make_raster(it["codes"], it.get("weights"), o, it.get("mask"))
                for it, o in zip(items, outs)]
-    opts = options(tile)
     dev = items[0]["codes"].device if items else torch.device("cuda")
+    if isinstance(tile, str):
+        tile = autotune_batched(items, n_fields, stream)
+    opts = options(tile)
     ws = workspace(fa_batched_workspace_size(rasters, n_fields, opts), dev)
     st = fa_accumulate_batched(rasters, n_fields, ws, opts, None, stream)
     if st != FA_OK:
@@ -309,12 +371,31 @@ def accumulate_batched(items, n_fields: int = 0, tile=None, check: bool = False,
     return outs
 
 
+def autotune_batched(items, n_fields: int = 0, stream=None):
+    """The fastest tile shape for this batch (fa_autotune_batched on its inputs;
+    outputs go to scratch tensors)."""
+    outs = _batch_outputs(items, n_fields)
+    rasters = [make_raster(it["codes"], it.get("weights"), o, it.get("mask"))
+               for it, o in zip(items, outs)]
+    dev = items[0]["codes"].device
+    ws = torch.empty(max(fa_autotune_batched_workspace_size(rasters, n_fields), 1 << 20),
+                     dtype=torch.uint8, device=dev)
+    st, best = fa_autotune_batched(rasters, n_fields, ws, None, stream)
+    if st != FA_OK:
+        raise FlowAccError(st, "fa_autotune_batched")
+    return (best.tile_h, best.tile_w)
+
+
 class BatchPlan:
     """A batch captured once in a CUDA graph; run() replays it.  Holds its
-    own workspace, status block and output tensors."""
+    own workspace, status block and output tensors.  tile: None (64 x 64),
+    (h, w), or "auto" (autotune_batched first; the shape is kept in .tile)."""
 
     def __init__(self, items, n_fields: int = 0, tile=None, stream=None):
         self.items = items  # keep inputs alive
+        if isinstance(tile, str):
+            tile = autotune_batched(items, n_fields, stream)
+        self.tile = tile
         self.outs = _batch_outputs(items, n_fields)
         rasters = [make_raster(it["codes"], it.get("weights"), o, it.get("mask"))
                    for it, o in zip(items, self.outs)]

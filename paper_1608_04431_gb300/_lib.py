@@ -70,6 +70,12 @@ SIGNATURES = {
                                      _P]),
     "fa_batched_plan_create": (_I32, [ctypes.POINTER(fa_raster), _I32, _I32, _P, _SZ, _OPT, _P,
                                       _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "fa_autotune_workspace_size": (_SZ, [_I64, _I64, _OPT]),
+    "fa_autotune": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I32, _I64, _P, _SZ,
+                           _OPT, _P, _OPT]),
+    "fa_autotune_batched_workspace_size": (_SZ, [ctypes.POINTER(fa_raster), _I32, _I32, _OPT]),
+    "fa_autotune_batched": (_I32, [ctypes.POINTER(fa_raster), _I32, _I32, _P, _SZ, _OPT, _P,
+                                   _OPT]),
     "fa_plan_launch": (_I32, [_P, _P]),
     "fa_plan_destroy": (None, [_P]),
     "fa_timing_enable": (None, [_I32]),

@@ -135,3 +135,24 @@ def test_batched_host_logic_without_gpu(lib):
     assert st == _lib.FA_ERR_INVALID_ARG
     assert lib.fa_plan_launch(None, None) == _lib.FA_ERR_INVALID_ARG
     lib.fa_plan_destroy(None)
+
+
+def test_autotune_host_logic_without_gpu(lib):
+    o = _lib.fa_options()
+    fake = 1 << 20  # never dereferenced: every path below returns before a CUDA call
+    need = lib.fa_autotune_workspace_size(1000, 1200, ctypes.byref(o))
+    assert need >= lib.fa_workspace_size(1000, 1200, ctypes.byref(o)) > 0
+    best = _lib.fa_options()
+    # no candidate fits a tiny workspace
+    st = lib.fa_autotune(fake, 1000, 1200, 1200, None, 0, None, 0, fake, _lib.FA_OUT_U32, 1200,
+                         fake, 64, ctypes.byref(o), None, ctypes.byref(best))
+    assert st == _lib.FA_ERR_WORKSPACE
+    # NULL result
+    st = lib.fa_autotune(fake, 1000, 1200, 1200, None, 0, None, 0, fake, _lib.FA_OUT_U32, 1200,
+                         fake, need, ctypes.byref(o), None, None)
+    assert st == _lib.FA_ERR_INVALID_ARG
+    arr = (_lib.fa_raster * 1)(_raster(100, 100, 0, fake))
+    assert lib.fa_autotune_batched_workspace_size(arr, 1, 0, ctypes.byref(o)) >= \
+        lib.fa_batched_workspace_size(arr, 1, 0, ctypes.byref(o)) > 0
+    st = lib.fa_autotune_batched(arr, 1, 0, fake, 64, ctypes.byref(o), None, ctypes.byref(best))
+    assert st == _lib.FA_ERR_WORKSPACE
