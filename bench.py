@@ -447,9 +447,11 @@ def main():
     names = ["pass1_tile_solve", "perimeter_graph_resolve", "pass2_tile_finalize"]
     dom = int(np.argmax(ph))
     # algorithmic bytes per launch of each phase (counts): pass 1 reads the
-    # codes (1 B/cell), pass 2 reads the codes and writes uint32 (5 B/cell);
-    # the perimeter resolve moves O(perimeter) bytes (not counted).
-    alg = {0: cells * 1, 1: 0, 2: cells * 5}
+    # codes and writes A_loc into the output, which is the step's whole
+    # minimum (5 B/cell); the perimeter resolve and pass 2 (entry-forest
+    # records, offsets on ~12% of cells) move O(perimeter) and overhead bytes
+    # (not counted).
+    alg = {0: cells * 5, 1: 0, 2: 0}
     peak, peak_kind = peaks()
     ach = alg[dom] / (ph[dom] / 1e3) / 1e9 if alg[dom] else 0.0
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
