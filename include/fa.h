@@ -206,8 +206,8 @@ void fa_plan_destroy(fa_plan plan);
  * runs fa_accumulate on the caller's own inputs with each candidate shape
  * (64x64, 64x128, 128x64, 96x64, 64x96, 32x128, 128x32, 48x64, 32x64, 64x32,
  * 96x96, 128x128, skipping those the weighting or the workspace does not
- * allow), times each on `stream` with CUDA events (one untimed and two timed
- * calls; the call synchronises `stream`), writes the fastest shape to *best
+ * allow), times each on `stream` with CUDA events (one untimed call, then the
+ * fastest of three timed calls; the call synchronises `stream`), writes the fastest shape to *best
  * (other fields copied from opts, which may be NULL) and leaves that shape's
  * result in `out`.  Every shape gives the same counts, and float sums that
  * differ only by rounding.  Arguments as for fa_accumulate; the workspace

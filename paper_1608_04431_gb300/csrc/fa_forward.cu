@@ -123,7 +123,6 @@ __host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm, boo
     b += code_buf_bytes(th, tw) * (tma ? 2 : 1);  // effective codes (two TMA stages)
     b += nc * (valm ? 16 : 4);                // value and round inflow per cell
     b += nc * 2;                              // successor (jump pointer) per cell
-    b += nc * 2;                              // entry-forest claim tag per cell
     b += pm * 4;                              // segment -> where it joins another
     b += pm * 2 * 4;                          // exit rank per slot, entry list, segment ends, entry number
     b += (pm + 8) * 2;                        // inflow link -> slot
@@ -132,12 +131,11 @@ __host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm, boo
 
 __host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
     // segments: at most one per perimeter cell
-    const size_t nc = (size_t)th * cell_stride(tw), pc = (size_t)perim_count(th, tw);
+    const size_t pc = (size_t)perim_count(th, tw);
     size_t b = pc * 16;                       // inflow per segment (graph scale), then prefix sums
     b += pc * 8 * 2;                          // inflow at the tile scale, flow at the end
     b += pc * 4 * 2 + (pc + 1) * 4;           // join target, pending joins / fill, bucket start
     b += pc * 2 * 2;                          // join position, joins grouped by target
-    b += nc * 2;                              // position of every entry-forest cell
     return (b + 15) & ~size_t(15);
 }
 
@@ -330,8 +328,8 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
     long long *x64 = reinterpret_cast<long long *>(cells);
     long long *d64 = x64 + NC;
     uint16_t *J = reinterpret_cast<uint16_t *>(cells + (VALM ? 16 : 4) * (size_t)NC);
-    uint16_t *tag = J + NC;  // claiming segment + 1, 0 = free
-    uint32_t *segjoin = reinterpret_cast<uint32_t *>(tag + NC);
+    uint32_t *tagw = xd;  // after the rounds: claiming segment + 1 << 16 | position, 0 = free
+    uint32_t *segjoin = reinterpret_cast<uint32_t *>(J + NC);
     uint16_t *rank = reinterpret_cast<uint16_t *>(segjoin + a.pmax);
     uint16_t *entq = rank + a.pmax;
     uint16_t *segend = entq + a.pmax;
@@ -468,7 +466,6 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                     }
                 }
                 *reinterpret_cast<uint2 *>(J + wbase) = make_uint2(jw0, jw1);
-                *reinterpret_cast<uint2 *>(tag + wbase) = make_uint2(0u, 0u);
                 if constexpr (VALM == 0) {
                     *reinterpret_cast<uint4 *>(xd + wbase) =
                         make_uint4(valid & 1u, (valid >> 8) & 1u, (valid >> 16) & 1u, valid >> 24 & 1u);
@@ -689,52 +686,9 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
 
         }  // jump threads
 
-        // ---- Algorithm 2 for the entry cells, one segment per entry: claim
-        // cells along the path until it leaves the tile, ends, or reaches a
-        // cell another segment claimed (the extra warp, during the rounds)
-        if (!sep || tid >= njt) {
-            const int nent = s_nent;
-            uint32_t *efc = a.ef_cp + efb;
-            uint16_t *efs = a.ef_seg + efb;
-            const int q0 = sep ? tid - njt : tid, qs = sep ? nt - njt : nt;
-            for (int q = q0; q < nent; q += qs) {
-                int r, c;
-                cell_of(entq[q], h, w, r, c);
-                int pi = (r + 1) * S + c + X0, ci = r * WS + c;
-                uint16_t end = LINK_TERM;
-                uint32_t join = NO_JOIN;
-                for (int pos = 0; pos < n_in; ++pos) {
-                    const uint16_t old = atomicCAS(&tag[ci], (uint16_t)0, (uint16_t)(q + 1));
-                    if (old != 0) {  // joins segment old - 1 at cell ci
-                        join = ((uint32_t)(old - 1) << 16) | (uint32_t)ci;
-                        break;
-                    }
-                    const int idx = atomicAdd(&s_nef, 1);
-                    efc[idx] = ((uint32_t)ci << 16) | (uint32_t)pos;
-                    efs[idx] = (uint16_t)q;
-                    const int k = ec[pi];
-                    if (k < 1 || k > 8) break;  // NoFlow: the path ends here
-                    const int np = pi + off_of(k, S);
-                    const uint8_t et = ec[np];
-                    if (!et) break;  // into NoData or off the raster
-                    if (et & HALO) {  // leaves the tile: this cell is an exit
-                        end = rank[slot_of(r, c, h, w)];
-                        break;
-                    }
-                    pi = np;
-                    ci += dir_dr(k) * WS + dir_dc(k);
-                    r += dir_dr(k);
-                    c += dir_dc(k);
-                }
-                segend[q] = end;
-                segjoin[q] = join;
-            }
-        }
-        __syncthreads();
-
         // [phase] output
-        // ---- write A_loc (0 for NoData; unspecified on cycles); exit records;
-        // links of the entry cells; the entry forest's segment joins --------
+        // ---- write A_loc (0 for NoData; unspecified on cycles) and the exit
+        // records; the value array then holds the entry walks' claim tags ---
         const double inv = ldexp(1.0, -qt);
         // four cells per lane, as in the init loop; whole 16-byte stores when
         // the output row allows them
@@ -778,6 +732,55 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
             else vv = (double)x64[r * WS + c] * inv;
             a.node_val[tbase + rks] = vv;  // A_loc at the exit (the perimeter data's A)
         }
+        __syncthreads();
+        for (int q = tid; q < NC; q += nt) tagw[q] = 0u;
+        __syncthreads();
+
+        // ---- Algorithm 2 for the entry cells, one segment per entry: claim
+        // cells along the path until it leaves the tile, ends, or reaches a
+        // cell another segment claimed (the extra warp, during the rounds)
+        if (!sep || tid >= njt) {
+            const int nent = s_nent;
+            uint32_t *efc = a.ef_cp + efb;
+            uint16_t *efs = a.ef_seg + efb;
+            const int q0 = sep ? tid - njt : tid, qs = sep ? nt - njt : nt;
+            for (int q = q0; q < nent; q += qs) {
+                int r, c;
+                cell_of(entq[q], h, w, r, c);
+                int pi = (r + 1) * S + c + X0, ci = r * WS + c;
+                uint16_t end = LINK_TERM;
+                uint32_t join = NO_JOIN;
+                for (int pos = 0; pos < n_in; ++pos) {
+                    const uint32_t old =
+                        atomicCAS(&tagw[ci], 0u, ((uint32_t)(q + 1) << 16) | (uint32_t)pos);
+                    if (old != 0) {  // joins segment (old >> 16) - 1 at its position old & 0xFFFF
+                        join = old - (1u << 16);
+                        break;
+                    }
+                    const int idx = atomicAdd(&s_nef, 1);
+                    efc[idx] = ((uint32_t)ci << 16) | (uint32_t)pos;
+                    efs[idx] = (uint16_t)q;
+                    const int k = ec[pi];
+                    if (k < 1 || k > 8) break;  // NoFlow: the path ends here
+                    const int np = pi + off_of(k, S);
+                    const uint8_t et = ec[np];
+                    if (!et) break;  // into NoData or off the raster
+                    if (et & HALO) {  // leaves the tile: this cell is an exit
+                        end = rank[slot_of(r, c, h, w)];
+                        break;
+                    }
+                    pi = np;
+                    ci += dir_dr(k) * WS + dir_dc(k);
+                    r += dir_dr(k);
+                    c += dir_dc(k);
+                }
+                segend[q] = end;
+                segjoin[q] = join;
+            }
+        }
+        __syncthreads();
+
+        // ---- links of the entry cells; the entry forest's segment joins
         const int nent = s_nent;
         for (int j = tid; j < s_ninf; j += nt) a.inf_seg[infb + j] = eidx[lslot[j]];
         for (int e = tid; e < nent; e += nt) {
@@ -883,17 +886,12 @@ __global__ void __launch_bounds__(128) k_offsets(TileArgs A) {
     int *moff = pend + pc;                       // [pc + 1] start of e's joins in mlist
     uint16_t *mpos = reinterpret_cast<uint16_t *>(moff + pc + 1);  // [pc] position e joins at
     uint16_t *mlist = mpos + pc;                 // [pc] joining segments grouped by target
-    uint16_t *posmap = mlist + pc;               // [th * WS] position of every forest cell
 
     if (tid == 0) s_emax = INT_MIN;
     for (int e = tid; e < nseg; e += nt) {
         inS[e] = 0;
         pend[e] = 0;
         moff[e] = 0;
-    }
-    for (int j = tid; j < nef; j += nt) {
-        const uint32_t cp = a.ef_cp[eb + j];
-        posmap[cp >> 16] = (uint16_t)(cp & 0xFFFFu);
     }
     __syncthreads();
 
@@ -918,7 +916,7 @@ __global__ void __launch_bounds__(128) k_offsets(TileArgs A) {
         }
         const int p = (int)(m >> 16);
         par[e] = p;
-        mpos[e] = posmap[m & 0xFFFFu];
+        mpos[e] = (uint16_t)(m & 0xFFFFu);
         atomicAdd(&pend[p], 1);
         atomicAdd(&moff[p], 1);
     }

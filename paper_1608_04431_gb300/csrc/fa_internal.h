@@ -74,8 +74,8 @@ struct FwdWork {
     uint32_t *ef_hdr;      // [T*4] entry-forest cells, segments, inflow links, 0
     uint32_t *ef_cp;       // [T*th*tw] cell << 16 | position along its segment
     uint16_t *ef_seg;      // [T*th*tw] segment of the cell
-    uint32_t *seg_merge;   // [T*pmax] segment -> (segment << 16 | position) it
-                           //   joins, 0xFFFFFFFF if it ends at an exit or sink
+    uint32_t *seg_merge;   // [T*pmax] segment -> (segment << 16 | position on it)
+                           //   where it joins, 0xFFFFFFFF if it ends at an exit or sink
     uint32_t *inf_src;     // [T*(pmax+8)] inflow link: slot id of the exit outside
     uint16_t *inf_seg;     // [T*(pmax+8)] inflow link: segment it feeds
     int kmax;              // number of jump rounds
