@@ -419,37 +419,21 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                 uint32_t wbits[4] = {0u, 0u, 0u, 0u};  // raw weight bits (weights)
                 if (r < h && gq < groups) {
                     const int base = (r + 1) * S + c + X0;
-                    uint32_t L[3], Cw[3], Rw[3];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const uint32_t *p =
-                            reinterpret_cast<const uint32_t *>(ec + base + (d - 1) * S);
-                        L[d] = p[-1];
-                        Cw[d] = p[0];
-                        Rw[d] = p[1];
-                    }
-                    const uint32_t me = Cw[1];
-                    uint32_t stepw = 0;
-#pragma unroll
-                    for (int k = 1; k <= 8; ++k) {
-                        const int d = dir_dr(k) + 1, dc = dir_dc(k);
-                        const uint32_t nbr = dc == 0 ? Cw[d]
-                                                     : (dc > 0 ? __funnelshift_r(Cw[d], Rw[d], 8)
-                                                               : __funnelshift_l(L[d], Cw[d], 8));
-                        const uint32_t kk = 0x01010101u * (uint32_t)k;
-                        // this cell drains into the neighbour, a valid cell of the tile
-                        const uint32_t inside =
-                            __vcmpne4(nbr, 0u) & __vcmpeq4(nbr & 0x10101010u, 0u);
-                        stepw |= __vcmpeq4(me, kk) & inside & kk;
-                    }
+                    // each cell's code names its successor; it counts when the
+                    // target is a valid cell of the tile (not the halo ring)
+                    const uint32_t me = *reinterpret_cast<const uint32_t *>(ec + base);
                     const int nvalid = min(4, w - c);
                     const uint32_t colmask = nvalid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nvalid)) - 1u);
                     valid = __vcmpne4(me, 0u) & colmask;
                     uint32_t sc[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int st = (int)((stepw >> (8 * q)) & 15u);
-                        sc[q] = st ? (uint32_t)(wbase + q + dir_dr(st) * WS + dir_dc(st)) : 0xFFFFu;
+                        const int k = (int)((me >> (8 * q)) & 0xFFu);
+                        sc[q] = 0xFFFFu;  // no successor in the tile
+                        if (q < nvalid && k >= 1 && k <= 8) {
+                            const uint8_t et = ec[base + q + off_of(k, S)];
+                            if (et && !(et & HALO)) sc[q] = (uint32_t)(wbase + q + dir_dr(k) * WS + dir_dc(k));
+                        }
                     }
                     jw0 = sc[0] | (sc[1] << 16);
                     jw1 = sc[2] | (sc[3] << 16);
