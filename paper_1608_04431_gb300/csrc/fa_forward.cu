@@ -147,11 +147,12 @@ __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
 }
 
 
-// Load a tile's effective codes with a one-cell halo (Algorithm 1's F) into
-// ec.  Each lane first issues the loads for up to four rows (one 32-bit word of
-// interior codes, or the single halo byte its word holds), then converts and
-// stores them, so several global loads are in flight per lane.  Invalid codes
-// inside the tile are counted.
+// Load a tile's codes with a one-cell halo (Algorithm 1's F) into ec: valid
+// codes 1..9 as they are, NoData, masked, invalid and off-raster cells as 0,
+// bytes beyond the halo ring 0.  Each lane first issues the loads for up to
+// four rows (one 32-bit word of interior codes, or the single halo byte its
+// word holds), then converts and stores them, so several global loads are in
+// flight per lane.  Invalid codes inside the tile are counted.
 __device__ __forceinline__ void load_codes(const RasterDesc &ras, uint8_t *ec, int64_t R0, int64_t C0,
                                            int h, int w, int S, bool count_bad, int &nbad,
                                            long long &fbad) {
@@ -217,7 +218,7 @@ __device__ __forceinline__ void load_codes(const RasterDesc &ras, uint8_t *ec, i
                         continue;
                     }
                     if (k == 0 || ((mraw[u] >> (8 * j)) & 0xffu)) continue;
-                    v |= (k | (hcell ? HALO : 0u)) << (8 * j);
+                    v |= k << (8 * j);
                 }
                 reinterpret_cast<uint32_t *>(ec + hr * S)[wd] = v;
             }
@@ -225,57 +226,9 @@ __device__ __forceinline__ void load_codes(const RasterDesc &ras, uint8_t *ec, i
     }
 }
 
-// Bytes j = 0..3 of a word whose byte 0 is tile column c0 that lie in columns
-// lo..hi, as 0xFF bytes.
-__device__ __forceinline__ uint32_t col_mask(int c0, int lo, int hi) {
-    const int a = min(max(lo - c0, 0), 4), b = min(max(hi - c0 + 1, 0), 4);
-    return (uint32_t)(((1ull << (8 * b)) - 1ull) & ~((1ull << (8 * a)) - 1ull));
-}
+// A code byte names a valid cell (1..9: a direction or NoFlow).
+__device__ __forceinline__ bool vcode(uint32_t b) { return b - 1u < 9u; }
 
-// In-place conversion of a TMA-staged box (raw codes; row hr = tile row
-// hr - 1; tile column c at byte X0 + c) into effective codes: interior cells
-// keep valid codes (invalid ones become NoData and are counted); the one-cell
-// ring around the tile keeps valid codes with HALO set; everything else in the
-// box (neighbouring tiles' cells beyond the ring) is zeroed.  Four bytes per
-// lane, without branches except for the rare invalid code.
-__device__ __forceinline__ void transform_box(uint8_t *ec, int h, int w, int S, int64_t R0,
-                                              int64_t C0, int64_t cols, int &nbad,
-                                              long long &fbad) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int words = S >> 2;
-    // the byte masks of the lane's first word column (the common case of one
-    // word per lane: S <= 128)
-    const uint32_t keep0 = col_mask(4 * lane - X0, -1, w), inter0 = col_mask(4 * lane - X0, 0, w - 1);
-    for (int hr = warp; hr < h + 2; hr += nw) {
-        const bool irow = hr >= 1 && hr <= h;
-        uint32_t *row = reinterpret_cast<uint32_t *>(ec + hr * S);
-        for (int wd = lane; wd < words; wd += 32) {
-            const int c0 = 4 * wd - X0;
-            const uint32_t keep = wd == lane ? keep0 : col_mask(c0, -1, w);
-            const uint32_t inter = irow ? (wd == lane ? inter0 : col_mask(c0, 0, w - 1)) : 0u;
-            uint32_t v = row[wd] & keep;
-            const uint32_t bad = __vcmpgtu4(v, 0x09090909u);
-            const uint32_t badin = bad & inter;
-            if (badin) {
-                nbad += __popc(badin) >> 3;
-                const int j = (__ffs(badin) - 1) >> 3;
-                fbad = min(fbad, (long long)((R0 + hr - 1) * cols + (C0 + c0 + j)));
-            }
-            v &= ~bad;
-            v |= __vcmpne4(v, 0u) & (keep & ~inter) & 0x10101010u;
-            row[wd] = v;
-        }
-    }
-}
-
-// The in-tile successor direction of an interior cell: its code when the
-// target is a valid cell inside the tile, else 0.
-__device__ __forceinline__ uint32_t step_of(const uint8_t *ec, int i, int S) {
-    const int k = ec[i];
-    if (k < 1 || k > 8) return 0;
-    const uint8_t et = ec[i + off_of(k, S)];
-    return (et && !(et & HALO)) ? (uint32_t)k : 0u;
-}
 
 // ---------------------------------------------------------------------------
 // pass 1: tile solve
@@ -390,7 +343,9 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                 to_it = (t + (int64_t)gridDim.x < T) ? -2 - it : it;  // -2-it: the next stage was issued too
                 break;
             }
-            transform_box(ec, h, w, S, R0, C0, ras.cols, nbad, fbad);
+            // the staged box holds raw codes: readers take bytes 1..9 as
+            // valid and tell the halo ring by coordinates; invalid codes of
+            // the tile are counted in the init pass
         } else {
             load_codes(ras, ec, R0, C0, h, w, S, true, nbad, fbad);
         }
@@ -424,15 +379,23 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                     const uint32_t me = *reinterpret_cast<const uint32_t *>(ec + base);
                     const int nvalid = min(4, w - c);
                     const uint32_t colmask = nvalid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nvalid)) - 1u);
-                    valid = __vcmpne4(me, 0u) & colmask;
+                    valid = __vcmpgeu4(me, 0x01010101u) & __vcmpleu4(me, 0x09090909u) & colmask;
+                    if constexpr (TMA) {  // raw codes: count the invalid ones of the tile
+                        const uint32_t bad = __vcmpgtu4(me, 0x09090909u) & colmask;
+                        if (bad) {
+                            nbad += __popc(bad) >> 3;
+                            fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c + ((__ffs(bad) - 1) >> 3))));
+                        }
+                    }
                     uint32_t sc[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int k = (int)((me >> (8 * q)) & 0xFFu);
                         sc[q] = 0xFFFFu;  // no successor in the tile
                         if (q < nvalid && k >= 1 && k <= 8) {
-                            const uint8_t et = ec[base + q + off_of(k, S)];
-                            if (et && !(et & HALO)) sc[q] = (uint32_t)(wbase + q + dir_dr(k) * WS + dir_dc(k));
+                            const int tr = r + dir_dr(k), tc = c + q + dir_dc(k);
+                            if (tr >= 0 && tr < h && tc >= 0 && tc < w && vcode(ec[base + q + off_of(k, S)]))
+                                sc[q] = (uint32_t)(wbase + q + dir_dr(k) * WS + dir_dc(k));
                         }
                     }
                     jw0 = sc[0] | (sc[1] << 16);
@@ -483,12 +446,11 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                 rr = q - (2 * w + 4 + h);
                 cc = w;
             }
-            const uint8_t en = ec[(rr + 1) * S + cc + X0];
-            const int k = en & 15;
-            if (!(en & HALO) || k < 1 || k > 8) continue;  // NoData, off the raster, NoFlow
+            const int k = ec[(rr + 1) * S + cc + X0];
+            if (k < 1 || k > 8) continue;  // NoData, off the raster, NoFlow, invalid
             const int tr = rr + dir_dr(k), tc = cc + dir_dc(k);
             if (tr < 0 || tr >= h || tc < 0 || tc >= w) continue;  // drains elsewhere
-            if (!ec[(tr + 1) * S + tc + X0]) continue;             // into NoData
+            if (!vcode(ec[(tr + 1) * S + tc + X0])) continue;      // into NoData
             const int st = slot_of(tr, tc, h, w);
             eidx[st] = 0;  // an entry cell
             const int tyh = ty + (rr < 0 ? -1 : (rr >= h ? 1 : 0));
@@ -513,7 +475,10 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
             cell_of(s, h, w, r, c);
             const int i = (r + 1) * S + c + X0;
             const int k = ec[i];
-            if (k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO)) ++mine;
+            if (k >= 1 && k <= 8 && vcode(ec[i + off_of(k, S)])) {
+                const int tr = r + dir_dr(k), tc = c + dir_dc(k);
+                if (tr < 0 || tr >= h || tc < 0 || tc >= w) ++mine;  // a valid cell outside
+            }
         }
         int total;
         int rk = block_exclusive_scan(mine, s_warp, &total);  // (its barriers publish eidx)
@@ -522,7 +487,9 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
             cell_of(s, h, w, r, c);
             const int i = (r + 1) * S + c + X0;
             const int k = ec[i];
-            const bool ex = k >= 1 && k <= 8 && (ec[i + off_of(k, S)] & HALO);
+            const int trx = r + dir_dr(k), tcx = c + dir_dc(k);
+            const bool ex = k >= 1 && k <= 8 && (trx < 0 || trx >= h || tcx < 0 || tcx >= w) &&
+                            vcode(ec[i + off_of(k, S)]);
             rank[s] = ex ? (uint16_t)rk : LINK_TERM;
             if (ex) {
                 // where the exit's flow goes: a perimeter slot of a neighbouring tile
@@ -694,7 +661,7 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                 } else {
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
-                        const bool valid = jj < nvalid && ((codes4 >> (8 * jj)) & 0xFFu) != 0;
+                        const bool valid = jj < nvalid && vcode((codes4 >> (8 * jj)) & 0xFFu);
                         ov[jj] = valid ? __float_as_uint((float)((double)x64[wb + jj] * inv)) : 0u;
                     }
                 }
@@ -747,9 +714,9 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                     const int k = ec[pi];
                     if (k < 1 || k > 8) break;  // NoFlow: the path ends here
                     const int np = pi + off_of(k, S);
-                    const uint8_t et = ec[np];
-                    if (!et) break;  // into NoData or off the raster
-                    if (et & HALO) {  // leaves the tile: this cell is an exit
+                    if (!vcode(ec[np])) break;  // into NoData or off the raster
+                    const int tr = r + dir_dr(k), tc = c + dir_dc(k);
+                    if (tr < 0 || tr >= h || tc < 0 || tc >= w) {  // leaves the tile: an exit
                         end = rank[slot_of(r, c, h, w)];
                         break;
                     }
