@@ -701,7 +701,12 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                 int pi = (r + 1) * S + c + X0, ci = r * WS + c;
                 uint16_t end = LINK_TERM;
                 uint32_t join = NO_JOIN;
+                int k = ec[pi];  // this cell's code, carried from step to step
                 for (int pos = 0; pos < n_in; ++pos) {
+                    // the next cell and its code are read while the claim is in flight
+                    const bool dir = k >= 1 && k <= 8;
+                    const int np = dir ? pi + off_of(k, S) : pi;
+                    const int kn = ec[np];
                     const uint32_t old =
                         atomicCAS(&tagw[ci], 0u, ((uint32_t)(q + 1) << 16) | (uint32_t)pos);
                     if (old != 0) {  // joins segment (old >> 16) - 1 at its position old & 0xFFFF
@@ -711,10 +716,8 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                     const int idx = atomicAdd(&s_nef, 1);
                     efc[idx] = ((uint32_t)ci << 16) | (uint32_t)pos;
                     efs[idx] = (uint16_t)q;
-                    const int k = ec[pi];
-                    if (k < 1 || k > 8) break;  // NoFlow: the path ends here
-                    const int np = pi + off_of(k, S);
-                    if (!vcode(ec[np])) break;  // into NoData or off the raster
+                    if (!dir) break;         // NoFlow: the path ends here
+                    if (!vcode(kn)) break;   // into NoData or off the raster
                     const int tr = r + dir_dr(k), tc = c + dir_dc(k);
                     if (tr < 0 || tr >= h || tc < 0 || tc >= w) {  // leaves the tile: an exit
                         end = rank[slot_of(r, c, h, w)];
@@ -722,8 +725,9 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
                     }
                     pi = np;
                     ci += dir_dr(k) * WS + dir_dc(k);
-                    r += dir_dr(k);
-                    c += dir_dc(k);
+                    r = tr;
+                    c = tc;
+                    k = kn;
                 }
                 segend[q] = end;
                 segjoin[q] = join;
