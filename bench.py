@@ -144,15 +144,21 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(x: float, ws: int) -> float:
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest of every rank's x (the slowest rank's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank: int, ms_max: float, ws: int) -> float:
+    """Whole-job units/s: every rank processed units_per_rank in at most ms_max."""
+    return ws * units_per_rank / (ms_max / 1e3)
 
 
 def traffic_for(kernel: str):
@@ -431,7 +437,7 @@ def main():
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(ms, ws)
-    value = ws * cells / (ms_max / 1e3)
+    value = job_throughput(cells, ms_max, ws)
 
     # per-phase durations, live, on the launching stream
     phases = []
@@ -530,7 +536,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         mse = max_over_ranks(e0.elapsed_time(e1) / ke, ws)
-        line["e2e"] = {"value": ws * cells / (mse / 1e3), "unit": "cells/s",
+        line["e2e"] = {"value": job_throughput(cells, mse, ws), "unit": "cells/s",
                        "h2d_bytes_per_step": int(codes.nbytes),
                        "d2h_bytes_per_step": int(cells * 4), "ms_per_step": mse}
         # the result of the last step must be exact
