@@ -52,6 +52,7 @@ BYTES_PER_CELL_F32 = 9     # + 4 B float32 weight read
 WORKLOAD = "d8_dem_16384x16384"
 BATCH_N, BATCH_FIELDS, BATCH_SEED, BATCH_SHAPE_SEED = 64, 8, 301, 300
 ADJ_N, ADJ_SEED, ADJ_GAUGES = 8192, 401, 256
+D8_N, D8_SEED = 8192, 201
 
 
 def peaks():
@@ -177,12 +178,13 @@ def traffic_for(kernel: str):
 
 
 def source_sha1() -> str:
+    """Hash of the sources that define the forward kernels (pass 1, the
+    perimeter-graph resolve, pass 2)."""
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1608_04431_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in ("fa_common.cuh", "fa_forward.cu", "fa_internal.h"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 
@@ -305,6 +307,35 @@ def leg_batched(fa, dev, stream, opts, warmup, reps):
             # algorithmic bytes: 1 B code per cell, 4 B weight + 4 B output per pair
             "hbm_frac_step": (cells + 8 * pairs) / (ms_b / 1e3) / 1e9,  # divided by the peak below
             "tile": list(plan.tile), "status": int(st), "max_rel_diff_vs_plain": worst}
+
+
+def leg_d8(fa, dev, stream, warmup, reps, peak):
+    """D8 codes from the 8192^2 spectral DEM with its 1% NoData disk (the step
+    before accumulation): fa_d8_codes time and HBM fraction at its algorithmic
+    6 B/cell (4 B elevation + 1 B NoData read, 1 B code written).  Returns the
+    record and (elevations, NoData, codes) for the CPU-baseline leg's check."""
+    import torch
+
+    import synth
+
+    z = synth.spectral_dem(D8_N, D8_N, D8_SEED)
+    nd = synth.nodata_disk(D8_N, D8_N, D8_SEED + 7919).astype(np.uint8)
+    zt, ndt = torch.from_numpy(z).to(dev), torch.from_numpy(nd).to(dev)
+    out = torch.empty(z.shape, dtype=torch.uint8, device=dev)
+
+    def step():
+        e = fa.fa_d8_codes(zt, ndt, out, stream)
+        if e != fa.FA_OK:
+            raise fa.FlowAccError(e, "fa_d8_codes")
+
+    for _ in range(warmup):
+        step()
+    ms = _time(step, stream, reps)
+    cells = z.size
+    gbs = 6 * cells / (ms / 1e3) / 1e9
+    rec = {"rows": D8_N, "cols": D8_N, "cells": cells, "ms": ms, "cells_per_s": cells / (ms / 1e3),
+           "bytes_per_cell": 6, "achieved_gbs": gbs, "hbm_frac": gbs / peak}
+    return rec, (z, nd, out.cpu().numpy())
 
 
 def leg_adjoint(fa, dev, stream, opts, warmup, reps):
@@ -485,6 +516,7 @@ def main():
     }
     line["gpu_launches"] = args.steps * fa.fa_kernel_launches(ROWS, COLS, opts)
 
+    d8_data = None
     if not args.no_extra:
         # float32 weighted form on the same raster
         w_d = torch.from_numpy(synth.uniform_weights(codes.shape, WSEED)).to(dev)
@@ -551,6 +583,8 @@ def main():
             b["time_per_cell_vs_plain_f32"] = b["ns_per_cell_field"] / b["ns_per_cell_plain_f32"]
             line["forms"]["batched"] = b
             torch.cuda.empty_cache()
+            line["forms"]["d8_directions"], d8_data = leg_d8(fa, dev, stream, 3, 50, peak)
+            torch.cuda.empty_cache()
             a = leg_adjoint(fa, dev, stream, fa.options(TILE), 3, 20)
             a["hbm_frac_step"] = a["hbm_frac_step"] / peak
             a["time_per_cell_vs_plain_f32"] = (a["ms_adjoint"] / a["cells"]) / (msf / cells)
@@ -565,6 +599,16 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
                                 "sample": f"whole {ROWS}x{COLS} raster once ({dt:.1f} s)"}
         line["parity"] = {"vs_oracle": "bit-exact" if exact else "MISMATCH"}
+        if d8_data is not None:  # the direction step's oracle, timed on one core too
+            import oracle
+
+            z, nd, got_d8 = d8_data
+            t0 = time.perf_counter()
+            ref_d8 = oracle.d8(z, nd)
+            dt8 = time.perf_counter() - t0
+            rec = line["forms"]["d8_directions"]
+            rec["parity_vs_oracle"] = "bit-exact" if np.array_equal(got_d8, ref_d8) else "MISMATCH"
+            rec["cpu_oracle_cells_per_s"] = z.size / dt8
         if not exact:
             line["parity"]["mismatches"] = int((got != res.values.astype(np.uint32)).sum())
 

@@ -12,6 +12,8 @@ Functions (all on numpy arrays, row-major, row 0 = north):
   bruteforce(codes, w, mask)     -> FP64 path-walking sums straight from the
                                     definition (small rasters only)
   residual_u32(codes, A, mask)   -> number of cells violating Eq. 1 (mod 2^32)
+  d8(z, nodata)                  -> uint8 D8 codes from float32 elevations (the
+                                    direction step before accumulation)
 
 Each returns the values plus a ``state`` array: 0 NoData, 1 exact,
 2 unspecified (on a cycle; for the adjoint, on or upstream of a cycle).
@@ -58,6 +60,8 @@ def _load():
         lib.fa_oracle_weighted.restype = ctypes.c_int
         lib.fa_oracle_adjoint.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p, pi64, pi64]
         lib.fa_oracle_adjoint.restype = ctypes.c_int
+        lib.fa_oracle_d8.argtypes = [p, i64, i64, i64, p, i64, p]
+        lib.fa_oracle_d8.restype = ctypes.c_int
         lib.fa_oracle_bruteforce.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p]
         lib.fa_oracle_bruteforce.restype = ctypes.c_int
         lib.fa_oracle_residual_u32.argtypes = [p, i64, i64, i64, p, i64, p, i64, pi64]
@@ -158,3 +162,15 @@ def residual_u32(codes, A, mask=None):
     bad = _load().fa_oracle_residual_u32(_p(codes), R, C, C, _p(mask), C, _p(A), C,
                                          ctypes.byref(first))
     return int(bad), int(first.value)
+
+
+def d8(z, nodata=None) -> np.ndarray:
+    """D8 codes (uint8) from float32 elevations z; nodata: bool/uint8 mask or None.
+    Rules in fa_oracle.c (fa_oracle_d8)."""
+    lib = _load()
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    rows, cols = z.shape
+    out = np.zeros((rows, cols), dtype=np.uint8)
+    nd = None if nodata is None else np.ascontiguousarray(nodata, dtype=np.uint8)
+    lib.fa_oracle_d8(_p(z), rows, cols, cols, None if nd is None else _p(nd), cols, _p(out))
+    return out

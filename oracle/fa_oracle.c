@@ -280,3 +280,65 @@ int64_t fa_oracle_residual_u32(const uint8_t *codes, int64_t rows, int64_t cols,
     if (first) *first = f;
     return bad;
 }
+
+/*
+ * D8 flow codes from elevations, the step before accumulation (Section 2: a
+ * non-divergent metric sends a cell's flow to a single neighbour; D8 takes the
+ * steepest descent; flats are routed towards lower terrain only; Fig. 1 treats
+ * the direction step as a separate algorithm).  The rules, one per cell:
+ *   - NoData (nodata != NULL and nodata[cell] != 0): code 0;
+ *   - a cell on the raster's border drains off the grid, perpendicular to its
+ *     edge (N, S, W, E) and diagonally at the corners (NW, NE, SW, SE);
+ *   - otherwise the valid neighbour with the largest positive slope, slope =
+ *     drop for E, N, W, S and drop * (1/sqrt 2) for the diagonals, drop =
+ *     z(cell) - z(neighbour); neighbours are tried in the order E, NE, N, NW,
+ *     W, SW, S, SE and a later one must be strictly steeper to win;
+ *   - no positive slope: the first NoData neighbour in that order (flow leaves
+ *     the data there), else NoFlow (9).
+ * The decision is taken in float32: the drop is one float subtraction, the
+ * diagonal factor the float nearest 1/sqrt 2, one float multiplication each
+ * (built with -ffp-contract=off, so nothing is fused).
+ */
+int fa_oracle_d8(const float *z, int64_t rows, int64_t cols, int64_t pitch_z,
+                 const uint8_t *nodata, int64_t pitch_nd, uint8_t *codes) {
+    const float inv_sqrt2 = 0.70710678118654752440f;
+    for (int64_t r = 0; r < rows; ++r) {
+        for (int64_t c = 0; c < cols; ++c) {
+            uint8_t *out = &codes[r * cols + c];
+            if (nodata && nodata[r * pitch_nd + c]) {
+                *out = 0;
+                continue;
+            }
+            const int top = r == 0, bottom = r == rows - 1, left = c == 0, right = c == cols - 1;
+            if (top || bottom || left || right) {
+                if (top && left) *out = 4;
+                else if (top && right) *out = 2;
+                else if (bottom && left) *out = 6;
+                else if (bottom && right) *out = 8;
+                else if (top) *out = 3;
+                else if (bottom) *out = 7;
+                else if (left) *out = 5;
+                else *out = 1;
+                continue;
+            }
+            const float zc = z[r * pitch_z + c];
+            float best = 0.0f;
+            uint8_t code = 0, into_nodata = 0;
+            for (int k = 1; k <= 8; ++k) {
+                const int64_t rn = r + ODR[k], cn = c + ODC[k];
+                if (nodata && nodata[rn * pitch_nd + cn]) {
+                    if (!into_nodata) into_nodata = (uint8_t)k;
+                    continue;
+                }
+                const float drop = zc - z[rn * pitch_z + cn];
+                const float slope = (k == 1 || k == 3 || k == 5 || k == 7) ? drop : drop * inv_sqrt2;
+                if (slope > best) {
+                    best = slope;
+                    code = (uint8_t)k;
+                }
+            }
+            *out = code ? code : (into_nodata ? into_nodata : 9);
+        }
+    }
+    return 0;
+}

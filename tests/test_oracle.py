@@ -306,3 +306,55 @@ def test_synth_dem_is_drained(oracle_mod):
     assert not (codes == 9).any()
     nd = (codes == 0).mean()
     assert 0.005 < nd < 0.02
+
+
+# ---------------------------------------------------------------------------
+# D8 directions (the step before accumulation)
+# ---------------------------------------------------------------------------
+def test_d8_hand_example(oracle_mod):
+    # worked by hand: border cells drain outward (corners diagonal); (1,1)=5
+    # drops 4 to its SE neighbour (slope 4/sqrt2 = 2.83 > 1 to the E); (1,2)=4
+    # drops 3 to the S; (2,1)=6 drops 5 to the E; (2,2)=1 is a pit: NoFlow
+    z = np.array([[9, 9, 9, 9], [9, 5, 4, 9], [9, 6, 1, 9], [9, 9, 9, 9]], np.float32)
+    want = np.array([[4, 3, 3, 2], [5, 8, 7, 1], [5, 1, 9, 1], [6, 7, 7, 8]], np.uint8)
+    np.testing.assert_array_equal(oracle_mod.d8(z), want)
+
+
+def test_d8_ties_go_to_the_first_direction(oracle_mod):
+    z = np.full((3, 3), 5.0, np.float32)
+    z[1, 1] = 3.0
+    z[1, 2] = 1.0  # E, drop 2
+    z[2, 1] = 1.0  # S, drop 2: equal, E comes first
+    assert oracle_mod.d8(z)[1, 1] == 1
+    z[2, 1] = 0.9999  # S now strictly steeper
+    assert oracle_mod.d8(z)[1, 1] == 7
+
+
+def test_d8_nodata_and_flats(oracle_mod):
+    z = np.full((5, 5), 2.0, np.float32)
+    nd = np.zeros((5, 5), np.uint8)
+    assert oracle_mod.d8(z)[2, 2] == 9  # a flat interior cell: NoFlow
+    nd[1, 2] = 1  # N of the centre
+    nd[3, 2] = 1  # S of the centre
+    got = oracle_mod.d8(z, nd)
+    assert got[2, 2] == 3  # no lower neighbour: the first NoData one (N before S)
+    assert got[1, 2] == 0 and got[3, 2] == 0
+
+
+def test_d8_tilted_plane(oracle_mod):
+    R, C = 6, 9
+    z = -np.tile(np.arange(C, dtype=np.float32), (R, 1))  # falls to the east
+    got = oracle_mod.d8(z)
+    assert (got[1:-1, 1:-1] == 1).all()
+    assert (got[0, 1:-1] == 3).all() and (got[-1, 1:-1] == 7).all()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_d8_matches_the_generator_on_integer_dems(oracle_mod, seed):
+    # the input generator's D8 (synth, double precision, its own code) decides
+    # the same on integer elevations: drops are exact and no cardinal slope can
+    # come within float rounding of a diagonal one at these magnitudes
+    g = np.random.default_rng(seed)
+    z = g.integers(0, 60, size=(40, 57)).astype(np.float32)
+    nd = (g.random(z.shape) < 0.05).astype(np.uint8)
+    np.testing.assert_array_equal(oracle_mod.d8(z, nd), synth.d8_codes(z, nd.astype(bool)))
