@@ -200,6 +200,30 @@ fa_status fa_plan_launch(fa_plan plan, void *stream);
 void fa_plan_destroy(fa_plan plan);
 
 /*
+ * D8 flow codes from elevations: the direction step that runs before the
+ * accumulation (Section 2: a non-divergent metric sends a cell's flow to a
+ * single neighbour; D8 follows the steepest descent; flats are routed towards
+ * lower terrain only; Fig. 1 treats this step as a separate algorithm).
+ *   dem      [rows x pitch_dem] float32 elevations (device, 4-byte aligned).
+ *   nodata   [rows x pitch_nodata] uint8 (device) or NULL: nonzero = NoData.
+ *   codes    [rows x pitch_codes] uint8 output (device), in this file's code
+ *            encoding.
+ * Per cell: NoData gets 0; a border cell drains off the grid (N, S, W or E,
+ * diagonal at the corners); otherwise the valid neighbour with the largest
+ * positive slope (drop, times 1/sqrt 2 for diagonals; ties to the first of
+ * E, NE, N, NW, W, SW, S, SE); with no positive slope, the first NoData
+ * neighbour in that order, else NoFlow.  Slopes are decided in float32 with
+ * correctly rounded operations (no fused multiply-add), so results are exact
+ * and platform-independent.  NaN elevations are not NoData: use the mask.
+ * Asynchronous on `stream`; rows or cols == 0 enqueue nothing.  Returns
+ * FA_ERR_INVALID_ARG for negative sizes, NULL buffers, pitches below cols or
+ * a misaligned dem, FA_ERR_CUDA if the launch fails.
+ */
+fa_status fa_d8_codes(const float *dem, int64_t rows, int64_t cols, int64_t pitch_dem,
+                      const uint8_t *nodata, int64_t pitch_nodata, uint8_t *codes,
+                      int64_t pitch_codes, void *stream);
+
+/*
  * Tile-shape autotuner.  The tile shape trades work inside a tile against the
  * size of the perimeter graph (Section 3.2 grows with the number of tiles),
  * and the best trade depends on the raster, so it is measured: fa_autotune

@@ -28,7 +28,7 @@ __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumula
            "fa_accumulate_noalloc", "fa_accumulate_adjoint", "fa_status_read", "adjoint", "FlowAccumulate",
            "fa_timing_enable", "fa_timing_read", "accumulate",
            "fa_autotune_workspace_size", "fa_autotune", "fa_autotune_batched_workspace_size",
-           "fa_autotune_batched", "autotune", "autotune_batched",
+           "fa_autotune_batched", "autotune", "autotune_batched", "fa_d8_codes", "d8_codes",
            "FlowAccError", "options"]
 
 
@@ -110,6 +110,13 @@ def fa_accumulate_adjoint(codes, mask, grad_out, grad_w, workspace, opts=None, d
         _ptr(codes), rows, cols, _pitch(codes), _ptr(mask), _pitch(mask), _ptr(grad_out),
         _pitch(grad_out), _ptr(grad_w), _pitch(grad_w), _ptr(workspace), workspace.numel(),
         ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_d8_codes(dem, nodata, codes, stream=None) -> int:
+    """Enqueue fa_d8_codes: uint8 D8 codes from float32 elevations."""
+    rows, cols = dem.shape
+    return _lib.load().fa_d8_codes(_ptr(dem), rows, cols, _pitch(dem), _ptr(nodata), _pitch(nodata),
+                                   _ptr(codes), _pitch(codes), _stream_ptr(stream))
 
 
 def fa_autotune_workspace_size(rows: int, cols: int, opts: fa_options | None = None) -> int:
@@ -215,6 +222,19 @@ def workspace(nbytes: int, device) -> torch.Tensor:
         ws = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=key)
         _ws_cache[key] = ws
     return ws
+
+
+def d8_codes(dem: torch.Tensor, nodata: torch.Tensor | None = None, out=None, stream=None):
+    """D8 codes (uint8 [R, C]) from float32 elevations on the device; nodata:
+    uint8 [R, C] or None."""
+    if dem.dtype != torch.float32 or not dem.is_cuda:
+        raise TypeError("dem must be a float32 CUDA tensor")
+    if out is None:
+        out = torch.empty(dem.shape, dtype=torch.uint8, device=dem.device)
+    st = fa_d8_codes(dem, nodata, out, stream)
+    if st != FA_OK:
+        raise FlowAccError(st, "fa_d8_codes")
+    return out
 
 
 _tile_cache: dict = {}

@@ -70,6 +70,7 @@ SIGNATURES = {
                                      _P]),
     "fa_batched_plan_create": (_I32, [ctypes.POINTER(fa_raster), _I32, _I32, _P, _SZ, _OPT, _P,
                                       _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "fa_d8_codes": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P]),
     "fa_autotune_workspace_size": (_SZ, [_I64, _I64, _OPT]),
     "fa_autotune": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I32, _I64, _P, _SZ,
                            _OPT, _P, _OPT]),

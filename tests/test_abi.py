@@ -156,3 +156,13 @@ def test_autotune_host_logic_without_gpu(lib):
         lib.fa_batched_workspace_size(arr, 1, 0, ctypes.byref(o)) > 0
     st = lib.fa_autotune_batched(arr, 1, 0, fake, 64, ctypes.byref(o), None, ctypes.byref(best))
     assert st == _lib.FA_ERR_WORKSPACE
+
+
+def test_d8_rejects_bad_args_without_gpu(lib):
+    fake = 1 << 20  # never dereferenced
+    assert lib.fa_d8_codes(fake, -1, 5, 5, None, 0, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_d8_codes(fake, 5, 5, 4, None, 0, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_d8_codes(fake, 5, 5, 5, None, 0, fake, 4, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_d8_codes(fake, 5, 5, 5, fake, 2, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_d8_codes(fake + 2, 5, 5, 5, None, 0, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_d8_codes(None, 0, 5, 5, None, 0, None, 5, None) == _lib.FA_OK  # empty
