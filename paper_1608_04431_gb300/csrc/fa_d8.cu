@@ -17,10 +17,10 @@
 // rounded multiplication by the float nearest 1/sqrt 2 (no fused operation),
 // so every platform takes the same decision.
 //
-// One thread computes four consecutive cells of a row from the 3 x 6 window
-// of elevations (and NoData bytes) around them: the pass reads each
-// elevation from DRAM about once (neighbours come from L1) and writes one
-// byte per cell.
+// One thread computes four consecutive cells of eight consecutive rows,
+// sliding a 3 x 6 window of elevations (and NoData bits) down the rows: each
+// row of the window is loaded once (one 16-byte load and two scalars), and
+// each output row is one 4-byte store.
 #include <algorithm>
 
 #include "fa_common.cuh"
@@ -51,47 +51,69 @@ __device__ __forceinline__ uint32_t border_code(bool top, bool bottom, bool left
     return 1;
 }
 
+constexpr int kRows = 8;  // consecutive rows per thread (rolling window)
+
+// Row rr of the window around the thread's four cells c0..c0+3: elevations of
+// columns c0-1..c0+4 and a NoData bit per column (0 outside the raster).
+__device__ __forceinline__ void load_row(const D8Args &a, int64_t rr, int64_t c0, bool vz, bool vn,
+                                         float v[6], uint32_t &nd) {
+    nd = 0u;
+    if (rr < 0 || rr >= a.rows) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) v[j] = 0.0f;
+        return;
+    }
+    const float *zr = a.z + rr * a.pz;
+    if (vz) {
+        const float4 m = __ldg(reinterpret_cast<const float4 *>(zr + c0));
+        v[1] = m.x;
+        v[2] = m.y;
+        v[3] = m.z;
+        v[4] = m.w;
+    } else {
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) v[j] = c0 + j - 1 < a.cols ? __ldg(zr + c0 + j - 1) : 0.0f;
+    }
+    v[0] = c0 >= 1 ? __ldg(zr + c0 - 1) : 0.0f;
+    v[5] = c0 + 4 < a.cols ? __ldg(zr + c0 + 4) : 0.0f;
+    if (a.nd) {
+        const uint8_t *nr = a.nd + rr * a.pnd;
+        if (vn) {
+            const uint32_t m = __vcmpne4(__ldg(reinterpret_cast<const unsigned int *>(nr + c0)), 0u);
+            // byte b (all ones when NoData) -> window bit b + 1
+            nd = ((m & 1u) << 1) | ((m >> 6) & 4u) | ((m >> 13) & 8u) | ((m >> 20) & 16u);
+        } else {
+#pragma unroll
+            for (int j = 1; j <= 4; ++j)
+                if (c0 + j - 1 < a.cols && __ldg(nr + c0 + j - 1)) nd |= 1u << j;
+        }
+        if (c0 >= 1 && __ldg(nr + c0 - 1)) nd |= 1u;
+        if (c0 + 4 < a.cols && __ldg(nr + c0 + 4)) nd |= 32u;
+    }
+}
+
+// One thread: four consecutive cells of kRows consecutive rows, keeping the
+// window's previous two rows in registers so each row is loaded once.
 __global__ void __launch_bounds__(256, 4) k_d8(D8Args a) {
     const int64_t G = (a.cols + 3) >> 2;  // four-cell groups per row
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
     const int64_t c0 = 4 * g;
-    const bool vz = ((reinterpret_cast<uintptr_t>(a.z) | ((uintptr_t)a.pz << 2)) & 15) == 0 &&
-                    c0 + 4 <= a.cols;
-    const bool vo = ((reinterpret_cast<uintptr_t>(a.out) | (uintptr_t)a.po) & 3) == 0 &&
-                    c0 + 4 <= a.cols;
-    for (int64_t r = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; r < a.rows;
-         r += (int64_t)gridDim.y * blockDim.y) {
-        // window: rows r-1..r+1, columns c0-1..c0+4 (outside the raster unused)
-        float v[3][6];
-        uint32_t ndm[3] = {0u, 0u, 0u};  // bit j: NoData at window column j
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int64_t rr = r + d - 1;
-            const bool rin = rr >= 0 && rr < a.rows;
-            const float *zr = a.z + (rin ? rr : r) * a.pz;
-            if (vz && rin) {
-                const float4 m = __ldg(reinterpret_cast<const float4 *>(zr + c0));
-                v[d][1] = m.x;
-                v[d][2] = m.y;
-                v[d][3] = m.z;
-                v[d][4] = m.w;
-            } else {
-#pragma unroll
-                for (int j = 1; j <= 4; ++j)
-                    v[d][j] = (rin && c0 + j - 1 < a.cols) ? __ldg(zr + c0 + j - 1) : 0.0f;
-            }
-            v[d][0] = (rin && c0 >= 1) ? __ldg(zr + c0 - 1) : 0.0f;
-            v[d][5] = (rin && c0 + 4 < a.cols) ? __ldg(zr + c0 + 4) : 0.0f;
-            if (a.nd && rin) {
-                const uint8_t *nr = a.nd + rr * a.pnd;
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    const int64_t cc = c0 + j - 1;
-                    if (cc >= 0 && cc < a.cols && __ldg(nr + cc)) ndm[d] |= 1u << j;
-                }
-            }
-        }
+    const bool full = c0 + 4 <= a.cols;
+    const bool vz = full && ((reinterpret_cast<uintptr_t>(a.z) | ((uintptr_t)a.pz << 2)) & 15) == 0;
+    const bool vn = full && ((reinterpret_cast<uintptr_t>(a.nd) | (uintptr_t)a.pnd) & 3) == 0;
+    const bool vo = full && ((reinterpret_cast<uintptr_t>(a.out) | (uintptr_t)a.po) & 3) == 0;
+    const int64_t r0 = ((int64_t)blockIdx.y * blockDim.y + threadIdx.y) * kRows;
+    if (r0 >= a.rows) return;
+    float v[3][6];  // rows r-1, r, r+1
+    uint32_t ndm[3];
+    load_row(a, r0 - 1, c0, vz, vn, v[0], ndm[0]);
+    load_row(a, r0, c0, vz, vn, v[1], ndm[1]);
+#pragma unroll 1
+    for (int i = 0; i < kRows; ++i) {
+        const int64_t r = r0 + i;
+        if (r >= a.rows) break;
+        load_row(a, r + 1, c0, vz, vn, v[2], ndm[2]);
         uint32_t codes = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -130,6 +152,14 @@ __global__ void __launch_bounds__(256, 4) k_d8(D8Args a) {
         } else {
             for (int q = 0; q < 4 && c0 + q < a.cols; ++q) orow[q] = (uint8_t)(codes >> (8 * q));
         }
+        // slide the window down one row
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            v[0][j] = v[1][j];
+            v[1][j] = v[2][j];
+        }
+        ndm[0] = ndm[1];
+        ndm[1] = ndm[2];
     }
 }
 
@@ -145,8 +175,10 @@ extern "C" fa_status fa_d8_codes(const float *dem, int64_t rows, int64_t cols, i
     if (reinterpret_cast<uintptr_t>(dem) & 3) return FA_ERR_INVALID_ARG;
     D8Args a{dem, pitch_dem, nodata, pitch_nodata, codes, pitch_codes, rows, cols};
     const int64_t G = (cols + 3) >> 2;
+    const int64_t chunks = (rows + kRows - 1) / kRows;  // row chunks of kRows
+    if ((chunks + 3) / 4 > 65535) return FA_ERR_INVALID_ARG;  // more than 2^21 rows
     const dim3 block(64, 4);
-    const dim3 grid((unsigned)((G + 63) / 64), (unsigned)std::min<int64_t>((rows + 3) / 4, 65535));
+    const dim3 grid((unsigned)((G + 63) / 64), (unsigned)((chunks + 3) / 4));
     k_d8<<<grid, block, 0, (cudaStream_t)stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ERR_CUDA;
 }
