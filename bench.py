@@ -549,6 +549,28 @@ def main():
                                        / 1e9 / peak}}
         del w_d, outf, work_f
 
+        # packed codes (two per byte, 4.5 B/cell) on the same raster and tile;
+        # packing runs before the timed region
+        pk = fa.pack_codes(codes_d)
+        out_p = torch.empty_like(out_d)
+        opts_p = fa.options(tile, code_format=fa.FA_CODES_NIBBLE)
+
+        def step_packed():
+            s = fa.fa_accumulate(pk, None, None, out_p, fa.FA_OUT_U32, work, opts_p, None, stream)
+            if s != fa.FA_OK:
+                raise fa.FlowAccError(s, "fa_accumulate packed")
+
+        for _ in range(args.warmup):
+            step_packed()
+        msp = _time(step_packed, stream, k2)
+        line["forms"]["plain_u32_packed"] = {
+            "cells_per_s": cells / (msp / 1e3), "ms": msp, "tile": list(tile),
+            "bytes_per_cell": 4.5,
+            "hbm_frac_step": cells * 4.5 / (msp / 1e3) / 1e9 / peak,
+            "identical_to_byte_codes": bool(torch.equal(out_p.view(torch.int32),
+                                                        out_d.view(torch.int32)))}
+        del pk, out_p
+
         # end to end through the public API from pinned host buffers
         h_codes = torch.from_numpy(codes).pin_memory()
         h_out = torch.empty((ROWS, COLS), dtype=torch.uint32).pin_memory()

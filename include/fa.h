@@ -9,9 +9,11 @@
  * a per-tile solve (Algorithm 1) that also links each perimeter cell to the
  * tile exit its flow path reaches (Algorithm 2), a global solve over those
  * perimeter links (Section 3.2), and a finalising per-tile pass that adds the
- * flow entering each tile along its downstream paths (Algorithm 3, Section 3.3;
- * EVICT strategy: the tile solve is recomputed, nothing per-cell is kept
- * between passes).
+ * flow entering each tile along its downstream paths (Algorithm 3, Section 3.3).
+ * The tile solve runs once: its result stays in the output raster, and the
+ * cells on the in-tile paths of the tile's entry cells are recorded in the
+ * workspace, so the finalising pass reads neither the codes nor the weights
+ * (the RETAIN strategy of Section 3, with the output raster as the store).
  *
  * Raster conventions (all entry points):
  *  - Row-major, row 0 = north; every raster argument has its own row pitch in
@@ -24,6 +26,12 @@
  *    9 = NoFlow.  Codes 10..255 are invalid: reported as FA_ERR_BAD_CODE in the
  *    device status and treated as NoData.  The paper fixes one byte and ten
  *    values per code (Section 4, Data Types) but no numbering; this is ours.
+ *  - Packed codes (fa_options.code_format = FA_CODES_NIBBLE): the same values
+ *    in four bits, two cells per byte.  Cell c of row r is in byte
+ *    r * pitch_codes + c / 2, low nibble for even c, high nibble for odd c;
+ *    pitch_codes counts BYTES and must be >= (cols + 1) / 2.  Nibbles 10..15
+ *    are invalid as above.  Section 4 notes that ten values fit in half a
+ *    byte; this halves the code traffic (4.5 B/cell for counts instead of 5).
  *  - Optional NoData mask (uint8, nonzero = NoData); a cell is NoData if its
  *    code is 0 or invalid or its mask byte is nonzero.
  *  - A cell has no downstream cell (its flow leaves the system) when it is
@@ -90,13 +98,20 @@ typedef enum { FA_OUT_U32 = 0, FA_OUT_F32 = 1 } fa_out_dtype;
  * FA_ERR_INVALID_ARG.  Results do not depend on the tile shape, except for
  * the rounding of floating-point sums.
  * flags: FA_OPT_NO_TMA disables staging code tiles into shared memory with the
- * Tensor Memory Accelerator (used when the raster allows it: 16-byte aligned
- * codes and pitch, tile width a multiple of 16, no mask raster); results are
- * identical either way. */
+ * Tensor Memory Accelerator (used when the raster allows it: byte codes,
+ * 16-byte aligned codes and pitch, tile width a multiple of 16, no mask
+ * raster); results are identical either way.
+ * code_format: FA_CODES_BYTE (0, one byte per cell) or FA_CODES_NIBBLE (1, two
+ * cells per byte; see the raster conventions above).  It applies to every
+ * codes argument of the call (fa_accumulate, fa_accumulate_noalloc,
+ * fa_accumulate_adjoint, fa_autotune and every raster of a batch); other
+ * values are FA_ERR_INVALID_ARG. */
 #define FA_OPT_NO_TMA 1
+#define FA_CODES_BYTE 0
+#define FA_CODES_NIBBLE 1
 typedef struct {
     int32_t tile_h, tile_w;
-    int32_t flags, reserved;
+    int32_t flags, code_format;
 } fa_options;
 
 /* Library version as major*10000 + minor*100 + patch. */
@@ -148,7 +163,8 @@ fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t cols, int64_
  * Errors (returned before anything is enqueued): FA_ERR_INVALID_ARG for
  * n_rasters < 0, n_fields outside 0..FA_MAX_FIELDS, a bad tile shape, and, for
  * a non-empty raster, NULL codes, NULL or 4-byte-misaligned out[k] or
- * weights[k] (k < max(n_fields, 1)), or a pitch below cols; FA_ERR_WORKSPACE
+ * weights[k] (k < max(n_fields, 1)), or a pitch below cols (below (cols + 1)
+ * / 2 for packed codes); FA_ERR_WORKSPACE
  * for a NULL, not 256-byte-aligned or too small workspace; FA_ERR_CUDA if a
  * launch or copy fails.  Rasters with rows == 0 or cols == 0 are skipped.
  * Device-side findings (bad codes, cycles, non-finite weights) go to the
@@ -222,6 +238,30 @@ void fa_plan_destroy(fa_plan plan);
 fa_status fa_d8_codes(const float *dem, int64_t rows, int64_t cols, int64_t pitch_dem,
                       const uint8_t *nodata, int64_t pitch_nodata, uint8_t *codes,
                       int64_t pitch_codes, void *stream);
+
+/*
+ * Code translation and packing.  Rasters coded in another scheme (for example
+ * one bit per direction, 1 = E, 2 = SE, 4 = S, ..., 128 = NE) are brought to
+ * this file's codes through a table, and codes can be packed two per byte for
+ * FA_CODES_NIBBLE (Section 4: ten values fit in half a byte).
+ *   src        [rows x pitch_src] uint8 (device), one byte per cell.
+ *   table      HOST array of 256 bytes: cell value v becomes table[v]; NULL
+ *              keeps v.  The table is copied into the launch, so it may be
+ *              reused as soon as the call returns.
+ *   dst        device output in dst_format: FA_CODES_BYTE writes
+ *              [rows x pitch_dst] bytes (pitch_dst >= cols); FA_CODES_NIBBLE
+ *              writes [rows x pitch_dst] bytes of packed codes (pitch_dst >=
+ *              (cols + 1) / 2), where a translated value above 15 is written
+ *              as 15 (invalid either way) and the unused high nibble of an
+ *              odd-width row's last byte is 0.
+ * src and dst must not overlap.  Asynchronous on `stream`; rows or cols == 0
+ * enqueue nothing.  Returns FA_ERR_INVALID_ARG for negative sizes, NULL
+ * buffers, short pitches or an unknown dst_format, FA_ERR_CUDA if the launch
+ * fails.
+ */
+fa_status fa_recode(const uint8_t *src, int64_t rows, int64_t cols, int64_t pitch_src,
+                    const uint8_t *table, uint8_t *dst, int64_t pitch_dst, int32_t dst_format,
+                    void *stream);
 
 /*
  * Tile-shape autotuner.  The tile shape trades work inside a tile against the

@@ -14,6 +14,8 @@ Functions (all on numpy arrays, row-major, row 0 = north):
   residual_u32(codes, A, mask)   -> number of cells violating Eq. 1 (mod 2^32)
   d8(z, nodata)                  -> uint8 D8 codes from float32 elevations (the
                                     direction step before accumulation)
+  unpack_nibbles(packed, cols)   -> uint8 codes from codes stored two per byte
+  recode(codes, table)           -> codes translated through a 256-entry table
 
 Each returns the values plus a ``state`` array: 0 NoData, 1 exact,
 2 unspecified (on a cycle; for the adjoint, on or upstream of a cycle).
@@ -174,3 +176,27 @@ def d8(z, nodata=None) -> np.ndarray:
     nd = None if nodata is None else np.ascontiguousarray(nodata, dtype=np.uint8)
     lib.fa_oracle_d8(_p(z), rows, cols, cols, None if nd is None else _p(nd), cols, _p(out))
     return out
+
+
+def unpack_nibbles(packed, cols: int) -> np.ndarray:
+    """One code per cell from codes stored two per byte.  Section 4 notes that
+    the ten code values fit in half a byte; the stored layout (the library's
+    packed format) puts cell c of a row in byte c // 2, in the low four bits
+    when c is even and the high four bits when c is odd."""
+    p = np.asarray(packed, dtype=np.uint8)
+    rows = p.shape[0]
+    out = np.zeros((rows, cols), dtype=np.uint8)
+    for c in range(cols):
+        byte = p[:, c // 2]
+        out[:, c] = (byte & 0x0F) if c % 2 == 0 else (byte >> 4)
+    return out
+
+
+def recode(codes, table) -> np.ndarray:
+    """Codes of another scheme translated cell by cell: value v becomes
+    table[v] (a 256-entry table)."""
+    t = np.frombuffer(bytes(bytearray(table)), dtype=np.uint8)
+    if t.size != 256:
+        raise ValueError("a code table has 256 entries")
+    c = np.asarray(codes, dtype=np.uint8)
+    return t[c]

@@ -19,6 +19,7 @@ from . import _lib
 from ._lib import (FA_ERR_BAD_CODE, FA_ERR_CUDA, FA_ERR_CYCLE, FA_ERR_INVALID_ARG,  # noqa: F401
                    FA_ERR_NONFINITE, FA_ERR_TIMEOUT, FA_ERR_TOO_LARGE, FA_ERR_WORKSPACE,
                    FA_NOALLOC_SCRATCH_BYTES, FA_OK, FA_OPT_NO_TMA, FA_OUT_F32, FA_OUT_U32,
+                   FA_CODES_BYTE, FA_CODES_NIBBLE,
                    FA_STATUS_WORDS,
                    FA_WARN_OVERFLOW, STATUS_NAMES, fa_options, fa_raster, FA_MAX_FIELDS)
 
@@ -29,6 +30,7 @@ __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumula
            "fa_timing_enable", "fa_timing_read", "accumulate",
            "fa_autotune_workspace_size", "fa_autotune", "fa_autotune_batched_workspace_size",
            "fa_autotune_batched", "autotune", "autotune_batched", "fa_d8_codes", "d8_codes",
+           "fa_recode", "recode", "pack_codes", "PackedCodes", "power_of_two_table",
            "FlowAccError", "options"]
 
 
@@ -38,11 +40,56 @@ class FlowAccError(RuntimeError):
         super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
 
 
-def options(tile=None, flags: int = 0) -> fa_options:
+def options(tile=None, flags: int = 0, code_format: int = FA_CODES_BYTE) -> fa_options:
     o = fa_options()
     if tile is not None:
         o.tile_h, o.tile_w = int(tile[0]), int(tile[1])
     o.flags = int(flags)
+    o.code_format = int(code_format)
+    return o
+
+
+class PackedCodes:
+    """D8 codes packed two per byte (FA_CODES_NIBBLE): the code of cell (r, c)
+    is in data[r, c // 2], low four bits for even c, high four bits for odd c.
+    data: uint8 CUDA tensor [R, >= (cols + 1) // 2] with unit column stride.
+    Accepted wherever byte codes are; the calls set code_format themselves."""
+
+    def __init__(self, data: torch.Tensor, cols: int):
+        if data.dtype != torch.uint8 or data.dim() != 2:
+            raise TypeError("packed codes must be a 2-D uint8 tensor")
+        if cols < 0 or data.shape[1] < (cols + 1) // 2:
+            raise ValueError("packed codes hold fewer than (cols + 1) // 2 bytes per row")
+        self.data = data
+        self.cols = int(cols)
+
+    @property
+    def shape(self):
+        return (self.data.shape[0], self.cols)
+
+    @property
+    def device(self):
+        return self.data.device
+
+    @property
+    def is_cuda(self):
+        return self.data.is_cuda
+
+    @property
+    def dtype(self):
+        return self.data.dtype
+
+    def data_ptr(self):
+        return self.data.data_ptr()
+
+
+def _with_format(codes, opts):
+    """A copy of opts whose code_format matches the type of `codes`."""
+    o = fa_options()
+    if opts is not None:
+        o.tile_h, o.tile_w, o.flags, o.code_format = opts.tile_h, opts.tile_w, opts.flags, opts.code_format
+    if isinstance(codes, PackedCodes):
+        o.code_format = FA_CODES_NIBBLE
     return o
 
 
@@ -58,6 +105,8 @@ def _ptr(t):
 def _pitch(t):
     if t is None:
         return 0
+    if isinstance(t, PackedCodes):
+        t = t.data
     if t.dim() != 2 or t.stride(1) != 1:
         raise ValueError("rasters must be 2-D with unit column stride")
     return t.stride(0)
@@ -86,7 +135,7 @@ def fa_accumulate(codes, weights, mask, out, out_dtype, workspace, opts=None, d_
     return _lib.load().fa_accumulate(
         _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(mask),
         _pitch(mask), _ptr(out), out_dtype, _pitch(out), _ptr(workspace), workspace.numel(),
-        ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
+        ctypes.byref(_with_format(codes, opts)), _ptr(d_status), _stream_ptr(stream))
 
 
 def fa_accumulate_noalloc(codes, weights, mask, out, out_dtype, opts=None, d_status=None,
@@ -98,7 +147,7 @@ def fa_accumulate_noalloc(codes, weights, mask, out, out_dtype, opts=None, d_sta
     rows, cols = codes.shape
     return _lib.load().fa_accumulate_noalloc(
         _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(mask),
-        _pitch(mask), _ptr(out), out_dtype, _pitch(out), ctypes.byref(opts or fa_options()),
+        _pitch(mask), _ptr(out), out_dtype, _pitch(out), ctypes.byref(_with_format(codes, opts)),
         _ptr(d_status), _stream_ptr(stream))
 
 
@@ -109,7 +158,7 @@ def fa_accumulate_adjoint(codes, mask, grad_out, grad_w, workspace, opts=None, d
     return _lib.load().fa_accumulate_adjoint(
         _ptr(codes), rows, cols, _pitch(codes), _ptr(mask), _pitch(mask), _ptr(grad_out),
         _pitch(grad_out), _ptr(grad_w), _pitch(grad_w), _ptr(workspace), workspace.numel(),
-        ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
+        ctypes.byref(_with_format(codes, opts)), _ptr(d_status), _stream_ptr(stream))
 
 
 def fa_d8_codes(dem, nodata, codes, stream=None) -> int:
@@ -117,6 +166,22 @@ def fa_d8_codes(dem, nodata, codes, stream=None) -> int:
     rows, cols = dem.shape
     return _lib.load().fa_d8_codes(_ptr(dem), rows, cols, _pitch(dem), _ptr(nodata), _pitch(nodata),
                                    _ptr(codes), _pitch(codes), _stream_ptr(stream))
+
+
+def fa_recode(src, table, dst, dst_format: int, cols: int | None = None, stream=None) -> int:
+    """Enqueue fa_recode: src uint8 [R, C] codes through a 256-byte table (or
+    None) into dst (bytes, or packed codes when dst_format is FA_CODES_NIBBLE;
+    cols defaults to src's width)."""
+    rows, c = src.shape
+    cols = c if cols is None else cols
+    tab = None
+    if table is not None:
+        tb = bytes(bytearray(table))
+        if len(tb) != 256:
+            raise ValueError("a code table has 256 entries")
+        tab = (ctypes.c_uint8 * 256).from_buffer_copy(tb)
+    return _lib.load().fa_recode(_ptr(src), rows, cols, _pitch(src), tab, _ptr(dst), _pitch(dst),
+                                 int(dst_format), _stream_ptr(stream))
 
 
 def fa_autotune_workspace_size(rows: int, cols: int, opts: fa_options | None = None) -> int:
@@ -130,7 +195,7 @@ def fa_autotune(codes, weights, mask, out, out_dtype, workspace, opts=None, stre
     st = _lib.load().fa_autotune(
         _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(mask),
         _pitch(mask), _ptr(out), out_dtype, _pitch(out), _ptr(workspace), workspace.numel(),
-        ctypes.byref(opts or fa_options()), _stream_ptr(stream), ctypes.byref(best))
+        ctypes.byref(_with_format(codes, opts)), _stream_ptr(stream), ctypes.byref(best))
     return st, best
 
 
@@ -237,6 +302,43 @@ def d8_codes(dem: torch.Tensor, nodata: torch.Tensor | None = None, out=None, st
     return out
 
 
+def power_of_two_table() -> bytes:
+    """A code table (for recode / fa_recode) from the one-bit-per-direction
+    scheme 1 = E, 2 = SE, 4 = S, 8 = SW, 16 = W, 32 = NW, 64 = N, 128 = NE to
+    this library's codes; 0 stays NoData and every other value becomes 10
+    (invalid: reported as FA_ERR_BAD_CODE and treated as NoData)."""
+    t = bytearray([10] * 256)
+    t[0] = 0
+    for bit, code in ((1, 1), (2, 8), (4, 7), (8, 6), (16, 5), (32, 4), (64, 3), (128, 2)):
+        t[bit] = code
+    return bytes(t)
+
+
+def recode(src: torch.Tensor, table=None, packed: bool = False, out=None, stream=None):
+    """src uint8 [R, C] codes translated through a 256-entry table (None keeps
+    the values): a uint8 [R, C] tensor, or PackedCodes when packed=True."""
+    if src.dtype != torch.uint8 or not src.is_cuda:
+        raise TypeError("src must be a uint8 CUDA tensor")
+    R, C = src.shape
+    if packed:
+        if out is None:
+            out = PackedCodes(torch.empty((R, (C + 1) // 2), dtype=torch.uint8, device=src.device), C)
+        dst, fmt = out.data, FA_CODES_NIBBLE
+    else:
+        if out is None:
+            out = torch.empty((R, C), dtype=torch.uint8, device=src.device)
+        dst, fmt = out, FA_CODES_BYTE
+    st = fa_recode(src, table, dst, fmt, C, stream)
+    if st != FA_OK:
+        raise FlowAccError(st, "fa_recode")
+    return out
+
+
+def pack_codes(codes: torch.Tensor, table=None, stream=None) -> PackedCodes:
+    """Byte codes (optionally through a table) packed two per byte."""
+    return recode(codes, table, packed=True, stream=stream)
+
+
 _tile_cache: dict = {}
 
 
@@ -245,7 +347,7 @@ def autotune(codes: torch.Tensor, weights: torch.Tensor | None = None,
     """The fastest tile shape for this raster (fa_autotune on the given inputs),
     remembered per (device, shape, weighted, masked) for tile="auto"."""
     R, C = codes.shape
-    key = (codes.device, R, C, weights is not None, mask is not None)
+    key = (codes.device, R, C, weights is not None, mask is not None, isinstance(codes, PackedCodes))
     if key not in _tile_cache:
         out_dtype = FA_OUT_U32 if weights is None else FA_OUT_F32
         out = torch.empty((R, C), dtype=torch.uint32 if weights is None else torch.float32,
@@ -261,8 +363,9 @@ def autotune(codes: torch.Tensor, weights: torch.Tensor | None = None,
 def accumulate(codes: torch.Tensor, weights: torch.Tensor | None = None,
                mask: torch.Tensor | None = None, out_dtype=None, tile=None,
                out: torch.Tensor | None = None, check: bool = False, stream=None, flags: int = 0):
-    """Flow accumulation of one raster.  codes: uint8 [R, C] CUDA tensor;
-    weights: float32 [R, C] or None (counts); mask: uint8 [R, C] or None.
+    """Flow accumulation of one raster.  codes: uint8 [R, C] CUDA tensor or
+    PackedCodes; weights: float32 [R, C] or None (counts); mask: uint8 [R, C]
+    or None.
     Returns uint32 counts (no weights, default) or float32 sums.  tile: None
     (64 x 64), (h, w), or "auto" (autotune() once per raster shape).
     check=True synchronises and raises FlowAccError on any device-reported
@@ -318,7 +421,9 @@ class FlowAccumulate(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, weights, codes, mask=None, tile=None):
-        ctx.save_for_backward(codes, mask) if mask is not None else ctx.save_for_backward(codes)
+        raw = codes.data if isinstance(codes, PackedCodes) else codes
+        ctx.save_for_backward(raw, mask) if mask is not None else ctx.save_for_backward(raw)
+        ctx.packed_cols = codes.cols if isinstance(codes, PackedCodes) else None
         ctx.has_mask = mask is not None
         ctx.tile = tile
         return accumulate(codes, weights.contiguous(), mask, out_dtype=FA_OUT_F32, tile=tile)
@@ -326,7 +431,7 @@ class FlowAccumulate(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         saved = ctx.saved_tensors
-        codes = saved[0]
+        codes = saved[0] if ctx.packed_cols is None else PackedCodes(saved[0], ctx.packed_cols)
         mask = saved[1] if ctx.has_mask else None
         gw = adjoint(codes, grad_out.contiguous().float(), mask, tile=ctx.tile)
         return gw, None, None, None
@@ -336,7 +441,8 @@ class FlowAccumulate(torch.autograd.Function):
 # batches
 # ---------------------------------------------------------------------------
 def make_raster(codes: torch.Tensor, weights=None, outs=None, mask: torch.Tensor | None = None):
-    """fa_raster for one raster: codes uint8 [R, C]; weights: list of float32
+    """fa_raster for one raster: codes uint8 [R, C] (or PackedCodes, with the
+    batch's code_format set to FA_CODES_NIBBLE); weights: list of float32
     [R, C] fields (or None for counts); outs: matching output tensors."""
     r = fa_raster()
     R, C = codes.shape
@@ -368,6 +474,14 @@ def _batch_outputs(items, n_fields):
     return outs
 
 
+def _batch_format(items) -> int:
+    """The code format of a batch: all byte codes or all PackedCodes."""
+    packed = {isinstance(it["codes"], PackedCodes) for it in items}
+    if len(packed) > 1:
+        raise ValueError("a batch holds either byte codes or packed codes, not both")
+    return FA_CODES_NIBBLE if packed == {True} else FA_CODES_BYTE
+
+
 def accumulate_batched(items, n_fields: int = 0, tile=None, check: bool = False, stream=None):
     """Flow accumulation of many rasters in one pass.  items: list of dicts with
     'codes' (uint8 [R, C]), optional 'weights' (list of n_fields float32 [R, C])
@@ -379,7 +493,7 @@ def accumulate_batched(items, n_fields: int = 0, tile=None, check: bool = False,
     dev = items[0]["codes"].device if items else torch.device("cuda")
     if isinstance(tile, str):
         tile = autotune_batched(items, n_fields, stream)
-    opts = options(tile)
+    opts = options(tile, code_format=_batch_format(items))
     ws = workspace(fa_batched_workspace_size(rasters, n_fields, opts), dev)
     st = fa_accumulate_batched(rasters, n_fields, ws, opts, None, stream)
     if st != FA_OK:
@@ -398,9 +512,10 @@ def autotune_batched(items, n_fields: int = 0, stream=None):
     rasters = [make_raster(it["codes"], it.get("weights"), o, it.get("mask"))
                for it, o in zip(items, outs)]
     dev = items[0]["codes"].device
-    ws = torch.empty(max(fa_autotune_batched_workspace_size(rasters, n_fields), 1 << 20),
+    opts = options(code_format=_batch_format(items))
+    ws = torch.empty(max(fa_autotune_batched_workspace_size(rasters, n_fields, opts), 1 << 20),
                      dtype=torch.uint8, device=dev)
-    st, best = fa_autotune_batched(rasters, n_fields, ws, None, stream)
+    st, best = fa_autotune_batched(rasters, n_fields, ws, opts, stream)
     if st != FA_OK:
         raise FlowAccError(st, "fa_autotune_batched")
     return (best.tile_h, best.tile_w)
@@ -419,7 +534,7 @@ class BatchPlan:
         self.outs = _batch_outputs(items, n_fields)
         rasters = [make_raster(it["codes"], it.get("weights"), o, it.get("mask"))
                    for it, o in zip(items, self.outs)]
-        opts = options(tile)
+        opts = options(tile, code_format=_batch_format(items))
         dev = items[0]["codes"].device
         self.ws = torch.empty(max(fa_batched_workspace_size(rasters, n_fields, opts), 1 << 20),
                               dtype=torch.uint8, device=dev)

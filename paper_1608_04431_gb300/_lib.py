@@ -24,6 +24,8 @@ FA_OUT_U32 = 0
 FA_OUT_F32 = 1
 FA_STATUS_WORDS = 4
 FA_OPT_NO_TMA = 1
+FA_CODES_BYTE = 0
+FA_CODES_NIBBLE = 1
 
 STATUS_NAMES = {
     FA_OK: "FA_OK", FA_WARN_OVERFLOW: "FA_WARN_OVERFLOW", FA_ERR_INVALID_ARG: "FA_ERR_INVALID_ARG",
@@ -36,7 +38,7 @@ STATUS_NAMES = {
 
 class fa_options(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("code_format", ctypes.c_int32)]
 
 
 FA_MAX_FIELDS = 16
@@ -71,6 +73,7 @@ SIGNATURES = {
     "fa_batched_plan_create": (_I32, [ctypes.POINTER(fa_raster), _I32, _I32, _P, _SZ, _OPT, _P,
                                       _P, ctypes.POINTER(ctypes.c_void_p)]),
     "fa_d8_codes": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P]),
+    "fa_recode": (_I32, [_P, _I64, _I64, _I64, _P, _P, _I64, _I32, _P]),
     "fa_autotune_workspace_size": (_SZ, [_I64, _I64, _OPT]),
     "fa_autotune": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I32, _I64, _P, _SZ,
                            _OPT, _P, _OPT]),

@@ -32,6 +32,7 @@ struct AdjArgs {
     int th, tw, tiles_x, pmax;
     const uint8_t *codes;
     int64_t pc;
+    int nib;  // codes packed two per byte: column c in byte c / 2, odd c high nibble
     const uint8_t *mask;
     int64_t pm;
     const float *g;
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(256) k_adj_tile(AdjArgs a) {
         const int64_t gr = R0 - 1 + hr, gc = C0 - 1 + hc;
         uint8_t e = 0;
         if (gr >= 0 && gr < a.rows && gc >= 0 && gc < a.cols) {
-            const uint8_t k = a.codes[gr * a.pc + gc];
+            const uint32_t k = a.nib ? ((uint32_t)a.codes[gr * a.pc + (gc >> 1)] >> ((gc & 1) << 2)) & 15u
+                                     : (uint32_t)a.codes[gr * a.pc + gc];
             const bool inside = hr >= 1 && hr <= h && hc >= 1 && hc <= w;
             if (k >= 1 && k <= 9 && !(a.mask && a.mask[gr * a.pm + gc]))
                 e = k | (inside ? 0 : HALO);
@@ -430,6 +432,7 @@ cudaError_t launch_adjoint(const Geom &g, const uint8_t *codes, int64_t pc, cons
     aa.pmax = g.pmax;
     aa.codes = codes;
     aa.pc = pc;
+    aa.nib = g.code_format == FA_CODES_NIBBLE;
     aa.mask = mask;
     aa.pm = pm;
     aa.g = gin;

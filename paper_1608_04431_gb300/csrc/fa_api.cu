@@ -89,7 +89,7 @@ extern "C" fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t c
     const bool empty = rows == 0 || cols == 0;
     if (!empty) {
         if (!codes || !out) return FA_ERR_INVALID_ARG;
-        if (pitch_codes < cols || pitch_out < cols) return FA_ERR_INVALID_ARG;
+        if (pitch_codes < code_row_bytes(cols, g.code_format) || pitch_out < cols) return FA_ERR_INVALID_ARG;
         if (weights && pitch_w < cols) return FA_ERR_INVALID_ARG;
         if (mask && pitch_mask < cols) return FA_ERR_INVALID_ARG;
         if (!aligned(out, 4) || (weights && !aligned(weights, 4))) return FA_ERR_INVALID_ARG;
@@ -139,7 +139,8 @@ extern "C" fa_status fa_accumulate_adjoint(const uint8_t *codes, int64_t rows, i
     const bool empty = rows == 0 || cols == 0;
     if (!empty) {
         if (!codes || !grad_out || !grad_w) return FA_ERR_INVALID_ARG;
-        if (pitch_codes < cols || pitch_g < cols || pitch_gw < cols) return FA_ERR_INVALID_ARG;
+        if (pitch_codes < code_row_bytes(cols, g.code_format) || pitch_g < cols || pitch_gw < cols)
+            return FA_ERR_INVALID_ARG;
         if (mask && pitch_mask < cols) return FA_ERR_INVALID_ARG;
         if (!aligned(grad_out, 4) || !aligned(grad_w, 4)) return FA_ERR_INVALID_ARG;
     }

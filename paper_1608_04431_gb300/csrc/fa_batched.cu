@@ -44,7 +44,8 @@ fa_status plan_batch(const fa_raster *rasters, int32_t n, int32_t k, const fa_op
         if (r.rows < 0 || r.cols < 0) return FA_ERR_INVALID_ARG;
         const bool empty = r.rows == 0 || r.cols == 0;
         if (!empty) {
-            if (!r.codes || r.pitch_codes < r.cols || r.pitch_out < r.cols) return FA_ERR_INVALID_ARG;
+            if (!r.codes || r.pitch_codes < code_row_bytes(r.cols, L.g.code_format) || r.pitch_out < r.cols)
+                return FA_ERR_INVALID_ARG;
             if (r.mask && r.pitch_mask < r.cols) return FA_ERR_INVALID_ARG;
             if (k > 0 && r.pitch_w < r.cols) return FA_ERR_INVALID_ARG;
         }

@@ -35,6 +35,7 @@ namespace fa {
 struct TileArgs {
     RasterDesc one;  // the raster of a single-raster call
     int th, tw, pmax;
+    int nib;  // codes packed two per byte (FA_CODES_NIBBLE)
     uint32_t *nexit;
     uint16_t *link;
     uint32_t *node_dst;
@@ -147,18 +148,32 @@ __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
 }
 
 
+// Code of raster column gc in a row of packed codes: low nibble for even
+// columns, high nibble for odd ones.
+__device__ __forceinline__ uint32_t nibble_at(const uint8_t *row, int64_t gc) {
+    return ((uint32_t)row[gc >> 1] >> ((gc & 1) << 2)) & 15u;
+}
+
+// Four packed codes (one 16-bit load) spread to one byte each.
+__device__ __forceinline__ uint32_t spread_nibbles(uint32_t hw) {
+    return (hw & 0xFu) | ((hw & 0xF0u) << 4) | ((hw & 0xF00u) << 8) | ((hw & 0xF000u) << 12);
+}
+
 // Load a tile's codes with a one-cell halo (Algorithm 1's F) into ec: valid
 // codes 1..9 as they are, NoData, masked, invalid and off-raster cells as 0,
 // bytes beyond the halo ring 0.  Each lane first issues the loads for up to
 // four rows (one 32-bit word of interior codes, or the single halo byte its
 // word holds), then converts and stores them, so several global loads are in
-// flight per lane.  Invalid codes inside the tile are counted.
+// flight per lane.  Invalid codes inside the tile are counted.  Packed codes
+// (nib) are spread to one byte per cell on the way.
 __device__ __forceinline__ void load_codes(const RasterDesc &ras, uint8_t *ec, int64_t R0, int64_t C0,
-                                           int h, int w, int S, bool count_bad, int &nbad,
+                                           int h, int w, int S, bool nib, bool count_bad, int &nbad,
                                            long long &fbad) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // bytes: 4-byte loads of four codes; packed: 2-byte loads of four codes
     const bool fast =
-        ((reinterpret_cast<uintptr_t>(ras.codes) | (uintptr_t)ras.pc | (uintptr_t)C0) & 3) == 0;
+        nib ? ((reinterpret_cast<uintptr_t>(ras.codes) | (uintptr_t)ras.pc) & 1) == 0 && (C0 & 3) == 0
+            : ((reinterpret_cast<uintptr_t>(ras.codes) | (uintptr_t)ras.pc | (uintptr_t)C0) & 3) == 0;
     const int words = S >> 2;
     constexpr int U = 4;
     for (int hr0 = warp; hr0 < h + 2; hr0 += U * nw) {
@@ -174,10 +189,19 @@ __device__ __forceinline__ void load_codes(const RasterDesc &ras, uint8_t *ec, i
                 if (hr >= h + 2 || wd >= words) continue;
                 const int64_t gr = R0 - 1 + hr;
                 if (gr < 0 || gr >= ras.rows) continue;
-                const uint8_t *row = ras.codes + gr * ras.pc + C0;
+                const uint8_t *prow = ras.codes + gr * ras.pc;  // packed: indexed by raster column
+                const uint8_t *row = prow + C0;
                 const uint8_t *mrow = ras.mask ? ras.mask + gr * ras.pm + C0 : nullptr;
                 if (c0 >= 0 && c0 + 3 < w) {
-                    if (fast) {
+                    if (nib) {
+                        const int64_t gc = C0 + c0;
+                        if (fast) {
+                            raw[u] = spread_nibbles(*reinterpret_cast<const uint16_t *>(prow + (gc >> 1)));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) raw[u] |= nibble_at(prow, gc + j) << (8 * j);
+                        }
+                    } else if (fast) {
                         raw[u] = *reinterpret_cast<const uint32_t *>(row + c0);
                     } else {
                         raw[u] = (uint32_t)row[c0] | ((uint32_t)row[c0 + 1] << 8) |
@@ -192,7 +216,7 @@ __device__ __forceinline__ void load_codes(const RasterDesc &ras, uint8_t *ec, i
                         const int c = c0 + j;
                         if (c < -1 || c > w) continue;
                         if (C0 + c < 0 || C0 + c >= ras.cols) continue;
-                        raw[u] |= (uint32_t)row[c] << (8 * j);
+                        raw[u] |= (nib ? nibble_at(prow, C0 + c) : (uint32_t)row[c]) << (8 * j);
                         if (mrow) mraw[u] |= (uint32_t)(mrow[c] ? 1 : 0) << (8 * j);
                     }
                 }
@@ -347,7 +371,7 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
             // valid and tell the halo ring by coordinates; invalid codes of
             // the tile are counted in the init pass
         } else {
-            load_codes(ras, ec, R0, C0, h, w, S, true, nbad, fbad);
+            load_codes(ras, ec, R0, C0, h, w, S, a.nib != 0, true, nbad, fbad);
         }
         __syncthreads();
 
@@ -1152,6 +1176,8 @@ bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g) {
     g.tiles_x = (int)((cols + tw - 1) / tw);
     g.pmax = 2 * th + 2 * tw;
     g.flags = opts ? opts->flags : 0;
+    g.code_format = opts ? opts->code_format : FA_CODES_BYTE;
+    if (g.code_format != FA_CODES_BYTE && g.code_format != FA_CODES_NIBBLE) return false;
     // node ids are tile * pmax + rank in 32 bits
     if ((double)g.tiles() * g.pmax >= 4.0e9) return false;
     return true;
@@ -1337,6 +1363,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     ta.th = g.th;
     ta.tw = g.tw;
     ta.pmax = g.pmax;
+    ta.nib = g.code_format == FA_CODES_NIBBLE;
     ta.nexit = ws.nexit;
     ta.link = ws.link;
     ta.node_dst = ws.node_dst;
@@ -1352,7 +1379,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     ta.inf_seg = ws.inf_seg;
 
     timing_mark(0, s);
-    const bool tma = !(g.flags & FA_OPT_NO_TMA) && ta.rtab == nullptr;
+    const bool tma = !(g.flags & FA_OPT_NO_TMA) && ta.rtab == nullptr && !ta.nib;
     e = val_mode ? launch_solve<1>(g, ta, tma_codes, tma_pc, tma_mask, tma, s)
                  : launch_solve<0>(g, ta, tma_codes, tma_pc, tma_mask, tma, s);
     if (e != cudaSuccess) return e;

@@ -18,8 +18,14 @@ struct Geom {
     int tiles_x, tiles_y;
     int pmax;            // per-tile slot capacity: 2*th + 2*tw >= perimeter cells
     int flags;           // FA_OPT_* from fa_options
+    int code_format;     // FA_CODES_BYTE or FA_CODES_NIBBLE
     int64_t tiles() const { return (int64_t)tiles_x * tiles_y; }
 };
+
+// Bytes a row of codes needs in a code format (the smallest valid pitch).
+inline int64_t code_row_bytes(int64_t cols, int code_format) {
+    return code_format == FA_CODES_NIBBLE ? (cols + 1) / 2 : cols;
+}
 
 bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g);
 

@@ -67,7 +67,7 @@ extern "C" fa_status fa_accumulate_noalloc(const uint8_t *codes, int64_t rows, i
     const bool empty = rows == 0 || cols == 0;
     if (!empty) {
         if (!codes || !out) return FA_ERR_INVALID_ARG;
-        if (pitch_codes < cols || pitch_out < cols) return FA_ERR_INVALID_ARG;
+        if (pitch_codes < code_row_bytes(cols, g.code_format) || pitch_out < cols) return FA_ERR_INVALID_ARG;
         if (weights && pitch_w < cols) return FA_ERR_INVALID_ARG;
         if (mask && pitch_mask < cols) return FA_ERR_INVALID_ARG;
         if (!aligned_to(out, 4) || (weights && !aligned_to(weights, 4))) return FA_ERR_INVALID_ARG;

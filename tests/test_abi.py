@@ -166,3 +166,58 @@ def test_d8_rejects_bad_args_without_gpu(lib):
     assert lib.fa_d8_codes(fake, 5, 5, 5, fake, 2, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
     assert lib.fa_d8_codes(fake + 2, 5, 5, 5, None, 0, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
     assert lib.fa_d8_codes(None, 0, 5, 5, None, 0, None, 5, None) == _lib.FA_OK  # empty
+
+
+def test_packed_codes_host_logic_without_gpu(lib):
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: validation fails first
+    nib = _lib.fa_options(0, 0, 0, _lib.FA_CODES_NIBBLE)
+    bad = _lib.fa_options(0, 0, 0, 2)  # unknown code format
+    assert lib.fa_workspace_size(100, 100, ctypes.byref(bad)) == 0
+    assert lib.fa_workspace_size(100, 100, ctypes.byref(nib)) == \
+        lib.fa_workspace_size(100, 100, ctypes.byref(_lib.fa_options()))
+    st = lib.fa_accumulate(fake, 10, 11, 11, None, 0, None, 0, fake, _lib.FA_OUT_U32, 11,
+                           fake, 1 << 30, ctypes.byref(bad), None, None)
+    assert st == _lib.FA_ERR_INVALID_ARG
+    # packed rows of 11 cells need 6 bytes: pitch 5 is short, 6 passes on to
+    # the workspace check
+    st = lib.fa_accumulate(fake, 10, 11, 5, None, 0, None, 0, fake, _lib.FA_OUT_U32, 11,
+                           fake, 16, ctypes.byref(nib), None, None)
+    assert st == _lib.FA_ERR_INVALID_ARG
+    st = lib.fa_accumulate(fake, 10, 11, 6, None, 0, None, 0, fake, _lib.FA_OUT_U32, 11,
+                           fake, 16, ctypes.byref(nib), None, None)
+    assert st == _lib.FA_ERR_WORKSPACE
+    st = lib.fa_accumulate_adjoint(fake, 10, 11, 5, None, 0, fake, 11, fake, 11, fake, 16,
+                                   ctypes.byref(nib), None, None)
+    assert st == _lib.FA_ERR_INVALID_ARG
+    st = lib.fa_accumulate_adjoint(fake, 10, 11, 6, None, 0, fake, 11, fake, 11, fake, 16,
+                                   ctypes.byref(nib), None, None)
+    assert st == _lib.FA_ERR_WORKSPACE
+    r = _raster(10, 11, 0, 1 << 20, pitch=11)
+    r.pitch_codes = 5
+    arr = (_lib.fa_raster * 1)(r)
+    assert lib.fa_batched_workspace_size(arr, 1, 0, ctypes.byref(nib)) == 0
+    arr[0].pitch_codes = 6
+    assert lib.fa_batched_workspace_size(arr, 1, 0, ctypes.byref(nib)) > 0
+    assert lib.fa_batched_workspace_size(arr, 1, 0, ctypes.byref(_lib.fa_options())) == 0
+
+
+def test_recode_rejects_bad_args_without_gpu(lib):
+    fake = 1 << 20  # never dereferenced
+    B, N = _lib.FA_CODES_BYTE, _lib.FA_CODES_NIBBLE
+    assert lib.fa_recode(fake, -1, 5, 5, None, fake, 5, B, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_recode(fake, 5, 5, 5, None, fake, 5, 2, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_recode(None, 5, 5, 5, None, fake, 5, B, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_recode(fake, 5, 5, 4, None, fake, 5, B, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_recode(fake, 5, 5, 5, None, fake, 4, B, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_recode(fake, 5, 5, 5, None, fake, 2, N, None) == _lib.FA_ERR_INVALID_ARG
+    assert lib.fa_recode(None, 0, 5, 5, None, None, 0, N, None) == _lib.FA_OK  # empty
+
+
+def test_power_of_two_table():
+    # typed from the scheme: E 1, SE 2, S 4, SW 8, W 16, NW 32, N 64, NE 128
+    import paper_1608_04431_gb300 as fa
+    t = fa.power_of_two_table()
+    want = {0: 0, 1: 1, 2: 8, 4: 7, 8: 6, 16: 5, 32: 4, 64: 3, 128: 2}
+    assert len(t) == 256
+    for v in range(256):
+        assert t[v] == want.get(v, 10)

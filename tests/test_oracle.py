@@ -358,3 +358,47 @@ def test_d8_matches_the_generator_on_integer_dems(oracle_mod, seed):
     z = g.integers(0, 60, size=(40, 57)).astype(np.float32)
     nd = (g.random(z.shape) < 0.05).astype(np.uint8)
     np.testing.assert_array_equal(oracle_mod.d8(z, nd), synth.d8_codes(z, nd.astype(bool)))
+
+
+# ---------------------------------------------------------------------------
+# Packed and foreign codes (input decoding in front of Eq. 1)
+# ---------------------------------------------------------------------------
+def test_unpack_nibbles_hand_example(oracle_mod):
+    # the 3x3 hand example with its codes packed by hand: row "8 7 6" is byte
+    # 0x78 (8 low, 7 high) then 0x06; rows "1 7 5" are 0x71, 0x05
+    g = _golden.load("hand_3x3.txt")
+    packed = np.array([[0x78, 0x06], [0x71, 0x05], [0x71, 0x05]], np.uint8)
+    codes = oracle_mod.unpack_nibbles(packed, 3)
+    np.testing.assert_array_equal(codes, g["codes"])
+    np.testing.assert_array_equal(oracle_mod.counts(codes).values, g["counts"])
+
+
+def test_unpack_nibble_order(oracle_mod):
+    # byte 0x91: cell 0 = 1 (E) into cell 1 = 9 (NoFlow), counts 1 and 2;
+    # swapped nibbles would read 9 then 1 and give 1 and 1
+    codes = oracle_mod.unpack_nibbles(np.array([[0x91]], np.uint8), 2)
+    np.testing.assert_array_equal(codes, [[1, 9]])
+    np.testing.assert_array_equal(oracle_mod.counts(codes).values, [[1, 2]])
+    # odd width: the last byte's high nibble lies beyond the row and is ignored
+    codes = oracle_mod.unpack_nibbles(np.array([[0x91, 0xF5]], np.uint8), 3)
+    np.testing.assert_array_equal(codes, [[1, 9, 5]])
+
+
+def test_unpacked_bad_nibbles_are_counted(oracle_mod):
+    # nibbles 10..15 are invalid codes, counted like invalid bytes
+    codes = oracle_mod.unpack_nibbles(np.array([[0xA1, 0x9F]], np.uint8), 4)
+    np.testing.assert_array_equal(codes, [[1, 10, 15, 9]])
+    assert oracle_mod.counts(codes).n_bad == 2
+
+
+def test_recode_power_of_two_hand_example(oracle_mod):
+    # the 3x3 hand example in the one-bit-per-direction scheme (E 1, SE 2, S 4,
+    # SW 8, W 16, NW 32, N 64, NE 128), with its table typed from that scheme
+    g = _golden.load("hand_3x3.txt")
+    foreign = np.array([[2, 4, 8], [1, 4, 16], [1, 4, 16]], np.uint8)
+    table = bytearray(256)
+    for bit, code in {1: 1, 2: 8, 4: 7, 8: 6, 16: 5, 32: 4, 64: 3, 128: 2}.items():
+        table[bit] = code
+    codes = oracle_mod.recode(foreign, table)
+    np.testing.assert_array_equal(codes, g["codes"])
+    np.testing.assert_array_equal(oracle_mod.counts(codes).values, g["counts"])
