@@ -98,9 +98,9 @@ typedef enum { FA_OUT_U32 = 0, FA_OUT_F32 = 1 } fa_out_dtype;
  * FA_ERR_INVALID_ARG.  Results do not depend on the tile shape, except for
  * the rounding of floating-point sums.
  * flags: FA_OPT_NO_TMA disables staging code tiles into shared memory with the
- * Tensor Memory Accelerator (used when the raster allows it: byte codes,
- * 16-byte aligned codes and pitch, tile width a multiple of 16, no mask
- * raster); results are identical either way.
+ * Tensor Memory Accelerator (used for single rasters when they allow it:
+ * 16-byte aligned codes and pitch, tile width a multiple of 16 (32 for packed
+ * codes), no mask raster); results are identical either way.
  * code_format: FA_CODES_BYTE (0, one byte per cell) or FA_CODES_NIBBLE (1, two
  * cells per byte; see the raster conventions above).  It applies to every
  * codes argument of the call (fa_accumulate, fa_accumulate_noalloc,

@@ -101,6 +101,21 @@ __host__ __device__ inline size_t code_buf_bytes(int th, int tw) {
     return (((size_t)(th + 2) * tile_stride(tw)) + 127) & ~size_t(127);
 }
 
+// Packed codes (two per byte) staged by TMA: the box starts PX0 cells (16
+// bytes) left of the tile, so that its first byte is a 16-byte column when the
+// tile width is a multiple of 32; byte b of a box row holds cells C0 - PX0 +
+// 2b and + 1.  A box row covers the S cells of a code-buffer row (which starts
+// X0 cells left of the tile): S / 2 + 8 bytes, rounded to 16.
+constexpr int PX0 = 32;
+__host__ __device__ inline int packed_box_bytes(int tw) { return ((tile_stride(tw) / 2 + 8 + 15) / 16) * 16; }
+__host__ __device__ inline size_t packed_buf_bytes(int th, int tw) {
+    return (((size_t)(th + 2) * packed_box_bytes(tw)) + 127) & ~size_t(127);
+}
+
+// How pass 1 gets its codes: plain loads, TMA-staged bytes, or TMA-staged
+// packed codes spread to bytes in shared memory.
+enum { LOAD_PLAIN = 0, LOAD_TMA = 1, LOAD_TMA_PACKED = 2 };
+
 // Row stride of the compact per-cell arrays (word, sums, claim tags): a
 // multiple of four so that a four-cell group is one 16-byte store.
 __host__ __device__ inline int cell_stride(int tw) { return (tw + 3) & ~3; }
@@ -118,10 +133,12 @@ __host__ __device__ inline int jump_threads(int th, int tw) {
 }
 __host__ __device__ inline int solve_threads(int th, int tw) { return jump_threads(th, tw); }
 
-__host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm, bool tma) {
+__host__ __device__ inline size_t solve_smem_bytes(int th, int tw, int valm, int load) {
     const size_t nc = (size_t)th * cell_stride(tw), pm = (size_t)(2 * th + 2 * tw);
     size_t b = 128;                           // alignment slack of the dynamic window
-    b += code_buf_bytes(th, tw) * (tma ? 2 : 1);  // effective codes (two TMA stages)
+    // codes: one buffer; two TMA stages; or two packed stages and one buffer
+    b += load == LOAD_TMA_PACKED ? 2 * packed_buf_bytes(th, tw) + code_buf_bytes(th, tw)
+                                 : code_buf_bytes(th, tw) * (load == LOAD_TMA ? 2 : 1);
     b += nc * (valm ? 16 : 4);                // value and round inflow per cell
     b += nc * 2;                              // successor (jump pointer) per cell
     b += pm * 4;                              // segment -> where it joins another
@@ -143,7 +160,7 @@ __host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
 __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
     return (int64_t)(th + 2) * tile_stride(tw) <= 65535 && (int64_t)th * tw <= 16384 &&
            (int64_t)th * cell_stride(tw) <= 16384 &&
-           solve_smem_bytes(th, tw, valm, false) <= 227 * 1024 &&
+           solve_smem_bytes(th, tw, valm, LOAD_PLAIN) <= 227 * 1024 &&
            offsets_smem_bytes(th, tw) <= 227 * 1024;
 }
 
@@ -260,7 +277,9 @@ __device__ __forceinline__ bool vcode(uint32_t b) { return b - 1u < 9u; }
 // Persistent CTAs: each block solves tiles t = blockIdx.x, + gridDim.x, ...
 // With TMA the codes of tile t + gridDim.x (box of S x (th+2) bytes at column
 // C0 - X0, row R0 - 1; outside the raster reads as 0 = NoData) are staged into
-// the other shared buffer while tile t is solved.
+// the other shared buffer while tile t is solved.  Packed codes are staged the
+// same way (half as many bytes) and spread to one byte per cell when their
+// tile begins.
 //
 // Besides A_loc and the perimeter records (Algorithms 1 and 2) a tile records
 // its entry forest for pass 2: the cells on the in-tile paths downstream of
@@ -273,7 +292,7 @@ constexpr uint16_t NO_ENTRY = 0xFFFFu;
 
 // A block of solve_threads(tile) threads (up to 1024), each owning at most KG
 // four-cell groups of the compact arrays during the jump rounds.
-template <int VALM, bool TMA>
+template <int VALM, int TMA>
 __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constant__ CUtensorMap tmap) {
     typedef typename std::conditional<VALM == 0, uint32_t, long long>::type PV;
     const TileArgs &a = A;
@@ -291,14 +310,18 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
     const int NC = a.th * WS;
     const int64_t T = a.T;
 
-    // shared layout: code buffers (two with TMA, each 128-byte aligned for the
-    // bulk copies), then the per-cell arrays
+    // shared layout: code buffers (two TMA stages, each 128-byte aligned for
+    // the bulk copies; packed: two packed stages and the spread buffer), then
+    // the per-cell arrays
     const size_t CB = code_buf_bytes(a.th, a.tw);
+    const size_t STG = TMA == LOAD_TMA_PACKED ? packed_buf_bytes(a.th, a.tw) : CB;
+    const int PB = packed_box_bytes(a.tw);
     uint8_t *base128 = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem) + 127) &
                                                    ~uintptr_t(127));
     uint8_t *cbuf0 = base128;
-    uint8_t *cbuf1 = base128 + (TMA ? CB : 0);
-    uint8_t *cells = base128 + (TMA ? 2 : 1) * CB;
+    uint8_t *cbuf1 = base128 + (TMA ? STG : 0);
+    uint8_t *spread = base128 + 2 * STG;  // packed: the codes of the current tile, one byte each
+    uint8_t *cells = base128 + (TMA == LOAD_TMA_PACKED ? 2 * STG + CB : (TMA ? 2 : 1) * CB);
     // counts: per cell its value x (low 16 bits) and the inflow of the current
     // jump round (high 16 bits); weights: 64-bit fixed-point x and inflow
     uint32_t *xd = reinterpret_cast<uint32_t *>(cells);
@@ -329,8 +352,13 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
     __syncthreads();
     auto issue = [&](int tn, int bb) {  // one thread: stage tile tn's codes into buffer bb
         const int tyn = tn / A.one.tiles_x, txn = tn - tyn * A.one.tiles_x;  // TMA: one raster only
-        mbar_expect_tx(&s_bar[bb], (uint32_t)NB);
-        tma_load_2d(bb ? cbuf1 : cbuf0, &tmap, txn * a.tw - X0, tyn * a.th - 1, &s_bar[bb]);
+        if constexpr (TMA == LOAD_TMA_PACKED) {  // x in bytes: (C0 - PX0) / 2, a multiple of 16
+            mbar_expect_tx(&s_bar[bb], (uint32_t)((a.th + 2) * PB));
+            tma_load_2d(bb ? cbuf1 : cbuf0, &tmap, (txn * a.tw - PX0) / 2, tyn * a.th - 1, &s_bar[bb]);
+        } else {
+            mbar_expect_tx(&s_bar[bb], (uint32_t)NB);
+            tma_load_2d(bb ? cbuf1 : cbuf0, &tmap, txn * a.tw - X0, tyn * a.th - 1, &s_bar[bb]);
+        }
     };
     if (TMA && tid == 0 && blockIdx.x < T) issue(blockIdx.x, 0);
 
@@ -346,7 +374,7 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
         const int P = perim_count(h, w);
         const size_t tbase = (size_t)t * a.pmax;
         const size_t efb = (size_t)t * a.th * a.tw, infb = (size_t)t * (a.pmax + 8);
-        uint8_t *ec = (TMA && (it & 1)) ? cbuf1 : cbuf0;
+        uint8_t *ec = TMA == LOAD_TMA_PACKED ? spread : ((TMA && (it & 1)) ? cbuf1 : cbuf0);
         if (tid == 0) {
             s_nent = 0;
             s_maxw = 0;
@@ -370,6 +398,22 @@ __global__ void __launch_bounds__(1024) k_solve(TileArgs A, const __grid_constan
             // the staged box holds raw codes: readers take bytes 1..9 as
             // valid and tell the halo ring by coordinates; invalid codes of
             // the tile are counted in the init pass
+            if constexpr (TMA == LOAD_TMA_PACKED) {
+                // spread the packed box to one byte per cell: code-buffer word
+                // wd (cells C0 - X0 + 4wd ..) is box bytes 2wd + 8 and 2wd + 9.
+                // Cells right of the raster are NoData, the spare high nibble
+                // of an odd-width row included (left of it and above or below
+                // it the box already reads 0).
+                const uint8_t *stg = (it & 1) ? cbuf1 : cbuf0;
+                const int W4 = S >> 2;
+                for (int i = tid; i < (a.th + 2) * W4; i += nt) {
+                    const int hr = i / W4, wd = i - hr * W4;
+                    uint32_t v = spread_nibbles(*reinterpret_cast<const uint16_t *>(stg + hr * PB + 2 * wd + 8));
+                    const int64_t keep = ras.cols - (C0 - X0 + 4 * wd);  // cells of the word inside
+                    if (keep < 4) v = keep <= 0 ? 0u : (v & ((1u << (8 * keep)) - 1u));
+                    reinterpret_cast<uint32_t *>(spread + hr * S)[wd] = v;
+                }
+            }
         } else {
             load_codes(ras, ec, R0, C0, h, w, S, a.nib != 0, true, nbad, fbad);
         }
@@ -1251,17 +1295,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 // TMA staging of code tiles: a 2-D uint8 map over the raster with a box of
 // tile_stride(tw) x (th + 2) bytes.  Needs a 16-byte aligned base and pitch,
 // a tile width that is a multiple of 16 (so every box starts on a 16-byte
-// column), box sides <= 256 and no separate mask raster.
+// column), box sides <= 256 and no separate mask raster.  Packed codes: a map
+// over the (cols + 1) / 2 bytes of each row with a box of
+// packed_box_bytes(tw) x (th + 2) bytes; the tile width must be a multiple of
+// 32 so that every box starts on a 16-byte column ((C0 - PX0) / 2 bytes).
 static bool make_code_map(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,
-                          CUtensorMap *m) {
+                          bool packed, CUtensorMap *m) {
     if (mask || !codes) return false;
-    if (((uintptr_t)codes & 15) || (pc & 15) || (g.tw & 15)) return false;
-    const int S = tile_stride(g.tw);
+    if (((uintptr_t)codes & 15) || (pc & 15) || (g.tw & (packed ? 31 : 15))) return false;
+    const int S = packed ? packed_box_bytes(g.tw) : tile_stride(g.tw);
     if (S > 256 || g.th + 2 > 256) return false;
     if (g.cols >= (int64_t(1) << 31) || g.rows >= (int64_t(1) << 31)) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
     if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)g.cols, (cuuint64_t)g.rows};
+    cuuint64_t dims[2] = {(cuuint64_t)code_row_bytes(g.cols, packed ? FA_CODES_NIBBLE : FA_CODES_BYTE),
+                          (cuuint64_t)g.rows};
     cuuint64_t strides[1] = {(cuuint64_t)pc};
     cuuint32_t box[2] = {(cuuint32_t)S, (cuuint32_t)(g.th + 2)};
     cuuint32_t es[2] = {1, 1};
@@ -1283,7 +1331,7 @@ static int sm_count() {
 
 // Shared-memory limit and blocks per SM of k_solve<VALM, TMA> for a tile shape
 // (set and queried once per shape).
-template <int VALM, bool TMA>
+template <int VALM, int TMA>
 static cudaError_t solve_config(const Geom &g, int &blocks_per_sm) {
     static int configured = 0;
     static int per_sm = 0, per_sm_smem = -1, per_sm_nt = -1;
@@ -1308,7 +1356,7 @@ static cudaError_t offsets_config(const Geom &g) {
     return set_smem(k_offsets<VALM>, offsets_smem_bytes(g.th, g.tw), configured);
 }
 
-template <int VALM, bool TMA>
+template <int VALM, int TMA>
 static cudaError_t launch_solve_k(const Geom &g, const TileArgs &ta, const CUtensorMap &m,
                                   cudaStream_t s) {
     int per_sm = 1;
@@ -1324,10 +1372,13 @@ static cudaError_t launch_solve(const Geom &g, const TileArgs &ta, const uint8_t
                                 int64_t pc, const uint8_t *mask, bool allow_tma, cudaStream_t s) {
     CUtensorMap m;
     std::memset(&m, 0, sizeof(m));
-    if (allow_tma && solve_smem_bytes(g.th, g.tw, VALM, true) <= 227 * 1024 &&
-        make_code_map(g, codes, pc, mask, &m))
-        return launch_solve_k<VALM, true>(g, ta, m, s);
-    return launch_solve_k<VALM, false>(g, ta, m, s);
+    const bool packed = g.code_format == FA_CODES_NIBBLE;
+    const int mode = packed ? LOAD_TMA_PACKED : LOAD_TMA;
+    if (allow_tma && solve_smem_bytes(g.th, g.tw, VALM, mode) <= 227 * 1024 &&
+        make_code_map(g, codes, pc, mask, packed, &m))
+        return packed ? launch_solve_k<VALM, LOAD_TMA_PACKED>(g, ta, m, s)
+                      : launch_solve_k<VALM, LOAD_TMA>(g, ta, m, s);
+    return launch_solve_k<VALM, LOAD_PLAIN>(g, ta, m, s);
 }
 
 template <int VALM>
@@ -1343,7 +1394,7 @@ static cudaError_t launch_offsets(const Geom &g, const TileArgs &ta, cudaStream_
 // never stage codes by TMA.
 cudaError_t prepare_forward(const Geom &g, int val_mode) {
     int per_sm = 1;
-    cudaError_t e = val_mode ? solve_config<1, false>(g, per_sm) : solve_config<0, false>(g, per_sm);
+    cudaError_t e = val_mode ? solve_config<1, LOAD_PLAIN>(g, per_sm) : solve_config<0, LOAD_PLAIN>(g, per_sm);
     if (e == cudaSuccess) e = val_mode ? offsets_config<1>(g) : offsets_config<0>(g);
     sm_count();
     return e;
@@ -1379,7 +1430,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     ta.inf_seg = ws.inf_seg;
 
     timing_mark(0, s);
-    const bool tma = !(g.flags & FA_OPT_NO_TMA) && ta.rtab == nullptr && !ta.nib;
+    const bool tma = !(g.flags & FA_OPT_NO_TMA) && ta.rtab == nullptr;
     e = val_mode ? launch_solve<1>(g, ta, tma_codes, tma_pc, tma_mask, tma, s)
                  : launch_solve<0>(g, ta, tma_codes, tma_pc, tma_mask, tma, s);
     if (e != cudaSuccess) return e;

@@ -97,8 +97,9 @@ def test_packed_random_with_cycles(oracle_mod, seed, R, C, tile, pitch):
 @pytest.mark.parametrize("R,C,tile", [(1000, 1000, None), (777, 1301, (64, 128)), (513, 640, (32, 64)),
                                       (300, 299, (96, 64))])
 def test_packed_dem_matches_bytes_and_oracle(oracle_mod, R, C, tile):
-    # byte codes take the TMA-staged path where the raster allows it, packed
-    # codes the plain loads: both must agree with the oracle bit for bit
+    # either form takes the TMA-staged path where the raster allows it (for
+    # packed rows: a 16-byte pitch, here only 640 columns), else plain loads:
+    # both must agree with the oracle bit for bit
     codes = synth.dem_codes(R, C, 81)
     ref = oracle_mod.counts(codes)
     pk = packed_dev(codes)
@@ -238,3 +239,34 @@ def test_packed_dem_16384(oracle_mod):
     assert status()[0] == fa.FA_OK
     ref = oracle_mod.counts(oracle_mod.unpack_nibbles(pk.data.cpu().numpy(), 16384))
     np.testing.assert_array_equal(got, ref.values.astype(np.uint32))
+
+
+@pytest.mark.parametrize("R,C,pitch,tile", [(1024, 2048, 1024, None), (1000, 1001, 512, (64, 64)),
+                                            (333, 517, 272, (32, 64)), (129, 260, 144, (16, 32)),
+                                            (700, 301, 160, (96, 96)), (64, 8191, 4096, (64, 128)),
+                                            (97, 63, 48, (128, 32))])
+def test_packed_tma_and_plain_loads_agree(oracle_mod, R, C, pitch, tile):
+    """Packed rows with a 16-byte pitch and tile widths that are multiples of
+    32 are staged by TMA; the result must equal the plain loads, the byte
+    codes and the oracle.  The spare high nibble of an odd-width row holds a
+    valid code (W, which would flow into the row's last cell) and the pitch
+    padding holds garbage: neither may be read as a cell."""
+    codes = synth.dem_codes(R, C, 131)
+    p = pack(codes, pitch)
+    if C % 2:
+        p[:, C // 2] |= 5 << 4
+    p[:, (C + 1) // 2:] = 0x55
+    ref = oracle_mod.counts(oracle_mod.unpack_nibbles(p[:, :(C + 1) // 2], C))
+    t = dev(p)
+    pk = fa.PackedCodes(t[:, :(C + 1) // 2], C)
+    a = to_np(fa.accumulate(pk, tile=tile))
+    assert status()[0] == fa.FA_OK
+    b = to_np(fa.accumulate(pk, tile=tile, flags=fa.FA_OPT_NO_TMA))
+    c = to_np(fa.accumulate(dev(codes), tile=tile))
+    np.testing.assert_array_equal(a, ref.values.astype(np.uint32))
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+    w = dev(synth.uniform_weights((R, C), 132))
+    fw = to_np(fa.accumulate(pk, w, tile=tile))
+    gw = to_np(fa.accumulate(pk, w, tile=tile, flags=fa.FA_OPT_NO_TMA))
+    np.testing.assert_array_equal(fw, gw)
