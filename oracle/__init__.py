@@ -49,26 +49,31 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _configure(lib):
+    """Declares the argument and result types of the oracle's C functions on a
+    loaded copy of the library and returns it."""
+    i64, p = ctypes.c_int64, ctypes.c_void_p
+    pi64 = ctypes.POINTER(ctypes.c_int64)
+    lib.fa_oracle_counts.argtypes = [p, i64, i64, i64, p, i64, p, p, pi64, pi64]
+    lib.fa_oracle_counts.restype = ctypes.c_int
+    lib.fa_oracle_weighted.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p, pi64, pi64]
+    lib.fa_oracle_weighted.restype = ctypes.c_int
+    lib.fa_oracle_adjoint.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p, pi64, pi64]
+    lib.fa_oracle_adjoint.restype = ctypes.c_int
+    lib.fa_oracle_d8.argtypes = [p, i64, i64, i64, p, i64, p]
+    lib.fa_oracle_d8.restype = ctypes.c_int
+    lib.fa_oracle_bruteforce.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p]
+    lib.fa_oracle_bruteforce.restype = ctypes.c_int
+    lib.fa_oracle_residual_u32.argtypes = [p, i64, i64, i64, p, i64, p, i64, pi64]
+    lib.fa_oracle_residual_u32.restype = ctypes.c_int64
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        i64, p = ctypes.c_int64, ctypes.c_void_p
-        pi64 = ctypes.POINTER(ctypes.c_int64)
-        lib.fa_oracle_counts.argtypes = [p, i64, i64, i64, p, i64, p, p, pi64, pi64]
-        lib.fa_oracle_counts.restype = ctypes.c_int
-        lib.fa_oracle_weighted.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p, pi64, pi64]
-        lib.fa_oracle_weighted.restype = ctypes.c_int
-        lib.fa_oracle_adjoint.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p, pi64, pi64]
-        lib.fa_oracle_adjoint.restype = ctypes.c_int
-        lib.fa_oracle_d8.argtypes = [p, i64, i64, i64, p, i64, p]
-        lib.fa_oracle_d8.restype = ctypes.c_int
-        lib.fa_oracle_bruteforce.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p]
-        lib.fa_oracle_bruteforce.restype = ctypes.c_int
-        lib.fa_oracle_residual_u32.argtypes = [p, i64, i64, i64, p, i64, p, i64, pi64]
-        lib.fa_oracle_residual_u32.restype = ctypes.c_int64
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(_LIB))
     return _lib
 
 

@@ -194,9 +194,13 @@ def test_bruteforce_random_with_cycles(oracle_mod, seed, R, C):
     cnt_expect, _ = py_walk(codes, None, mask)
     rc = oracle_mod.counts(codes, mask)
     np.testing.assert_array_equal(rc.values[ok], cnt_expect[ok].astype(np.uint64))
-    # the C brute-force walker agrees with the Python one on exact cells
+    # the C brute-force walker agrees with the Python one on exact cells, with
+    # weights and with unit weights, and finds the same cycle cells
     bf = oracle_mod.bruteforce(codes, w, mask)
     np.testing.assert_allclose(bf.values[ok], expect[ok], rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(bf.state == 2, cyc)
+    bfc = oracle_mod.bruteforce(codes, None, mask)
+    np.testing.assert_array_equal(bfc.values[ok], cnt_expect[ok])
 
 
 def test_mask_equals_nodata_code(oracle_mod):
