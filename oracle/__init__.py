@@ -8,6 +8,8 @@ gcc) plus the numpy marshalling below.
 Functions (all on numpy arrays, row-major, row 0 = north):
   counts(codes, mask)            -> uint64 upslope counts (Eq. 1, w = 1)
   weighted(codes, w, mask)       -> FP64 weighted accumulation (Eq. 1)
+  absorb(codes, a, w, mask)      -> FP64 accumulation with absorption (Eq. 1,
+                                    alpha = a(n) in [0, 1] towards d(n))
   adjoint(codes, g, mask)        -> FP64 lam = (I - P)^-T g (downstream path sums)
   bruteforce(codes, w, mask)     -> FP64 path-walking sums straight from the
                                     definition (small rasters only)
@@ -60,6 +62,8 @@ def _configure(lib):
     lib.fa_oracle_weighted.restype = ctypes.c_int
     lib.fa_oracle_adjoint.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p, pi64, pi64]
     lib.fa_oracle_adjoint.restype = ctypes.c_int
+    lib.fa_oracle_absorb.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, i64, p, p, pi64, pi64]
+    lib.fa_oracle_absorb.restype = ctypes.c_int
     lib.fa_oracle_d8.argtypes = [p, i64, i64, i64, p, i64, p]
     lib.fa_oracle_d8.restype = ctypes.c_int
     lib.fa_oracle_bruteforce.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, p]
@@ -126,6 +130,29 @@ def weighted(codes, w, mask=None) -> Result:
     nc, nb = ctypes.c_int64(0), ctypes.c_int64(0)
     rc = _load().fa_oracle_weighted(_p(codes), R, C, C, _p(mask), C, _p(w), C, _p(out), _p(st),
                                     ctypes.byref(nc), ctypes.byref(nb))
+    if rc:
+        raise MemoryError("oracle: allocation failed")
+    return Result(out, st, nc.value, nb.value)
+
+
+def absorb(codes, a, w=None, mask=None) -> Result:
+    """Accumulation with absorption in FP64: A(p) = w(p) + sum of a(n) A(n)
+    over the cells n draining into p; a: float32 factors in [0, 1]; w: float32
+    weights or None (unit)."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.shape != codes.shape:
+        raise ValueError("a shape differs from codes")
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if w.shape != codes.shape:
+            raise ValueError("weights shape differs from codes")
+    out = np.empty((R, C), dtype=np.float64)
+    st = np.empty((R, C), dtype=np.uint8)
+    nc, nb = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = _load().fa_oracle_absorb(_p(codes), R, C, C, _p(mask), C, _p(w), C, _p(a), C, _p(out),
+                                  _p(st), ctypes.byref(nc), ctypes.byref(nb))
     if rc:
         raise MemoryError("oracle: allocation failed")
     return Result(out, st, nc.value, nb.value)

@@ -160,6 +160,39 @@ int fa_oracle_weighted(const uint8_t *codes, int64_t rows, int64_t cols, int64_t
 }
 
 /*
+ * Accumulation with absorption: Eq. 1 with alpha(n, p) = a(n) for the one
+ * downstream cell p of n (and 0 elsewhere), a(n) in [0, 1] -- Section 2 lets
+ * flow be absorbed on its way downhill but never increased, so the share a
+ * cell passes on is at most what it holds:
+ *     A(p) = w(p) + sum over n with d(n) = p of a(n) A(n).
+ * Same Kahn order as fa_oracle_weighted (FP64); w NULL means unit weights.
+ * a(n) of a cell without a downstream cell is never used.
+ */
+int fa_oracle_absorb(const uint8_t *codes, int64_t rows, int64_t cols, int64_t pitch,
+                     const uint8_t *mask, int64_t mpitch, const float *w, int64_t wpitch,
+                     const float *a, int64_t apitch, double *out, uint8_t *state,
+                     int64_t *n_cycle, int64_t *n_bad) {
+    raster R = {codes, mask, rows, cols, pitch, mpitch};
+    int64_t n = rows * cols;
+    int64_t *next = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    uint8_t *deg = (uint8_t *)malloc((size_t)(n ? n : 1));
+    if (!next || !order || !deg) { free(next); free(order); free(deg); return -1; }
+    int64_t nv;
+    int64_t popped = kahn_order(&R, next, order, deg, n_bad, &nv);
+    memset(out, 0, (size_t)n * sizeof(double));
+    for (int64_t j = 0; j < popped; ++j) {
+        int64_t c = order[j];
+        int64_t r = c / cols, cc = c % cols;
+        out[c] += w ? (double)w[r * wpitch + cc] : 1.0;
+        if (next[c] >= 0) out[next[c]] += (double)a[r * apitch + cc] * out[c];
+    }
+    fill_state(n, next, order, popped, state, n_cycle);
+    free(next); free(order); free(deg);
+    return 0;
+}
+
+/*
  * Transpose product (the adjoint of Eq. 1 with alpha in {0,1}): with
  * A = (I - P)^-1 w, the gradient of <g, A> with respect to w is
  * lam = (I - P)^-T g, i.e. lam(c) = g(c) + lam(d(c)), the sum of g along c's

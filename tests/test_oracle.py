@@ -406,3 +406,104 @@ def test_recode_power_of_two_hand_example(oracle_mod):
     codes = oracle_mod.recode(foreign, table)
     np.testing.assert_array_equal(codes, g["codes"])
     np.testing.assert_array_equal(oracle_mod.counts(codes).values, g["counts"])
+
+
+# ---------------------------------------------------------------------------
+# Absorption (Eq. 1 with alpha(n, d(n)) = a(n) in [0, 1])
+# ---------------------------------------------------------------------------
+def py_walk_absorb(codes, a, w=None, mask=None):
+    """Definition by path walking (pure Python): each valid cell y adds w(y)
+    times the product of a over the cells it has left behind to every cell on
+    its downstream path.  Returns (values, on_cycle)."""
+    R, C = codes.shape
+    out = np.zeros((R, C))
+    _, cyc = py_walk(codes, None, mask)
+    for r in range(R):
+        for c in range(C):
+            if not _valid(codes, mask, r, c) or cyc[r, c]:
+                continue
+            share = 1.0 if w is None else float(w[r, c])
+            cur, steps = (r, c), 0
+            while cur is not None and steps <= R * C:
+                out[cur] += share
+                share *= float(a[cur])
+                cur = _down(codes, mask, *cur)
+                steps += 1
+    return out, cyc
+
+
+def test_absorb_hand_example(oracle_mod):
+    # the 3x3 hand example with half of every cell's flow passed on: the centre
+    # gets 1 + 0.5 * (five unit cells) = 3.5; the bottom centre gets
+    # 1 + 0.5 * (3.5 + 1 + 1) = 3.75.  With weights 1..9 the centre gets
+    # 5 + 0.5 * (1 + 2 + 3 + 4 + 6) = 13 and the bottom centre
+    # 8 + 0.5 * (13 + 7 + 9) = 22.5
+    g = _golden.load("hand_3x3.txt")
+    half = np.full((3, 3), 0.5, np.float32)
+    np.testing.assert_array_equal(oracle_mod.absorb(g["codes"], half).values,
+                                  [[1, 1, 1], [1, 3.5, 1], [1, 3.75, 1]])
+    np.testing.assert_array_equal(oracle_mod.absorb(g["codes"], half, g["weights"]).values,
+                                  [[1, 2, 3], [4, 13, 6], [7, 22.5, 9]])
+
+
+def test_absorb_special_factors(oracle_mod):
+    codes = synth.random_codes(40, 53, 61)
+    mask = (synth.rng(62).random(codes.shape) < 0.03).astype(np.uint8)
+    w = synth.uniform_weights(codes.shape, 63)
+    # nothing absorbed: plain accumulation
+    one = oracle_mod.absorb(codes, np.ones(codes.shape, np.float32), w, mask)
+    ref = oracle_mod.weighted(codes, w, mask)
+    ok = ref.state == 1
+    np.testing.assert_array_equal(one.state, ref.state)
+    np.testing.assert_array_equal(one.values[ok], ref.values[ok])
+    cnt = oracle_mod.absorb(codes, np.ones(codes.shape, np.float32), None, mask)
+    np.testing.assert_array_equal(cnt.values[ok], oracle_mod.counts(codes, mask).values[ok])
+    # everything absorbed: each cell keeps its own weight
+    zero = oracle_mod.absorb(codes, np.zeros(codes.shape, np.float32), w, mask)
+    np.testing.assert_array_equal(zero.values[ok], w[ok].astype(np.float64))
+    assert (zero.values[ref.state == 0] == 0).all()
+
+
+@pytest.mark.parametrize("a", [0.25, 0.9, 0.999])
+def test_absorb_geometric_row(oracle_mod, a):
+    # one row draining east with a constant factor: A(c) = 1 + a + ... + a^c
+    C = 300
+    codes = np.ones((1, C), np.uint8)
+    got = oracle_mod.absorb(codes, np.full((1, C), a, np.float32)).values[0]
+    af = float(np.float32(a))
+    want = (1.0 - af ** (np.arange(C) + 1.0)) / (1.0 - af)
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("seed,R,C", [(71, 17, 23), (72, 40, 40), (73, 1, 60), (74, 33, 9)])
+def test_absorb_bruteforce(oracle_mod, seed, R, C):
+    codes = synth.random_codes(R, C, seed)
+    mask = (synth.rng(seed + 5).random((R, C)) < 0.03).astype(np.uint8)
+    a = synth.uniform_weights((R, C), seed + 6)
+    w = synth.lognormal_weights((R, C), seed + 7)
+    expect, cyc = py_walk_absorb(codes, a, w, mask)
+    res = oracle_mod.absorb(codes, a, w, mask)
+    np.testing.assert_array_equal(res.state == 2, cyc)
+    ok = res.state == 1
+    np.testing.assert_allclose(res.values[ok], expect[ok], rtol=1e-12, atol=1e-300)
+
+
+def test_absorb_residual_on_a_dem(oracle_mod):
+    # Eq. 1 cell by cell: A(p) - w(p) - sum of a(n) A(n) over n draining into p
+    codes = synth.dem_codes(120, 97, 75)
+    a = synth.uniform_weights(codes.shape, 76, 0.5, 1.0)
+    w = synth.uniform_weights(codes.shape, 77)
+    A = oracle_mod.absorb(codes, a, w).values
+    R, C = codes.shape
+    resid = np.zeros((R, C))
+    for r in range(R):
+        for c in range(C):
+            if not _valid(codes, None, r, c):
+                continue
+            s = A[r, c] - w[r, c]
+            for k, (dr, dc) in STEP.items():
+                rr, cc = r - dr, c - dc  # the neighbour that would step onto (r, c)
+                if _valid(codes, None, rr, cc) and int(codes[rr, cc]) == k:
+                    s -= float(a[rr, cc]) * A[rr, cc]
+            resid[r, c] = abs(s) / max(A[r, c], 1.0)
+    assert resid.max() < 1e-12

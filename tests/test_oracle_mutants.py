@@ -85,6 +85,15 @@ C_MUTANTS = {
         "        double wy = w ? (double)w[r * wpitch + c] : 2.0;"),
     "residual check: the cell's own unit left out": (
         "                expect = 1u;", "                expect = 0u;"),
+    "absorption: the receiving cell's factor": (
+        "out[next[c]] += (double)a[r * apitch + cc] * out[c];",
+        "out[next[c]] += (double)a[next[c]] * out[c];"),
+    "absorption: factor ignored": (
+        "out[next[c]] += (double)a[r * apitch + cc] * out[c];",
+        "out[next[c]] += out[c];"),
+    "absorption: own weight absorbed too": (
+        "        out[c] += w ? (double)w[r * wpitch + cc] : 1.0;",
+        "        out[c] += (w ? (double)w[r * wpitch + cc] : 1.0) * (double)a[r * apitch + cc];"),
     "D8: ties go to the later direction": (
         "                if (slope > best) {", "                if (slope >= best) {"),
     "D8: no distance factor on diagonals": (
