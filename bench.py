@@ -49,6 +49,8 @@ SEED, WSEED = 201, 202
 TILE = (64, 64)
 BYTES_PER_CELL_COUNTS = 5  # 1 B code read + 4 B uint32 written (algorithmic minimum)
 BYTES_PER_CELL_F32 = 9     # + 4 B float32 weight read
+BYTES_PER_CELL_ABSORB = 13  # + 4 B float32 factor read
+ASEED = 205                 # absorption factors, U[0.9, 1)
 WORKLOAD = "d8_dem_16384x16384"
 BATCH_N, BATCH_FIELDS, BATCH_SEED, BATCH_SHAPE_SEED = 64, 8, 301, 300
 ADJ_N, ADJ_SEED, ADJ_GAUGES = 8192, 401, 256
@@ -387,6 +389,51 @@ def leg_adjoint(fa, dev, stream, opts, warmup, reps):
             "status": int(st), "dot_identity_rel_err": abs(lhs - rhs) / max(abs(lhs), 1e-30)}
 
 
+def leg_absorb(fa, dev, stream, codes_d, ms_f32, cells, warmup, reps, peak):
+    """Accumulation with absorption on the bench raster: weights U[0, 1)
+    and factors U[0.9, 1) drawn on the device with seeded generators; time
+    per step, phases, and the HBM fraction at 13 B/cell (1 B code, 4 B weight,
+    4 B factor read, 4 B float32 written)."""
+    import torch
+
+    g = torch.Generator(device=dev)
+    g.manual_seed(WSEED)
+    w = torch.rand(codes_d.shape, generator=g, device=dev, dtype=torch.float32)
+    g.manual_seed(ASEED)
+    a = torch.rand(codes_d.shape, generator=g, device=dev, dtype=torch.float32) * 0.1 + 0.9
+    a.clamp_(max=1.0)
+    out = torch.empty(codes_d.shape, dtype=torch.float32, device=dev)
+    opts = fa.options(TILE)
+    work = torch.empty(fa.fa_absorb_workspace_size(*codes_d.shape, opts), dtype=torch.uint8,
+                       device=dev)
+
+    def step():
+        s = fa.fa_accumulate_absorb(codes_d, w, a, None, out, work, opts, None, stream)
+        if s != fa.FA_OK:
+            raise fa.FlowAccError(s, "fa_accumulate_absorb")
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    st = fa.fa_status_read(None, work, stream)
+    ms = _time(step, stream, reps)
+    fa.fa_timing_enable(True)
+    ph = []
+    for _ in range(3):
+        step()
+        ph.append(fa.fa_timing_read())
+    fa.fa_timing_enable(False)
+    ph = np.mean(np.array(ph), axis=0).tolist()
+    gbs = cells * BYTES_PER_CELL_ABSORB / (ms / 1e3) / 1e9
+    rec = {"ms": ms, "cells_per_s": cells / (ms / 1e3), "tile": list(TILE),
+           "bytes_per_cell": BYTES_PER_CELL_ABSORB, "hbm_frac_step": gbs / peak,
+           "phases_ms": dict(zip(["pass1_tile_solve", "perimeter_graph_resolve",
+                                  "pass2_tile_resolve"], ph)),
+           "time_vs_plain_f32": ms / ms_f32, "status": int(st[0])}
+    del w, a, out, work
+    return rec
+
+
 def main():
     global ROWS, COLS, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -570,6 +617,10 @@ def main():
             "identical_to_byte_codes": bool(torch.equal(out_p.view(torch.int32),
                                                         out_d.view(torch.int32)))}
         del pk, out_p
+
+        # absorption: every cell passes a share a ~ U[0.9, 1) of its flow on
+        line["forms"]["absorb"] = leg_absorb(fa, dev, stream, codes_d, msf, cells, args.warmup,
+                                             k2, peak)
 
         # end to end through the public API from pinned host buffers
         h_codes = torch.from_numpy(codes).pin_memory()

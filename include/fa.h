@@ -350,6 +350,40 @@ fa_status fa_accumulate_adjoint(const uint8_t *codes, int64_t rows, int64_t cols
                                 const fa_options *opts, int32_t *d_status, void *stream);
 
 /*
+ * Accumulation with absorption.  Eq. 1 in full: A(p) = w(p) + sum of
+ * alpha(n, p) A(n), where alpha(n, p) is the fraction of n's accumulated flow
+ * that reaches p and flow may be absorbed but never increased on its way
+ * (Section 2).  For a one-successor (D8) metric alpha(n, p) is nonzero only
+ * for p = d(n), so it is one factor a(n) per cell:
+ *     A(p) = w(p) + sum over n with d(n) = p of a(n) A(n),   0 <= a(n) <= 1.
+ * a = 1 everywhere gives fa_accumulate's float sums.  Same tile decomposition
+ * (Sections 3.1-3.3): a tile solve that also records, for every perimeter
+ * cell, the exit its path reaches and the product of a along the way; a
+ * perimeter-graph solve with those products as multipliers; and a second tile
+ * solve with the flow entering each tile added at its entry cells (EVICT).
+ * All arithmetic is integer (64-bit fixed point per tile, 128-bit across
+ * tiles, factors in 1.63 fixed point), so results are bitwise reproducible.
+ *   codes, mask        as in fa_accumulate (opts->code_format applies).
+ *   weights            [rows x pitch_w] float32 (device) or NULL (unit weights).
+ *   factors            [rows x pitch_f] float32 a(n) in [0, 1] (device); the
+ *                      factor of a cell without a downstream cell is unused.
+ *   out                [rows x pitch_out] float32 (device); 0 at NoData.
+ *   workspace          >= fa_absorb_workspace_size() bytes, 256-byte aligned.
+ * Tiles must hold at most 4096 cells (default 64 x 64); other shapes return
+ * FA_ERR_INVALID_ARG, as do NULL codes, factors or out, short pitches and
+ * misaligned float buffers.  Device-side findings: FA_ERR_NONFINITE for a
+ * non-finite weight or a factor outside [0, 1] (results unspecified),
+ * FA_ERR_BAD_CODE and FA_ERR_CYCLE as for fa_accumulate.
+ */
+size_t fa_absorb_workspace_size(int64_t rows, int64_t cols, const fa_options *opts);
+fa_status fa_accumulate_absorb(const uint8_t *codes, int64_t rows, int64_t cols,
+                               int64_t pitch_codes, const float *weights, int64_t pitch_w,
+                               const float *factors, int64_t pitch_f, const uint8_t *mask,
+                               int64_t pitch_mask, float *out, int64_t pitch_out, void *workspace,
+                               size_t ws_bytes, const fa_options *opts, int32_t *d_status,
+                               void *stream);
+
+/*
  * Copies the device status block back (synchronises `stream`) and maps it to
  * the most severe fa_status: BAD_CODE, then CYCLE, NONFINITE, TIMEOUT, then
  * FA_WARN_OVERFLOW, else FA_OK.  count / first_index may be NULL.

@@ -31,6 +31,7 @@ __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumula
            "fa_autotune_workspace_size", "fa_autotune", "fa_autotune_batched_workspace_size",
            "fa_autotune_batched", "autotune", "autotune_batched", "fa_d8_codes", "d8_codes",
            "fa_recode", "recode", "pack_codes", "PackedCodes", "power_of_two_table",
+           "fa_absorb_workspace_size", "fa_accumulate_absorb", "absorb",
            "FlowAccError", "options"]
 
 
@@ -159,6 +160,22 @@ def fa_accumulate_adjoint(codes, mask, grad_out, grad_w, workspace, opts=None, d
         _ptr(codes), rows, cols, _pitch(codes), _ptr(mask), _pitch(mask), _ptr(grad_out),
         _pitch(grad_out), _ptr(grad_w), _pitch(grad_w), _ptr(workspace), workspace.numel(),
         ctypes.byref(_with_format(codes, opts)), _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_absorb_workspace_size(rows: int, cols: int, opts: fa_options | None = None) -> int:
+    return _lib.load().fa_absorb_workspace_size(rows, cols, ctypes.byref(opts or fa_options()))
+
+
+def fa_accumulate_absorb(codes, weights, factors, mask, out, workspace, opts=None, d_status=None,
+                         stream=None) -> int:
+    """Enqueue fa_accumulate_absorb: A(p) = w(p) + sum of a(n) A(n) over the
+    cells n draining into p (float32 out)."""
+    rows, cols = codes.shape
+    return _lib.load().fa_accumulate_absorb(
+        _ptr(codes), rows, cols, _pitch(codes), _ptr(weights), _pitch(weights), _ptr(factors),
+        _pitch(factors), _ptr(mask), _pitch(mask), _ptr(out), _pitch(out), _ptr(workspace),
+        workspace.numel(), ctypes.byref(_with_format(codes, opts)), _ptr(d_status),
+        _stream_ptr(stream))
 
 
 def fa_d8_codes(dem, nodata, codes, stream=None) -> int:
@@ -412,6 +429,30 @@ def adjoint(codes: torch.Tensor, grad_out: torch.Tensor, mask: torch.Tensor | No
         st, _, _ = fa_status_read(None, ws, stream)
         if st < 0:
             raise FlowAccError(st, "fa_accumulate_adjoint (device)")
+    return out
+
+
+def absorb(codes, factors: torch.Tensor, weights: torch.Tensor | None = None,
+           mask: torch.Tensor | None = None, tile=None, out: torch.Tensor | None = None,
+           check: bool = False, stream=None):
+    """Accumulation with absorption: every cell n passes the fraction
+    factors[n] (float32 in [0, 1]) of its accumulated flow downstream.
+    codes: uint8 [R, C] or PackedCodes; weights: float32 or None (unit).
+    Returns float32 [R, C]."""
+    if factors.dtype != torch.float32:
+        raise TypeError("factors must be float32")
+    R, C = codes.shape
+    if out is None:
+        out = torch.empty((R, C), dtype=torch.float32, device=codes.device)
+    opts = options(tile)
+    ws = workspace(fa_absorb_workspace_size(R, C, opts), codes.device)
+    st = fa_accumulate_absorb(codes, weights, factors, mask, out, ws, opts, None, stream)
+    if st != FA_OK:
+        raise FlowAccError(st, "fa_accumulate_absorb")
+    if check:
+        st, _, _ = fa_status_read(None, ws, stream)
+        if st < 0:
+            raise FlowAccError(st, "fa_accumulate_absorb (device)")
     return out
 
 

@@ -74,6 +74,9 @@ SIGNATURES = {
                                       _P, ctypes.POINTER(ctypes.c_void_p)]),
     "fa_d8_codes": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P]),
     "fa_recode": (_I32, [_P, _I64, _I64, _I64, _P, _P, _I64, _I32, _P]),
+    "fa_absorb_workspace_size": (_SZ, [_I64, _I64, _OPT]),
+    "fa_accumulate_absorb": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64,
+                                    _P, _SZ, _OPT, _P, _P]),
     "fa_autotune_workspace_size": (_SZ, [_I64, _I64, _OPT]),
     "fa_autotune": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I32, _I64, _P, _SZ,
                            _OPT, _P, _OPT]),

@@ -221,3 +221,26 @@ def test_power_of_two_table():
     assert len(t) == 256
     for v in range(256):
         assert t[v] == want.get(v, 10)
+
+
+def test_absorb_host_logic_without_gpu(lib):
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: validation fails first
+    o = _lib.fa_options()
+    assert lib.fa_absorb_workspace_size(100, 100, ctypes.byref(o)) > 0
+    big = _lib.fa_options(128, 64, 0, 0)  # 8192 cells: above the 4096-cell tile limit
+    assert lib.fa_absorb_workspace_size(100, 100, ctypes.byref(big)) == 0
+
+    def call(codes=fake, pc=10, factors=fake, pf=10, out=fake, po=10, ws=fake, nbytes=1 << 30,
+             opts=o):
+        return lib.fa_accumulate_absorb(codes, 10, 10, pc, None, 0, factors, pf, None, 0, out, po,
+                                        ws, nbytes, ctypes.byref(opts), None, None)
+
+    assert call(codes=None) == _lib.FA_ERR_INVALID_ARG
+    assert call(factors=None) == _lib.FA_ERR_INVALID_ARG
+    assert call(out=None) == _lib.FA_ERR_INVALID_ARG
+    assert call(pf=9) == _lib.FA_ERR_INVALID_ARG
+    assert call(po=9) == _lib.FA_ERR_INVALID_ARG
+    assert call(factors=ctypes.c_void_p((1 << 20) + 2)) == _lib.FA_ERR_INVALID_ARG
+    assert call(opts=big) == _lib.FA_ERR_INVALID_ARG
+    assert call(ws=None) == _lib.FA_ERR_WORKSPACE
+    assert call(nbytes=64) == _lib.FA_ERR_WORKSPACE
