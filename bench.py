@@ -51,6 +51,7 @@ BYTES_PER_CELL_COUNTS = 5  # 1 B code read + 4 B uint32 written (algorithmic min
 BYTES_PER_CELL_F32 = 9     # + 4 B float32 weight read
 BYTES_PER_CELL_ABSORB = 13  # + 4 B float32 factor read
 ASEED = 205                 # absorption factors, U[0.9, 1)
+ABS_TILE = (32, 64)         # the absorption default tile
 WORKLOAD = "d8_dem_16384x16384"
 BATCH_N, BATCH_FIELDS, BATCH_SEED, BATCH_SHAPE_SEED = 64, 8, 301, 300
 ADJ_N, ADJ_SEED, ADJ_GAUGES = 8192, 401, 256
@@ -403,7 +404,7 @@ def leg_absorb(fa, dev, stream, codes_d, ms_f32, cells, warmup, reps, peak):
     a = torch.rand(codes_d.shape, generator=g, device=dev, dtype=torch.float32) * 0.1 + 0.9
     a.clamp_(max=1.0)
     out = torch.empty(codes_d.shape, dtype=torch.float32, device=dev)
-    opts = fa.options(TILE)
+    opts = fa.options(ABS_TILE)
     work = torch.empty(fa.fa_absorb_workspace_size(*codes_d.shape, opts), dtype=torch.uint8,
                        device=dev)
 
@@ -425,7 +426,7 @@ def leg_absorb(fa, dev, stream, codes_d, ms_f32, cells, warmup, reps, peak):
     fa.fa_timing_enable(False)
     ph = np.mean(np.array(ph), axis=0).tolist()
     gbs = cells * BYTES_PER_CELL_ABSORB / (ms / 1e3) / 1e9
-    rec = {"ms": ms, "cells_per_s": cells / (ms / 1e3), "tile": list(TILE),
+    rec = {"ms": ms, "cells_per_s": cells / (ms / 1e3), "tile": list(ABS_TILE),
            "bytes_per_cell": BYTES_PER_CELL_ABSORB, "hbm_frac_step": gbs / peak,
            "phases_ms": dict(zip(["pass1_tile_solve", "perimeter_graph_resolve",
                                   "pass2_tile_resolve"], ph)),

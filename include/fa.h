@@ -369,7 +369,8 @@ fa_status fa_accumulate_adjoint(const uint8_t *codes, int64_t rows, int64_t cols
  *                      factor of a cell without a downstream cell is unused.
  *   out                [rows x pitch_out] float32 (device); 0 at NoData.
  *   workspace          >= fa_absorb_workspace_size() bytes, 256-byte aligned.
- * Tiles must hold at most 4096 cells (default 64 x 64); other shapes return
+ * Tiles must hold at most 4096 cells (a shape left at 0 here means 32 x 64,
+ * the fastest measured); other shapes return
  * FA_ERR_INVALID_ARG, as do NULL codes, factors or out, short pitches and
  * misaligned float buffers.  Device-side findings: FA_ERR_NONFINITE for a
  * non-finite weight or a factor outside [0, 1] (results unspecified),

@@ -100,6 +100,18 @@ __device__ __forceinline__ long long float_to_fix(float x, int q) {
     return (b >> 31) ? -(long long)v : (long long)v;
 }
 
+// Adds a 64-bit two's-complement value to a shared-memory word with two 32-bit
+// atomics: the carry of each addition into the high word is known from the
+// low word's old value, so the high word receives exactly the carries of all
+// additions.
+__device__ __forceinline__ void smem_add64(long long *p, long long v) {
+    uint32_t *w = reinterpret_cast<uint32_t *>(p);
+    const uint32_t lo = (uint32_t)(unsigned long long)v, hi = (uint32_t)((unsigned long long)v >> 32);
+    const uint32_t old = atomicAdd(&w[0], lo);
+    const uint32_t h = hi + (old + lo < old ? 1u : 0u);
+    if (h) atomicAdd(&w[1], h);
+}
+
 // 2^e as a float, -126 <= e <= 127
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
@@ -322,16 +334,33 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
     __syncthreads();
     const int q = abs_tile_scale(s_emax == INT_MIN ? 0 : s_emax, (int64_t)n_in + P + 8);
 
-    // ---- values at the tile's scale
-    for (int j = tid; j < n_in; j += nt) {
-        const int r = j / w, c = j - r * w;
-        long long x = 0;
-        if (ec[(r + 1) * W2 + (c + 1)]) x = float_to_fix(a.w ? a.w[(R0 + r) * a.pw + (C0 + c)] : 1.0f, q);
-        X[j] = x;
-        D[j] = 0;
-    }
-    __syncthreads();
+    auto is_exit = [&](int i) {
+        const int k = ec[i] & 15;
+        return k >= 1 && k <= 8 && (ec[i + off_of(k, W2)] & HALO);
+    };
+    // a path ends at a cell without an in-tile successor (pointer doubling on
+    // an in-tile cycle whose length is a power of two also comes back to the
+    // cell itself, so the pointer alone does not tell)
+    auto is_end = [&](int i) {
+        const int k = ec[i] & 15;
+        if (k < 1 || k > 8) return true;
+        const uint8_t en = ec[i + off_of(k, W2)];
+        return !en || (en & HALO);
+    };
+    const int maxr = ceil_log2(n_in > 1 ? n_in : 2) + 2;
+    int ncyc = 0;
+    long long fcyc = NO_INDEX;
+
     if constexpr (PASS == 2) {
+        // ---- values at the tile's scale, the inflow added at entry cells
+        for (int j = tid; j < n_in; j += nt) {
+            const int r = j / w, c = j - r * w;
+            long long x = 0;
+            if (ec[(r + 1) * W2 + (c + 1)]) x = float_to_fix(a.w ? a.w[(R0 + r) * a.pw + (C0 + c)] : 1.0f, q);
+            X[j] = x;
+            D[j] = 0;
+        }
+        __syncthreads();
         for (int i = tid; i < NH; i += nt) {
             const uint8_t e = ec[i];
             if (!(e & HALO) || (e & 15) > 8) continue;
@@ -346,82 +375,124 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
             const u128 v = scale128_q63(a.G[node], a.node_fac[node]);
             const u128 vq = shift_signed(v, q - qf);  // forest scale -> tile scale
             const int p = (nr - 1) * w + (nc - 1);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&X[p]), (unsigned long long)(uint64_t)vq);
+            smem_add64(&X[p], (long long)(uint64_t)vq);
         }
         __syncthreads();
-    }
 
-    // ---- pointer jumping with multipliers: x_{k+1}(v) = x_k(v) + sum over u
-    // with J_k(u) = v of M_k(u) x_k(u); J_{k+1} = J_k o J_k, M_{k+1}(u) =
-    // M_k(u) M_k(J_k(u)) (the product of a over the 2^(k+1) cells u leaves)
-    int maxr = ceil_log2(n_in > 1 ? n_in : 2) + 2;
-    int active = 0;
-    for (int j = tid; j < n_in; j += nt) active |= J[j] != ABS_NONE;
-    active = __syncthreads_or(active);
-    for (int round = 0; round < maxr && active; ++round) {
-        for (int j = tid; j < n_in; j += nt) {
-            const uint16_t nx = J[j];
-            if (nx != ABS_NONE)
-                atomicAdd(reinterpret_cast<unsigned long long *>(&D[nx]),
-                          (unsigned long long)scale_q63(X[j], M[j]));
-        }
-        __syncthreads();
-        uint16_t nj[ABS_CPT];
-        uint64_t nm[ABS_CPT];
-        int act = 0;
-#pragma unroll
-        for (int u = 0; u < ABS_CPT; ++u) {
-            const int j = tid + u * nt;
-            nj[u] = ABS_NONE;
-            nm[u] = 0;
-            if (j >= n_in) continue;
-            X[j] += D[j];
-            D[j] = 0;
-            const uint16_t nx = J[j];
-            if (nx != ABS_NONE) {
-                nj[u] = J[nx];
-                if (nj[u] != ABS_NONE) {
-                    nm[u] = mul_q63(M[j], M[nx]);
-                    act = 1;
+        // ---- pointer jumping with multipliers: x_{k+1}(v) = x_k(v) + sum over
+        // u with J_k(u) = v of M_k(u) x_k(u); J_{k+1} = J_k o J_k, M_{k+1}(u) =
+        // M_k(u) M_k(J_k(u)) (the product of a over the 2^(k+1) cells u leaves)
+        int active = 0;
+        for (int j = tid; j < n_in; j += nt) active |= J[j] != ABS_NONE;
+        active = __syncthreads_or(active);
+        for (int round = 0; round < maxr && active; ++round) {
+            for (int j = tid; j < n_in; j += nt) {
+                const uint16_t nx = J[j];
+                if (nx != ABS_NONE) {
+                    const long long v = scale_q63(X[j], M[j]);
+                    if (v) smem_add64(&D[nx], v);
                 }
             }
-        }
-        __syncthreads();
+            __syncthreads();
+            uint16_t nj[ABS_CPT];
+            uint64_t nm[ABS_CPT];
+            int act = 0;
 #pragma unroll
-        for (int u = 0; u < ABS_CPT; ++u) {
-            const int j = tid + u * nt;
-            if (j >= n_in) continue;
-            J[j] = nj[u];
-            M[j] = nm[u];
-        }
-        active = __syncthreads_or(act);
-    }
-    // cells whose pointers never ran out are on (or drain into) an in-tile cycle
-    int ncyc = 0;
-    long long fcyc = NO_INDEX;
-    if (active) {
-        for (int j = tid; j < n_in; j += nt)
-            if (J[j] != ABS_NONE) {
-                ++ncyc;
-                fcyc = min(fcyc, (long long)((R0 + j / w) * a.cols + (C0 + j % w)));
+            for (int u = 0; u < ABS_CPT; ++u) {
+                const int j = tid + u * nt;
+                nj[u] = ABS_NONE;
+                nm[u] = 0;
+                if (j >= n_in) continue;
+                X[j] += D[j];
+                D[j] = 0;
+                const uint16_t nx = J[j];
+                if (nx != ABS_NONE) {
+                    nj[u] = J[nx];
+                    if (nj[u] != ABS_NONE) {
+                        nm[u] = mul_q63(M[j], M[nx]);
+                        act = 1;
+                    }
+                }
             }
-    }
-
-    if constexpr (PASS == 2) {
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < ABS_CPT; ++u) {
+                const int j = tid + u * nt;
+                if (j >= n_in) continue;
+                J[j] = nj[u];
+                M[j] = nm[u];
+            }
+            active = __syncthreads_or(act);
+        }
         for (int j = tid; j < n_in; j += nt) {
             const int r = j / w, c = j - r * w;
             a.out[(size_t)(R0 + r) * a.po + (C0 + c)] =
                 ec[(r + 1) * W2 + (c + 1)] ? fix_to_float(X[j], q) : 0.0f;
         }
-        return;
     } else {
+        // ---- every cell's path end R and the product of a along the way Pp
+        // (excluding the end), by gather jumping: R(j) -> R(R(j)),
+        // Pp(j) -> Pp(j) Pp(R(j)); a path's last cell points at itself with
+        // product 1.  J and M hold R and Pp.
+        for (int j = tid; j < n_in; j += nt) {
+            if (J[j] == ABS_NONE) {
+                J[j] = (uint16_t)j;
+                M[j] = Q63_ONE;
+            }
+            X[j] = 0;
+        }
+        __syncthreads();
+        int active = 1;
+        for (int round = 0; round < maxr && active; ++round) {
+            // a cell whose pointer already names its path's end is settled:
+            // nothing to read, multiply or write
+            uint16_t nj[ABS_CPT];
+            uint64_t nm[ABS_CPT];
+            int act = 0, moved = 0;
+#pragma unroll
+            for (int u = 0; u < ABS_CPT; ++u) {
+                const int j = tid + u * nt;
+                nj[u] = ABS_NONE;
+                if (j >= n_in) continue;
+                const uint16_t nx = J[j];
+                const uint16_t n2 = J[nx];
+                if (n2 == nx) continue;
+                nj[u] = n2;
+                nm[u] = mul_q63(M[j], M[nx]);
+                moved |= 1 << u;
+                act |= J[n2] != n2;  // not settled after this round
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < ABS_CPT; ++u) {
+                if (!((moved >> u) & 1)) continue;
+                const int j = tid + u * nt;
+                J[j] = nj[u];
+                M[j] = nm[u];
+            }
+            active = __syncthreads_or(act);
+        }
+        // ---- A_loc at the exits: every cell y adds w(y) Pp(y) to the exit its
+        // path ends at (cells whose jumps never settled lie on or drain into
+        // an in-tile cycle)
+        for (int j = tid; j < n_in; j += nt) {
+            const int r = j / w, c = j - r * w;
+            if (!ec[(r + 1) * W2 + (c + 1)]) continue;
+            const int last = J[j];
+            const int lr = last / w, lc = last - lr * w;
+            const int li = (lr + 1) * W2 + (lc + 1);
+            if (J[last] != last || !is_end(li)) {
+                ++ncyc;
+                fcyc = min(fcyc, (long long)((R0 + r) * a.cols + (C0 + c)));
+                continue;
+            }
+            if (!is_exit(li)) continue;
+            const long long x = scale_q63(float_to_fix(a.w ? a.w[(R0 + r) * a.pw + (C0 + c)] : 1.0f, q), M[j]);
+            if (x) smem_add64(&X[last], x);
+        }
         // ---- exits in slot order
         const int chunk = (P + nt - 1) / nt;
         const int s0 = min(P, tid * chunk), s1 = min(P, s0 + chunk);
-        auto is_exit = [&](int i) {
-            const int k = ec[i] & 15;
-            return k >= 1 && k <= 8 && (ec[i + off_of(k, W2)] & HALO);
-        };
         int mine = 0;
         for (int s = s0; s < s1; ++s) {
             int r, c;
@@ -429,7 +500,7 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
             mine += is_exit((r + 1) * W2 + (c + 1));
         }
         int total;
-        int rk = block_exclusive_scan(mine, s_warp, &total);
+        int rk = block_exclusive_scan(mine, s_warp, &total);  // its barriers publish X
         const size_t tbase = (size_t)t * a.pmax;
         for (int s = s0; s < s1; ++s) {
             int r, c;
@@ -447,53 +518,7 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
                 rank[s] = LINK_TERM;
             }
         }
-        // ---- every cell's path end and the product of a along the way, by
-        // gather jumping: R(j) -> R(R(j)), Pp(j) -> Pp(j) Pp(R(j)); a path's
-        // last cell points at itself with product 1
-        for (int j = tid; j < n_in; j += nt) {
-            const int r = j / w, c = j - r * w;
-            const int i = (r + 1) * W2 + (c + 1);
-            uint16_t nx = (uint16_t)j;
-            uint64_t m = Q63_ONE;
-            const int k = ec[i] & 15;
-            if (ec[i] && k <= 8) {
-                const uint8_t en = ec[i + off_of(k, W2)];
-                if (en && !(en & HALO)) {
-                    nx = (uint16_t)((r + dir_dr(k)) * w + (c + dir_dc(k)));
-                    const float av = a.a[(R0 + r) * a.pa + (C0 + c)];
-                    m = (av >= 0.0f && av <= 1.0f) ? factor_q63(av) : 0;
-                }
-            }
-            J[j] = nx;
-            M[j] = m;
-        }
         __syncthreads();
-        active = 1;
-        for (int round = 0; round < maxr && active; ++round) {
-            uint16_t nj[ABS_CPT];
-            uint64_t nm[ABS_CPT];
-            int act = 0;
-#pragma unroll
-            for (int u = 0; u < ABS_CPT; ++u) {
-                const int j = tid + u * nt;
-                nj[u] = 0;
-                nm[u] = 0;
-                if (j >= n_in) continue;
-                const uint16_t nx = J[j];
-                nj[u] = J[nx];
-                nm[u] = nx == j ? M[j] : mul_q63(M[j], M[nx]);
-                act |= nj[u] != nx;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < ABS_CPT; ++u) {
-                const int j = tid + u * nt;
-                if (j >= n_in) continue;
-                J[j] = nj[u];
-                M[j] = nm[u];
-            }
-            active = __syncthreads_or(act);
-        }
         for (int s = tid; s < P; s += nt) {
             int r, c;
             cell_of(s, h, w, r, c);
@@ -502,8 +527,9 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
             uint64_t prod = 0;
             if (ec[(r + 1) * W2 + (c + 1)]) {
                 const int last = J[j];
-                const int lr = last / w, lc = last - (last / w) * w;
-                if (is_exit((lr + 1) * W2 + (lc + 1))) lk = rank[slot_of(lr, lc, h, w)];
+                const int lr = last / w, lc = last - lr * w;
+                if (J[last] == last && is_exit((lr + 1) * W2 + (lc + 1)))  // an exit is a path end
+                    lk = rank[slot_of(lr, lc, h, w)];
                 prod = M[j];
             }
             a.link[tbase + s] = lk;
@@ -782,9 +808,19 @@ using namespace fa;
 
 static bool aligned4(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
 
+// Options with the absorption default tile (32 x 64: two tile blocks per SM,
+// the fastest of the measured shapes) where the caller left the shape at 0.
+static fa_options absorb_options(const fa_options *opts) {
+    fa_options o = opts ? *opts : fa_options{0, 0, 0, 0};
+    if (!o.tile_h) o.tile_h = 32;
+    if (!o.tile_w) o.tile_w = 64;
+    return o;
+}
+
 extern "C" size_t fa_absorb_workspace_size(int64_t rows, int64_t cols, const fa_options *opts) {
     Geom g;
-    if (!make_geom(rows, cols, opts, g) || !absorb_tile_ok(g)) return 0;
+    const fa_options o = absorb_options(opts);
+    if (!make_geom(rows, cols, &o, g) || !absorb_tile_ok(g)) return 0;
     AbsWork w;
     return carve_absorb(nullptr, ~size_t(0) >> 1, g, w);
 }
@@ -796,7 +832,8 @@ extern "C" fa_status fa_accumulate_absorb(const uint8_t *codes, int64_t rows, in
                                           int64_t pitch_out, void *workspace, size_t ws_bytes,
                                           const fa_options *opts, int32_t *d_status, void *stream) {
     Geom g;
-    if (!make_geom(rows, cols, opts, g) || !absorb_tile_ok(g)) return FA_ERR_INVALID_ARG;
+    const fa_options o = absorb_options(opts);
+    if (!make_geom(rows, cols, &o, g) || !absorb_tile_ok(g)) return FA_ERR_INVALID_ARG;
     const bool empty = rows == 0 || cols == 0;
     if (!empty) {
         if (!codes || !factors || !out) return FA_ERR_INVALID_ARG;

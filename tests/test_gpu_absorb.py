@@ -125,6 +125,22 @@ def test_packed_codes_and_determinism(oracle_mod):
     assert torch.equal(x, y) and torch.equal(x, z)
 
 
+@pytest.mark.parametrize("codes,tile", [([[1, 5]], None), ([[1, 7], [3, 5]], (2, 2)),
+                                        ([[1, 7], [3, 5]], (1, 1)), ([[1, 1, 6], [9, 3, 5]], None)])
+def test_cycles_flagged(oracle_mod, codes, tile):
+    # in-tile cycles of length 2 and 4 (pointer doubling comes back to the
+    # cell itself on those), a cross-tile 4-cycle, and a 3-cycle fed by a cell
+    codes = np.array(codes, np.uint8)
+    a = np.full(codes.shape, 0.75, np.float32)
+    ref = oracle_mod.absorb(codes, a)
+    assert ref.n_cycle > 0
+    got = fa.absorb(dev(codes), dev(a), tile=tile).cpu().numpy()
+    st, count, _ = status()
+    assert st == fa.FA_ERR_CYCLE and count > 0
+    ok = ref.state == 1
+    np.testing.assert_allclose(got[ok], ref.values[ok], rtol=RTOL)
+
+
 def test_bad_factors_flagged():
     R, C = 40, 50
     codes = synth.dem_codes(R, C, 171)
