@@ -447,6 +447,9 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up and timed steps (for ncu): no clock sampling, phase "
                          "timing, extra legs or CPU baseline")
+    ap.add_argument("--profile-absorb", action="store_true",
+                    help="with --profile: after the timed steps, three calls of the absorption "
+                         "form on the same raster")
     ap.add_argument("--tile", default="auto",
                     help="tile shape HxW for the plain leg, or 'auto' (fa_autotune; default)")
     ap.add_argument("--size", type=int, default=ROWS,
@@ -521,6 +524,22 @@ def main():
     # per-phase durations, live, on the launching stream
     phases = []
     if args.profile:
+        if args.profile_absorb:
+            g = torch.Generator(device=dev)
+            g.manual_seed(WSEED)
+            w_d = torch.rand(codes_d.shape, generator=g, device=dev, dtype=torch.float32)
+            g.manual_seed(ASEED)
+            a_d = (torch.rand(codes_d.shape, generator=g, device=dev) * 0.1 + 0.9).clamp_(max=1.0)
+            out_a = torch.empty(codes_d.shape, dtype=torch.float32, device=dev)
+            opts_a = fa.options(ABS_TILE)
+            work_a = torch.empty(fa.fa_absorb_workspace_size(ROWS, COLS, opts_a),
+                                 dtype=torch.uint8, device=dev)
+            for _ in range(3):
+                s = fa.fa_accumulate_absorb(codes_d, w_d, a_d, None, out_a, work_a, opts_a, None,
+                                            stream)
+                if s != fa.FA_OK:
+                    raise fa.FlowAccError(s, "fa_accumulate_absorb")
+            torch.cuda.synchronize()
         print(json.dumps({"profile_run": True, "ms_per_step": ms_max}), flush=True)
         return
     fa.fa_timing_enable(True)
