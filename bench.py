@@ -431,8 +431,9 @@ def leg_absorb(fa, dev, stream, codes_d, ms_f32, cells, warmup, reps, peak):
            "phases_ms": dict(zip(["pass1_tile_solve", "perimeter_graph_resolve",
                                   "pass2_tile_resolve"], ph)),
            "time_vs_plain_f32": ms / ms_f32, "status": int(st[0])}
+    data = (w.cpu().numpy(), a.cpu().numpy(), out.cpu().numpy())  # for the oracle check
     del w, a, out, work
-    return rec
+    return rec, data
 
 
 def main():
@@ -583,7 +584,7 @@ def main():
     }
     line["gpu_launches"] = args.steps * fa.fa_kernel_launches(ROWS, COLS, opts)
 
-    d8_data = None
+    d8_data = absorb_data = None
     if not args.no_extra:
         # float32 weighted form on the same raster
         w_d = torch.from_numpy(synth.uniform_weights(codes.shape, WSEED)).to(dev)
@@ -639,8 +640,10 @@ def main():
         del pk, out_p
 
         # absorption: every cell passes a share a ~ U[0.9, 1) of its flow on
-        line["forms"]["absorb"] = leg_absorb(fa, dev, stream, codes_d, msf, cells, args.warmup,
-                                             k2, peak)
+        line["forms"]["absorb"], absorb_data = leg_absorb(fa, dev, stream, codes_d, msf, cells,
+                                                          args.warmup, k2, peak)
+        if rank != 0 or args.no_cpu_baseline:
+            absorb_data = None
 
         # end to end through the public API from pinned host buffers
         h_codes = torch.from_numpy(codes).pin_memory()
@@ -702,6 +705,23 @@ def main():
             rec = line["forms"]["d8_directions"]
             rec["parity_vs_oracle"] = "bit-exact" if np.array_equal(got_d8, ref_d8) else "MISMATCH"
             rec["cpu_oracle_cells_per_s"] = z.size / dt8
+        if absorb_data is not None:  # absorption's oracle (FP64), timed on one core
+            import oracle
+
+            w_h, a_h, got_a = absorb_data
+            t0 = time.perf_counter()
+            ref_a = oracle.absorb(codes, a_h, w_h)
+            dta = time.perf_counter() - t0
+            ok = ref_a.state == 1
+            err = np.abs(got_a[ok].astype(np.float64) - ref_a.values[ok])
+            bound = 2e-5 * np.abs(ref_a.values[ok]) + 1e-9 * np.abs(ref_a.values[ok]).max()
+            rec = line["forms"]["absorb"]
+            rec["parity_vs_oracle"] = ("within 2e-5 relative" if bool((err <= bound).all())
+                                       else "MISMATCH")
+            rec["max_rel_err_vs_oracle"] = float(np.max(err / np.maximum(np.abs(ref_a.values[ok]),
+                                                                         1e-300)))
+            rec["cpu_oracle_cells_per_s"] = codes.size / dta
+            del absorb_data, ref_a
         if not exact:
             line["parity"]["mismatches"] = int((got != res.values.astype(np.uint32)).sum())
 

@@ -138,6 +138,27 @@ __device__ __forceinline__ int fix128_exp(u128 v, int qf) {
     return 127 - clz128(a) - qf;
 }
 
+// floor(n / d) for n, d < 2^16 as one multiply: with m = ceil(2^32 / d),
+// n m / 2^32 exceeds n / d by less than n / 2^32 < 1 / d, which cannot reach
+// the next integer
+struct FastDiv {
+    uint64_t m;
+    __device__ explicit FastDiv(int d) : m(((1ull << 32) + (uint64_t)d - 1) / (uint64_t)d) {}
+    __device__ int operator()(int n) const { return (int)(((uint64_t)(uint32_t)n * m) >> 32); }
+};
+
+// cell m of the halo ring of an (h + 2) x W2 box: top row, bottom row, then
+// the left and right columns between them
+__device__ __forceinline__ void ring_cell(int m, int h, int W2, int &hr, int &hc) {
+    if (m < W2) { hr = 0; hc = m; return; }
+    m -= W2;
+    if (m < W2) { hr = h + 1; hc = m; return; }
+    m -= W2;
+    if (m < h) { hr = 1 + m; hc = 0; return; }
+    hr = 1 + (m - h);
+    hc = W2 - 1;
+}
+
 __host__ __device__ inline int ceil_log2(int64_t n) {
     int k = 0;
     while (((int64_t)1 << k) < n) ++k;
@@ -238,6 +259,8 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
     const int NC = a.th * a.tw;  // compact cell j = r * w + c, j < h * w
     const int n_in = h * w;
     const int P = perim_count(h, w);
+    const int NR = 2 * W2 + 2 * h;  // halo ring cells
+    const FastDiv div_w(w), div_W2(W2);
 
     long long *X = reinterpret_cast<long long *>(smem);
     long long *D = X + NC;
@@ -257,7 +280,7 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
     int nbad = 0;
     long long fbad = NO_INDEX;
     for (int i = tid; i < NH; i += nt) {
-        const int hr = i / W2, hc = i - hr * W2;
+        const int hr = div_W2(i), hc = i - hr * W2;
         const int64_t gr = R0 - 1 + hr, gc = C0 - 1 + hc;
         uint8_t e = 0;
         if (gr >= 0 && gr < a.rows && gc >= 0 && gc < a.cols) {
@@ -277,7 +300,7 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
     int emax = INT_MIN, bad_factor = 0;
     long long fbf = NO_INDEX;
     for (int j = tid; j < n_in; j += nt) {
-        const int r = j / w, c = j - r * w;
+        const int r = div_w(j), c = j - r * w;
         const int i = (r + 1) * W2 + (c + 1);
         const uint8_t e = ec[i];
         uint16_t nx = ABS_NONE;
@@ -315,13 +338,17 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
         const uint32_t gm = a.misc[0];
         qf = abs_forest_scale(gm == EMAX_NONE ? 0 : (int)gm - EMAX_BIAS, a.rows * a.cols);
         int emi = INT_MIN;
-        for (int i = tid; i < NH; i += nt) {
+        for (int m = tid; m < NR; m += nt) {
+            int hr, hc;
+            ring_cell(m, h, W2, hr, hc);
+            const int i = hr * W2 + hc;
             const uint8_t e = ec[i];
             if (!(e & HALO) || (e & 15) > 8) continue;
-            const int k = e & 15, n = i + off_of(k, W2);
-            const int nr = n / W2, nc = n - nr * W2;
-            if (nr < 1 || nr > h || nc < 1 || nc > w || !ec[n] || (ec[n] & HALO)) continue;
-            const int hr = i / W2, hc = i - hr * W2;
+            const int k = e & 15;
+            const int nr = hr + dir_dr(k), nc = hc + dir_dc(k);
+            if (nr < 1 || nr > h || nc < 1 || nc > w) continue;
+            const int n = nr * W2 + nc;
+            if (!ec[n] || (ec[n] & HALO)) continue;
             const size_t gs = abs_global_slot(a, R0 - 1 + hr, C0 - 1 + hc);
             const uint16_t lk = a.link[gs];
             if (lk == LINK_TERM) continue;  // never: h's successor is valid and outside its tile
@@ -354,20 +381,24 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
     if constexpr (PASS == 2) {
         // ---- values at the tile's scale, the inflow added at entry cells
         for (int j = tid; j < n_in; j += nt) {
-            const int r = j / w, c = j - r * w;
+            const int r = div_w(j), c = j - r * w;
             long long x = 0;
             if (ec[(r + 1) * W2 + (c + 1)]) x = float_to_fix(a.w ? a.w[(R0 + r) * a.pw + (C0 + c)] : 1.0f, q);
             X[j] = x;
             D[j] = 0;
         }
         __syncthreads();
-        for (int i = tid; i < NH; i += nt) {
+        for (int m = tid; m < NR; m += nt) {
+            int hr, hc;
+            ring_cell(m, h, W2, hr, hc);
+            const int i = hr * W2 + hc;
             const uint8_t e = ec[i];
             if (!(e & HALO) || (e & 15) > 8) continue;
-            const int k = e & 15, n = i + off_of(k, W2);
-            const int nr = n / W2, nc = n - nr * W2;
-            if (nr < 1 || nr > h || nc < 1 || nc > w || !ec[n] || (ec[n] & HALO)) continue;
-            const int hr = i / W2, hc = i - hr * W2;
+            const int k = e & 15;
+            const int nr = hr + dir_dr(k), nc = hc + dir_dc(k);
+            if (nr < 1 || nr > h || nc < 1 || nc > w) continue;
+            const int n = nr * W2 + nc;
+            if (!ec[n] || (ec[n] & HALO)) continue;
             const size_t gs = abs_global_slot(a, R0 - 1 + hr, C0 - 1 + hc);
             const uint16_t lk = a.link[gs];
             if (lk == LINK_TERM) continue;
@@ -425,7 +456,7 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
             active = __syncthreads_or(act);
         }
         for (int j = tid; j < n_in; j += nt) {
-            const int r = j / w, c = j - r * w;
+            const int r = div_w(j), c = j - r * w;
             a.out[(size_t)(R0 + r) * a.po + (C0 + c)] =
                 ec[(r + 1) * W2 + (c + 1)] ? fix_to_float(X[j], q) : 0.0f;
         }
@@ -476,10 +507,10 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
         // path ends at (cells whose jumps never settled lie on or drain into
         // an in-tile cycle)
         for (int j = tid; j < n_in; j += nt) {
-            const int r = j / w, c = j - r * w;
+            const int r = div_w(j), c = j - r * w;
             if (!ec[(r + 1) * W2 + (c + 1)]) continue;
             const int last = J[j];
-            const int lr = last / w, lc = last - lr * w;
+            const int lr = div_w(last), lc = last - lr * w;
             const int li = (lr + 1) * W2 + (lc + 1);
             if (J[last] != last || !is_end(li)) {
                 ++ncyc;
@@ -527,7 +558,7 @@ __global__ void __launch_bounds__(1024) k_abs_tile(AbsArgs a) {
             uint64_t prod = 0;
             if (ec[(r + 1) * W2 + (c + 1)]) {
                 const int last = J[j];
-                const int lr = last / w, lc = last - lr * w;
+                const int lr = div_w(last), lc = last - lr * w;
                 if (J[last] == last && is_exit((lr + 1) * W2 + (lc + 1)))  // an exit is a path end
                     lk = rank[slot_of(lr, lc, h, w)];
                 prod = M[j];

@@ -115,6 +115,25 @@ __global__ void __launch_bounds__(256, 4) k_d8(D8Args a) {
         if (r >= a.rows) break;
         load_row(a, r + 1, c0, vz, vn, v[2], ndm[2]);
         uint32_t codes = 0;
+        if (!(ndm[0] | ndm[1] | ndm[2]) && r > 0 && r < a.rows - 1 && c0 > 0 && c0 + 4 < a.cols) {
+            // the common case: four interior cells and no NoData in the window
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float zc = v[1][q + 1];
+                float best = 0.0f;
+                uint32_t pick = 9u;
+#pragma unroll
+                for (int k = 1; k <= 8; ++k) {
+                    const float drop = __fsub_rn(zc, v[fa::dir_dr(k) + 1][q + 1 + fa::dir_dc(k)]);
+                    const float slope = (k & 1) ? drop : __fmul_rn(drop, kInvSqrt2);
+                    if (slope > best) {
+                        best = slope;
+                        pick = (uint32_t)k;
+                    }
+                }
+                codes |= pick << (8 * q);
+            }
+        } else
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t c = c0 + q;
