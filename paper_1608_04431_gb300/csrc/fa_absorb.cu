@@ -4,12 +4,13 @@
 //     A(p) = w(p) + sum over n with d(n) = p of a(n) A(n).
 // Same tile decomposition as the plain forms (Section 3):
 //
-//   pass 1  k_abs_tile<1>  per tile: A_loc by pointer jumping with products of
-//                          a along the jumps; the exits ranked, each with
-//                          A_loc(e), a(e) and the slot d(e) leads to; every
-//                          perimeter slot with the exit its in-tile path
-//                          reaches (Algorithm 2) and the product of a along
-//                          that path.
+//   pass 1  k_abs_tile<1>  per tile: every cell's in-tile path end and the
+//                          product of a along the way, by gather pointer
+//                          jumping; A_loc of each exit as the sum of w times
+//                          that product over the cells whose paths end there;
+//                          the exits ranked, each with A_loc(e), a(e) and the
+//                          slot d(e) leads to; every perimeter slot with the
+//                          exit its path reaches (Algorithm 2) and its product.
 //   forest  k_abs_forest_* G(e) = A_loc(e) + sum over exits e' leading to e of
 //                          a(e') P(d(e')) G(e'), P the product of a from the
 //                          entry d(e') to e: pointer jumping with multipliers
