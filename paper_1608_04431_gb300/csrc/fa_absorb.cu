@@ -56,15 +56,16 @@ __device__ __forceinline__ uint64_t factor_q63(float a) {
     return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0);
 }
 
-// (x y) >> 63 for Q1.63 factors x, y <= 2^63
+// (x y) >> 63 for Q1.63 factors x, y <= 2^63.  For y < 2^63 that is the high
+// word of x (2y); y = 2^63 is the factor 1.
 __device__ __forceinline__ uint64_t mul_q63(uint64_t x, uint64_t y) {
-    return (__umul64hi(x, y) << 1) | ((x * y) >> 63);
+    return y == Q63_ONE ? x : __umul64hi(x, y << 1);
 }
 
 // a signed 64-bit fixed-point value times a Q1.63 factor (truncated to zero)
 __device__ __forceinline__ long long scale_q63(long long x, uint64_t m) {
     const uint64_t ax = x < 0 ? (uint64_t)(-x) : (uint64_t)x;
-    const uint64_t r = (__umul64hi(ax, m) << 1) | ((ax * m) >> 63);
+    const uint64_t r = m == Q63_ONE ? ax : __umul64hi(ax, m << 1);
     return x < 0 ? -(long long)r : (long long)r;
 }
 
