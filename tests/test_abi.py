@@ -244,3 +244,17 @@ def test_absorb_host_logic_without_gpu(lib):
     assert call(opts=big) == _lib.FA_ERR_INVALID_ARG
     assert call(ws=None) == _lib.FA_ERR_WORKSPACE
     assert call(nbytes=64) == _lib.FA_ERR_WORKSPACE
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/*.h is a C ABI: it must compile as C99 with warnings as errors."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use_header.c"
+    src.write_text("".join(f'#include "{os.path.basename(h)}"\n' for h in HEADERS) +
+                   "int main(void) { fa_options o = {0, 0, FA_OPT_NO_TMA, FA_CODES_NIBBLE};\n"
+                   "  (void)o; return fa_version() > 0 ? 0 : 1; }\n")
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)])
