@@ -180,6 +180,27 @@ def traffic_for(kernel: str):
     return rec.get("bytes_per_launch")
 
 
+def issue_roofline(kernel: str, ms: float, sm_mhz: float, sms: int, path=None):
+    """The kernel's achieved instruction issue rate against the GPU's ceiling:
+    warp instructions per launch (from the same ncu capture as its traffic,
+    scaled to the launch, valid only for the hashed kernel sources) over the
+    live launch duration, against 4 warp instructions per clock per SM (one
+    per scheduler) at the sampled SM clock.  None when unknown or stale."""
+    try:
+        with open(path or os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+        if not rec or rec.get("source_sha1") != source_sha1() or not (ms > 0 and sm_mhz > 0 and sms > 0):
+            return None
+        inst = float(rec["warp_instructions_per_launch"])
+    except Exception:
+        return None
+    achieved = inst / (ms / 1e3)
+    peak = sms * 4 * sm_mhz * 1e6
+    return {"bound": "issue", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_launch": inst}
+
+
 def source_sha1() -> str:
     """Hash of the sources that define the forward kernels (pass 1, the
     perimeter-graph resolve, pass 2)."""
@@ -583,6 +604,9 @@ def main():
         "clocks": clocks,
     }
     line["gpu_launches"] = args.steps * fa.fa_kernel_launches(ROWS, COLS, opts)
+    # what bounds the dominant kernel in fact: instruction issue, not HBM
+    line["roofline_issue"] = issue_roofline(names[dom], ph[dom], clocks.get("sm_mhz") or 0.0,
+                                            torch.cuda.get_device_properties(dev).multi_processor_count)
 
     d8_data = absorb_data = None
     if not args.no_extra:
