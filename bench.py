@@ -165,9 +165,11 @@ def job_throughput(units_per_rank: int, ms_max: float, ws: int) -> float:
     return ws * units_per_rank / (ms_max / 1e3)
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, cells: int = ROWS * COLS):
     """dram bytes per launch recorded from an ncu capture of this exact kernel
-    source (profiles/traffic.json); None when absent or stale."""
+    source (profiles/traffic.json), scaled from the launch it describes to
+    `cells` (traffic grows with the number of tiles); None when absent or
+    stale."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel)
@@ -175,12 +177,13 @@ def traffic_for(kernel: str):
         return None
     if not rec:
         return None
-    if rec.get("source_sha1") != source_sha1():
+    if rec.get("source_sha1") != source_sha1() or "bytes_per_launch" not in rec:
         return None
-    return rec.get("bytes_per_launch")
+    return int(round(rec["bytes_per_launch"] * cells / rec.get("launch_cells", cells)))
 
 
-def issue_roofline(kernel: str, ms: float, sm_mhz: float, sms: int, path=None):
+def issue_roofline(kernel: str, ms: float, sm_mhz: float, sms: int, path=None,
+                   cells: int = ROWS * COLS):
     """The kernel's achieved instruction issue rate against the GPU's ceiling:
     warp instructions per launch (from the same ncu capture as its traffic,
     scaled to the launch, valid only for the hashed kernel sources) over the
@@ -191,7 +194,7 @@ def issue_roofline(kernel: str, ms: float, sm_mhz: float, sms: int, path=None):
             rec = json.load(f).get(kernel)
         if not rec or rec.get("source_sha1") != source_sha1() or not (ms > 0 and sm_mhz > 0 and sms > 0):
             return None
-        inst = float(rec["warp_instructions_per_launch"])
+        inst = float(rec["warp_instructions_per_launch"]) * cells / rec.get("launch_cells", cells)
     except Exception:
         return None
     achieved = inst / (ms / 1e3)
@@ -582,7 +585,7 @@ def main():
     ach = alg[dom] / (ph[dom] / 1e3) / 1e9 if alg[dom] else 0.0
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "peak_kind": peak_kind,
-            "traffic": traffic_for(names[dom])}
+            "traffic": traffic_for(names[dom], cells)}
     step_ach = cells * BYTES_PER_CELL_COUNTS / (ms / 1e3) / 1e9
     roof_step = {"bound": "hbm", "achieved": step_ach, "peak": peak, "unit": "GB/s",
                  "frac": step_ach / peak, "bytes_per_cell": BYTES_PER_CELL_COUNTS}
@@ -606,7 +609,8 @@ def main():
     line["gpu_launches"] = args.steps * fa.fa_kernel_launches(ROWS, COLS, opts)
     # what bounds the dominant kernel in fact: instruction issue, not HBM
     line["roofline_issue"] = issue_roofline(names[dom], ph[dom], clocks.get("sm_mhz") or 0.0,
-                                            torch.cuda.get_device_properties(dev).multi_processor_count)
+                                            torch.cuda.get_device_properties(dev).multi_processor_count,
+                                            cells=cells)
 
     d8_data = absorb_data = None
     if not args.no_extra:

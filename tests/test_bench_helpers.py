@@ -24,3 +24,12 @@ def test_issue_roofline_unknown_or_stale(tmp_path):
                                                       "warp_instructions_per_launch": 1.0}}))
     assert bench.issue_roofline("pass1_tile_solve", 5.0, 2000.0, 100, path=str(stale)) is None
     assert bench.issue_roofline("pass1_tile_solve", 5.0, 2000.0, 100, path=str(tmp_path / "none")) is None
+
+
+def test_recorded_counts_scale_with_the_raster():
+    full = bench.traffic_for("pass1_tile_solve", 16384 * 16384)
+    quarter = bench.traffic_for("pass1_tile_solve", 8192 * 8192)
+    assert full and quarter and abs(4 * quarter - full) <= 4
+    a = bench.issue_roofline("pass1_tile_solve", 1.0, 2000.0, 100, cells=16384 * 16384)
+    b = bench.issue_roofline("pass1_tile_solve", 1.0, 2000.0, 100, cells=8192 * 8192)
+    assert abs(a["warp_instructions_per_launch"] - 4 * b["warp_instructions_per_launch"]) < 1.0
