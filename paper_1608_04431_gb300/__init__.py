@@ -8,6 +8,10 @@ also allocates the output and a cached workspace.
 
 Flow accumulation (the paper's Eq. 1 with alpha in {0,1}): for every valid
 cell p, A(p) = w(p) + sum of A(n) over neighbours n that drain into p.
+Besides the plain form: batches (accumulate_batched, BatchPlan), the adjoint
+(adjoint, FlowAccumulate), absorption (absorb: Eq. 1 with one factor per
+cell), D8 codes from elevations (d8_codes), packed and translated codes
+(PackedCodes, pack_codes, recode) and the tile-shape autotuner (autotune).
 """
 from __future__ import annotations
 
