@@ -299,7 +299,10 @@ _ws_cache: dict = {}
 
 
 def workspace(nbytes: int, device) -> torch.Tensor:
-    """A cached uint8 workspace of at least nbytes on `device` (torch memory)."""
+    """A cached uint8 workspace of at least nbytes on `device` (torch memory).
+    accumulate, absorb, adjoint and autotune share this one buffer per device,
+    so their calls must not overlap on the GPU: issue them on one stream, or
+    give concurrent calls their own workspaces through the fa_* functions."""
     key = torch.device(device)
     if key.type == "cuda" and key.index is None:  # "cuda" and "cuda:N" share one buffer
         key = torch.device("cuda", torch.cuda.current_device())
