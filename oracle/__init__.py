@@ -24,7 +24,10 @@ Each returns the values plus a ``state`` array: 0 NoData, 1 exact,
 
 Parity status: every function is pinned by tests/test_oracle.py (hand-worked
 examples, closed forms, conservation, brute force, cycle cases, the adjoint
-dot-product identity and central finite differences).
+dot-product identity and central finite differences), and
+tests/test_oracle_mutants.py shows that planted mistakes in a copy of this
+oracle (one-line changes to the C source, or a replaced decoder) each make a
+pin fail.
 """
 from __future__ import annotations
 
