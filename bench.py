@@ -165,13 +165,13 @@ def job_throughput(units_per_rank: int, ms_max: float, ws: int) -> float:
     return ws * units_per_rank / (ms_max / 1e3)
 
 
-def traffic_for(kernel: str, cells: int = ROWS * COLS):
+def traffic_for(kernel: str, cells: int = ROWS * COLS, path=None):
     """dram bytes per launch recorded from an ncu capture of this exact kernel
     source (profiles/traffic.json), scaled from the launch it describes to
     `cells` (traffic grows with the number of tiles); None when absent or
     stale."""
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        with open(path or os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel)
     except Exception:
         return None
@@ -742,7 +742,7 @@ def main():
             dta = time.perf_counter() - t0
             ok = ref_a.state == 1
             err = np.abs(got_a[ok].astype(np.float64) - ref_a.values[ok])
-            bound = 2e-5 * np.abs(ref_a.values[ok]) + 1e-9 * np.abs(ref_a.values[ok]).max()
+            bound = 2e-5 * np.abs(ref_a.values[ok])
             rec = line["forms"]["absorb"]
             rec["parity_vs_oracle"] = ("within 2e-5 relative" if bool((err <= bound).all())
                                        else "MISMATCH")

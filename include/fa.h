@@ -307,11 +307,12 @@ fa_status fa_autotune_batched(const fa_raster *rasters, int32_t n_rasters, int32
  * the process exits), and the call allocates nothing.
  *  - Size limit: rasters whose fa_workspace_size() exceeds
  *    FA_NOALLOC_SCRATCH_BYTES return FA_ERR_TOO_LARGE with nothing enqueued
- *    (with the default 64 x 64 tiles that is roughly 15 million cells, e.g.
- *    3800 x 3800).
- *  - The first call on each device looks up the buffer's device address
- *    (cudaGetSymbolAddress, which may load the library's module); make that
- *    first call outside any stream capture.
+ *    (with the default 64 x 64 tiles that is about 5.9 million cells: square
+ *    rasters up to 2432 x 2432 fit, 2450 x 2450 does not).
+ *  - Every call looks up the buffer's device address on the current device
+ *    (cudaGetSymbolAddress); the first call on a device may load the
+ *    library's module there, so make that first call outside any stream
+ *    capture.
  *  - All calls on a device share the buffer: calls that can overlap on the GPU
  *    race and give wrong results; order them on one stream or synchronise.
  *  - d_status may be NULL, in which case device-detected conditions are
@@ -392,6 +393,22 @@ fa_status fa_accumulate_absorb(const uint8_t *codes, int64_t rows, int64_t cols,
  */
 fa_status fa_status_read(const int32_t *d_status, const void *workspace, void *stream,
                          int64_t *count, int64_t *first_index);
+
+/*
+ * Self-test of the bounded device wait.  The staged tile loads of pass 1 wait
+ * on an mbarrier for each copy; that wait gives up after a time limit, sets
+ * FA_FLAG_TIMEOUT in the status block and lets the kernel return, so a copy
+ * that never completes becomes an error status instead of a hang.  This call
+ * runs that same wait, with a limit of limit_ns nanoseconds (0 .. 1e10),
+ * against a barrier phase that no arrival or copy will ever complete, with no
+ * copy in flight: the status block d_status (device int32[FA_STATUS_WORDS],
+ * 8-byte aligned, required) is reset and then records FA_FLAG_TIMEOUT with a
+ * count of 1, which fa_status_read reports as FA_ERR_TIMEOUT.  The GPU context
+ * stays usable.  The paper has no counterpart (it has no device waits).
+ * Asynchronous on `stream`; FA_ERR_INVALID_ARG for a NULL or misaligned
+ * d_status or a limit out of range, FA_ERR_CUDA if the launch fails.
+ */
+fa_status fa_selftest_wait_timeout(int64_t limit_ns, int32_t *d_status, void *stream);
 
 /*
  * Phase timing (a tracing aid, not part of the computation).  While enabled,

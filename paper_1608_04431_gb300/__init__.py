@@ -31,7 +31,7 @@ __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumula
            "fa_batched_workspace_size", "fa_accumulate_batched", "fa_batched_plan_create",
            "fa_plan_launch", "fa_plan_destroy", "accumulate_batched", "BatchPlan",
            "fa_accumulate_noalloc", "fa_accumulate_adjoint", "fa_status_read", "adjoint", "FlowAccumulate",
-           "fa_timing_enable", "fa_timing_read", "accumulate",
+           "fa_timing_enable", "fa_timing_read", "accumulate", "fa_selftest_wait_timeout",
            "fa_autotune_workspace_size", "fa_autotune", "fa_autotune_batched_workspace_size",
            "fa_autotune_batched", "autotune", "autotune_batched", "fa_d8_codes", "d8_codes",
            "fa_recode", "recode", "pack_codes", "PackedCodes", "power_of_two_table",
@@ -277,6 +277,14 @@ def fa_status_read(d_status=None, workspace=None, stream=None):
     st = _lib.load().fa_status_read(_ptr(d_status), _ptr(workspace), _stream_ptr(stream),
                                     ctypes.byref(cnt), ctypes.byref(first))
     return st, cnt.value, first.value
+
+
+def fa_selftest_wait_timeout(limit_ns: int, d_status, stream=None) -> int:
+    """Enqueue the bounded-wait self-test: one device wait that can never
+    complete gives up after limit_ns and records FA_FLAG_TIMEOUT in d_status
+    (read it back with fa_status_read).  Returns the host-side status."""
+    return _lib.load().fa_selftest_wait_timeout(int(limit_ns), _ptr(d_status),
+                                                _stream_ptr(stream))
 
 
 def fa_timing_enable(on: bool) -> None:

@@ -18,6 +18,10 @@ extern "C" int32_t fa_version(void) { return 100; }
 // ---- phase timing ---------------------------------------------------------
 namespace {
 bool g_timing = false;
+// per host thread: phase events are not recorded while set (tuning loops,
+// graph capture, the no-allocation entry point), whatever g_timing says, so
+// one thread suppressing them never changes another thread's setting
+thread_local bool t_quiet = false;
 cudaEvent_t g_ev[kMaxPhase + 1];
 bool g_ev_made = false;
 int g_phases = 0;
@@ -25,7 +29,7 @@ int g_phases = 0;
 
 namespace fa {
 void timing_mark(int i, cudaStream_t s) {
-    if (!g_timing || i > kMaxPhase) return;
+    if (!g_timing || t_quiet || i > kMaxPhase) return;
     if (!g_ev_made) {
         for (int j = 0; j <= kMaxPhase; ++j) cudaEventCreate(&g_ev[j]);
         g_ev_made = true;
@@ -33,11 +37,11 @@ void timing_mark(int i, cudaStream_t s) {
     cudaEventRecord(g_ev[i], s);
 }
 void timing_set_count(int n) {
-    if (g_timing) g_phases = n;
+    if (g_timing && !t_quiet) g_phases = n;
 }
 bool timing_swap(bool on) {
-    const bool was = g_timing;
-    g_timing = on;
+    const bool was = !t_quiet;
+    t_quiet = !on;
     return was;
 }
 }  // namespace fa

@@ -94,7 +94,8 @@ size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry
 constexpr int kMaxPhase = 8;
 void timing_mark(int i, cudaStream_t s);
 void timing_set_count(int n);
-// sets whether phase timing records events; returns the previous setting
+// on this host thread only: allows (true) or suppresses (false) phase
+// events; returns the previous setting of this thread
 bool timing_swap(bool on);
 
 // Configures the forward kernels (shared-memory limits, device queries) so

@@ -10,43 +10,22 @@
 //
 // The buffer is a file-scope __device__ array.  On the host its name only
 // stands in for the symbol; the device address comes from
-// cudaGetSymbolAddress, looked up once per device (with that device current)
-// on the first call made on that device and cached afterwards.  Every call on
-// a device shares the one buffer: calls that may overlap on the GPU (different
-// streams, or host threads without ordering between them) race and corrupt
-// each other's results, so serialise them.  The buffer keeps whatever the
-// previous call left in it; the pipeline resets the parts it reads before
-// writing them (the status block and the round counters are cleared by its
-// first kernel; every per-tile and per-node record is written before it is
-// read), so no stale value reaches a result.
-#include <mutex>
-
+// cudaGetSymbolAddress, asked on every call with the caller's device current
+// (cheap once the module is loaded, and never stale: a device reset or a new
+// primary context may load the module at another address).  The first call on
+// a device may load the library's module there, so make it outside any stream
+// capture.  Every call on a device shares the one buffer: calls that may
+// overlap on the GPU (different streams, or host threads without ordering
+// between them) race and corrupt each other's results, so serialise them.
+// The buffer keeps whatever the previous call left in it; the pipeline resets
+// the parts it reads before writing them (the status block and the round
+// counters are cleared by its first kernel; every per-tile and per-node record
+// is written before it is read), so no stale value reaches a result.
 #include "fa_internal.h"
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FA_NOALLOC_SCRATCH_BYTES];
-
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kMaxDevices];
-
-// Device address of the scratch array on the current device (nullptr on a
-// CUDA error).  Looked up once per device.
-void *scratch_for_current_device(cudaError_t &err) {
-    int dev = 0;
-    err = cudaGetDevice(&dev);
-    if (err != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (err != cudaSuccess) return nullptr;
-        g_noalloc_ptr[dev] = p;
-    }
-    return g_noalloc_ptr[dev];
-}
 
 bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
@@ -64,6 +43,11 @@ extern "C" fa_status fa_accumulate_noalloc(const uint8_t *codes, int64_t rows, i
     if (out_dtype != FA_OUT_U32 && out_dtype != FA_OUT_F32) return FA_ERR_INVALID_ARG;
     if (out_dtype == FA_OUT_U32 && weights) return FA_ERR_INVALID_ARG;
     if (!forward_tile_ok(g, out_dtype == FA_OUT_F32 ? 1 : 0)) return FA_ERR_INVALID_ARG;
+    {
+        FwdWork need;
+        if (carve_forward(nullptr, 0, g, need, true) > (size_t)FA_NOALLOC_SCRATCH_BYTES)
+            return FA_ERR_TOO_LARGE;
+    }
     const bool empty = rows == 0 || cols == 0;
     if (!empty) {
         if (!codes || !out) return FA_ERR_INVALID_ARG;
@@ -73,17 +57,16 @@ extern "C" fa_status fa_accumulate_noalloc(const uint8_t *codes, int64_t rows, i
         if (!aligned_to(out, 4) || (weights && !aligned_to(weights, 4))) return FA_ERR_INVALID_ARG;
     }
     if (d_status && !aligned_to(d_status, 8)) return FA_ERR_INVALID_ARG;
+    void *scratch = nullptr;
+    if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch)
+        return FA_ERR_CUDA;
     FwdWork w;
-    if (carve_forward(nullptr, 0, g, w, true) > (size_t)FA_NOALLOC_SCRATCH_BYTES)
-        return FA_ERR_TOO_LARGE;
-    cudaError_t err;
-    void *scratch = scratch_for_current_device(err);
-    if (!scratch) return FA_ERR_CUDA;
     carve_forward(scratch, (size_t)FA_NOALLOC_SCRATCH_BYTES, g, w, false);
-    // phase timing would create CUDA events on first use: keep it off here
+    // phase timing would create CUDA events on first use: none on this thread
     const bool timing = timing_swap(false);
-    err = launch_forward(g, codes, pitch_codes, mask, pitch_mask, weights, pitch_w, out, pitch_out,
-                         out_dtype == FA_OUT_F32 ? 1 : 0, w, d_status, (cudaStream_t)stream);
+    const cudaError_t err =
+        launch_forward(g, codes, pitch_codes, mask, pitch_mask, weights, pitch_w, out, pitch_out,
+                       out_dtype == FA_OUT_F32 ? 1 : 0, w, d_status, (cudaStream_t)stream);
     timing_swap(timing);
     return err == cudaSuccess ? FA_OK : FA_ERR_CUDA;
 }

@@ -70,6 +70,31 @@ def test_noalloc_matches_fa_accumulate_on_consecutive_calls():
     np.testing.assert_array_equal(_u32(out_c), ref_a)
 
 
+@pytest.mark.gpu
+def test_noalloc_staged_code_tiles_match_and_oracle(oracle_mod):
+    """An unmasked raster whose width is a multiple of 16, so that pass 1
+    stages its code tiles by TMA (with the bounded barrier wait) inside the
+    no-allocation entry point too: bit for bit against fa_accumulate, and the
+    counts against the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    status = torch.zeros(fa.FA_STATUS_WORDS, dtype=torch.int32, device=dev)
+    codes = synth.dem_codes(1536, 2048, 11)
+    c = torch.from_numpy(codes).to(dev)
+    assert c.data_ptr() % 16 == 0
+    ref = _u32(fa.accumulate(c))
+    for _ in range(2):  # two calls in a row on the shared buffer
+        out = torch.full(codes.shape, 7, dtype=torch.uint32, device=dev)
+        st = fa.fa_accumulate_noalloc(c, None, None, out, fa.FA_OUT_U32, fa.options(), status,
+                                      stream)
+        assert st == fa.FA_OK
+        assert fa.fa_status_read(status, None, stream)[0] == fa.FA_OK
+        np.testing.assert_array_equal(_u32(out), ref)
+    np.testing.assert_array_equal(ref, oracle_mod.counts(codes).values.astype(np.uint32))
+
+
 def test_noalloc_rejects_rasters_beyond_its_buffer():
     """Host-side check: a raster whose scratch would not fit the fixed buffer
     is refused with FA_ERR_TOO_LARGE before anything reaches a GPU."""
@@ -82,3 +107,16 @@ def test_noalloc_rejects_rasters_beyond_its_buffer():
     st = lib.fa_accumulate_noalloc(fake, n, n, n, None, 0, None, 0, fake, fa.FA_OUT_U32, n,
                                    ctypes.byref(o), None, None)
     assert st == fa.FA_ERR_TOO_LARGE
+
+
+@pytest.mark.parametrize("n,fits", [(2400, True), (2432, True), (2450, False)])
+def test_noalloc_size_boundary(n, fits):
+    """The limit stated in include/fa.h for the default 64 x 64 tiles: square
+    rasters up to 2432 x 2432 pass the size check, 2450 x 2450 does not.  NULL
+    buffers make an accepted size fail the later pointer check, so nothing is
+    ever enqueued."""
+    lib = fa._lib.load()
+    o = fa.fa_options()
+    st = lib.fa_accumulate_noalloc(None, n, n, n, None, 0, None, 0, None, fa.FA_OUT_U32, n,
+                                   ctypes.byref(o), None, None)
+    assert st == (fa.FA_ERR_INVALID_ARG if fits else fa.FA_ERR_TOO_LARGE)
