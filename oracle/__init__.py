@@ -14,6 +14,10 @@ Functions (all on numpy arrays, row-major, row 0 = north):
   bruteforce(codes, w, mask)     -> FP64 path-walking sums straight from the
                                     definition (small rasters only)
   residual_u32(codes, A, mask)   -> number of cells violating Eq. 1 (mod 2^32)
+  residual_u32_rows(...)         -> the same on a band of rows
+  outlet_sum_u32(codes, A, ...)  -> conservation: sum of A over terminal cells
+                                    and the number of valid cells
+  verify_counts_u32(codes, A)    -> both over row bands on host threads (any size)
   d8(z, nodata)                  -> uint8 D8 codes from float32 elevations (the
                                     direction step before accumulation)
   unpack_nibbles(packed, cols)   -> uint8 codes from codes stored two per byte
@@ -73,6 +77,11 @@ def _configure(lib):
     lib.fa_oracle_bruteforce.restype = ctypes.c_int
     lib.fa_oracle_residual_u32.argtypes = [p, i64, i64, i64, p, i64, p, i64, pi64]
     lib.fa_oracle_residual_u32.restype = ctypes.c_int64
+    lib.fa_oracle_residual_u32_rows.argtypes = [p, i64, i64, i64, p, i64, p, i64, i64, i64, pi64]
+    lib.fa_oracle_residual_u32_rows.restype = ctypes.c_int64
+    lib.fa_oracle_outlet_sum_u32.argtypes = [p, i64, i64, i64, p, i64, p, i64, i64, i64,
+                                             ctypes.POINTER(ctypes.c_uint64), pi64]
+    lib.fa_oracle_outlet_sum_u32.restype = None
     return lib
 
 
@@ -199,6 +208,60 @@ def residual_u32(codes, A, mask=None):
     bad = _load().fa_oracle_residual_u32(_p(codes), R, C, C, _p(mask), C, _p(A), C,
                                          ctypes.byref(first))
     return int(bad), int(first.value)
+
+
+def residual_u32_rows(codes, A, r_begin: int, r_end: int, mask=None):
+    """The Eq. 1 residual check of residual_u32 on rows r_begin..r_end-1 only
+    (neighbours read from the whole raster): (mismatches, first_index)."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    A = np.ascontiguousarray(A, dtype=np.uint32)
+    first = ctypes.c_int64(-1)
+    bad = _load().fa_oracle_residual_u32_rows(_p(codes), R, C, C, _p(mask), C, _p(A), C,
+                                              int(r_begin), int(r_end), ctypes.byref(first))
+    return int(bad), int(first.value)
+
+
+def outlet_sum_u32(codes, A, r_begin: int = 0, r_end: int | None = None, mask=None):
+    """Conservation on rows r_begin..r_end-1: (sum of A over terminal cells,
+    number of valid cells).  Over a whole acyclic raster with unit weights
+    they are equal (modulo 2^32 if a count wrapped)."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    A = np.ascontiguousarray(A, dtype=np.uint32)
+    s, nv = ctypes.c_uint64(0), ctypes.c_int64(0)
+    _load().fa_oracle_outlet_sum_u32(_p(codes), R, C, C, _p(mask), C, _p(A), C, int(r_begin),
+                                     int(R if r_end is None else r_end), ctypes.byref(s),
+                                     ctypes.byref(nv))
+    return int(s.value), int(nv.value)
+
+
+def verify_counts_u32(codes, A, threads: int = 1, band: int = 1024, mask=None):
+    """Complete check of uint32 counts on an acyclic raster of any size: the
+    Eq. 1 residual at every cell and conservation, over row bands in a pool
+    of host threads (the C calls release the interpreter lock).  Returns a
+    dict with mismatches, first mismatching index, outlet sum, valid cells
+    and whether conservation holds exactly and modulo 2^32."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    codes, mask = _prep(codes, mask)
+    A = np.ascontiguousarray(A, dtype=np.uint32)
+    R = codes.shape[0]
+    bands = [(r, min(R, r + band)) for r in range(0, R, band)]
+
+    def one(b):
+        bad, f = residual_u32_rows(codes, A, b[0], b[1], mask)
+        s, nv = outlet_sum_u32(codes, A, b[0], b[1], mask)
+        return bad, f, s, nv
+
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        res = list(ex.map(one, bands))
+    bad = sum(r[0] for r in res)
+    firsts = [r[1] for r in res if r[1] >= 0]
+    s = sum(r[2] for r in res)
+    nv = sum(r[3] for r in res)
+    return {"mismatches": bad, "first": min(firsts) if firsts else -1, "outlet_sum": s,
+            "n_valid": nv, "conserved": s == nv, "conserved_mod_2_32": (s - nv) % (1 << 32) == 0}
 
 
 def d8(z, nodata=None) -> np.ndarray:

@@ -287,12 +287,30 @@ int fa_oracle_bruteforce(const uint8_t *codes, int64_t rows, int64_t cols, int64
  * whole raster exact.  Returns the number of mismatching cells; *first gets the
  * first mismatching index (r*cols+c) or -1.
  */
+int64_t fa_oracle_residual_u32_rows(const uint8_t *codes, int64_t rows, int64_t cols,
+                                    int64_t pitch, const uint8_t *mask, int64_t mpitch,
+                                    const uint32_t *A, int64_t apitch, int64_t r_begin,
+                                    int64_t r_end, int64_t *first);
+
 int64_t fa_oracle_residual_u32(const uint8_t *codes, int64_t rows, int64_t cols, int64_t pitch,
                                const uint8_t *mask, int64_t mpitch, const uint32_t *A,
                                int64_t apitch, int64_t *first) {
+    return fa_oracle_residual_u32_rows(codes, rows, cols, pitch, mask, mpitch, A, apitch, 0, rows,
+                                       first);
+}
+
+/* The same check restricted to the rows r_begin .. r_end - 1 of the raster
+ * (the neighbours are still read from the whole raster), so that disjoint row
+ * bands of one raster can be checked independently. */
+int64_t fa_oracle_residual_u32_rows(const uint8_t *codes, int64_t rows, int64_t cols,
+                                    int64_t pitch, const uint8_t *mask, int64_t mpitch,
+                                    const uint32_t *A, int64_t apitch, int64_t r_begin,
+                                    int64_t r_end, int64_t *first) {
     raster R = {codes, mask, rows, cols, pitch, mpitch};
     int64_t bad = 0, f = -1;
-    for (int64_t r = 0; r < rows; ++r)
+    if (r_begin < 0) r_begin = 0;
+    if (r_end > rows) r_end = rows;
+    for (int64_t r = r_begin; r < r_end; ++r)
         for (int64_t c = 0; c < cols; ++c) {
             uint32_t expect;
             if (!valid_cell(&R, r, c)) {
@@ -312,6 +330,34 @@ int64_t fa_oracle_residual_u32(const uint8_t *codes, int64_t rows, int64_t cols,
         }
     if (first) *first = f;
     return bad;
+}
+
+/*
+ * Conservation (Eq. 1 summed over the raster): every valid cell's weight
+ * ends in exactly one terminal cell, a valid cell without a downstream cell
+ * (NoFlow, or flow off the grid or into NoData).  Over the rows r_begin ..
+ * r_end - 1 this adds A over the terminal cells (as uint64, from uint32
+ * results) into *outlet_sum and counts the valid cells into *n_valid.  Over a
+ * whole acyclic raster with unit weights the two totals are equal, and equal
+ * modulo 2^32 when some terminal count wrapped in uint32.
+ */
+void fa_oracle_outlet_sum_u32(const uint8_t *codes, int64_t rows, int64_t cols, int64_t pitch,
+                              const uint8_t *mask, int64_t mpitch, const uint32_t *A,
+                              int64_t apitch, int64_t r_begin, int64_t r_end,
+                              uint64_t *outlet_sum, int64_t *n_valid) {
+    raster R = {codes, mask, rows, cols, pitch, mpitch};
+    uint64_t s = 0;
+    int64_t nv = 0;
+    if (r_begin < 0) r_begin = 0;
+    if (r_end > rows) r_end = rows;
+    for (int64_t r = r_begin; r < r_end; ++r)
+        for (int64_t c = 0; c < cols; ++c) {
+            if (!valid_cell(&R, r, c)) continue;
+            ++nv;
+            if (downstream(&R, r, c) < 0) s += A[r * apitch + c];
+        }
+    *outlet_sum = s;
+    *n_valid = nv;
 }
 
 /*

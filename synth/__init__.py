@@ -51,6 +51,8 @@ def _load():
         i64, p = ctypes.c_int64, ctypes.c_void_p
         lib.synth_priority_flood_eps.argtypes = [p, p, i64, i64, ctypes.c_float]
         lib.synth_priority_flood_eps.restype = ctypes.c_int
+        lib.synth_priority_flood_eps4.argtypes = [p, p, i64, i64, ctypes.c_float]
+        lib.synth_priority_flood_eps4.restype = ctypes.c_int
         lib.synth_d8.argtypes = [p, p, i64, i64, p]
         lib.synth_d8.restype = None
         lib.synth_bilinear_up.argtypes = [p, i64, i64, i64, p]
@@ -109,10 +111,15 @@ def nodata_disk(rows: int, cols: int, seed: int, frac: float = 0.01, radius: flo
     return (rr * rr + ccs * ccs) <= radius * radius
 
 
-def priority_flood_eps(dem: np.ndarray, nodata: np.ndarray, eps: float = 1e-4) -> np.ndarray:
+def priority_flood_eps(dem: np.ndarray, nodata: np.ndarray, eps: float = 1e-4,
+                       edge_only: bool = False) -> np.ndarray:
+    """Priority-flood eps fill; edge_only spreads the flood to the four edge
+    neighbours only, so that every filled cell is strictly above an edge
+    neighbour."""
     z = np.ascontiguousarray(dem, dtype=np.float32).copy()
     nd = np.ascontiguousarray(nodata, dtype=np.uint8)
-    rc = _load().synth_priority_flood_eps(_ptr(z), _ptr(nd), z.shape[0], z.shape[1], float(eps))
+    fn = _load().synth_priority_flood_eps4 if edge_only else _load().synth_priority_flood_eps
+    rc = fn(_ptr(z), _ptr(nd), z.shape[0], z.shape[1], float(eps))
     if rc != 0:
         raise MemoryError("priority flood: allocation failed")
     return z
@@ -328,3 +335,132 @@ def gauges(valid_mask: np.ndarray, counts: np.ndarray, n: int, seed: int, min_co
     cand = np.flatnonzero((counts.ravel() >= min_count) & valid_mask.ravel())
     g = rng(seed)
     return np.sort(g.choice(cand, size=min(n, cand.size), replace=False))
+
+
+# ---------------------------------------------------------------------------
+# the 1e10-cell scale raster, generated on a torch device band by band
+# ---------------------------------------------------------------------------
+def _fmix32(h, torch):
+    """murmur3's 32-bit finaliser on int64 tensors holding values < 2^32."""
+    m = 0xFFFFFFFF
+    h = h ^ (h >> 16)
+    h = (h * 0x85EBCA6B) & m
+    h = h ^ (h >> 13)
+    h = (h * 0xC2B2AE35) & m
+    return h ^ (h >> 16)
+
+
+def cell_noise(idx, seed: int, amp: float, torch):
+    """Counter-based white noise U[-amp, amp) for global cell indices idx
+    (int64 tensor): two rounds of murmur3's finaliser over (seed, index), top
+    24 bits as a uniform fraction, in float64.  The same cell gets the same
+    value whichever band computes it."""
+    lo = idx & 0xFFFFFFFF
+    hi = idx >> 32
+    h = _fmix32(hi ^ (seed & 0xFFFFFFFF), torch)
+    h = _fmix32(lo ^ h, torch)
+    u = (h >> 8).to(torch.float64) * (1.0 / (1 << 24))
+    return (u * 2.0 - 1.0) * amp
+
+
+def scale_coarse(coarse_rows: int, coarse_cols: int, seed: int, eps: float = 1e-4) -> np.ndarray:
+    """The coarse level of the scale raster: spectral DEM, eps-filled by
+    priority flood (no NoData), float32."""
+    key = f"scale_coarse4/{coarse_rows}/{coarse_cols}/{seed}/{eps}"
+
+    def make():
+        dem = spectral_dem(coarse_rows, coarse_cols, seed)
+        return priority_flood_eps(dem, np.zeros(dem.shape, dtype=bool), eps, edge_only=True)
+
+    return _cached(key, make)
+
+
+def _bilinear_axis(n_fine: int, n_coarse: int, f: int, torch, dev):
+    """Per fine index along one axis: the lower coarse index of its patch and
+    its fraction.  Fine cell i sits at coarse coordinate x = i / f, so every
+    coarse cell centre is also a fine cell centre and the fine cells on a line
+    between two coarse centres interpolate those two alone; past the last
+    coarse centre the last patch is extended linearly (no clamp)."""
+    x = torch.arange(n_fine, device=dev, dtype=torch.float64) / f
+    x0 = torch.clamp(torch.floor(x), 0, max(n_coarse - 2, 0)).to(torch.int64)
+    return x0, x - x0.to(torch.float64)
+
+
+def scale_codes_device(coarse_rows: int, coarse_cols: int, factor: int, seed: int,
+                       noise_seed: int, noise_amp: float = 0.5, band: int = 256,
+                       device="cuda"):
+    """uint8 D8 codes of the scale raster, generated on `device` (a torch
+    device) band by band; returns a [coarse_rows*factor, coarse_cols*factor]
+    uint8 tensor there.
+
+    S is the eps-filled coarse spectral DEM bilinearly upsampled by `factor`
+    (float64, exact for these weights); Z = S + white noise U[-amp, amp)
+    (counter-based, cell_noise).  Each interior cell drains to the neighbour
+    with the steepest Z descent (drop / distance, diagonal distance sqrt 2,
+    ties to the first of E, NE, N, NW, W, SW, S, SE) among the neighbours that
+    are strictly lower in S; with none it is NoFlow.  Border cells drain off
+    the grid (perpendicular, diagonal at the corners).  Because every step
+    goes strictly down in S the codes are acyclic, and because S has no
+    depressions flow follows the coarse drainage across the raster; the noise
+    only picks among the descending neighbours.  This stands in for filling
+    the noisy fine raster itself, whose priority flood over 1e10 cells takes
+    tens of minutes on a host."""
+    import torch
+
+    dev = torch.device(device)
+    F = torch.from_numpy(scale_coarse(coarse_rows, coarse_cols, seed)).to(dev, torch.float64)
+    R, C = coarse_rows * factor, coarse_cols * factor
+    codes = torch.empty((R, C), dtype=torch.uint8, device=dev)
+    xc0, fx = _bilinear_axis(C, coarse_cols, factor, torch, dev)
+    yc0_all, fy_all = _bilinear_axis(R, coarse_rows, factor, torch, dev)
+    xc1 = torch.clamp(xc0 + 1, max=coarse_cols - 1)
+    colidx = torch.arange(C, device=dev, dtype=torch.int64)
+    inv_sqrt2 = 1.0 / np.sqrt(2.0)
+    dirs = [(1, 0, 1), (2, -1, 1), (3, -1, 0), (4, -1, -1), (5, 0, -1), (6, 1, -1), (7, 1, 0),
+            (8, 1, 1)]
+    for r0 in range(0, R, band):
+        r1 = min(R, r0 + band)
+        ra, rb = max(0, r0 - 1), min(R, r1 + 1)  # rows of S and Z with a halo row
+        y0 = yc0_all[ra:rb]
+        y1 = torch.clamp(y0 + 1, max=coarse_rows - 1)
+        fy = fy_all[ra:rb, None]
+        top = F[y0][:, xc0] * (1.0 - fx) + F[y0][:, xc1] * fx
+        bot = F[y1][:, xc0] * (1.0 - fx) + F[y1][:, xc1] * fx
+        S = top * (1.0 - fy) + bot * fy
+        del top, bot
+        rows_idx = torch.arange(ra, rb, device=dev, dtype=torch.int64)[:, None]
+        Z = S + cell_noise(rows_idx * C + colidx[None, :], noise_seed, noise_amp, torch)
+        # a halo row beyond the raster's edge is never lower in S
+        if ra == r0:
+            S = torch.cat([torch.full((1, C), float("inf"), dtype=torch.float64, device=dev), S])
+            Z = torch.cat([torch.zeros((1, C), dtype=torch.float64, device=dev), Z])
+        if rb == r1:
+            S = torch.cat([S, torch.full((1, C), float("inf"), dtype=torch.float64, device=dev)])
+            Z = torch.cat([Z, torch.zeros((1, C), dtype=torch.float64, device=dev)])
+        # rows r0..r1-1 sit at 1..r1-r0 of the haloed arrays
+        i0, i1 = 1, 1 + (r1 - r0)
+        Sc, Zc = S[i0:i1, 1:C - 1], Z[i0:i1, 1:C - 1]
+        best = torch.full(Sc.shape, -float("inf"), dtype=torch.float64, device=dev)
+        code = torch.full(Sc.shape, 9, dtype=torch.uint8, device=dev)
+        for k, dr, dc in dirs:
+            Sn = S[i0 + dr:i1 + dr, 1 + dc:C - 1 + dc]
+            Zn = Z[i0 + dr:i1 + dr, 1 + dc:C - 1 + dc]
+            slope = Zc - Zn
+            if dr and dc:
+                slope = slope * inv_sqrt2
+            take = (Sn < Sc) & (slope > best)
+            best = torch.where(take, slope, best)
+            code = torch.where(take, torch.full_like(code, k), code)
+        out = codes[r0:r1]
+        out[:, 1:C - 1] = code
+        # border cells drain off the grid
+        out[:, 0] = 5
+        out[:, C - 1] = 1
+        if r0 == 0:
+            out[0, :] = 3
+            out[0, 0], out[0, C - 1] = 4, 2
+        if r1 == R:
+            out[-1, :] = 7
+            out[-1, 0], out[-1, C - 1] = 6, 8
+        del S, Z, best, code
+    return codes

@@ -103,8 +103,25 @@ static void rheap_free(rheap *h) {
  * z (non-negative) is modified in place; nodata != 0 marks NoData cells (left
  * untouched).  Returns 0, or -1 on allocation failure.
  */
+static int priority_flood(float *z, const uint8_t *nodata, int64_t rows, int64_t cols, float eps,
+                          int kstep);
+
 int synth_priority_flood_eps(float *z, const uint8_t *nodata, int64_t rows, int64_t cols,
                              float eps) {
+    return priority_flood(z, nodata, rows, cols, eps, 1);
+}
+
+/* The same with the flood spreading to the four edge neighbours only (E, N,
+ * W, S): every cell that is not a seed ends strictly above one of its edge
+ * neighbours.  A bilinear upsampling of such a surface keeps a strictly lower
+ * neighbour at every fine cell (used for the 1e10-cell scale raster). */
+int synth_priority_flood_eps4(float *z, const uint8_t *nodata, int64_t rows, int64_t cols,
+                              float eps) {
+    return priority_flood(z, nodata, rows, cols, eps, 2);
+}
+
+static int priority_flood(float *z, const uint8_t *nodata, int64_t rows, int64_t cols, float eps,
+                          int kstep) {
     int64_t n = rows * cols;
     uint8_t *closed = (uint8_t *)calloc((size_t)n, 1);
     if (!closed) return -1;
@@ -131,7 +148,7 @@ int synth_priority_flood_eps(float *z, const uint8_t *nodata, int64_t rows, int6
         int64_t ti;
         if (rheap_pop(&h, &tz, &ti)) { rc = -1; break; }
         int64_t r = ti / cols, c = ti % cols;
-        for (int k = 1; k <= 8; ++k) {
+        for (int k = 1; k <= 8; k += kstep) {
             int64_t rr = r + SDR[k], cc = c + SDC[k];
             if (rr < 0 || cc < 0 || rr >= rows || cc >= cols) continue;
             int64_t j = rr * cols + cc;

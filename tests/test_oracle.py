@@ -303,6 +303,74 @@ def test_residual_verifier(oracle_mod):
     assert bad >= 1 and first <= 10 * 80 + 20 + 80 + 1
 
 
+def test_residual_rows_partition_the_raster(oracle_mod):
+    """The band form of the residual check: disjoint bands that cover the
+    raster find exactly the mismatches of the whole-raster check, each in the
+    band holding the planted cell (Eq. 1 is checked cell by cell, so a band
+    needs no other band's verdict)."""
+    codes = synth.dem_codes(90, 70, 62)
+    A = oracle_mod.counts(codes).values.astype(np.uint32)
+    B = A.copy()
+    B[47, 33] += 5
+    whole = oracle_mod.residual_u32(codes, B)
+    bands = [oracle_mod.residual_u32_rows(codes, B, r, min(90, r + 16)) for r in range(0, 90, 16)]
+    assert sum(b for b, _ in bands) == whole[0] >= 1
+    assert min(f for _, f in bands if f >= 0) == whole[1]
+    hit = [i for i, (b, _) in enumerate(bands) if b]
+    assert 47 // 16 in hit and all(abs(i * 16 - 47) <= 17 for i in hit)
+    assert all(oracle_mod.residual_u32_rows(codes, A, r, r + 16)[0] == 0 for r in range(0, 90, 16))
+
+
+def test_outlet_sum_hand_5x5(oracle_mod):
+    """Conservation on the hand-worked 5x5 raster: its terminal cells hold
+    19 (off the grid at (0,0)), 2 (into NoData at (2,3)) and 3 (NoFlow at
+    (4,2)), 24 in all, one per valid cell.  The counts come from the golden
+    file, not from the oracle's solver."""
+    g = _golden.load("hand_5x5.txt")
+    A = g["counts"].astype(np.uint32)
+    s, nv = oracle_mod.outlet_sum_u32(g["codes"], A)
+    assert (s, nv) == (24, 24)
+    # bands add up; a wrong terminal value breaks it, a wrong inner value does not
+    parts = [oracle_mod.outlet_sum_u32(g["codes"], A, r, r + 2) for r in range(0, 5, 2)]
+    assert sum(p[0] for p in parts) == 24 and sum(p[1] for p in parts) == 24
+    B = A.copy()
+    B[4, 2] += 1
+    assert oracle_mod.outlet_sum_u32(g["codes"], B)[0] == 25
+    B = A.copy()
+    B[1, 1] += 1
+    assert oracle_mod.outlet_sum_u32(g["codes"], B)[0] == 24
+
+
+def test_outlet_sum_closed_form_and_mask(oracle_mod):
+    """All-east raster, A(r, c) = c + 1 (closed form): the terminal cells are
+    the last column, each holding cols; with a masked column the cells west
+    of it end there instead."""
+    rows, cols = 7, 9
+    codes = np.full((rows, cols), 1, np.uint8)
+    A = np.tile(np.arange(1, cols + 1, dtype=np.uint32), (rows, 1))
+    assert oracle_mod.outlet_sum_u32(codes, A) == (rows * cols, rows * cols)
+    mask = np.zeros((rows, cols), np.uint8)
+    mask[:, 4] = 1
+    Am = np.where(np.arange(cols) < 4, np.arange(1, cols + 1), np.arange(cols) - 4)
+    Am = np.tile(Am.astype(np.uint32), (rows, 1))
+    Am[:, 4] = 0
+    assert oracle_mod.outlet_sum_u32(codes, Am, mask=mask) == (rows * 8, rows * 8)
+    v = oracle_mod.verify_counts_u32(codes, Am, threads=2, band=3, mask=mask)
+    assert v["mismatches"] == 0 and v["conserved"]
+
+
+def test_verify_counts_finds_a_planted_error(oracle_mod):
+    codes = synth.dem_codes(120, 64, 63)
+    A = oracle_mod.counts(codes).values.astype(np.uint32)
+    v = oracle_mod.verify_counts_u32(codes, A, threads=3, band=10)
+    assert v["mismatches"] == 0 and v["first"] == -1 and v["conserved"]
+    assert v["n_valid"] == int(((codes >= 1) & (codes <= 9)).sum())
+    B = A.copy()
+    B[77, 5] -= 1
+    v = oracle_mod.verify_counts_u32(codes, B, threads=3, band=10)
+    assert v["mismatches"] >= 1 and v["first"] <= 77 * 64 + 5
+
+
 def test_synth_dem_is_drained(oracle_mod):
     codes = synth.dem_codes(200, 173, 71)
     r = oracle_mod.counts(codes)

@@ -53,6 +53,12 @@ def first_failing_pin(mod):
 
 # (unique text in fa_oracle.c, its replacement)
 C_MUTANTS = {
+    "conservation: every valid cell counted as a terminal": (
+        "            if (downstream(&R, r, c) < 0) s += A[r * apitch + c];",
+        "            s += A[r * apitch + c];"),
+    "band residual: the last row of a band skipped": (
+        "    for (int64_t r = r_begin; r < r_end; ++r)\n        for (int64_t c = 0; c < cols; ++c) {\n            uint32_t expect;",
+        "    for (int64_t r = r_begin; r < r_end - 1; ++r)\n        for (int64_t c = 0; c < cols; ++c) {\n            uint32_t expect;"),
     "direction table: NE steps south": (
         "static const int ODR[10] = {0, 0, -1, -1, -1, 0, 1, 1, 1, 0};",
         "static const int ODR[10] = {0, 0, 1, -1, -1, 0, 1, 1, 1, 0};"),
