@@ -56,6 +56,18 @@ WORKLOAD = "d8_dem_16384x16384"
 BATCH_N, BATCH_FIELDS, BATCH_SEED, BATCH_SHAPE_SEED = 64, 8, 301, 300
 ADJ_N, ADJ_SEED, ADJ_GAUGES = 8192, 401, 256
 D8_N, D8_SEED = 8192, 201
+# the scale raster: 6250^2 coarse spectral DEM x16 = 100000^2 (1e10 cells)
+SCALE_COARSE, SCALE_F, SCALE_SEED, SCALE_NSEED, SCALE_WSEED = 6250, 16, 501, 502, 503
+TUNE_ROWS = 16384        # the autotuner times candidate tiles on this many rows
+CPU_SAMPLE_ROWS = 2048   # the oracle's bounded sample of the scale raster
+
+
+def pass_bytes(cells: int):
+    """Algorithmic bytes per launch of each phase (counts): pass 1 reads the
+    codes and writes A_loc into the output, the step's whole minimum (5
+    B/cell); the perimeter resolve and pass 2 move O(perimeter) and overhead
+    bytes, not counted."""
+    return {0: cells * BYTES_PER_CELL_COUNTS, 1: 0, 2: 0}
 
 
 def peaks():
@@ -227,19 +239,34 @@ def cpu_oracle_time(codes, sample_rows=None):
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the CPU oracle (Algorithm 1 over a whole raster,
+    one host thread) on bounded samples of the headline workload, printed as
+    the contract's JSON line.  Under torchrun only rank 0 runs."""
     if rank != 0:
         return
-    import synth
-
-    codes = synth.dem_codes(ROWS, COLS, SEED)
     steps = max(1, min(args.steps, 3))
-    rows = ROWS // 4  # each step: a 4096-row band (~6.7e7 cells, a few seconds on one core)
+    if args.workload == "scale":
+        n = args.scale_coarse
+        R = C = n * SCALE_F
+        rows = min(R, CPU_SAMPLE_ROWS)
+        codes = scale_sample_codes(args, rows)  # generated on the host, before any timing
+        workload = f"d8_scale_{R}x{C}"
+        sample = f"rows 0..{rows - 1} of the {R}x{C} scale raster as a raster of their own"
+    else:
+        import synth
+
+        R, C = ROWS, COLS
+        rows = ROWS // 4  # each step: a 4096-row band (~6.7e7 cells, a few seconds on one core)
+        codes = synth.dem_codes(ROWS, COLS, SEED)[:rows]
+        workload = f"d8_dem_{ROWS}x{COLS}"
+        sample = f"first {rows} rows of the {ROWS}x{COLS} raster per step"
+    codes = np.ascontiguousarray(codes)
     vals = []
     for _ in range(max(0, min(args.warmup, 1))):
-        cpu_oracle_time(codes, rows)
+        cpu_oracle_time(codes)
     t_all = 0.0
     for _ in range(steps):
-        v, dt, _, shape = cpu_oracle_time(codes, rows)
+        v, dt, _, shape = cpu_oracle_time(codes)
         vals.append(v)
         t_all += dt
     value = float(np.mean(vals))
@@ -248,10 +275,10 @@ def run_reference(args, ws, rank):
         "value": value, "unit": "cells/s", "n_gpus": args.gpus, "steps": steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_all / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "uint64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rows": ROWS, "cols": COLS, "seed": SEED,
+        "config": {"workload": workload, "rows": R, "cols": C,
                    "reference": "CPU oracle (Kahn queue over the whole raster, Algorithm 1), 1 thread"},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {rows} rows of the {ROWS}x{COLS} raster per step"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -460,15 +487,54 @@ def leg_absorb(fa, dev, stream, codes_d, ms_f32, cells, warmup, reps, peak):
     return rec, data
 
 
+def headline_codes(args, dev):
+    """uint8 codes of the headline raster on `dev`, its workload name and a
+    description of its recipe."""
+    import torch
+
+    import synth
+
+    if args.workload == "scale":
+        n = args.scale_coarse
+        codes_d = synth.scale_codes_device(n, n, SCALE_F, SCALE_SEED, SCALE_NSEED, device=dev)
+        R, C = codes_d.shape
+        return codes_d, f"d8_scale_{R}x{C}", (
+            f"coarse {n}x{n} spectral DEM (seed {SCALE_SEED}) eps-filled (4-connected), "
+            f"bilinear x{SCALE_F}, noise U[-0.5,0.5] m (seed {SCALE_NSEED}); steepest descent "
+            "among neighbours lower in the upsampled surface (acyclic, no NoData)")
+    codes = synth.dem_codes(ROWS, COLS, SEED)
+    return torch.from_numpy(codes).to(dev), f"d8_dem_{ROWS}x{COLS}", (
+        f"spectral DEM (seed {SEED}), 1% NoData disk, priority-flood eps fill, D8")
+
+
+def scale_sample_codes(args, rows: int):
+    """The first `rows` rows of the headline raster, generated on the host
+    (bit-identical to the device generator's rows), as its own raster."""
+    import synth
+
+    if args.workload != "scale":
+        return synth.dem_codes(ROWS, COLS, SEED)[:rows]
+    n = args.scale_coarse
+    full = synth.scale_codes_rows(n, n, SCALE_F, SCALE_SEED, SCALE_NSEED, 0, rows)
+    return full
+
+
 def main():
     global ROWS, COLS, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "dem16384"],
+                    help="headline raster: the 1e10-cell scale raster (default) or the "
+                         "16384^2 spectral DEM")
+    ap.add_argument("--scale-coarse", type=int, default=SCALE_COARSE,
+                    help="coarse side of the scale raster (x16 fine); smaller only for "
+                         "profiler captures and quick checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the f32 and e2e legs")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the end-to-end, f32 and 16384^2 legs")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up and timed steps (for ncu): no clock sampling, phase "
                          "timing, extra legs or CPU baseline")
@@ -476,13 +542,12 @@ def main():
                     help="with --profile: after the timed steps, three calls of the absorption "
                          "form on the same raster")
     ap.add_argument("--tile", default="auto",
-                    help="tile shape HxW for the plain leg, or 'auto' (fa_autotune; default)")
+                    help="tile shape HxW for the headline, or 'auto' (fa_autotune; default)")
     ap.add_argument("--size", type=int, default=ROWS,
-                    help="raster side; smaller than the default only for profiler captures")
+                    help="side of the 16384^2 DEM; smaller only for profiler captures")
     args = ap.parse_args()
     if args.size != ROWS:
         ROWS = COLS = args.size
-        WORKLOAD = f"d8_dem_{ROWS}x{COLS}"
     if args.profile:
         args.no_extra = args.no_cpu_baseline = True
     if args.warmup < 3:
@@ -501,18 +566,24 @@ def main():
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    codes = synth.dem_codes(ROWS, COLS, SEED)
-    cells = codes.size
-    codes_d = torch.from_numpy(codes).to(dev)
-    out_d = torch.empty((ROWS, COLS), dtype=torch.uint32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = peaks()
+    t_gen = time.perf_counter()
+    codes_d, WORKLOAD, recipe = headline_codes(args, dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    R, C = codes_d.shape
+    cells = R * C
     if args.tile == "auto":
-        tile = fa.autotune(codes_d)  # before the timed region
+        # tuned on a band of the raster (its first rows) before the timed region
+        tile = fa.autotune(codes_d[:min(R, TUNE_ROWS)])
+        fa._ws_cache.clear()
+        torch.cuda.empty_cache()
     else:
         tile = tuple(int(v) for v in args.tile.lower().split("x"))
     opts = fa.options(tile)
-    wsz = fa.fa_workspace_size(ROWS, COLS, opts)
-    work = torch.empty(wsz, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    work = torch.empty(fa.fa_workspace_size(R, C, opts), dtype=torch.uint8, device=dev)
+    out_d = torch.empty((R, C), dtype=torch.uint32, device=dev)
 
     def step_counts():
         st = fa.fa_accumulate(codes_d, None, None, out_d, fa.FA_OUT_U32, work, opts, None, stream)
@@ -523,8 +594,9 @@ def main():
         step_counts()
     torch.cuda.synchronize()
     st = fa.fa_status_read(None, work, stream)
-    if st[0] != fa.FA_OK:
+    if st[0] not in (fa.FA_OK, fa.FA_WARN_OVERFLOW):
         raise fa.FlowAccError(st[0], "device status")
+    overflow = st[0] == fa.FA_WARN_OVERFLOW
 
     sampler = ClockSampler(local)
     if not args.profile:
@@ -546,8 +618,6 @@ def main():
     ms_max = max_over_ranks(ms, ws)
     value = job_throughput(cells, ms_max, ws)
 
-    # per-phase durations, live, on the launching stream
-    phases = []
     if args.profile:
         if args.profile_absorb:
             g = torch.Generator(device=dev)
@@ -557,7 +627,7 @@ def main():
             a_d = (torch.rand(codes_d.shape, generator=g, device=dev) * 0.1 + 0.9).clamp_(max=1.0)
             out_a = torch.empty(codes_d.shape, dtype=torch.float32, device=dev)
             opts_a = fa.options(ABS_TILE)
-            work_a = torch.empty(fa.fa_absorb_workspace_size(ROWS, COLS, opts_a),
+            work_a = torch.empty(fa.fa_absorb_workspace_size(R, C, opts_a),
                                  dtype=torch.uint8, device=dev)
             for _ in range(3):
                 s = fa.fa_accumulate_absorb(codes_d, w_d, a_d, None, out_a, work_a, opts_a, None,
@@ -565,126 +635,67 @@ def main():
                 if s != fa.FA_OK:
                     raise fa.FlowAccError(s, "fa_accumulate_absorb")
             torch.cuda.synchronize()
-        print(json.dumps({"profile_run": True, "ms_per_step": ms_max}), flush=True)
+        print(json.dumps({"profile_run": True, "ms_per_step": ms_max, "workload": WORKLOAD}),
+              flush=True)
         return
+
+    # per-phase durations, live, on the launching stream
+    phases = []
     fa.fa_timing_enable(True)
-    for _ in range(5):
+    for _ in range(3):
         step_counts()
         phases.append(fa.fa_timing_read())
     fa.fa_timing_enable(False)
     ph = np.mean(np.array(phases), axis=0).tolist()
     names = ["pass1_tile_solve", "perimeter_graph_resolve", "pass2_tile_finalize"]
     dom = int(np.argmax(ph))
-    # algorithmic bytes per launch of each phase (counts): pass 1 reads the
-    # codes and writes A_loc into the output, which is the step's whole
-    # minimum (5 B/cell); the perimeter resolve and pass 2 (entry-forest
-    # records, offsets on ~12% of cells) move O(perimeter) and overhead bytes
-    # (not counted).
-    alg = {0: cells * 5, 1: 0, 2: 0}
-    peak, peak_kind = peaks()
+    alg = pass_bytes(cells)
     ach = alg[dom] / (ph[dom] / 1e3) / 1e9 if alg[dom] else 0.0
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "peak_kind": peak_kind,
-            "traffic": traffic_for(names[dom], cells)}
+            "bytes_per_launch": alg[dom], "traffic": traffic_for(names[dom], cells)}
     step_ach = cells * BYTES_PER_CELL_COUNTS / (ms / 1e3) / 1e9
     roof_step = {"bound": "hbm", "achieved": step_ach, "peak": peak, "unit": "GB/s",
                  "frac": step_ach / peak, "bytes_per_cell": BYTES_PER_CELL_COUNTS}
-
     line = {
         "metric": "cells/s (D8 flow accumulation, uint32 counts)", "value": value,
         "unit": "cells/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rows": ROWS, "cols": COLS, "seed": SEED,
+        "config": {"workload": WORKLOAD, "rows": R, "cols": C, "recipe": recipe,
                    "tile": list(tile),
-                   "tile_choice": "fa_autotune" if args.tile == "auto" else "fixed",
-                   "weights": "unit",
-                   "out": "uint32",
-                   "l2": "inputs+outputs 1.34 GB > 129 MB L2, no flush",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                   "tile_choice": ("fa_autotune on the first %d rows" % min(R, TUNE_ROWS))
+                   if args.tile == "auto" else "fixed",
+                   "weights": "unit", "out": "uint32",
+                   "l2": "inputs+outputs %.1f GB > 129 MB L2, no flush" % (cells * 5 / 1e9),
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "generation_s": round(t_gen, 1)},
         "roofline": roof, "roofline_step": roof_step,
         "phases_ms": dict(zip(names, ph)),
         "clocks": clocks,
     }
-    line["gpu_launches"] = args.steps * fa.fa_kernel_launches(ROWS, COLS, opts)
-    # what bounds the dominant kernel in fact: instruction issue, not HBM
+    line["gpu_launches"] = args.steps * fa.fa_kernel_launches(R, C, opts)
     line["roofline_issue"] = issue_roofline(names[dom], ph[dom], clocks.get("sm_mhz") or 0.0,
                                             torch.cuda.get_device_properties(dev).multi_processor_count,
                                             cells=cells)
+    if overflow:
+        line["status"] = "FA_WARN_OVERFLOW (a count reached 2^32; outputs are mod 2^32)"
 
-    d8_data = absorb_data = None
+    got_h = codes_h = None
+    forms = {}
     if not args.no_extra:
-        # float32 weighted form on the same raster
-        w_d = torch.from_numpy(synth.uniform_weights(codes.shape, WSEED)).to(dev)
-        outf = torch.empty((ROWS, COLS), dtype=torch.float32, device=dev)
-        tile_f = fa.autotune(codes_d, w_d)
-        opts_f = fa.options(tile_f)
-        work_f = torch.empty(fa.fa_workspace_size(ROWS, COLS, opts_f), dtype=torch.uint8,
-                             device=dev)
-
-        def step_f32():
-            s = fa.fa_accumulate(codes_d, w_d, None, outf, fa.FA_OUT_F32, work_f, opts_f, None,
-                                 stream)
-            if s != fa.FA_OK:
-                raise fa.FlowAccError(s, "fa_accumulate f32")
-
-        for _ in range(args.warmup):
-            step_f32()
-        torch.cuda.synchronize()
-        k2 = max(10, args.steps // 3)
-        e0.record(stream)
-        for _ in range(k2):
-            step_f32()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msf = e0.elapsed_time(e1) / k2
-        line["forms"] = {"plain_u32": {"cells_per_s": cells / (ms / 1e3), "ms": ms},
-                         "plain_f32": {"cells_per_s": cells / (msf / 1e3), "ms": msf,
-                                       "tile": list(tile_f),
-                                       "hbm_frac_step": cells * BYTES_PER_CELL_F32 / (msf / 1e3)
-                                       / 1e9 / peak}}
-        del w_d, outf, work_f
-
-        # packed codes (two per byte, 4.5 B/cell) on the same raster and tile;
-        # packing runs before the timed region
-        pk = fa.pack_codes(codes_d)
-        out_p = torch.empty_like(out_d)
-        opts_p = fa.options(tile, code_format=fa.FA_CODES_NIBBLE)
-
-        def step_packed():
-            s = fa.fa_accumulate(pk, None, None, out_p, fa.FA_OUT_U32, work, opts_p, None, stream)
-            if s != fa.FA_OK:
-                raise fa.FlowAccError(s, "fa_accumulate packed")
-
-        for _ in range(args.warmup):
-            step_packed()
-        msp = _time(step_packed, stream, k2)
-        line["forms"]["plain_u32_packed"] = {
-            "cells_per_s": cells / (msp / 1e3), "ms": msp, "tile": list(tile),
-            "bytes_per_cell": 4.5,
-            "hbm_frac_step": cells * 4.5 / (msp / 1e3) / 1e9 / peak,
-            "identical_to_byte_codes": bool(torch.equal(out_p.view(torch.int32),
-                                                        out_d.view(torch.int32)))}
-        del pk, out_p
-
-        # absorption: every cell passes a share a ~ U[0.9, 1) of its flow on
-        line["forms"]["absorb"], absorb_data = leg_absorb(fa, dev, stream, codes_d, msf, cells,
-                                                          args.warmup, k2, peak)
-        if rank != 0 or args.no_cpu_baseline:
-            absorb_data = None
-
         # end to end through the public API from pinned host buffers
-        h_codes = torch.from_numpy(codes).pin_memory()
-        h_out = torch.empty((ROWS, COLS), dtype=torch.uint32).pin_memory()
-        ke = max(5, args.steps // 20)
+        h_codes = torch.empty((R, C), dtype=torch.uint8).pin_memory()
+        h_codes.copy_(codes_d)
+        h_out = torch.empty((R, C), dtype=torch.uint32).pin_memory()
+        ke = 3 if cells > 2e9 else max(5, args.steps // 4)
 
         def step_e2e():
             codes_d.copy_(h_codes, non_blocking=True)
             step_counts()
             h_out.copy_(out_d, non_blocking=True)
 
-        for _ in range(3):
-            step_e2e()
+        step_e2e()
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(ke):
@@ -693,65 +704,109 @@ def main():
         torch.cuda.synchronize()
         mse = max_over_ranks(e0.elapsed_time(e1) / ke, ws)
         line["e2e"] = {"value": job_throughput(cells, mse, ws), "unit": "cells/s",
-                       "h2d_bytes_per_step": int(codes.nbytes),
-                       "d2h_bytes_per_step": int(cells * 4), "ms_per_step": mse}
-        # the result of the last step must be exact
-        got = h_out.view(torch.int32).numpy().view(np.uint32)
-        del h_codes
+                       "h2d_bytes_per_step": int(cells), "d2h_bytes_per_step": int(cells * 4),
+                       "ms_per_step": mse, "steps": ke}
+        codes_h = h_codes.numpy()
+        got_h = h_out.view(torch.int32).numpy().view(np.uint32)
 
-        # batched and adjoint forms against the plain kernel, same GPU
-        if rank == 0:
-            b = leg_batched(fa, dev, stream, opts, 2, 5)
-            b["hbm_frac_step"] = b["hbm_frac_step"] / peak
-            b["ns_per_cell_plain_f32"] = msf * 1e6 / cells
-            b["time_per_cell_vs_plain_f32"] = b["ns_per_cell_field"] / b["ns_per_cell_plain_f32"]
-            line["forms"]["batched"] = b
-            torch.cuda.empty_cache()
-            line["forms"]["d8_directions"], d8_data = leg_d8(fa, dev, stream, 3, 50, peak)
-            torch.cuda.empty_cache()
-            a = leg_adjoint(fa, dev, stream, fa.options(TILE), 3, 20)
-            a["hbm_frac_step"] = a["hbm_frac_step"] / peak
-            a["time_per_cell_vs_plain_f32"] = (a["ms_adjoint"] / a["cells"]) / (msf / cells)
-            line["forms"]["adjoint"] = a
-            torch.cuda.empty_cache()
-    else:
-        got = out_d.view(torch.int32).cpu().numpy().view(np.uint32)
+        # float32 weights on the headline raster: w ~ U[0, 1), drawn on the device
+        del out_d
+        torch.cuda.empty_cache()
+        w_d = torch.empty((R, C), dtype=torch.float32, device=dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(SCALE_WSEED if args.workload == "scale" else WSEED)
+        for r0 in range(0, R, 8192):
+            w_d[r0:r0 + 8192].uniform_(0.0, 1.0, generator=g)
+        outf = torch.empty((R, C), dtype=torch.float32, device=dev)
+
+        def step_f32():
+            s = fa.fa_accumulate(codes_d, w_d, None, outf, fa.FA_OUT_F32, work, opts, None, stream)
+            if s != fa.FA_OK:
+                raise fa.FlowAccError(s, "fa_accumulate f32")
+
+        for _ in range(3):
+            step_f32()
+        kf = 5 if cells > 2e9 else max(10, args.steps // 3)
+        msf_h = _time(step_f32, stream, kf)
+        stf = fa.fa_status_read(None, work, stream)[0]
+        forms["headline_f32"] = {
+            "workload": WORKLOAD, "ms": msf_h, "cells_per_s": cells / (msf_h / 1e3),
+            "tile": list(tile), "bytes_per_cell": BYTES_PER_CELL_F32,
+            "hbm_frac_step": cells * BYTES_PER_CELL_F32 / (msf_h / 1e3) / 1e9 / peak,
+            "status": int(stf),
+            "parity_vs_oracle": ("FP32 parity at 1e10 unverified: the FP64 oracle needs about "
+                                 "300 GB of host memory" if cells > 2e9 else "see forms")}
+        del w_d, outf
+    del codes_d, work
+    torch.cuda.empty_cache()
+
+    d8_data = absorb_data = dem_got = None
+    if not args.no_extra:
+        forms_dem, d8_data, absorb_data, dem_got = legs_dem16384(fa, dev, stream, peak, args,
+                                                                 rank, ws)
+        forms.update(forms_dem)
+    if forms:
+        line["forms"] = forms
 
     if not args.no_cpu_baseline and rank == 0:
-        v, dt, res, shape = cpu_oracle_time(codes)
-        exact = bool(np.array_equal(got, res.values.astype(np.uint32)))
-        line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                                "sample": f"whole {ROWS}x{COLS} raster once ({dt:.1f} s)"}
-        line["parity"] = {"vs_oracle": "bit-exact" if exact else "MISMATCH"}
-        if d8_data is not None:  # the direction step's oracle, timed on one core too
-            import oracle
+        import oracle
 
+        # the oracle on a bounded sample of the headline workload
+        rows_s = CPU_SAMPLE_ROWS if args.workload == "scale" else ROWS
+        sample = codes_h[:rows_s] if codes_h is not None else scale_sample_codes(args, rows_s)
+        oracle.build()
+        t0 = time.perf_counter()
+        res = oracle.counts(np.ascontiguousarray(sample))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sample.size / dt, "unit": "cells/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"rows 0..{sample.shape[0] - 1} of the {R}x{C} headline "
+                                          f"raster as a raster of their own ({sample.size:.3g} "
+                                          f"cells, {dt:.1f} s)"}
+        del res
+        if got_h is not None:
+            t0 = time.perf_counter()
+            v = oracle.verify_counts_u32(codes_h, got_h, threads=os.cpu_count() or 1,
+                                         band=1024)
+            line["parity"] = {
+                "vs_oracle": "Eq. 1 residual at every cell and conservation" + (
+                    " exact" if v["mismatches"] == 0 and v["conserved"] else
+                    (" (conserved modulo 2^32)" if v["mismatches"] == 0 and v["conserved_mod_2_32"]
+                     else ": MISMATCH")),
+                "residual_mismatches": v["mismatches"], "first_mismatch": v["first"],
+                "outlet_sum": v["outlet_sum"], "valid_cells": v["n_valid"],
+                "check_s": round(time.perf_counter() - t0, 1),
+                "note": "the residual check is complete for integer counts on an acyclic raster"}
+        if dem_got is not None:
+            dcodes = synth.dem_codes(ROWS, COLS, SEED)
+            ref = oracle.counts(dcodes).values.astype(np.uint32)
+            forms["plain_u32_dem"]["parity_vs_oracle"] = (
+                "bit-exact" if np.array_equal(dem_got, ref) else "MISMATCH")
+            del ref
+        if d8_data is not None:  # the direction step's oracle, timed on one core too
             z, nd, got_d8 = d8_data
             t0 = time.perf_counter()
             ref_d8 = oracle.d8(z, nd)
             dt8 = time.perf_counter() - t0
-            rec = line["forms"]["d8_directions"]
+            rec = forms["d8_directions"]
             rec["parity_vs_oracle"] = "bit-exact" if np.array_equal(got_d8, ref_d8) else "MISMATCH"
             rec["cpu_oracle_cells_per_s"] = z.size / dt8
         if absorb_data is not None:  # absorption's oracle (FP64), timed on one core
-            import oracle
-
             w_h, a_h, got_a = absorb_data
+            dcodes = synth.dem_codes(ROWS, COLS, SEED)
             t0 = time.perf_counter()
-            ref_a = oracle.absorb(codes, a_h, w_h)
+            ref_a = oracle.absorb(dcodes, a_h, w_h)
             dta = time.perf_counter() - t0
             ok = ref_a.state == 1
             err = np.abs(got_a[ok].astype(np.float64) - ref_a.values[ok])
             bound = 2e-5 * np.abs(ref_a.values[ok])
-            rec = line["forms"]["absorb"]
+            rec = forms["absorb"]
             rec["parity_vs_oracle"] = ("within 2e-5 relative" if bool((err <= bound).all())
                                        else "MISMATCH")
             rec["max_rel_err_vs_oracle"] = float(np.max(err / np.maximum(np.abs(ref_a.values[ok]),
                                                                          1e-300)))
-            rec["cpu_oracle_cells_per_s"] = codes.size / dta
+            rec["cpu_oracle_cells_per_s"] = dcodes.size / dta
             del absorb_data, ref_a
-        if not exact:
-            line["parity"]["mismatches"] = int((got != res.values.astype(np.uint32)).sum())
 
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -759,6 +814,113 @@ def main():
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def legs_dem16384(fa, dev, stream, peak, args, rank, ws):
+    """The forms measured on the 16384^2 spectral DEM: plain uint32 counts,
+    float32 weights, packed codes, absorption, batches, D8 directions and the
+    adjoint (8192^2), each against the plain kernel on the same GPU."""
+    import torch
+
+    import synth
+
+    forms = {}
+    codes = synth.dem_codes(ROWS, COLS, SEED)
+    cells = codes.size
+    codes_d = torch.from_numpy(codes).to(dev)
+    tile = fa.autotune(codes_d)
+    opts = fa.options(tile)
+    work = torch.empty(fa.fa_workspace_size(ROWS, COLS, opts), dtype=torch.uint8, device=dev)
+    out_d = torch.empty((ROWS, COLS), dtype=torch.uint32, device=dev)
+
+    def step_counts():
+        st = fa.fa_accumulate(codes_d, None, None, out_d, fa.FA_OUT_U32, work, opts, None, stream)
+        if st != fa.FA_OK:
+            raise fa.FlowAccError(st, "fa_accumulate")
+
+    for _ in range(3):
+        step_counts()
+    k2 = max(10, args.steps)
+    ms = _time(step_counts, stream, k2)
+    fa.fa_timing_enable(True)
+    ph = []
+    for _ in range(3):
+        step_counts()
+        ph.append(fa.fa_timing_read())
+    fa.fa_timing_enable(False)
+    ph = np.mean(np.array(ph), axis=0).tolist()
+    forms["plain_u32_dem"] = {
+        "workload": f"d8_dem_{ROWS}x{COLS}", "ms": ms, "cells_per_s": cells / (ms / 1e3),
+        "tile": list(tile), "hbm_frac_step": cells * BYTES_PER_CELL_COUNTS / (ms / 1e3) / 1e9 / peak,
+        "phases_ms": dict(zip(["pass1_tile_solve", "perimeter_graph_resolve",
+                               "pass2_tile_finalize"], ph))}
+    dem_got = out_d.view(torch.int32).cpu().numpy().view(np.uint32)
+
+    # float32 weighted form on the same raster
+    w_d = torch.from_numpy(synth.uniform_weights(codes.shape, WSEED)).to(dev)
+    outf = torch.empty((ROWS, COLS), dtype=torch.float32, device=dev)
+    tile_f = fa.autotune(codes_d, w_d)
+    opts_f = fa.options(tile_f)
+    work_f = torch.empty(fa.fa_workspace_size(ROWS, COLS, opts_f), dtype=torch.uint8, device=dev)
+
+    def step_f32():
+        s = fa.fa_accumulate(codes_d, w_d, None, outf, fa.FA_OUT_F32, work_f, opts_f, None, stream)
+        if s != fa.FA_OK:
+            raise fa.FlowAccError(s, "fa_accumulate f32")
+
+    for _ in range(3):
+        step_f32()
+    msf = _time(step_f32, stream, k2)
+    forms["plain_f32_dem"] = {"workload": f"d8_dem_{ROWS}x{COLS}", "cells_per_s": cells / (msf / 1e3),
+                              "ms": msf, "tile": list(tile_f),
+                              "hbm_frac_step": cells * BYTES_PER_CELL_F32 / (msf / 1e3) / 1e9 / peak}
+    del w_d, outf, work_f
+
+    # packed codes (two per byte, 4.5 B/cell) on the same raster and tile
+    pk = fa.pack_codes(codes_d)
+    out_p = torch.empty_like(out_d)
+    opts_p = fa.options(tile, code_format=fa.FA_CODES_NIBBLE)
+
+    def step_packed():
+        s = fa.fa_accumulate(pk, None, None, out_p, fa.FA_OUT_U32, work, opts_p, None, stream)
+        if s != fa.FA_OK:
+            raise fa.FlowAccError(s, "fa_accumulate packed")
+
+    for _ in range(3):
+        step_packed()
+    msp = _time(step_packed, stream, k2)
+    forms["plain_u32_packed"] = {
+        "cells_per_s": cells / (msp / 1e3), "ms": msp, "tile": list(tile), "bytes_per_cell": 4.5,
+        "hbm_frac_step": cells * 4.5 / (msp / 1e3) / 1e9 / peak,
+        "identical_to_byte_codes": bool(torch.equal(out_p.view(torch.int32),
+                                                    out_d.view(torch.int32)))}
+    del pk, out_p
+
+    forms["absorb"], absorb_data = leg_absorb(fa, dev, stream, codes_d, msf, cells, 3, k2, peak)
+    if rank != 0 or args.no_cpu_baseline:
+        absorb_data = None
+    del codes_d, work, out_d
+    fa._ws_cache.clear()
+    torch.cuda.empty_cache()
+
+    d8_data = None
+    if rank == 0:
+        b = leg_batched(fa, dev, stream, opts, 2, 5)
+        b["hbm_frac_step"] = b["hbm_frac_step"] / peak
+        b["ns_per_cell_plain_f32"] = msf * 1e6 / cells
+        b["time_per_cell_vs_plain_f32"] = b["ns_per_cell_field"] / b["ns_per_cell_plain_f32"]
+        forms["batched"] = b
+        torch.cuda.empty_cache()
+        forms["d8_directions"], d8_data = leg_d8(fa, dev, stream, 3, 50, peak)
+        torch.cuda.empty_cache()
+        a = leg_adjoint(fa, dev, stream, fa.options(TILE), 3, 20)
+        a["hbm_frac_step"] = a["hbm_frac_step"] / peak
+        a["time_per_cell_vs_plain_f32"] = (a["ms_adjoint"] / a["cells"]) / (msf / cells)
+        forms["adjoint"] = a
+        fa._ws_cache.clear()
+        torch.cuda.empty_cache()
+    return forms, d8_data, absorb_data, dem_got
+
 
 
 if __name__ == "__main__":

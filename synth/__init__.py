@@ -388,10 +388,11 @@ def _bilinear_axis(n_fine: int, n_coarse: int, f: int, torch, dev):
 
 def scale_codes_device(coarse_rows: int, coarse_cols: int, factor: int, seed: int,
                        noise_seed: int, noise_amp: float = 0.5, band: int = 256,
-                       device="cuda"):
+                       device="cuda", rows=None):
     """uint8 D8 codes of the scale raster, generated on `device` (a torch
     device) band by band; returns a [coarse_rows*factor, coarse_cols*factor]
-    uint8 tensor there.
+    uint8 tensor there, or only the rows rows[0] .. rows[1] - 1 of it (the
+    same values: every cell is computed from its own neighbourhood).
 
     S is the eps-filled coarse spectral DEM bilinearly upsampled by `factor`
     (float64, exact for these weights); Z = S + white noise U[-amp, amp)
@@ -410,7 +411,8 @@ def scale_codes_device(coarse_rows: int, coarse_cols: int, factor: int, seed: in
     dev = torch.device(device)
     F = torch.from_numpy(scale_coarse(coarse_rows, coarse_cols, seed)).to(dev, torch.float64)
     R, C = coarse_rows * factor, coarse_cols * factor
-    codes = torch.empty((R, C), dtype=torch.uint8, device=dev)
+    lo, hi = (0, R) if rows is None else (max(0, int(rows[0])), min(R, int(rows[1])))
+    codes = torch.empty((max(0, hi - lo), C), dtype=torch.uint8, device=dev)
     xc0, fx = _bilinear_axis(C, coarse_cols, factor, torch, dev)
     yc0_all, fy_all = _bilinear_axis(R, coarse_rows, factor, torch, dev)
     xc1 = torch.clamp(xc0 + 1, max=coarse_cols - 1)
@@ -418,8 +420,8 @@ def scale_codes_device(coarse_rows: int, coarse_cols: int, factor: int, seed: in
     inv_sqrt2 = 1.0 / np.sqrt(2.0)
     dirs = [(1, 0, 1), (2, -1, 1), (3, -1, 0), (4, -1, -1), (5, 0, -1), (6, 1, -1), (7, 1, 0),
             (8, 1, 1)]
-    for r0 in range(0, R, band):
-        r1 = min(R, r0 + band)
+    for r0 in range(lo, hi, band):
+        r1 = min(hi, r0 + band)
         ra, rb = max(0, r0 - 1), min(R, r1 + 1)  # rows of S and Z with a halo row
         y0 = yc0_all[ra:rb]
         y1 = torch.clamp(y0 + 1, max=coarse_rows - 1)
@@ -451,7 +453,7 @@ def scale_codes_device(coarse_rows: int, coarse_cols: int, factor: int, seed: in
             take = (Sn < Sc) & (slope > best)
             best = torch.where(take, slope, best)
             code = torch.where(take, torch.full_like(code, k), code)
-        out = codes[r0:r1]
+        out = codes[r0 - lo:r1 - lo]
         out[:, 1:C - 1] = code
         # border cells drain off the grid
         out[:, 0] = 5
@@ -464,3 +466,11 @@ def scale_codes_device(coarse_rows: int, coarse_cols: int, factor: int, seed: in
             out[-1, 0], out[-1, C - 1] = 6, 8
         del S, Z, best, code
     return codes
+
+
+def scale_codes_rows(coarse_rows: int, coarse_cols: int, factor: int, seed: int,
+                     noise_seed: int, r0: int, r1: int, noise_amp: float = 0.5) -> np.ndarray:
+    """Rows r0 .. r1 - 1 of the scale raster generated on the host (torch on
+    the CPU), the same bytes as scale_codes_device gives for those rows."""
+    return scale_codes_device(coarse_rows, coarse_cols, factor, seed, noise_seed, noise_amp,
+                              device="cpu", rows=(r0, r1)).numpy()
