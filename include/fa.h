@@ -8,12 +8,11 @@
  * The library computes it with the paper's tile decomposition (Section 3):
  * a per-tile solve (Algorithm 1) that also links each perimeter cell to the
  * tile exit its flow path reaches (Algorithm 2), a global solve over those
- * perimeter links (Section 3.2), and a finalising per-tile pass that adds the
- * flow entering each tile along its downstream paths (Algorithm 3, Section 3.3).
- * The tile solve runs once: its result stays in the output raster, and the
- * cells on the in-tile paths of the tile's entry cells are recorded in the
- * workspace, so the finalising pass reads neither the codes nor the weights
- * (the RETAIN strategy of Section 3, with the output raster as the store).
+ * perimeter links (Section 3.2), and a finalising per-tile pass that solves
+ * each tile again with the flow entering it from other tiles added at its
+ * entry cells (Algorithm 3, Section 3.3; the EVICT strategy of Section 3:
+ * nothing per cell is kept between the passes, the codes and weights are read
+ * twice and the output written once).
  *
  * Raster conventions (all entry points):
  *  - Row-major, row 0 = north; every raster argument has its own row pitch in
@@ -89,13 +88,11 @@ typedef enum { FA_OUT_U32 = 0, FA_OUT_F32 = 1 } fa_out_dtype;
 #define FA_FLAG_TIMEOUT 8
 #define FA_FLAG_NONFINITE 16
 
-/* Tile shape: 0 = library default (64 x 64).  1 <= tile_h, tile_w,
- * tile_h * tile_w <= 16384 and tile_h * (tile_w rounded up to a multiple of
- * 4) <= 16384; the per-tile shared memory must also fit (all such shapes for
- * counts; up to about 11000 cells with weights, e.g. 96 x 96 or 64 x 128).
- * The tile's halo rows must also keep (tile_h + 2) * (tile_w + 32 rounded up
- * to a multiple of 16) <= 65535.  Other shapes return
- * FA_ERR_INVALID_ARG.  Results do not depend on the tile shape, except for
+/* Tile shape: 0 = library default (64 x 64).  1 <= tile_h, tile_w and
+ * tile_h * tile_w <= 8192 (a tile cell's index fits 14 bits); the tile's
+ * shared memory must also fit, which rules out only very narrow, tall tiles
+ * (the staged codes take (tile_h + 2) * (tile_w + 32 rounded up to a multiple
+ * of 16) bytes).  Other shapes return FA_ERR_INVALID_ARG.  Results do not depend on the tile shape, except for
  * the rounding of floating-point sums.
  * flags: FA_OPT_NO_TMA disables staging code tiles into shared memory with the
  * Tensor Memory Accelerator (used for single rasters when they allow it:
@@ -134,8 +131,9 @@ size_t fa_workspace_size(int64_t rows, int64_t cols, const fa_options *opts);
  *            for unit weights (upslope cell counts).
  *   mask     [rows x pitch_mask] uint8 NoData mask (device) or NULL.
  *   out      [rows x pitch_out] uint32 (FA_OUT_U32, counts mod 2^32; requires
- *            weights == NULL) or float32 (FA_OUT_F32; sums kept in 64-bit fixed
- *            point inside tiles and 128-bit fixed point across tiles, then
+ *            weights == NULL) or float32 (FA_OUT_F32; sums kept as
+ *            compensated float pairs, about 48 bits, added in a fixed order
+ *            inside tiles, and in 128-bit fixed point across tiles, then
  *            rounded once to float32).
  *   workspace, ws_bytes: caller-owned device scratch, >= fa_workspace_size().
  *   d_status: device int32[FA_STATUS_WORDS] or NULL (see above).
@@ -150,14 +148,15 @@ fa_status fa_accumulate(const uint8_t *codes, int64_t rows, int64_t cols, int64_
 /*
  * Batches.  Many rasters, each with its own shape, and up to FA_MAX_FIELDS
  * weight fields sharing one raster's codes, accumulated in one pass of the
- * tile pipeline (Sections 3.1-3.3 applied to every (raster, field) pair): the
- * tiles of all pairs form one tile sequence for the persistent tile solve,
- * one perimeter-graph resolve covers all of them (its nodes are (tile, exit),
- * so no flow crosses from one pair to another), and one offset pass finishes
- * them.  Each result equals fa_accumulate on that raster and field with the
- * same tile shape: bit for bit for uint32 counts; float32 sums may differ in
- * the last place, since the perimeter graph's fixed-point scale is set by the
- * largest raster of the batch.  Every raster uses opts' tile shape; batches
+ * tile pipeline (Sections 3.1-3.3): the tiles of all rasters form one tile
+ * sequence for the persistent tile passes, each tile's flow topology is
+ * worked out once from its codes and used for every field in turn, and one
+ * perimeter-graph resolve carries all fields (its nodes are (tile, exit), so
+ * no flow crosses from one raster to another).  Each result equals
+ * fa_accumulate on that raster and field with the same tile shape: bit for
+ * bit for uint32 counts; float32 sums may differ in the last place, since the
+ * perimeter graph's fixed-point scale is set by the largest raster and
+ * weight of the batch.  Every raster uses opts' tile shape; batches
  * never stage codes by TMA.
  *
  * Errors (returned before anything is enqueued): FA_ERR_INVALID_ARG for
@@ -269,7 +268,7 @@ fa_status fa_recode(const uint8_t *src, int64_t rows, int64_t cols, int64_t pitc
  * and the best trade depends on the raster, so it is measured: fa_autotune
  * runs fa_accumulate on the caller's own inputs with each candidate shape
  * (64x64, 64x128, 128x64, 96x64, 64x96, 32x128, 128x32, 48x64, 32x64, 64x32,
- * 96x96, 128x128, skipping those the weighting or the workspace does not
+ * 32x256, 48x128, skipping those the weighting or the workspace does not
  * allow), times each on `stream` with CUDA events (one untimed call, then the
  * fastest of three timed calls; the call synchronises `stream`), writes the fastest shape to *best
  * (other fields copied from opts, which may be NULL) and leaves that shape's
@@ -307,8 +306,8 @@ fa_status fa_autotune_batched(const fa_raster *rasters, int32_t n_rasters, int32
  * the process exits), and the call allocates nothing.
  *  - Size limit: rasters whose fa_workspace_size() exceeds
  *    FA_NOALLOC_SCRATCH_BYTES return FA_ERR_TOO_LARGE with nothing enqueued
- *    (with the default 64 x 64 tiles that is about 5.9 million cells: square
- *    rasters up to 2432 x 2432 fit, 2450 x 2450 does not).
+ *    (with the default 64 x 64 tiles that is about 15 million cells: square
+ *    rasters up to 3904 x 3904 fit, 3905 x 3905 does not).
  *  - Every call looks up the buffer's device address on the current device
  *    (cudaGetSymbolAddress); the first call on a device may load the
  *    library's module there, so make that first call outside any stream

@@ -19,7 +19,7 @@ struct Shape {
 };
 // 64 x 64 first: the default, and the winner on ties
 const Shape kCandidates[] = {{64, 64},  {64, 128}, {128, 64}, {96, 64},  {64, 96}, {32, 128},
-                             {128, 32}, {48, 64},  {32, 64},  {64, 32},  {96, 96}, {128, 128}};
+                             {128, 32}, {48, 64},  {32, 64},  {64, 32},  {32, 256}, {48, 128}};
 constexpr int kReps = 3;  // timed runs per candidate after one untimed run
 
 fa_options with_shape(const fa_options *base, Shape s) {

@@ -1,12 +1,16 @@
 // Batched flow accumulation: many rasters, and several weight fields sharing
 // one raster's codes, in one pass of the tile pipeline.
 //
-// Every (raster, field) pair becomes one entry of a device table of raster
-// descriptors; the tiles of all entries are numbered globally, entry after
-// entry, and the persistent tile solve, the perimeter-graph resolve and the
-// offset pass each run once over that single tile queue.  Perimeter-graph
-// nodes are (global tile, exit rank), so flow never crosses from one entry to
-// another.  A plan captures the launches of one batch in a CUDA graph.
+// Every raster becomes one entry of a device table of raster descriptors
+// holding all its fields; the tiles of all rasters are numbered globally,
+// raster after raster, and the persistent tile passes and the perimeter-graph
+// resolve each run once over that single tile sequence.  A tile's flow
+// topology (successors, dependency counts, inflow masks, the cells that start
+// the walks, exits and entry links) is worked out once from its codes and
+// then used for each of its fields in turn; the resolve carries every
+// field's value per node over one shared pointer structure.  Perimeter-graph
+// nodes are (global tile, exit rank), so flow never crosses from one raster
+// to another.  A plan captures the launches of one batch in a CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -21,7 +25,7 @@ bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0;
 
 struct BatchLayout {
     Geom g;                         // tile shape; tiles_x = T, tiles_y = 1 for the carve
-    std::vector<RasterDesc> table;  // one entry per (raster, field)
+    std::vector<RasterDesc> table;  // one entry per raster, with all its fields
     int64_t T = 0;
     int64_t cells_bound = 0;
     int val_mode = 0;
@@ -51,35 +55,36 @@ fa_status plan_batch(const fa_raster *rasters, int32_t n, int32_t k, const fa_op
         }
         Geom gi;
         if (!make_geom(r.rows, r.cols, opts, gi)) return FA_ERR_INVALID_ARG;
-        for (int f = 0; f < nf; ++f) {
-            if (!empty) {
-                if (!r.out[f] || !aligned_to(r.out[f], 4)) return FA_ERR_INVALID_ARG;
-                if (k > 0 && (!r.weights[f] || !aligned_to(r.weights[f], 4))) return FA_ERR_INVALID_ARG;
-            }
-            if (empty) continue;
-            RasterDesc d;
-            std::memset(&d, 0, sizeof(d));
-            d.codes = r.codes;
-            d.pc = r.pitch_codes;
-            d.mask = r.mask;
-            d.pm = r.pitch_mask;
-            d.w = k > 0 ? r.weights[f] : nullptr;
-            d.pw = r.pitch_w;
-            d.out = r.out[f];
-            d.po = r.pitch_out;
-            d.rows = r.rows;
-            d.cols = r.cols;
-            d.tiles_x = gi.tiles_x;
-            d.tiles_y = gi.tiles_y;
-            d.tile_base = L.T;
-            L.table.push_back(d);
-            L.T += gi.tiles();
+        for (int f = 0; f < nf && !empty; ++f) {
+            if (!r.out[f] || !aligned_to(r.out[f], 4)) return FA_ERR_INVALID_ARG;
+            if (k > 0 && (!r.weights[f] || !aligned_to(r.weights[f], 4))) return FA_ERR_INVALID_ARG;
         }
+        if (empty) continue;
+        RasterDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.codes = r.codes;
+        d.pc = r.pitch_codes;
+        d.mask = r.mask;
+        d.pm = r.pitch_mask;
+        for (int f = 0; f < nf; ++f) {
+            d.w[f] = k > 0 ? r.weights[f] : nullptr;
+            d.out[f] = r.out[f];
+        }
+        d.pw = r.pitch_w;
+        d.po = r.pitch_out;
+        d.rows = r.rows;
+        d.cols = r.cols;
+        d.tiles_x = gi.tiles_x;
+        d.tiles_y = gi.tiles_y;
+        d.tile_base = L.T;
+        L.table.push_back(d);
+        L.T += gi.tiles();
         L.cells_bound = std::max<int64_t>(L.cells_bound, r.rows * r.cols);
     }
     if ((double)L.T * L.g.pmax >= 4.0e9) return FA_ERR_INVALID_ARG;
     L.g.tiles_x = (int)std::max<int64_t>(L.T, 1);
     L.g.tiles_y = 1;
+    L.g.nf = nf;
     FwdWork w;
     L.fwd_bytes = carve_forward(nullptr, 0, L.g, w, true);
     L.table_off = (L.fwd_bytes + 255) & ~size_t(255);

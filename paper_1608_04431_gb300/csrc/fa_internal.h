@@ -19,6 +19,7 @@ struct Geom {
     int pmax;            // per-tile slot capacity: 2*th + 2*tw >= perimeter cells
     int flags;           // FA_OPT_* from fa_options
     int code_format;     // FA_CODES_BYTE or FA_CODES_NIBBLE
+    int nf = 1;          // weight fields carried per raster (1 for counts)
     int64_t tiles() const { return (int64_t)tiles_x * tiles_y; }
 };
 
@@ -29,17 +30,18 @@ inline int64_t code_row_bytes(int64_t cols, int code_format) {
 
 bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g);
 
-// One raster of a batch as the kernels see it (device-resident table).  All
-// rasters of a batch share the tile shape; their tiles are numbered globally,
-// raster after raster, starting at tile_base.
+// One raster as the kernels see it (for batches, a device-resident table).
+// All rasters of a batch share the tile shape and the number of weight fields
+// (w[0 .. nf-1], out[0 .. nf-1]; counts use w[0] = NULL and out[0]); their
+// tiles are numbered globally, raster after raster, starting at tile_base.
 struct RasterDesc {
     const uint8_t *codes;
     int64_t pc;
     const uint8_t *mask;
     int64_t pm;
-    const float *w;
+    const float *w[FA_MAX_FIELDS];
     int64_t pw;
-    void *out;
+    void *out[FA_MAX_FIELDS];
     int64_t po;
     int64_t rows, cols;
     int32_t tiles_x, tiles_y;
@@ -64,26 +66,19 @@ struct Carver {
     bool fits() const { return cur <= end; }
 };
 
-// Forward workspace regions (device pointers).
+// Forward workspace regions (device pointers).  Perimeter-graph nodes are
+// (tile, exit rank) = tile * pmax + rank; per node and weight field f the
+// values sit at node * nf + f.
 struct FwdWork {
     void *status;          // StatusBlock (16 bytes)
     uint32_t *misc;        // [0] max |w| bits, [1..] per-round active counts
     uint32_t *nexit;       // [T] exits per tile
-    uint16_t *link;        // [T*pmax] perimeter slot -> exit rank, 0xFFFF = terminates
+    uint16_t *link;        // [T*pmax] perimeter slot -> exit rank its path reaches, 0xFFFF = none
     uint32_t *node_dst;    // [T*pmax] exit rank -> global slot id of its target cell
-    double *node_val;      // [T*pmax] exit rank -> tile-local accumulation A_loc
-    void *x;               // [T*pmax] u128 forest values (G after resolve)
-    void *dl0, *dl1;       // [T*pmax] u128 pending scatter buffers
+    double *node_val;      // [T*pmax*nf] exit rank -> tile-local accumulation A_loc
+    void *x;               // [T*pmax*nf] u128 forest values (G after resolve)
+    void *dl0, *dl1;       // [T*pmax*nf] u128 pending scatter buffers
     uint32_t *J0, *J1;     // [T*pmax] jump pointers
-    // entry forest of every tile (the union of the in-tile paths downstream
-    // of its entry cells), recorded by pass 1 for pass 2
-    uint32_t *ef_hdr;      // [T*4] entry-forest cells, segments, inflow links, 0
-    uint32_t *ef_cp;       // [T*th*tw] cell << 16 | position along its segment
-    uint16_t *ef_seg;      // [T*th*tw] segment of the cell
-    uint32_t *seg_merge;   // [T*pmax] segment -> (segment << 16 | position on it)
-                           //   where it joins, 0xFFFFFFFF if it ends at an exit or sink
-    uint32_t *inf_src;     // [T*(pmax+8)] inflow link: slot id of the exit outside
-    uint16_t *inf_seg;     // [T*(pmax+8)] inflow link: segment it feeds
     int kmax;              // number of jump rounds
 };
 
@@ -104,8 +99,9 @@ cudaError_t prepare_forward(const Geom &g, int val_mode);
 
 // Launch the forward pipeline over a batch described by a device table of
 // `nr` rasters (tiles numbered globally, `T` in all; every raster's weights
-// NULL and uint32 outputs when val_mode is 0); the workspace is carved for T
-// tiles.  cells_bound bounds the cell count of any raster (fixed-point scale).
+// NULL and uint32 outputs when val_mode is 0; g.nf fields per raster); the
+// workspace is carved for T tiles.  cells_bound bounds the cell count of any
+// raster (fixed-point scale).
 cudaError_t launch_forward_batched(const Geom &g, const RasterDesc *d_tab, int nr, int64_t T,
                                    int64_t cells_bound, int val_mode, const FwdWork &ws,
                                    void *status, cudaStream_t s);
