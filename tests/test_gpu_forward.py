@@ -250,7 +250,7 @@ def test_serpentine_8192():
 
 @pytest.mark.parametrize("R,C,pitch,tile", [(1024, 2048, 2048, None), (1000, 1000, 1008, (64, 64)),
                                             (333, 517, 528, (32, 48)), (129, 260, 272, (16, 16)),
-                                            (700, 300, 304, (96, 96))])
+                                            (700, 300, 304, (96, 80))])
 def test_tma_and_plain_loads_agree(oracle_mod, R, C, pitch, tile):
     """The TMA-staged and the plain-load tile paths give identical results
     (rasters with 16-byte aligned pitch and tile widths that are multiples of
