@@ -159,15 +159,12 @@ __host__ __device__ inline int walk_threads(int th, int tw) {
 // Shared memory of k_walk<MODE, PASS, LOAD> for a tile shape.
 __host__ __device__ inline size_t walk_smem_bytes(int th, int tw, int mode, int pass, int load) {
     const size_t n = (size_t)th * tw, pm = (size_t)(2 * th + 2 * tw);
-    const size_t nw = (size_t)walk_threads(th, tw) / 32;
     size_t b = 128;  // alignment slack of the dynamic window
     b += code_buf_bytes(th, tw) + (load == LOAD_TMA_PACKED ? packed_buf_bytes(th, tw) : 0);
     b += n * ((mode == 0 && pass == 2) ? 8 : 4);  // cell words
     b = (b + 15) & ~size_t(15);
     if (mode == 1) b += n * 8;                     // float pair sums
-    b += ((n + 31) / 32) * 4;                      // leaf bits
     b += pm * 4 + pm * 2 + pm;                     // exit targets, exit ranks, inflow masks
-    b += nw * 32;                                  // refill slots
     return (b + 15) & ~size_t(15);
 }
 
@@ -311,80 +308,57 @@ __device__ __forceinline__ uint32_t outside_slot(const RasterDesc &ras, const Ti
 }
 
 // ---------------------------------------------------------------------------
-// The walks of one tile (Algorithm 1).  Warp w owns the 32-cell chunks w,
-// w + nw, ... of the tile; leafbits marks the cells with no inflow inside the
-// tile.  An idle lane takes the next such cell of its warp's chunks (the
-// chunk's set bits are handed to the idle lanes in order) and walks it
-// downstream.
+// The walks of one tile (Algorithm 1).  Thread tid owns the cells tid + k * nt
+// (k < 64); `leaves` marks those with no inflow inside the tile.  A lane whose
+// walk ended takes its next own such cell and walks it downstream.
 // ---------------------------------------------------------------------------
 template <int MODE, class W>
-__device__ __forceinline__ void walk_tile(W *word, FF *val, const uint32_t *leafbits, int NC,
-                                          uint8_t *wslots, const int *nb) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-    uint8_t *slots = wslots + warp * 32;
-    uint32_t cur = 0;     // leaf bits of chunk q not yet handed out (warp-uniform)
-    int q = warp - nw;    // current chunk (warp-uniform)
+__device__ __forceinline__ void walk_tile(W *word, FF *val, unsigned long long leaves,
+                                          const int *nb) {
+    const int tid = threadIdx.x, nt = blockDim.x;
     bool act = false;
     uint32_t sc = SUCC_NONE;  // successor of the lane's cell
     W acc = 0;                // counts: the lane's cell's sum
     for (;;) {
-        uint32_t idle = __ballot_sync(0xffffffffu, !act);
-        while (idle) {
-            if (!cur) {
-                q += nw;
-                if (q >= NC) break;
-                cur = leafbits[q];
-                continue;
+        if (!act && leaves) {
+            const int k = __ffsll((long long)leaves) - 1;
+            leaves &= leaves - 1ull;
+            const W wv = word[tid + k * nt];
+            if constexpr (MODE == 0) {
+                acc = wv & CountWord<W>::ACC;
+                sc = (uint32_t)(wv >> CountWord<W>::SUCC) & SUCC_NONE;
+            } else {
+                sc = (uint32_t)wv & SUCC_NONE;
             }
-            const int nl = __popc(cur), ni = __popc(idle);
-            if ((cur >> lane) & 1u) slots[__popc(cur & lt)] = (uint8_t)lane;
-            __syncwarp();
-            const int my = __popc(idle & lt);
-            if (((idle >> lane) & 1u) && my < nl) {
-                const int u = q * 32 + slots[my];
-                const W wv = word[u];
-                if constexpr (MODE == 0) {
-                    acc = wv & CountWord<W>::ACC;
-                    sc = (uint32_t)(wv >> CountWord<W>::SUCC) & SUCC_NONE;
-                } else {
-                    sc = (uint32_t)wv & SUCC_NONE;
-                }
-                act = true;
-            }
-            const uint32_t pos = slots[ni < nl ? ni : 0];
-            cur = ni < nl ? (cur & (0xFFFFFFFFu << pos)) : 0u;
-            __syncwarp();
-            idle = __ballot_sync(0xffffffffu, !act);
+            act = true;
         }
         if (!__any_sync(0xffffffffu, act)) break;
-        if (act) {
-            if (sc == SUCC_NONE) {
-                act = false;  // an exit, a sink, or flow leaving the data
-            } else if constexpr (MODE == 0) {
-                const W old = atomicAdd(&word[sc], acc - CountWord<W>::ONE);
-                if ((old >> CountWord<W>::CNT) == 1) {  // the last inflow: continue from sc
-                    acc += old & CountWord<W>::ACC;
-                    sc = (uint32_t)(old >> CountWord<W>::SUCC) & SUCC_NONE;
-                } else {
-                    act = false;
-                }
+        if (!act) continue;
+        if (sc == SUCC_NONE) {
+            act = false;  // an exit, a sink, or flow leaving the data
+        } else if constexpr (MODE == 0) {
+            const W old = atomicAdd(&word[sc], acc - CountWord<W>::ONE);
+            if ((old >> CountWord<W>::CNT) == 1) {  // the last inflow: continue from sc
+                acc += old & CountWord<W>::ACC;
+                sc = (uint32_t)(old >> CountWord<W>::SUCC) & SUCC_NONE;
             } else {
-                const uint32_t old = atom_add_acq_rel(reinterpret_cast<uint32_t *>(&word[sc]), 0u - GW_ONE);
-                if ((old >> GW_CNT) == 1) {  // complete: own weight plus inflows in fixed order
-                    const int t = (int)sc;
-                    FF v = val[t];
-                    uint32_t pm = (old >> GW_PM) & 0xFFu;
-                    while (pm) {
-                        const int j = __ffs(pm) - 1;
-                        pm &= pm - 1u;
-                        v = ff_add(v, val[t + nb[j]]);
-                    }
-                    val[t] = v;
-                    sc = old & SUCC_NONE;
-                } else {
-                    act = false;
+                act = false;
+            }
+        } else {
+            const uint32_t old = atom_add_acq_rel(reinterpret_cast<uint32_t *>(&word[sc]), 0u - GW_ONE);
+            if ((old >> GW_CNT) == 1) {  // complete: own weight plus inflows in fixed order
+                const int t = (int)sc;
+                FF v = val[t];
+                uint32_t pm = (old >> GW_PM) & 0xFFu;
+                while (pm) {
+                    const int j = __ffs(pm) - 1;
+                    pm &= pm - 1u;
+                    v = ff_add(v, val[t + nb[j]]);
                 }
+                val[t] = v;
+                sc = old & SUCC_NONE;
+            } else {
+                act = false;
             }
         }
     }
@@ -398,7 +372,9 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint32_t *leaf
 // weights, integer counts; MODE 1: float weights (nf fields).
 // Persistent CTAs: each block takes tiles t = blockIdx.x, + gridDim.x, ...
 // With TMA the codes of the next tile are staged into shared memory while the
-// current one is walked (they are no longer read by then).
+// current one is walked (they are no longer read by then).  The cell words are
+// zero when a tile starts (cleared by the previous tile's last pass), so every
+// cell sets its own word and adds itself to its successor's in one pass.
 // ---------------------------------------------------------------------------
 template <int MODE, int PASS, int LOAD>
 __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A,
@@ -412,10 +388,11 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
     __shared__ __align__(8) uint64_t s_bar;
 
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int lane = tid & 31;
     const int th = a.th, tw = a.tw;
     const int S = tile_stride(tw);
-    const int n = th * tw, NC = (n + 31) >> 5;
+    const int n = th * tw;
+    const uint32_t rdiv = 0xFFFFFFFFu / (uint32_t)tw + 1u;  // r = umulhi(ci, rdiv) = ci / tw for ci < 2^13
     const int64_t T = a.T;
     const int nf = a.nf;
 
@@ -429,15 +406,11 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     FF *val = reinterpret_cast<FF *>(p);
     if (MODE == 1) p += (size_t)n * sizeof(FF);
-    uint32_t *leafbits = reinterpret_cast<uint32_t *>(p);
-    p += (size_t)NC * 4;
     uint32_t *pexit = reinterpret_cast<uint32_t *>(p);     // slot -> global slot id of its exit target
     p += (size_t)a.pmax * 4;
     uint16_t *prank = reinterpret_cast<uint16_t *>(p);     // slot -> exit rank, LINK_TERM if none
     p += (size_t)a.pmax * 2;
     uint8_t *pinf = p;                                     // slot -> neighbours outside draining in
-    p += a.pmax;
-    uint8_t *wslots = p;                                   // refill slots, 32 per warp
 
     int nbad = 0, ncyc = 0, nonfinite = 0, ovf = 0;
     long long fbad = NO_INDEX;
@@ -451,6 +424,7 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
             mbar_fence_init();
         }
     }
+    for (int ci = tid; ci < n; ci += nt) word[ci] = 0;
     __syncthreads();
     auto issue = [&](int64_t tn) {  // one thread: stage tile tn's codes (TMA: one raster only)
         const int tyn = (int)(tn / a.one.tiles_x), txn = (int)(tn - (int64_t)tyn * a.one.tiles_x);
@@ -512,61 +486,44 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
             __syncthreads();
         }
 
-        // [phase] init: every cell's word (successor, unit weight or nothing),
-        // the exits' targets, counts of invalid codes
-        for (int r = warp; r < th; r += nw) {
-            for (int c = lane; c < tw; c += 32) {
-                const int ci = r * tw + c;
-                if (r >= h || c >= w) {
-                    word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
-                    continue;
-                }
-                const int xi = (r + 1) * S + X0 + c;
-                const uint32_t k = cbuf[xi];
-                if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
-                    if (k > 9u) {
-                        ++nbad;
-                        fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
-                    }
-                }
-                if (!vcode(k)) {
-                    word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
-                    continue;
-                }
-                uint32_t sc = SUCC_NONE;
-                if (k <= 8u) {
-                    const int dr = dir_dr((int)k), dc = dir_dc((int)k);
-                    if (vcode(cbuf[xi + dr * S + dc])) {
-                        const int tr = r + dr, tc = c + dc;
-                        if ((unsigned)tr < (unsigned)h && (unsigned)tc < (unsigned)w) {
-                            sc = (uint32_t)(ci + dr * tw + dc);
-                        } else if (PASS == 1) {  // an exit: its flow enters the neighbouring tile
-                            pexit[slot_of(r, c, h, w)] = outside_slot(ras, a, ty, tx, R0, C0, h, w, tr, tc);
-                        }
-                    }
-                }
-                if constexpr (MODE == 0) word[ci] = ((W)sc << CountWord<W>::SUCC) | (W)1;
-                else word[ci] = sc;
+        // [phase] init, one pass: each cell sets its word (successor, unit
+        // weight) and adds one pending inflow to its successor's (with its
+        // own direction bit for float weights); exits record their targets;
+        // perimeter cells note which outside neighbours drain into them
+        for (int ci = tid; ci < n; ci += nt) {
+            const int r = (int)__umulhi((uint32_t)ci, rdiv), c = ci - r * tw;
+            if (r >= h || c >= w) {
+                word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
+                continue;
             }
-        }
-        __syncthreads();
-
-        // [phase] in-degree: every cell with a successor in the tile adds one
-        // pending inflow there (and, for float weights, its own direction
-        // bit); the perimeter cells note which outside neighbours drain in
-        for (int r = warp; r < h; r += nw) {
-            for (int c = lane; c < w; c += 32) {
-                const int ci = r * tw + c;
-                const uint32_t wv = (uint32_t)(MODE == 0 ? (word[ci] >> CountWord<W>::SUCC) : word[ci]);
-                const uint32_t sc = wv & SUCC_NONE;
-                if (sc == SUCC_NONE) continue;  // (NoData words carry SUCC_NONE too)
-                if constexpr (MODE == 0) {
-                    atomicAdd(&word[sc], CountWord<W>::ONE);
-                } else {
-                    const int k = cbuf[(r + 1) * S + X0 + c];
-                    atomicAdd(&word[sc], GW_ONE | (1u << (GW_PM + dir_rev(k) - 1)));
+            const int xi = (r + 1) * S + X0 + c;
+            const uint32_t k = cbuf[xi];
+            if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
+                if (k > 9u) {
+                    ++nbad;
+                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
                 }
             }
+            if (!vcode(k)) {  // nothing ever adds to a NoData cell's word
+                word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
+                continue;
+            }
+            uint32_t sc = SUCC_NONE;
+            if (k <= 8u) {
+                const int dr = dir_dr((int)k), dc = dir_dc((int)k);
+                if (vcode(cbuf[xi + dr * S + dc])) {
+                    const int tr = r + dr, tc = c + dc;
+                    if ((unsigned)tr < (unsigned)h && (unsigned)tc < (unsigned)w) {
+                        sc = (uint32_t)(ci + dr * tw + dc);
+                        if constexpr (MODE == 0) atomicAdd(&word[sc], CountWord<W>::ONE);
+                        else atomicAdd(&word[sc], GW_ONE | (1u << (GW_PM + dir_rev((int)k) - 1)));
+                    } else if (PASS == 1) {  // an exit: its flow enters the neighbouring tile
+                        pexit[slot_of(r, c, h, w)] = outside_slot(ras, a, ty, tx, R0, C0, h, w, tr, tc);
+                    }
+                }
+            }
+            if constexpr (MODE == 0) atomicAdd(&word[ci], ((W)sc << CountWord<W>::SUCC) | (W)1);
+            else atomicAdd(&word[ci], sc);
         }
         for (int s = tid; s < P; s += nt) {
             int r, c;
@@ -588,16 +545,12 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
             if (tid == 0 && t + gridDim.x < T) issue(t + gridDim.x);
         }
 
-        // cells with no inflow inside the tile start the walks
-        for (int q = warp; q < NC; q += nw) {
-            const int ci = q * 32 + lane;
-            bool leaf = false;
-            if (ci < n) {
-                const W wv = word[ci];
-                leaf = MODE == 0 ? (wv >> CountWord<W>::CNT) == 0 : ((uint32_t)wv >> GW_CNT) == 0;
-            }
-            const uint32_t b = __ballot_sync(0xffffffffu, leaf);
-            if (lane == 0) leafbits[q] = b;
+        // the lane's own cells with no inflow inside the tile start its walks
+        unsigned long long leaves = 0;
+        for (int k = 0, ci = tid; ci < n; ++k, ci += nt) {
+            const W wv = word[ci];
+            const bool leaf = MODE == 0 ? (wv >> CountWord<W>::CNT) == 0 : ((uint32_t)wv >> GW_CNT) == 0;
+            leaves |= (unsigned long long)leaf << k;
         }
 
         // exit ranks in slot order (pass 1)
@@ -620,35 +573,32 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                 ++rk;
             }
         }
-        __syncthreads();
 
         // [phase] walk, once per field
         for (int f = 0; f < nf; ++f) {
             if constexpr (MODE == 1) {
                 const float *wp = ras.w[f];
-                for (int r = warp; r < h; r += nw) {
-                    for (int c = lane; c < w; c += 32) {
-                        const int ci = r * tw + c;
-                        const uint32_t wv = word[ci];
-                        if (wv >= GW_SENT) continue;
-                        const float wf = wp ? wp[(R0 + r) * ras.pw + (C0 + c)] : 1.0f;
-                        if constexpr (PASS == 1) {
-                            const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
-                            if (b >= 0x7f800000u) nonfinite = 1;
-                            gmaxw = max(gmaxw, b);
-                        }
-                        val[ci] = FF{wf, 0.0f};
-                        if (f > 0)  // the pending counts again, from the inflow mask
-                            word[ci] = (wv & ((1u << GW_CNT) - 1u)) |
-                                       ((uint32_t)__popc((wv >> GW_PM) & 0xFFu) << GW_CNT);
+                for (int ci = tid; ci < n; ci += nt) {
+                    const uint32_t wv = word[ci];
+                    if (wv >= GW_SENT) continue;
+                    const int r = (int)__umulhi((uint32_t)ci, rdiv), c = ci - r * tw;
+                    const float wf = wp ? wp[(R0 + r) * ras.pw + (C0 + c)] : 1.0f;
+                    if constexpr (PASS == 1) {
+                        const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
+                        if (b >= 0x7f800000u) nonfinite = 1;
+                        gmaxw = max(gmaxw, b);
                     }
+                    val[ci] = FF{wf, 0.0f};
+                    if (f > 0)  // the pending counts again, from the inflow mask
+                        word[ci] = (wv & ((1u << GW_CNT) - 1u)) |
+                                   ((uint32_t)__popc((wv >> GW_PM) & 0xFFu) << GW_CNT);
                 }
-                __syncthreads();
             }
             if constexpr (PASS == 2) {
                 // the flow entering from other tiles, added at its entry cell
                 // (Algorithm 3), summed over the outside neighbours in a fixed
-                // order
+                // order (float pairs: after the cell's own weight is in place)
+                if constexpr (MODE == 1) __syncthreads();
                 const int qf = MODE == 1 ? fix_scale(a.fcells, *a.maxw) : 0;
                 for (int s = tid; s < P; s += nt) {
                     uint32_t m = pinf[s];
@@ -676,10 +626,10 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                     if constexpr (MODE == 0) word[ci] += (W)add;
                     else val[ci] = v;
                 }
-                __syncthreads();
             }
+            __syncthreads();
 
-            walk_tile<MODE, W>(word, val, leafbits, NC, wslots, s_nb);
+            walk_tile<MODE, W>(word, val, leaves, s_nb);
             __syncthreads();
 
             if constexpr (PASS == 1) {
@@ -695,41 +645,29 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                     else v = (double)val[ci].hi + (double)val[ci].lo;
                     a.node_val[(tbase + rk) * nf + f] = v;
                 }
-                if (f == 0) {
-                    // cells still waiting for inflow lie on a cycle inside the tile
-                    for (int r = warp; r < h; r += nw) {
-                        for (int c = lane; c < w; c += 32) {
-                            const W wv = word[r * tw + c];
-                            const uint32_t cnt = (uint32_t)(MODE == 0 ? (wv >> CountWord<W>::CNT) : ((uint32_t)wv >> GW_CNT));
-                            if (cnt != 0 && cnt != 15) {
-                                ++ncyc;
-                                fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
-                            }
-                        }
-                    }
-                }
             } else {
-                // the output raster of field f: A, 0 at NoData
-                for (int r = warp; r < h; r += nw) {
-                    uint32_t *orow = reinterpret_cast<uint32_t *>(ras.out[f]) + (size_t)(R0 + r) * ras.po + C0;
-                    for (int c = lane; c < w; c += 32) {
-                        const int ci = r * tw + c;
-                        const W wv = word[ci];
-                        uint32_t o = 0;
-                        if constexpr (MODE == 0) {
-                            if ((wv >> CountWord<W>::CNT) != 15) {
-                                const unsigned long long s64 = (unsigned long long)(wv & CountWord<W>::ACC);
-                                ovf |= (s64 >> 32) != 0;
-                                o = (uint32_t)s64;
-                            }
-                        } else {
-                            if ((uint32_t)wv < GW_SENT) o = __float_as_uint(ff_round(val[ci]));
+                // the output raster of field f: A, 0 at NoData; the words are
+                // cleared for the next tile after the last field
+                const bool last = f == nf - 1;
+                for (int ci = tid; ci < n; ci += nt) {
+                    const int r = (int)__umulhi((uint32_t)ci, rdiv), c = ci - r * tw;
+                    const W wv = word[ci];
+                    if (last) word[ci] = 0;
+                    if (r >= h || c >= w) continue;
+                    uint32_t o = 0;
+                    if constexpr (MODE == 0) {
+                        if ((wv >> CountWord<W>::CNT) != 15) {
+                            const unsigned long long s64 = (unsigned long long)(wv & CountWord<W>::ACC);
+                            ovf |= (s64 >> 32) != 0;
+                            o = (uint32_t)s64;
                         }
-                        orow[c] = o;
+                    } else {
+                        if ((uint32_t)wv < GW_SENT) o = __float_as_uint(ff_round(val[ci]));
                     }
+                    reinterpret_cast<uint32_t *>(ras.out[f])[(size_t)(R0 + r) * ras.po + C0 + c] = o;
                 }
             }
-            __syncthreads();
+            if (f + 1 < nf) __syncthreads();
         }
 
         if constexpr (PASS == 1) {
@@ -750,12 +688,25 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                 }
                 uint16_t lk = LINK_TERM;
                 if (cur >= 0) {
-                    const int rr = cur / tw, cc = cur - rr * tw;
+                    const int rr = (int)__umulhi((uint32_t)cur, rdiv), cc = cur - rr * tw;
                     if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
                 }
                 a.link[tbase + s] = lk;
             }
             if (tid == 0) a.nexit[t] = (uint32_t)nexits;
+            __syncthreads();
+            // cells still waiting for inflow lie on a cycle inside the tile;
+            // the words are cleared for the next tile
+            for (int ci = tid; ci < n; ci += nt) {
+                const W wv = word[ci];
+                word[ci] = 0;
+                const uint32_t cnt = (uint32_t)(MODE == 0 ? (wv >> CountWord<W>::CNT) : ((uint32_t)wv >> GW_CNT));
+                if (cnt != 0 && cnt != 15) {
+                    const int r = (int)__umulhi((uint32_t)ci, rdiv), c = ci - r * tw;
+                    ++ncyc;
+                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
+                }
+            }
         }
         __syncthreads();
         // [phase] end
