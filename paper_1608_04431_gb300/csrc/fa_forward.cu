@@ -392,7 +392,10 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
     const int th = a.th, tw = a.tw;
     const int S = tile_stride(tw);
     const int n = th * tw;
-    const uint32_t rdiv = 0xFFFFFFFFu / (uint32_t)tw + 1u;  // r = umulhi(ci, rdiv) = ci / tw for ci < 2^13
+    // ci / tw as umulhi(ci, rdiv), exact for ci < 2^13 and 2 <= tw <= 8192
+    // (the rounding error ci / 2^32 stays below 1 / tw); tw = 1 divides by itself
+    const uint32_t rdiv = tw > 1 ? 0xFFFFFFFFu / (uint32_t)tw + 1u : 0u;
+    auto row_of = [&](int ci) { return tw > 1 ? (int)__umulhi((uint32_t)ci, rdiv) : ci; };
     const int64_t T = a.T;
     const int nf = a.nf;
 
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
         // own direction bit for float weights); exits record their targets;
         // perimeter cells note which outside neighbours drain into them
         for (int ci = tid; ci < n; ci += nt) {
-            const int r = (int)__umulhi((uint32_t)ci, rdiv), c = ci - r * tw;
+            const int r = row_of(ci), c = ci - r * tw;
             if (r >= h || c >= w) {
                 word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
                 continue;
@@ -581,7 +584,7 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                 for (int ci = tid; ci < n; ci += nt) {
                     const uint32_t wv = word[ci];
                     if (wv >= GW_SENT) continue;
-                    const int r = (int)__umulhi((uint32_t)ci, rdiv), c = ci - r * tw;
+                    const int r = row_of(ci), c = ci - r * tw;
                     const float wf = wp ? wp[(R0 + r) * ras.pw + (C0 + c)] : 1.0f;
                     if constexpr (PASS == 1) {
                         const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
@@ -650,7 +653,7 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                 // cleared for the next tile after the last field
                 const bool last = f == nf - 1;
                 for (int ci = tid; ci < n; ci += nt) {
-                    const int r = (int)__umulhi((uint32_t)ci, rdiv), c = ci - r * tw;
+                    const int r = row_of(ci), c = ci - r * tw;
                     const W wv = word[ci];
                     if (last) word[ci] = 0;
                     if (r >= h || c >= w) continue;
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                 }
                 uint16_t lk = LINK_TERM;
                 if (cur >= 0) {
-                    const int rr = (int)__umulhi((uint32_t)cur, rdiv), cc = cur - rr * tw;
+                    const int rr = row_of(cur), cc = cur - rr * tw;
                     if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
                 }
                 a.link[tbase + s] = lk;
@@ -702,7 +705,7 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                 word[ci] = 0;
                 const uint32_t cnt = (uint32_t)(MODE == 0 ? (wv >> CountWord<W>::CNT) : ((uint32_t)wv >> GW_CNT));
                 if (cnt != 0 && cnt != 15) {
-                    const int r = (int)__umulhi((uint32_t)ci, rdiv), c = ci - r * tw;
+                    const int r = row_of(ci), c = ci - r * tw;
                     ++ncyc;
                     fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
                 }
