@@ -150,9 +150,11 @@ template <> struct CountWord<unsigned long long> {
 constexpr int GW_PM = 14, GW_CNT = 28;
 constexpr uint32_t GW_ONE = 1u << GW_CNT, GW_SENT = (15u << GW_CNT) | SUCC_NONE;
 
+// Threads of a tile block: one per 32 cells (so a lane's own cells fit one
+// 32-bit mask), at least a warp, at most 256.
 __host__ __device__ inline int walk_threads(int th, int tw) {
     const int n = th * tw;
-    const int t = ((n / 64 + 31) / 32) * 32;
+    const int t = ((n + 32 * 32 - 1) / (32 * 32)) * 32;
     return t < 32 ? 32 : (t > 256 ? 256 : t);
 }
 
@@ -309,20 +311,19 @@ __device__ __forceinline__ uint32_t outside_slot(const RasterDesc &ras, const Ti
 
 // ---------------------------------------------------------------------------
 // The walks of one tile (Algorithm 1).  Thread tid owns the cells tid + k * nt
-// (k < 64); `leaves` marks those with no inflow inside the tile.  A lane whose
+// (k < 32); `leaves` marks those with no inflow inside the tile.  A lane whose
 // walk ended takes its next own such cell and walks it downstream.
 // ---------------------------------------------------------------------------
 template <int MODE, class W>
-__device__ __forceinline__ void walk_tile(W *word, FF *val, unsigned long long leaves,
-                                          const int *nb) {
+__device__ __forceinline__ void walk_tile(W *word, FF *val, uint32_t leaves, const int *nb) {
     const int tid = threadIdx.x, nt = blockDim.x;
     bool act = false;
     uint32_t sc = SUCC_NONE;  // successor of the lane's cell
     W acc = 0;                // counts: the lane's cell's sum
     for (;;) {
         if (!act && leaves) {
-            const int k = __ffsll((long long)leaves) - 1;
-            leaves &= leaves - 1ull;
+            const int k = __ffs(leaves) - 1;
+            leaves &= leaves - 1u;
             const W wv = word[tid + k * nt];
             if constexpr (MODE == 0) {
                 acc = wv & CountWord<W>::ACC;
@@ -377,8 +378,8 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, unsigned long long l
 // cell sets its own word and adds itself to its successor's in one pass.
 // ---------------------------------------------------------------------------
 template <int MODE, int PASS, int LOAD>
-__global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A,
-                                              const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_constant__ TileArgs A,
+                                                                const __grid_constant__ CUtensorMap tmap) {
     typedef typename std::conditional<MODE == 0 && PASS == 2, unsigned long long, uint32_t>::type W;
     const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -493,28 +494,45 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
         // weight) and adds one pending inflow to its successor's (with its
         // own direction bit for float weights); exits record their targets;
         // perimeter cells note which outside neighbours drain into them
-        for (int ci = tid; ci < n; ci += nt) {
-            const int r = row_of(ci), c = ci - r * tw;
-            if (r >= h || c >= w) {
-                word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
-                continue;
+        for (int ci0 = tid; ci0 < n; ci0 += 4 * nt) {
+            // four cells per thread at a time: their code loads, then their
+            // targets' code loads, are in flight together
+            int cis[4], xis[4];
+            uint32_t ks[4], tks[4];
+            bool in[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ci = ci0 + u * nt;
+                const int r = row_of(ci), c = ci - r * tw;
+                cis[u] = ci;
+                in[u] = ci < n && r < h && c < w;
+                xis[u] = (r + 1) * S + X0 + c;
+                ks[u] = in[u] ? cbuf[xis[u]] : 0u;
             }
-            const int xi = (r + 1) * S + X0 + c;
-            const uint32_t k = cbuf[xi];
-            if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
-                if (k > 9u) {
-                    ++nbad;
-                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t k = ks[u];
+                tks[u] = (k - 1u < 8u) ? cbuf[xis[u] + dir_dr((int)k) * S + dir_dc((int)k)] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ci = cis[u];
+                if (ci >= n) continue;
+                const uint32_t k = ks[u];
+                const int r = row_of(ci), c = ci - r * tw;
+                if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
+                    if (in[u] && k > 9u) {
+                        ++nbad;
+                        fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
+                    }
                 }
-            }
-            if (!vcode(k)) {  // nothing ever adds to a NoData cell's word
-                word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
-                continue;
-            }
-            uint32_t sc = SUCC_NONE;
-            if (k <= 8u) {
-                const int dr = dir_dr((int)k), dc = dir_dc((int)k);
-                if (vcode(cbuf[xi + dr * S + dc])) {
+                if (!in[u] || !vcode(k)) {  // nothing ever adds to a NoData cell's word
+                    word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
+                    continue;
+                }
+                uint32_t sc = SUCC_NONE;
+                if (k <= 8u && vcode(tks[u])) {
+                    const int dr = dir_dr((int)k), dc = dir_dc((int)k);
                     const int tr = r + dr, tc = c + dc;
                     if ((unsigned)tr < (unsigned)h && (unsigned)tc < (unsigned)w) {
                         sc = (uint32_t)(ci + dr * tw + dc);
@@ -524,9 +542,9 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
                         pexit[slot_of(r, c, h, w)] = outside_slot(ras, a, ty, tx, R0, C0, h, w, tr, tc);
                     }
                 }
+                if constexpr (MODE == 0) atomicAdd(&word[ci], ((W)sc << CountWord<W>::SUCC) | (W)1);
+                else atomicAdd(&word[ci], sc);
             }
-            if constexpr (MODE == 0) atomicAdd(&word[ci], ((W)sc << CountWord<W>::SUCC) | (W)1);
-            else atomicAdd(&word[ci], sc);
         }
         for (int s = tid; s < P; s += nt) {
             int r, c;
@@ -549,11 +567,14 @@ __global__ void __launch_bounds__(256) k_walk(const __grid_constant__ TileArgs A
         }
 
         // the lane's own cells with no inflow inside the tile start its walks
-        unsigned long long leaves = 0;
-        for (int k = 0, ci = tid; ci < n; ++k, ci += nt) {
+        uint32_t leaves = 0;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int ci = tid + k * nt;
+            if (ci >= n) break;
             const W wv = word[ci];
             const bool leaf = MODE == 0 ? (wv >> CountWord<W>::CNT) == 0 : ((uint32_t)wv >> GW_CNT) == 0;
-            leaves |= (unsigned long long)leaf << k;
+            leaves |= (uint32_t)leaf << k;
         }
 
         // exit ranks in slot order (pass 1)
