@@ -166,7 +166,8 @@ __host__ __device__ inline size_t walk_smem_bytes(int th, int tw, int mode, int 
     b += n * ((mode == 0 && pass == 2) ? 8 : 4);  // cell words
     b = (b + 15) & ~size_t(15);
     if (mode == 1) b += n * 8;                     // float pair sums
-    b += pm * 4 + pm * 2 + pm;                     // exit targets, exit ranks, inflow masks
+    b += n * 2;                                    // queued cells (walk starts, entry cells)
+    b += pm * 4 + pm * 2 + pm * 2 + pm;            // exit targets, exit ranks, entry list, inflow masks
     return (b + 15) & ~size_t(15);
 }
 
@@ -310,28 +311,35 @@ __device__ __forceinline__ uint32_t outside_slot(const RasterDesc &ras, const Ti
 }
 
 // ---------------------------------------------------------------------------
-// The walks of one tile (Algorithm 1).  Thread tid owns the cells tid + k * nt
-// (k < 32); `leaves` marks those with no inflow inside the tile.  A lane whose
-// walk ended takes its next own such cell and walks it downstream.
+// The walks of one tile (Algorithm 1).  Warp w holds the queue q[0 .. qn) of
+// the cells with no inflow inside the tile from its share of the tile; each
+// idle lane takes the next queued cell (idle lanes take consecutive entries,
+// in lane order) and walks it downstream.
 // ---------------------------------------------------------------------------
 template <int MODE, class W>
-__device__ __forceinline__ void walk_tile(W *word, FF *val, uint32_t leaves, const int *nb) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+__device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, int qn,
+                                          const int *nb) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    int pos = 0;              // next queue entry (warp-uniform)
     bool act = false;
     uint32_t sc = SUCC_NONE;  // successor of the lane's cell
     W acc = 0;                // counts: the lane's cell's sum
     for (;;) {
-        if (!act && leaves) {
-            const int k = __ffs(leaves) - 1;
-            leaves &= leaves - 1u;
-            const W wv = word[tid + k * nt];
-            if constexpr (MODE == 0) {
-                acc = wv & CountWord<W>::ACC;
-                sc = (uint32_t)(wv >> CountWord<W>::SUCC) & SUCC_NONE;
-            } else {
-                sc = (uint32_t)wv & SUCC_NONE;
+        if (pos < qn) {
+            const uint32_t idle = __ballot_sync(0xffffffffu, !act);
+            const int my = pos + __popc(idle & lt);
+            if (!act && my < qn) {
+                const W wv = word[q[my]];
+                if constexpr (MODE == 0) {
+                    acc = wv & CountWord<W>::ACC;
+                    sc = (uint32_t)(wv >> CountWord<W>::SUCC) & SUCC_NONE;
+                } else {
+                    sc = (uint32_t)wv & SUCC_NONE;
+                }
+                act = true;
             }
-            act = true;
+            pos += __popc(idle);
         }
         if (!__any_sync(0xffffffffu, act)) break;
         if (!act) continue;
@@ -339,12 +347,9 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, uint32_t leaves, con
             act = false;  // an exit, a sink, or flow leaving the data
         } else if constexpr (MODE == 0) {
             const W old = atomicAdd(&word[sc], acc - CountWord<W>::ONE);
-            if ((old >> CountWord<W>::CNT) == 1) {  // the last inflow: continue from sc
-                acc += old & CountWord<W>::ACC;
-                sc = (uint32_t)(old >> CountWord<W>::SUCC) & SUCC_NONE;
-            } else {
-                act = false;
-            }
+            act = (old >> CountWord<W>::CNT) == 1;  // the last inflow: continue from sc
+            acc += old & CountWord<W>::ACC;
+            sc = (uint32_t)(old >> CountWord<W>::SUCC) & SUCC_NONE;
         } else {
             const uint32_t old = atom_add_acq_rel(reinterpret_cast<uint32_t *>(&word[sc]), 0u - GW_ONE);
             if ((old >> GW_CNT) == 1) {  // complete: own weight plus inflows in fixed order
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_flags;
+    __shared__ int s_flags, s_nent;
     __shared__ int s_nb[8];
     __shared__ __align__(8) uint64_t s_bar;
 
@@ -410,9 +415,14 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     FF *val = reinterpret_cast<FF *>(p);
     if (MODE == 1) p += (size_t)n * sizeof(FF);
+    uint16_t *queue = reinterpret_cast<uint16_t *>(p);     // walk starts, then entry cells
+    p += (size_t)n * 2;
+    p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     uint32_t *pexit = reinterpret_cast<uint32_t *>(p);     // slot -> global slot id of its exit target
     p += (size_t)a.pmax * 4;
     uint16_t *prank = reinterpret_cast<uint16_t *>(p);     // slot -> exit rank, LINK_TERM if none
+    p += (size_t)a.pmax * 2;
+    uint16_t *pent = reinterpret_cast<uint16_t *>(p);      // the entry cells' slots
     p += (size_t)a.pmax * 2;
     uint8_t *pinf = p;                                     // slot -> neighbours outside draining in
 
@@ -458,6 +468,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             prank[s] = LINK_TERM;
             pinf[s] = 0;
         }
+        if (tid == 0) s_nent = 0;
 
         // [phase] codes of the tile and its one-cell halo ring
         if constexpr (LOAD != LOAD_PLAIN) {
@@ -559,6 +570,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 if (kh >= 1 && kh <= 8 && nr + dir_dr(kh) == r && nc + dir_dc(kh) == c) m |= 1u << j;
             }
             pinf[s] = (uint8_t)m;
+            if (PASS == 1 && m) pent[atomicAdd(&s_nent, 1)] = (uint16_t)s;
         }
         if constexpr (LOAD == LOAD_TMA) fence_proxy_async();  // the code buffer is refilled by TMA
         __syncthreads();
@@ -566,16 +578,24 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             if (tid == 0 && t + gridDim.x < T) issue(t + gridDim.x);
         }
 
-        // the lane's own cells with no inflow inside the tile start its walks
-        uint32_t leaves = 0;
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            const int ci = tid + k * nt;
-            if (ci >= n) break;
-            const W wv = word[ci];
-            const bool leaf = MODE == 0 ? (wv >> CountWord<W>::CNT) == 0 : ((uint32_t)wv >> GW_CNT) == 0;
-            leaves |= (uint32_t)leaf << k;
+        // the cells with no inflow inside the tile start the walks: warp w
+        // queues those of its share of the tile (32-cell chunks c0 .. c1)
+        const int nch = (n + 31) >> 5, warp = tid >> 5, nw = nt >> 5;
+        const int c0 = (int)((int64_t)nch * warp / nw), c1 = (int)((int64_t)nch * (warp + 1) / nw);
+        uint16_t *wq = queue + c0 * 32;
+        int qn = 0;
+        for (int ch = c0; ch < c1; ++ch) {
+            const int ci = ch * 32 + lane;
+            bool leaf = false;
+            if (ci < n) {
+                const W wv = word[ci];
+                leaf = MODE == 0 ? (wv >> CountWord<W>::CNT) == 0 : ((uint32_t)wv >> GW_CNT) == 0;
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, leaf);
+            if (leaf) wq[qn + __popc(b & ((1u << lane) - 1u))] = (uint16_t)ci;
+            qn += __popc(b);
         }
+        __syncwarp();
 
         // exit ranks in slot order (pass 1)
         int nexits = 0;
@@ -653,7 +673,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             }
             __syncthreads();
 
-            walk_tile<MODE, W>(word, val, leaves, s_nb);
+            walk_tile<MODE, W>(word, val, wq, qn, s_nb);
             __syncthreads();
 
             if constexpr (PASS == 1) {
@@ -695,27 +715,43 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
         }
 
         if constexpr (PASS == 1) {
-            // Algorithm 2 for the entry cells: the exit each one's path reaches
-            for (int s = tid; s < P; s += nt) {
-                if (!pinf[s] || prank[s] != LINK_TERM) continue;
-                int r, c;
-                cell_of(s, h, w, r, c);
-                int cur = r * tw + c, steps = 0;
+            // Algorithm 2 for the entry cells: the exit each one's path
+            // reaches.  Warp w takes its share of the entry list; an idle
+            // lane takes the next entry and follows its path.
+            {
+                const int ne = s_nent;
+                const int e1 = (int)((int64_t)ne * (warp + 1) / nw);
+                int pos = (int)((int64_t)ne * warp / nw), cur = 0, slot = 0, steps = 0;
+                bool act = false;
                 for (;;) {
-                    const uint32_t sc = (uint32_t)(MODE == 0 ? (word[cur] >> CountWord<W>::SUCC) : word[cur]) & SUCC_NONE;
-                    if (sc == SUCC_NONE) break;
-                    cur = (int)sc;
-                    if (++steps > n) {  // a cycle: the path never ends
-                        cur = -1;
-                        break;
+                    if (pos < e1) {
+                        const uint32_t idle = __ballot_sync(0xffffffffu, !act);
+                        const int my = pos + __popc(idle & ((1u << lane) - 1u));
+                        if (!act && my < e1) {
+                            int r, c;
+                            slot = pent[my];
+                            cell_of(slot, h, w, r, c);
+                            cur = r * tw + c;
+                            steps = 0;
+                            act = true;
+                        }
+                        pos += __popc(idle);
                     }
+                    if (!__any_sync(0xffffffffu, act)) break;
+                    if (!act) continue;
+                    const uint32_t sc = (uint32_t)(MODE == 0 ? (word[cur] >> CountWord<W>::SUCC) : word[cur]) & SUCC_NONE;
+                    if (sc != SUCC_NONE && ++steps <= n) {
+                        cur = (int)sc;
+                        continue;
+                    }
+                    uint16_t lk = LINK_TERM;  // the path ends inside the tile (or on a cycle)
+                    if (sc == SUCC_NONE) {
+                        const int rr = row_of(cur), cc = cur - rr * tw;
+                        if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
+                    }
+                    a.link[tbase + slot] = lk;
+                    act = false;
                 }
-                uint16_t lk = LINK_TERM;
-                if (cur >= 0) {
-                    const int rr = row_of(cur), cc = cur - rr * tw;
-                    if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
-                }
-                a.link[tbase + s] = lk;
             }
             if (tid == 0) a.nexit[t] = (uint32_t)nexits;
             __syncthreads();
