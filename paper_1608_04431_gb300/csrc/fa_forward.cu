@@ -119,39 +119,47 @@ __host__ __device__ inline size_t packed_buf_bytes(int th, int tw) {
 enum { LOAD_PLAIN = 0, LOAD_TMA = 1, LOAD_TMA_PACKED = 2 };
 
 // ---------------------------------------------------------------------------
-// Cell words.  Cells of a tile are numbered ci = r * tw + c (tile row r, tile
-// column c, nominal tile width tw), at most MAX_TILE_CELLS of them, so a cell
-// index fits 14 bits and SUCC_NONE (no downstream cell inside the tile: an
-// exit, a sink or a cell whose flow leaves the data) is never an index.
-// Pending-inflow counts sit in the top four bits; 15 (with successor bits
-// SUCC_NONE) marks a cell that never takes part (NoData, or outside a ragged
-// tile).
+// Cell words.  The words of a tile and of the one-cell ring around it are
+// numbered wi = (r + 1) * W2 + (c + 1), W2 = tw + 2 (tile row r, tile column
+// c; the ring at r = -1, r = th, c = -1, c = tw), at most 2^14 - 1 of them,
+// so a word index fits 14 bits and SUCC_NONE is never one.  Pending-inflow
+// counts sit in the top four bits.  Every word that is not a valid cell of
+// the tile (NoData, off the raster, outside a ragged tile, or the ring) holds
+// the count SENT_CNT: at most eight cells add one to it and a walk reaching
+// it takes one off again, so it never reads as complete (0) or as the last
+// inflow (1) and its sums are never used.  A cell's successor is simply the
+// word its code points at, so the one-pass init needs neither the target's
+// code nor bounds; a walk that reaches a SENT_CNT word stops there.
 // ---------------------------------------------------------------------------
 constexpr int MAX_TILE_CELLS = 8192;
+constexpr int MAX_TILE_WORDS = 16383;
 constexpr uint32_t SUCC_NONE = 0x3FFFu;
+constexpr uint32_t SENT_CNT = 7;
+
+__host__ __device__ inline int tile_words(int th, int tw) { return (th + 2) * (tw + 2); }
 
 // counts: (pending << CNT) | (successor << SUCC) | partial sum; 32-bit words
 // in pass 1 (a tile sum is at most 8192 < 2^14), 64-bit words in pass 2,
 // where the flow entering from other tiles (up to 2^46 cells) is added.
+// Sums that walks bring to a SENT_CNT word may carry into its successor bits,
+// never into its count.
 template <class W> struct CountWord;
 template <> struct CountWord<uint32_t> {
     static constexpr int SUCC = 14, CNT = 28;
-    static constexpr uint32_t ACC = (1u << 14) - 1, ONE = 1u << 28,
-                              SENT = (15u << 28) | (SUCC_NONE << 14);
+    static constexpr uint32_t ACC = (1u << 14) - 1, ONE = 1u << 28, SENT = SENT_CNT << 28;
 };
 template <> struct CountWord<unsigned long long> {
     static constexpr int SUCC = 46, CNT = 60;
     static constexpr unsigned long long ACC = (1ull << 46) - 1, ONE = 1ull << 60,
-                                        SENT = (15ull << 60) | ((unsigned long long)SUCC_NONE << 46);
+                                        SENT = (unsigned long long)SENT_CNT << 60;
 };
 // float weights: (pending << GW_CNT) | (mask of the neighbours draining into
 // the cell << GW_PM) | successor; the sums live in a separate array of
 // compensated float pairs.
 constexpr int GW_PM = 14, GW_CNT = 28;
-constexpr uint32_t GW_ONE = 1u << GW_CNT, GW_SENT = (15u << GW_CNT) | SUCC_NONE;
+constexpr uint32_t GW_ONE = 1u << GW_CNT, GW_SENT = SENT_CNT << GW_CNT;
 
-// Threads of a tile block: one per 32 cells (so a lane's own cells fit one
-// 32-bit mask), at least a warp, at most 256.
+// Threads of a tile block: one per 32 cells, at least a warp, at most 256.
 __host__ __device__ inline int walk_threads(int th, int tw) {
     const int n = th * tw;
     const int t = ((n + 32 * 32 - 1) / (32 * 32)) * 32;
@@ -160,24 +168,25 @@ __host__ __device__ inline int walk_threads(int th, int tw) {
 
 // Shared memory of k_walk<MODE, PASS, LOAD> for a tile shape.
 __host__ __device__ inline size_t walk_smem_bytes(int th, int tw, int mode, int pass, int load) {
-    const size_t n = (size_t)th * tw, pm = (size_t)(2 * th + 2 * tw);
+    const size_t nwd = (size_t)tile_words(th, tw), pm = (size_t)(2 * th + 2 * tw);
     size_t b = 128;  // alignment slack of the dynamic window
     b += code_buf_bytes(th, tw) + (load == LOAD_TMA_PACKED ? packed_buf_bytes(th, tw) : 0);
-    b += n * ((mode == 0 && pass == 2) ? 8 : 4);  // cell words
+    b += nwd * ((mode == 0 && pass == 2) ? 8 : 4);  // cell words
     b = (b + 15) & ~size_t(15);
-    if (mode == 1) b += n * 8;                     // float pair sums
-    b += n * 2;                                    // queued cells (walk starts, entry cells)
-    b += pm * 4 + pm * 2 + pm * 2 + pm;            // exit targets, exit ranks, entry list, inflow masks
+    if (mode == 1) b += nwd * 8;                     // float pair sums
+    b += nwd * 2;                                    // queued walk starts
+    b = (b + 15) & ~size_t(15);
+    b += pm * 4 + pm * 2 + pm * 2 + pm;              // exit targets, exit ranks, entry list, inflow masks
     return (b + 15) & ~size_t(15);
 }
 
 __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
     if (th < 1 || tw < 1 || (int64_t)th * tw > MAX_TILE_CELLS) return false;
+    if ((int64_t)(th + 2) * (tw + 2) > MAX_TILE_WORDS) return false;
     for (int pass = 1; pass <= 2; ++pass)
         if (walk_smem_bytes(th, tw, valm, pass, LOAD_TMA_PACKED) > 227 * 1024) return false;
     return true;
 }
-
 
 // Code of raster column gc in a row of packed codes: low nibble for even
 // columns, high nibble for odd ones.
@@ -312,9 +321,8 @@ __device__ __forceinline__ uint32_t outside_slot(const RasterDesc &ras, const Ti
 
 // ---------------------------------------------------------------------------
 // The walks of one tile (Algorithm 1).  Warp w holds the queue q[0 .. qn) of
-// the cells with no inflow inside the tile from its share of the tile; each
-// idle lane takes the next queued cell (idle lanes take consecutive entries,
-// in lane order) and walks it downstream.
+// the cells with no inflow inside the tile from its share of the tile; idle
+// lanes take the next queued cells in lane order and walk them downstream.
 // ---------------------------------------------------------------------------
 template <int MODE, class W>
 __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, int qn,
@@ -326,8 +334,10 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, i
     uint32_t sc = SUCC_NONE;  // successor of the lane's cell
     W acc = 0;                // counts: the lane's cell's sum
     for (;;) {
-        if (pos < qn) {
-            const uint32_t idle = __ballot_sync(0xffffffffu, !act);
+        const uint32_t idle = __ballot_sync(0xffffffffu, !act);
+        if (pos >= qn) {
+            if (idle == 0xffffffffu) break;
+        } else if (idle) {
             const int my = pos + __popc(idle & lt);
             if (!act && my < qn) {
                 const W wv = word[q[my]];
@@ -341,10 +351,9 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, i
             }
             pos += __popc(idle);
         }
-        if (!__any_sync(0xffffffffu, act)) break;
         if (!act) continue;
         if (sc == SUCC_NONE) {
-            act = false;  // an exit, a sink, or flow leaving the data
+            act = false;  // NoFlow: the path ends here
         } else if constexpr (MODE == 0) {
             const W old = atomicAdd(&word[sc], acc - CountWord<W>::ONE);
             act = (old >> CountWord<W>::CNT) == 1;  // the last inflow: continue from sc
@@ -352,7 +361,8 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, i
             sc = (uint32_t)(old >> CountWord<W>::SUCC) & SUCC_NONE;
         } else {
             const uint32_t old = atom_add_acq_rel(reinterpret_cast<uint32_t *>(&word[sc]), 0u - GW_ONE);
-            if ((old >> GW_CNT) == 1) {  // complete: own weight plus inflows in fixed order
+            act = (old >> GW_CNT) == 1;
+            if (act) {  // complete: own weight plus inflows in a fixed order
                 const int t = (int)sc;
                 FF v = val[t];
                 uint32_t pm = (old >> GW_PM) & 0xFFu;
@@ -363,8 +373,6 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, i
                 }
                 val[t] = v;
                 sc = old & SUCC_NONE;
-            } else {
-                act = false;
             }
         }
     }
@@ -378,9 +386,10 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, i
 // weights, integer counts; MODE 1: float weights (nf fields).
 // Persistent CTAs: each block takes tiles t = blockIdx.x, + gridDim.x, ...
 // With TMA the codes of the next tile are staged into shared memory while the
-// current one is walked (they are no longer read by then).  The cell words are
-// zero when a tile starts (cleared by the previous tile's last pass), so every
-// cell sets its own word and adds itself to its successor's in one pass.
+// current one is walked (they are no longer read by then).  The words are
+// zero when a tile starts (cleared by the previous tile's last pass), so one
+// pass sets every word: each valid cell adds its own (successor, weight) and
+// one pending inflow to its successor's word, every other word its SENT_CNT.
 // ---------------------------------------------------------------------------
 template <int MODE, int PASS, int LOAD>
 __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_constant__ TileArgs A,
@@ -394,16 +403,18 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     __shared__ __align__(8) uint64_t s_bar;
 
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int th = a.th, tw = a.tw;
     const int S = tile_stride(tw);
-    const int n = th * tw;
-    // ci / tw as umulhi(ci, rdiv), exact for ci < 2^13 and 2 <= tw <= 8192
-    // (the rounding error ci / 2^32 stays below 1 / tw); tw = 1 divides by itself
-    const uint32_t rdiv = tw > 1 ? 0xFFFFFFFFu / (uint32_t)tw + 1u : 0u;
-    auto row_of = [&](int ci) { return tw > 1 ? (int)__umulhi((uint32_t)ci, rdiv) : ci; };
+    const int W2 = tw + 2, NWD = tile_words(th, tw);
+    // wi / W2 as umulhi(wi, rdiv), exact for wi < 2^14 and 3 <= W2 <= 8194
+    // (the rounding error wi / 2^32 stays below 1 / W2)
+    const uint32_t rdiv = 0xFFFFFFFFu / (uint32_t)W2 + 1u;
     const int64_t T = a.T;
     const int nf = a.nf;
+    const W SENT = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
+    constexpr int CNT = MODE == 0 ? CountWord<W>::CNT : GW_CNT;
+    constexpr int SUCC = MODE == 0 ? CountWord<W>::SUCC : 0;
 
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem) + 127) &
                                                 ~uintptr_t(127));
@@ -411,12 +422,12 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     uint8_t *stage = base + code_buf_bytes(th, tw);        // packed: the TMA stage
     uint8_t *p = stage + (LOAD == LOAD_TMA_PACKED ? packed_buf_bytes(th, tw) : 0);
     W *word = reinterpret_cast<W *>(p);
-    p += (size_t)n * sizeof(W);
+    p += (size_t)NWD * sizeof(W);
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     FF *val = reinterpret_cast<FF *>(p);
-    if (MODE == 1) p += (size_t)n * sizeof(FF);
-    uint16_t *queue = reinterpret_cast<uint16_t *>(p);     // walk starts, then entry cells
-    p += (size_t)n * 2;
+    if (MODE == 1) p += (size_t)NWD * sizeof(FF);
+    uint16_t *queue = reinterpret_cast<uint16_t *>(p);     // walk starts
+    p += (size_t)NWD * 2;
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     uint32_t *pexit = reinterpret_cast<uint32_t *>(p);     // slot -> global slot id of its exit target
     p += (size_t)a.pmax * 4;
@@ -430,7 +441,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     long long fbad = NO_INDEX;
     uint32_t gmaxw = 0;
 
-    if (tid < 8) s_nb[tid] = dir_dr(tid + 1) * tw + dir_dc(tid + 1);
+    if (tid < 8) s_nb[tid] = dir_dr(tid + 1) * W2 + dir_dc(tid + 1);
     if (tid == 0) {
         s_flags = 0;
         if (LOAD != LOAD_PLAIN) {
@@ -438,7 +449,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             mbar_fence_init();
         }
     }
-    for (int ci = tid; ci < n; ci += nt) word[ci] = 0;
+    for (int wi = tid; wi < NWD; wi += nt) word[wi] = 0;
     __syncthreads();
     auto issue = [&](int64_t tn) {  // one thread: stage tile tn's codes (TMA: one raster only)
         const int tyn = (int)(tn / a.one.tiles_x), txn = (int)(tn - (int64_t)tyn * a.one.tiles_x);
@@ -501,66 +512,46 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             __syncthreads();
         }
 
-        // [phase] init, one pass: each cell sets its word (successor, unit
-        // weight) and adds one pending inflow to its successor's (with its
-        // own direction bit for float weights); exits record their targets;
-        // perimeter cells note which outside neighbours drain into them
-        for (int ci0 = tid; ci0 < n; ci0 += 4 * nt) {
-            // four cells per thread at a time: their code loads, then their
-            // targets' code loads, are in flight together
-            int cis[4], xis[4];
-            uint32_t ks[4], tks[4];
-            bool in[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int ci = ci0 + u * nt;
-                const int r = row_of(ci), c = ci - r * tw;
-                cis[u] = ci;
-                in[u] = ci < n && r < h && c < w;
-                xis[u] = (r + 1) * S + X0 + c;
-                ks[u] = in[u] ? cbuf[xis[u]] : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t k = ks[u];
-                tks[u] = (k - 1u < 8u) ? cbuf[xis[u] + dir_dr((int)k) * S + dir_dc((int)k)] : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int ci = cis[u];
-                if (ci >= n) continue;
-                const uint32_t k = ks[u];
-                const int r = row_of(ci), c = ci - r * tw;
-                if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
-                    if (in[u] && k > 9u) {
-                        ++nbad;
-                        fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
-                    }
+        // [phase] init, one pass over every word (tile and ring): a valid
+        // cell adds its own successor and unit weight to its word and one
+        // pending inflow (with its direction bit for float weights) to the
+        // word its code points at; any other word adds its SENT_CNT
+        for (int wi = tid; wi < NWD; wi += nt) {
+            const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
+            const bool tile = (unsigned)r < (unsigned)h && (unsigned)c < (unsigned)w;
+            const uint32_t k = tile ? cbuf[hr * S + X0 + c] : 0u;
+            if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
+                if (tile && k > 9u) {
+                    ++nbad;
+                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
                 }
-                if (!in[u] || !vcode(k)) {  // nothing ever adds to a NoData cell's word
-                    word[ci] = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
-                    continue;
-                }
-                uint32_t sc = SUCC_NONE;
-                if (k <= 8u && vcode(tks[u])) {
-                    const int dr = dir_dr((int)k), dc = dir_dc((int)k);
-                    const int tr = r + dr, tc = c + dc;
-                    if ((unsigned)tr < (unsigned)h && (unsigned)tc < (unsigned)w) {
-                        sc = (uint32_t)(ci + dr * tw + dc);
-                        if constexpr (MODE == 0) atomicAdd(&word[sc], CountWord<W>::ONE);
-                        else atomicAdd(&word[sc], GW_ONE | (1u << (GW_PM + dir_rev((int)k) - 1)));
-                    } else if (PASS == 1) {  // an exit: its flow enters the neighbouring tile
-                        pexit[slot_of(r, c, h, w)] = outside_slot(ras, a, ty, tx, R0, C0, h, w, tr, tc);
-                    }
-                }
-                if constexpr (MODE == 0) atomicAdd(&word[ci], ((W)sc << CountWord<W>::SUCC) | (W)1);
-                else atomicAdd(&word[ci], sc);
             }
+            if (!vcode(k)) {
+                atomicAdd(&word[wi], SENT);
+                continue;
+            }
+            uint32_t sc = SUCC_NONE;
+            if (k <= 8u) {
+                sc = (uint32_t)(wi + dir_dr((int)k) * W2 + dir_dc((int)k));
+                if constexpr (MODE == 0) atomicAdd(&word[sc], CountWord<W>::ONE);
+                else atomicAdd(&word[sc], GW_ONE | (1u << (GW_PM + dir_rev((int)k) - 1)));
+            }
+            if constexpr (MODE == 0) atomicAdd(&word[wi], ((W)sc << SUCC) | (W)1);
+            else atomicAdd(&word[wi], sc);
         }
+        // the perimeter: exits (flow into a valid cell of another tile) and
+        // the outside neighbours draining into each perimeter cell
         for (int s = tid; s < P; s += nt) {
             int r, c;
             cell_of(s, h, w, r, c);
-            if (!vcode(cbuf[(r + 1) * S + X0 + c])) continue;
+            const int k = cbuf[(r + 1) * S + X0 + c];
+            if (!vcode(k)) continue;
+            if (PASS == 1 && k <= 8) {
+                const int tr = r + dir_dr(k), tc = c + dir_dc(k);
+                if (((unsigned)tr >= (unsigned)h || (unsigned)tc >= (unsigned)w) &&
+                    vcode(cbuf[(tr + 1) * S + X0 + tc]))
+                    pexit[s] = outside_slot(ras, a, ty, tx, R0, C0, h, w, tr, tc);
+            }
             uint32_t m = 0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -579,20 +570,16 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
         }
 
         // the cells with no inflow inside the tile start the walks: warp w
-        // queues those of its share of the tile (32-cell chunks c0 .. c1)
-        const int nch = (n + 31) >> 5, warp = tid >> 5, nw = nt >> 5;
+        // queues those of its share of the words (32-word chunks c0 .. c1)
+        const int nch = (NWD + 31) >> 5;
         const int c0 = (int)((int64_t)nch * warp / nw), c1 = (int)((int64_t)nch * (warp + 1) / nw);
         uint16_t *wq = queue + c0 * 32;
         int qn = 0;
         for (int ch = c0; ch < c1; ++ch) {
-            const int ci = ch * 32 + lane;
-            bool leaf = false;
-            if (ci < n) {
-                const W wv = word[ci];
-                leaf = MODE == 0 ? (wv >> CountWord<W>::CNT) == 0 : ((uint32_t)wv >> GW_CNT) == 0;
-            }
+            const int wi = ch * 32 + lane;
+            const bool leaf = wi < NWD && (word[wi] >> CNT) == 0;
             const uint32_t b = __ballot_sync(0xffffffffu, leaf);
-            if (leaf) wq[qn + __popc(b & ((1u << lane) - 1u))] = (uint16_t)ci;
+            if (leaf) wq[qn + __popc(b & ((1u << lane) - 1u))] = (uint16_t)wi;
             qn += __popc(b);
         }
         __syncwarp();
@@ -622,19 +609,19 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
         for (int f = 0; f < nf; ++f) {
             if constexpr (MODE == 1) {
                 const float *wp = ras.w[f];
-                for (int ci = tid; ci < n; ci += nt) {
-                    const uint32_t wv = word[ci];
-                    if (wv >= GW_SENT) continue;
-                    const int r = row_of(ci), c = ci - r * tw;
+                for (int wi = tid; wi < NWD; wi += nt) {
+                    const uint32_t wv = word[wi];
+                    if ((wv >> GW_CNT) >= SENT_CNT) continue;  // not a valid cell of the tile
+                    const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
                     const float wf = wp ? wp[(R0 + r) * ras.pw + (C0 + c)] : 1.0f;
                     if constexpr (PASS == 1) {
                         const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
                         if (b >= 0x7f800000u) nonfinite = 1;
                         gmaxw = max(gmaxw, b);
                     }
-                    val[ci] = FF{wf, 0.0f};
+                    val[wi] = FF{wf, 0.0f};
                     if (f > 0)  // the pending counts again, from the inflow mask
-                        word[ci] = (wv & ((1u << GW_CNT) - 1u)) |
+                        word[wi] = (wv & ((1u << GW_CNT) - 1u)) |
                                    ((uint32_t)__popc((wv >> GW_PM) & 0xFFu) << GW_CNT);
                 }
             }
@@ -649,9 +636,9 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                     if (!m) continue;
                     int r, c;
                     cell_of(s, h, w, r, c);
-                    const int ci = r * tw + c;
+                    const int wi = (r + 1) * W2 + c + 1;
                     FF v;
-                    if constexpr (MODE == 1) v = val[ci];
+                    if constexpr (MODE == 1) v = val[wi];
                     unsigned long long add = 0;
                     while (m) {
                         const int j = __ffs(m) - 1;
@@ -667,8 +654,8 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                             v = ff_add(v, fix2ff(reinterpret_cast<const u128 *>(a.G)[node * nf + f], qf));
                         }
                     }
-                    if constexpr (MODE == 0) word[ci] += (W)add;
-                    else val[ci] = v;
+                    if constexpr (MODE == 0) word[wi] += (W)add;
+                    else val[wi] = v;
                 }
             }
             __syncthreads();
@@ -683,30 +670,31 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                     if (rk == LINK_TERM) continue;
                     int r, c;
                     cell_of(s, h, w, r, c);
-                    const int ci = r * tw + c;
+                    const int wi = (r + 1) * W2 + c + 1;
                     double v;
-                    if constexpr (MODE == 0) v = (double)(word[ci] & CountWord<W>::ACC);
-                    else v = (double)val[ci].hi + (double)val[ci].lo;
+                    if constexpr (MODE == 0) v = (double)(word[wi] & CountWord<W>::ACC);
+                    else v = (double)val[wi].hi + (double)val[wi].lo;
                     a.node_val[(tbase + rk) * nf + f] = v;
                 }
             } else {
-                // the output raster of field f: A, 0 at NoData; the words are
-                // cleared for the next tile after the last field
+                // the output raster of field f: A at complete cells, 0 at
+                // NoData (and on cycles); the words are cleared for the next
+                // tile after the last field
                 const bool last = f == nf - 1;
-                for (int ci = tid; ci < n; ci += nt) {
-                    const int r = row_of(ci), c = ci - r * tw;
-                    const W wv = word[ci];
-                    if (last) word[ci] = 0;
-                    if (r >= h || c >= w) continue;
+                for (int wi = tid; wi < NWD; wi += nt) {
+                    const W wv = word[wi];
+                    if (last) word[wi] = 0;
+                    const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
+                    if ((unsigned)r >= (unsigned)h || (unsigned)c >= (unsigned)w) continue;
                     uint32_t o = 0;
-                    if constexpr (MODE == 0) {
-                        if ((wv >> CountWord<W>::CNT) != 15) {
+                    if ((wv >> CNT) == 0) {
+                        if constexpr (MODE == 0) {
                             const unsigned long long s64 = (unsigned long long)(wv & CountWord<W>::ACC);
                             ovf |= (s64 >> 32) != 0;
                             o = (uint32_t)s64;
+                        } else {
+                            o = __float_as_uint(ff_round(val[wi]));
                         }
-                    } else {
-                        if ((uint32_t)wv < GW_SENT) o = __float_as_uint(ff_round(val[ci]));
                     }
                     reinterpret_cast<uint32_t *>(ras.out[f])[(size_t)(R0 + r) * ras.po + C0 + c] = o;
                 }
@@ -716,53 +704,43 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
 
         if constexpr (PASS == 1) {
             // Algorithm 2 for the entry cells: the exit each one's path
-            // reaches.  Warp w takes its share of the entry list; an idle
-            // lane takes the next entry and follows its path.
-            {
-                const int ne = s_nent;
-                const int e1 = (int)((int64_t)ne * (warp + 1) / nw);
-                int pos = (int)((int64_t)ne * warp / nw), cur = 0, slot = 0, steps = 0;
-                bool act = false;
+            // reaches (the last valid cell of the tile on it, if on the
+            // perimeter and an exit); one entry per lane at a time
+            for (int e = tid; e < s_nent; e += nt) {
+                const int slot = pent[e];
+                int r, c;
+                cell_of(slot, h, w, r, c);
+                int cur = (r + 1) * W2 + c + 1, steps = 0;
+                W wc = word[cur];
                 for (;;) {
-                    if (pos < e1) {
-                        const uint32_t idle = __ballot_sync(0xffffffffu, !act);
-                        const int my = pos + __popc(idle & ((1u << lane) - 1u));
-                        if (!act && my < e1) {
-                            int r, c;
-                            slot = pent[my];
-                            cell_of(slot, h, w, r, c);
-                            cur = r * tw + c;
-                            steps = 0;
-                            act = true;
-                        }
-                        pos += __popc(idle);
+                    const uint32_t sc = (uint32_t)(wc >> SUCC) & SUCC_NONE;
+                    if (sc == SUCC_NONE) break;
+                    const W wn = word[sc];
+                    if ((wn >> CNT) >= SENT_CNT) break;  // leaves the tile or the data
+                    if (++steps > h * w) {              // a cycle: the path never ends
+                        cur = -1;
+                        break;
                     }
-                    if (!__any_sync(0xffffffffu, act)) break;
-                    if (!act) continue;
-                    const uint32_t sc = (uint32_t)(MODE == 0 ? (word[cur] >> CountWord<W>::SUCC) : word[cur]) & SUCC_NONE;
-                    if (sc != SUCC_NONE && ++steps <= n) {
-                        cur = (int)sc;
-                        continue;
-                    }
-                    uint16_t lk = LINK_TERM;  // the path ends inside the tile (or on a cycle)
-                    if (sc == SUCC_NONE) {
-                        const int rr = row_of(cur), cc = cur - rr * tw;
-                        if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
-                    }
-                    a.link[tbase + slot] = lk;
-                    act = false;
+                    cur = (int)sc;
+                    wc = wn;
                 }
+                uint16_t lk = LINK_TERM;
+                if (cur >= 0) {
+                    const int hr = (int)__umulhi((uint32_t)cur, rdiv), rr = hr - 1, cc = cur - hr * W2 - 1;
+                    if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
+                }
+                a.link[tbase + slot] = lk;
             }
             if (tid == 0) a.nexit[t] = (uint32_t)nexits;
             __syncthreads();
-            // cells still waiting for inflow lie on a cycle inside the tile;
-            // the words are cleared for the next tile
-            for (int ci = tid; ci < n; ci += nt) {
-                const W wv = word[ci];
-                word[ci] = 0;
-                const uint32_t cnt = (uint32_t)(MODE == 0 ? (wv >> CountWord<W>::CNT) : ((uint32_t)wv >> GW_CNT));
-                if (cnt != 0 && cnt != 15) {
-                    const int r = row_of(ci), c = ci - r * tw;
+            // cells still waiting for an inflow lie on a cycle inside the
+            // tile (a cycle cell misses exactly its predecessor on the
+            // cycle); the words are cleared for the next tile
+            for (int wi = tid; wi < NWD; wi += nt) {
+                const W wv = word[wi];
+                word[wi] = 0;
+                if ((wv >> CNT) == 1) {
+                    const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
                     ++ncyc;
                     fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
                 }
