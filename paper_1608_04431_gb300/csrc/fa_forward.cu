@@ -153,11 +153,13 @@ template <> struct CountWord<unsigned long long> {
     static constexpr unsigned long long ACC = (1ull << 46) - 1, ONE = 1ull << 60,
                                         SENT = (unsigned long long)SENT_CNT << 60;
 };
-// float weights: (pending << GW_CNT) | (mask of the neighbours draining into
-// the cell << GW_PM) | successor; the sums live in a separate array of
-// compensated float pairs.
+// float weights: (pending << GW_CNT) | GW_VALID for a valid cell of the tile
+// | (mask of the neighbours draining into the cell << GW_PM) | successor; the
+// sums live in a separate array of compensated float pairs.  (A valid cell
+// may have up to eight pending inflows, so the flag, not the count, tells it
+// from a SENT_CNT word before the walks.)
 constexpr int GW_PM = 14, GW_CNT = 28;
-constexpr uint32_t GW_ONE = 1u << GW_CNT, GW_SENT = SENT_CNT << GW_CNT;
+constexpr uint32_t GW_ONE = 1u << GW_CNT, GW_SENT = SENT_CNT << GW_CNT, GW_VALID = 1u << 27;
 
 // Threads of a tile block: one per 32 cells, at least a warp, at most 256.
 __host__ __device__ inline int walk_threads(int th, int tw) {
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 else atomicAdd(&word[sc], GW_ONE | (1u << (GW_PM + dir_rev((int)k) - 1)));
             }
             if constexpr (MODE == 0) atomicAdd(&word[wi], ((W)sc << SUCC) | (W)1);
-            else atomicAdd(&word[wi], sc);
+            else atomicAdd(&word[wi], sc | GW_VALID);
         }
         // the perimeter: exits (flow into a valid cell of another tile) and
         // the outside neighbours draining into each perimeter cell
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 const float *wp = ras.w[f];
                 for (int wi = tid; wi < NWD; wi += nt) {
                     const uint32_t wv = word[wi];
-                    if ((wv >> GW_CNT) >= SENT_CNT) continue;  // not a valid cell of the tile
+                    if (!(wv & GW_VALID)) continue;  // not a valid cell of the tile
                     const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
                     const float wf = wp ? wp[(R0 + r) * ras.pw + (C0 + c)] : 1.0f;
                     if constexpr (PASS == 1) {
