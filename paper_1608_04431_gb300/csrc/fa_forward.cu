@@ -613,7 +613,12 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 const float *wp = ras.w[f];
                 for (int wi = tid; wi < NWD; wi += nt) {
                     const uint32_t wv = word[wi];
-                    if (!(wv & GW_VALID)) continue;  // not a valid cell of the tile
+                    if (!(wv & GW_VALID)) {  // not a valid cell of the tile: its sentinel again
+                        if (f > 0)
+                            word[wi] = (wv & ((1u << GW_CNT) - 1u)) |
+                                       ((SENT_CNT + (uint32_t)__popc((wv >> GW_PM) & 0xFFu)) << GW_CNT);
+                        continue;
+                    }
                     const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
                     const float wf = wp ? wp[(R0 + r) * ras.pw + (C0 + c)] : 1.0f;
                     if constexpr (PASS == 1) {
