@@ -58,6 +58,8 @@ struct TileArgs {
     const void *G;  // resolved perimeter graph: u64 counts or u128 fixed-point sums, [node * nf + f]
     StatusBlock *st;
     uint32_t *maxw;
+    uint32_t *ef_hdr, *ef_cp, *seg_merge, *inf_src;  // counts: the entry forests (pass 1 -> pass 2)
+    uint16_t *ef_seg, *inf_seg;
     // batches: a table of rasters (nullptr for one raster), each with its
     // tiles numbered from its tile_base in one global tile sequence
     const RasterDesc *rtab;
@@ -135,6 +137,7 @@ constexpr int MAX_TILE_CELLS = 8192;
 constexpr int MAX_TILE_WORDS = 16383;
 constexpr uint32_t SUCC_NONE = 0x3FFFu;
 constexpr uint32_t SENT_CNT = 7;
+constexpr uint32_t NO_JOIN = 0xFFFFFFFFu;  // an entry-forest segment that joins no other
 
 __host__ __device__ inline int tile_words(int th, int tw) { return (th + 2) * (tw + 2); }
 
@@ -176,9 +179,21 @@ __host__ __device__ inline size_t walk_smem_bytes(int th, int tw, int mode, int 
     b += nwd * ((mode == 0 && pass == 2) ? 8 : 4);  // cell words
     b = (b + 15) & ~size_t(15);
     if (mode == 1) b += nwd * 8;                     // float pair sums
-    b += nwd * 2;                                    // queued walk starts
+    // queued walk starts (counts, pass 1: then the entry walks' claim tags)
+    b += nwd * ((mode == 0 && pass == 1) ? 4 : 2);
     b = (b + 15) & ~size_t(15);
     b += pm * 4 + pm * 2 + pm * 2 + pm;              // exit targets, exit ranks, entry list, inflow masks
+    if (mode == 0 && pass == 1) b = ((b + 3) & ~size_t(3)) + pm * 4 + pm * 2;  // segment joins and ends
+    return (b + 15) & ~size_t(15);
+}
+
+__host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
+    // segments: at most one per perimeter cell
+    const size_t pc = (size_t)perim_count(th, tw);
+    size_t b = pc * 16;                       // inflow per segment (graph scale), then prefix sums
+    b += pc * 8 * 2;                          // inflow at the tile scale, flow at the end
+    b += pc * 4 * 2 + (pc + 1) * 4;           // join target, pending joins / fill, bucket start
+    b += pc * 2 * 2;                          // join position, joins grouped by target
     return (b + 15) & ~size_t(15);
 }
 
@@ -187,7 +202,7 @@ __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
     if ((int64_t)(th + 2) * (tw + 2) > MAX_TILE_WORDS) return false;
     for (int pass = 1; pass <= 2; ++pass)
         if (walk_smem_bytes(th, tw, valm, pass, LOAD_TMA_PACKED) > 227 * 1024) return false;
-    return true;
+    return offsets_smem_bytes(th, tw) <= 227 * 1024;
 }
 
 // Code of raster column gc in a row of packed codes: low nibble for even
@@ -400,7 +415,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_flags, s_nent;
+    __shared__ int s_flags, s_nent, s_nef, s_ninf;
     __shared__ int s_nb[8];
     __shared__ __align__(8) uint64_t s_bar;
 
@@ -428,8 +443,10 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     FF *val = reinterpret_cast<FF *>(p);
     if (MODE == 1) p += (size_t)NWD * sizeof(FF);
+    constexpr bool RETAIN = MODE == 0 && PASS == 1;     // counts: A_loc stays in the output
     uint16_t *queue = reinterpret_cast<uint16_t *>(p);     // walk starts
-    p += (size_t)NWD * 2;
+    uint32_t *tag = reinterpret_cast<uint32_t *>(p);       // RETAIN, after the walks: claim tags
+    p += (size_t)NWD * (RETAIN ? 4 : 2);
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     uint32_t *pexit = reinterpret_cast<uint32_t *>(p);     // slot -> global slot id of its exit target
     p += (size_t)a.pmax * 4;
@@ -438,6 +455,11 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     uint16_t *pent = reinterpret_cast<uint16_t *>(p);      // the entry cells' slots
     p += (size_t)a.pmax * 2;
     uint8_t *pinf = p;                                     // slot -> neighbours outside draining in
+    p += a.pmax;
+    p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
+    uint32_t *segjoin = reinterpret_cast<uint32_t *>(p);   // RETAIN: segment -> where it joins another
+    p += (size_t)a.pmax * 4;
+    uint16_t *segend = reinterpret_cast<uint16_t *>(p);    // RETAIN: segment -> the exit it ends at
 
     int nbad = 0, ncyc = 0, nonfinite = 0, ovf = 0;
     long long fbad = NO_INDEX;
@@ -451,7 +473,10 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             mbar_fence_init();
         }
     }
-    for (int wi = tid; wi < NWD; wi += nt) word[wi] = 0;
+    for (int wi = tid; wi < NWD; wi += nt) {
+        word[wi] = 0;
+        if (RETAIN) tag[wi] = 0;
+    }
     __syncthreads();
     auto issue = [&](int64_t tn) {  // one thread: stage tile tn's codes (TMA: one raster only)
         const int tyn = (int)(tn / a.one.tiles_x), txn = (int)(tn - (int64_t)tyn * a.one.tiles_x);
@@ -481,7 +506,11 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             prank[s] = LINK_TERM;
             pinf[s] = 0;
         }
-        if (tid == 0) s_nent = 0;
+        if (tid == 0) {
+            s_nent = 0;
+            s_nef = 0;
+            s_ninf = 0;
+        }
 
         // [phase] codes of the tile and its one-cell halo ring
         if constexpr (LOAD != LOAD_PLAIN) {
@@ -563,7 +592,23 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 if (kh >= 1 && kh <= 8 && nr + dir_dr(kh) == r && nc + dir_dc(kh) == c) m |= 1u << j;
             }
             pinf[s] = (uint8_t)m;
-            if (PASS == 1 && m) pent[atomicAdd(&s_nent, 1)] = (uint16_t)s;
+            if (PASS == 1 && m) {
+                const int e = atomicAdd(&s_nent, 1);
+                pent[e] = (uint16_t)s;
+                if constexpr (RETAIN) {
+                    // inflow links: the exit outside (its slot id) and the
+                    // segment (entry) it feeds
+                    const int j0 = atomicAdd(&s_ninf, __popc(m));
+                    const size_t infb = (size_t)t * (a.pmax + 8);
+                    for (int jj = 0; m; ++jj) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1u;
+                        a.inf_src[infb + j0 + jj] =
+                            outside_slot(ras, a, ty, tx, R0, C0, h, w, r + dir_dr(j + 1), c + dir_dc(j + 1));
+                        a.inf_seg[infb + j0 + jj] = (uint16_t)e;
+                    }
+                }
+            }
         }
         if constexpr (LOAD == LOAD_TMA) fence_proxy_async();  // the code buffer is refilled by TMA
         __syncthreads();
@@ -709,47 +754,78 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             if (f + 1 < nf) __syncthreads();
         }
 
-        if constexpr (PASS == 1) {
-            // Algorithm 2 for the entry cells: the exit each one's path
-            // reaches (the last valid cell of the tile on it, if on the
-            // perimeter and an exit); one entry per lane at a time
+        if constexpr (RETAIN) {
+            // Algorithm 2 for the entry cells, recording the tile's entry
+            // forest for pass 2: the path of entry e is walked once, claiming
+            // its cells (tag (e + 1) << 16 | position); a walk that reaches a
+            // cell claimed by another walk stops and records the join there.
+            // Each walk's claimed run is a segment: the cells of segment e at
+            // positions 0, 1, ... in path order.
+            const size_t efb = (size_t)t * th * tw;
             for (int e = tid; e < s_nent; e += nt) {
                 const int slot = pent[e];
                 int r, c;
                 cell_of(slot, h, w, r, c);
-                int cur = (r + 1) * W2 + c + 1, steps = 0;
-                W wc = word[cur];
-                for (;;) {
-                    const uint32_t sc = (uint32_t)(wc >> SUCC) & SUCC_NONE;
-                    if (sc == SUCC_NONE) break;
-                    const W wn = word[sc];
-                    if ((wn >> CNT) >= SENT_CNT) break;  // leaves the tile or the data
-                    if (++steps > h * w) {              // a cycle: the path never ends
-                        cur = -1;
+                int cur = (r + 1) * W2 + c + 1;
+                uint16_t end = LINK_TERM;
+                uint32_t join = NO_JOIN;
+                for (int pos = 0; pos < h * w; ++pos) {
+                    const uint32_t old = atomicCAS(&tag[cur], 0u, ((uint32_t)(e + 1) << 16) | (uint32_t)pos);
+                    if (old != 0) {  // joins segment (old >> 16) - 1 at its position old & 0xFFFF
+                        join = old - (1u << 16);
+                        break;
+                    }
+                    const int idx = atomicAdd(&s_nef, 1);
+                    a.ef_cp[efb + idx] = ((uint32_t)cur << 16) | (uint32_t)pos;
+                    a.ef_seg[efb + idx] = (uint16_t)e;
+                    const uint32_t sc = (uint32_t)(word[cur] >> SUCC) & SUCC_NONE;
+                    if (sc == SUCC_NONE || (word[sc] >> CNT) >= SENT_CNT) {
+                        // the path leaves the tile here (an exit) or ends
+                        const int hr = (int)__umulhi((uint32_t)cur, rdiv), rr = hr - 1, cc = cur - hr * W2 - 1;
+                        if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) end = prank[slot_of(rr, cc, h, w)];
                         break;
                     }
                     cur = (int)sc;
-                    wc = wn;
                 }
-                uint16_t lk = LINK_TERM;
-                if (cur >= 0) {
-                    const int hr = (int)__umulhi((uint32_t)cur, rdiv), rr = hr - 1, cc = cur - hr * W2 - 1;
-                    if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
-                }
-                a.link[tbase + slot] = lk;
+                segend[e] = end;
+                segjoin[e] = join;
             }
-            if (tid == 0) a.nexit[t] = (uint32_t)nexits;
+            __syncthreads();
+            // the entries' links: follow the joins to the segment that ends
+            const int ne = s_nent;
+            for (int e = tid; e < ne; e += nt) {
+                a.seg_merge[tbase + e] = segjoin[e];
+                const int slot = pent[e];
+                if (prank[slot] != LINK_TERM) continue;  // an exit links to itself
+                int x = e;
+                for (int hop = 0; hop < ne && segjoin[x] != NO_JOIN; ++hop) x = (int)(segjoin[x] >> 16);
+                a.link[tbase + slot] = segjoin[x] == NO_JOIN ? segend[x] : LINK_TERM;
+            }
+            if (tid == 0)
+                reinterpret_cast<uint4 *>(a.ef_hdr)[t] =
+                    make_uint4((uint32_t)s_nef, (uint32_t)ne, (uint32_t)s_ninf, 0u);
+        } else if constexpr (PASS == 1) {
+            // Algorithm 2 for the entry cells: the exit each one's path
+            // reaches (the last valid cell of the tile on it, if on the
+            // perimeter and an exit); one entry per lane at a time            if (tid == 0) a.nexit[t] = (uint32_t)nexits;
             __syncthreads();
             // cells still waiting for an inflow lie on a cycle inside the
             // tile (a cycle cell misses exactly its predecessor on the
-            // cycle); the words are cleared for the next tile
+            // cycle); counts: A_loc goes to the output raster (0 at NoData
+            // and on cycles); the words are cleared for the next tile
             for (int wi = tid; wi < NWD; wi += nt) {
                 const W wv = word[wi];
                 word[wi] = 0;
+                if (RETAIN) tag[wi] = 0;
+                const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
                 if ((wv >> CNT) == 1) {
-                    const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
                     ++ncyc;
                     fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
+                }
+                if constexpr (RETAIN) {
+                    if ((unsigned)r < (unsigned)h && (unsigned)c < (unsigned)w)
+                        reinterpret_cast<uint32_t *>(ras.out[0])[(size_t)(R0 + r) * ras.po + C0 + c] =
+                            (wv >> CNT) == 0 ? (uint32_t)(wv & CountWord<W>::ACC) : 0u;
                 }
             }
         }
@@ -793,6 +869,220 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
         // shared memory: wait for it once more (bounded) before exiting
         if (LOAD != LOAD_PLAIN && timed_out) mbar_wait(&s_bar, (uint32_t)(it & 1), a.wait_ns);
     }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: add the flow entering each tile to the cells downstream of its entry
+// cells.  in(e), the flow arriving at entry e from outside, follows e's path:
+// every cell of segment e gets in(e), and from the cell where segment q joins
+// segment e onwards every cell also gets F(q), the flow at the end of q
+// (in(q) plus the F of every segment joining q).  So the offset of the cell at
+// position j of segment e is in(e) + sum of F(q) over the segments q joining e
+// at positions <= j.  Codes are not needed: pass 1 recorded the segments.
+// ---------------------------------------------------------------------------
+template <int VALM>
+__global__ void __launch_bounds__(128) k_offsets(const __grid_constant__ TileArgs A) {
+    typedef typename std::conditional<VALM == 0, unsigned long long, long long>::type OV;
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ int s_emax;
+    const TileArgs &a = A;
+    const int64_t t = blockIdx.x;
+    const uint4 hd = reinterpret_cast<const uint4 *>(a.ef_hdr)[t];
+    const int nef = (int)hd.x, nseg = (int)hd.y, ninf = (int)hd.z;
+    if (nseg == 0 || nef == 0) return;  // no flow enters this tile
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const RasterDesc &ras = raster_of(a, t);
+    const int lt = (int)(t - ras.tile_base);
+    const int ty = lt / ras.tiles_x, tx = lt - ty * ras.tiles_x;
+    const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
+    const int h = (int)min((int64_t)a.th, ras.rows - R0);
+    const int w = (int)min((int64_t)a.tw, ras.cols - C0);
+    const int W2 = a.tw + 2;  // cells are recorded by their word index (r + 1) * W2 + (c + 1)
+    const int P = perim_count(h, w);
+    const int pm = a.pmax;
+    const size_t tb = (size_t)t * pm, eb = (size_t)t * a.th * a.tw, ib = (size_t)t * (pm + 8);
+
+    // one segment per entry cell: nseg <= perimeter cells of the nominal tile
+    const int pc = perim_count(a.th, a.tw);
+    u128 *inS = reinterpret_cast<u128 *>(smem);  // [pc] in(e), perimeter-graph scale
+    OV *pre = reinterpret_cast<OV *>(inS);       //   later: prefix sums of F over grouped joins
+    OV *inT = reinterpret_cast<OV *>(inS + pc);  // [pc] in(e), this tile's scale
+    OV *F = inT + pc;                            // [pc] flow at the end of segment e
+    int *par = reinterpret_cast<int *>(F + pc);  // [pc] segment e joins, or -1
+    int *pend = par + pc;                        // [pc] joins into e not yet summed
+    int *mfill = pend;                           //   later: fill counts of the groups
+    int *moff = pend + pc;                       // [pc + 1] start of e's joins in mlist
+    uint16_t *mpos = reinterpret_cast<uint16_t *>(moff + pc + 1);  // [pc] position e joins at
+    uint16_t *mlist = mpos + pc;                 // [pc] joining segments grouped by target
+
+    if (tid == 0) s_emax = INT_MIN;
+    for (int e = tid; e < nseg; e += nt) {
+        inS[e] = 0;
+        pend[e] = 0;
+        moff[e] = 0;
+    }
+    __syncthreads();
+
+    // ---- in(e) = sum of G over the exits outside draining into entry e
+    for (int j = tid; j < ninf; j += nt) {
+        const uint32_t src = a.inf_src[ib + j];
+        const uint16_t lk = a.link[src];
+        if (lk == LINK_TERM) continue;  // never: a cell draining into this tile is an exit
+        const size_t gi = src - src % (uint32_t)pm + lk;
+        if constexpr (VALM == 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&inS[a.inf_seg[ib + j]]),
+                      reinterpret_cast<const unsigned long long *>(a.G)[gi]);
+        else
+            atomic_add_u128(&inS[a.inf_seg[ib + j]], reinterpret_cast<const u128 *>(a.G)[gi]);
+    }
+    // ---- the join tree of the segments
+    for (int e = tid; e < nseg; e += nt) {
+        const uint32_t m = a.seg_merge[tb + e];
+        if (m == NO_JOIN) {
+            par[e] = -1;
+            continue;
+        }
+        const int p = (int)(m >> 16);
+        par[e] = p;
+        mpos[e] = (uint16_t)(m & 0xFFFFu);
+        atomicAdd(&pend[p], 1);
+        atomicAdd(&moff[p], 1);
+    }
+    __syncthreads();
+    const int qf = VALM ? fix_scale(a.fcells, *a.maxw) : 0;
+    if constexpr (VALM == 1) {
+        int emax = INT_MIN;
+        for (int e = tid; e < nseg; e += nt) {
+            if (inS[e] == 0) continue;
+            int ex;
+            frexp(fabs(fix2d(inS[e], qf)), &ex);
+            emax = max(emax, ex);
+        }
+        if (emax != INT_MIN) atomicMax(&s_emax, emax);
+        __syncthreads();
+        if (s_emax == INT_MIN) return;  // no inflow at all
+    }
+    // offsets of this tile stay below P * max|in(e)| < 2^(emax + log2 P)
+    int qo = 0;
+    if constexpr (VALM == 1) {
+        int lp = 0;
+        while ((1 << lp) < P) ++lp;
+        qo = 62 - (s_emax + lp + 1);
+    }
+    for (int e = tid; e < nseg; e += nt) {
+        OV v;
+        if constexpr (VALM == 0) {
+            v = (OV)inS[e];
+        } else {
+            const int sh = qf - qo;  // from the graph scale to this tile's scale
+            const i128 si = (i128)inS[e];
+            v = (OV)(sh >= 0 ? (sh < 127 ? (si >> sh) : (si < 0 ? -1 : 0)) : (si << (-sh)));
+        }
+        inT[e] = v;
+        F[e] = v;
+    }
+    __syncthreads();
+
+    // ---- F over the join tree, leaves first (one warp; the rounds end when
+    // no segment became ready, at the latest after nseg rounds)
+    if (warp == 0) {
+        for (int round = 0; round <= nseg; ++round) {
+            bool any = false;
+            for (int e = lane; e < nseg; e += 32)
+                if (pend[e] == 0) {
+                    pend[e] = -2;  // ready: every join into e is summed
+                    any = true;
+                }
+            if (!__any_sync(0xffffffffu, any)) break;
+            __syncwarp();
+            for (int e = lane; e < nseg; e += 32) {
+                if (pend[e] != -2) continue;
+                pend[e] = -1;
+                const int p = par[e];
+                if (p >= 0) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&F[p]),
+                              (unsigned long long)F[e]);
+                    atomicSub(&pend[p], 1);
+                }
+            }
+            __syncwarp();
+        }
+        // group the joins by target: exclusive scan of the counts
+        int run = 0;
+        for (int b0 = 0; b0 < nseg; b0 += 32) {
+            const int e = b0 + lane;
+            const int cnt = e < nseg ? moff[e] : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (e < nseg) moff[e] = run + incl - cnt;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) moff[nseg] = run;
+    }
+    __syncthreads();
+    for (int e = tid; e < nseg; e += nt) mfill[e] = 0;
+    __syncthreads();
+    for (int e = tid; e < nseg; e += nt) {
+        const int p = par[e];
+        if (p >= 0) mlist[moff[p] + atomicAdd(&mfill[p], 1)] = (uint16_t)e;
+    }
+    __syncthreads();
+    // each target: its joins by position, then running sums of their F
+    for (int p = tid; p < nseg; p += nt) {
+        const int b = moff[p], n = moff[p + 1] - b;
+        for (int i = 1; i < n; ++i) {  // insertion sort (join lists are short)
+            const uint16_t x = mlist[b + i];
+            int j = i - 1;
+            while (j >= 0 && mpos[mlist[b + j]] > mpos[x]) {
+                mlist[b + j + 1] = mlist[b + j];
+                --j;
+            }
+            mlist[b + j + 1] = x;
+        }
+        OV run = 0;
+        for (int i = 0; i < n; ++i) {
+            run += F[mlist[b + i]];
+            pre[b + i] = run;
+        }
+    }
+    __syncthreads();
+
+    // ---- every forest cell: read-modify-write its output
+    int ovf = 0;
+    const double inv = ldexp(1.0, -qo);
+    for (int j = tid; j < nef; j += nt) {
+        const uint32_t cp = a.ef_cp[eb + j];
+        const int e = a.ef_seg[eb + j];
+        const int ci = (int)(cp >> 16), pos = (int)(cp & 0xFFFFu);
+        OV o = inT[e];
+        int lo = moff[e], hi = moff[e + 1];  // joins into e at positions <= pos
+        const int b = lo;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((int)mpos[mlist[mid]] <= pos) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo > b) o += pre[lo - 1];
+        if (!o) continue;
+        const int hr = ci / W2, r = hr - 1, c = ci - hr * W2 - 1;
+        const size_t oi = (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
+        if constexpr (VALM == 0) {
+            uint32_t *p = reinterpret_cast<uint32_t *>(ras.out[0]) + oi;
+            const unsigned long long s64 = (unsigned long long)*p + o;
+            if (s64 >> 32) ovf = 1;
+            *p = (uint32_t)s64;
+        } else {
+            float *p = reinterpret_cast<float *>(ras.out[0]) + oi;
+            *p = (float)((double)*p + (double)o * inv);
+        }
+    }
+    ovf = __syncthreads_or(ovf);
+    if (tid == 0 && ovf) status_report(a.st, FA_FLAG_OVERFLOW, 0, NO_INDEX);
 }
 
 // ---------------------------------------------------------------------------
@@ -978,6 +1268,13 @@ size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry
     w.dl1 = c.take<u128>(SV);
     w.J0 = c.take<uint32_t>(S);
     w.J1 = c.take<uint32_t>(S);
+    const size_t cells = T * (size_t)g.th * g.tw, inf = T * (size_t)(g.pmax + 8);
+    w.ef_hdr = c.take<uint32_t>(T * 4);
+    w.ef_cp = c.take<uint32_t>(cells);
+    w.ef_seg = c.take<uint16_t>(cells);
+    w.seg_merge = c.take<uint32_t>(S);
+    w.inf_src = c.take<uint32_t>(inf);
+    w.inf_seg = c.take<uint16_t>(inf);
     (void)dry;
     return c.used() + 256;
 }
@@ -1082,6 +1379,18 @@ static cudaError_t launch_walk_k(const Geom &g, const TileArgs &ta, const CUtens
     return cudaGetLastError();
 }
 
+static cudaError_t offsets_config(const Geom &g) {
+    static int configured = 0;
+    return set_smem(k_offsets<0>, offsets_smem_bytes(g.th, g.tw), configured);
+}
+
+static cudaError_t launch_offsets(const Geom &g, const TileArgs &ta, cudaStream_t s) {
+    cudaError_t e = offsets_config(g);
+    if (e != cudaSuccess) return e;
+    k_offsets<0><<<(unsigned)ta.T, 128, offsets_smem_bytes(g.th, g.tw), s>>>(ta);
+    return cudaGetLastError();
+}
+
 template <int MODE, int PASS>
 static cudaError_t launch_walk(const Geom &g, const TileArgs &ta, const uint8_t *codes,
                                int64_t pc, const uint8_t *mask, bool allow_tma, cudaStream_t s) {
@@ -1101,8 +1410,8 @@ cudaError_t prepare_forward(const Geom &g, int val_mode) {
     int per_sm = 1;
     cudaError_t e = val_mode ? walk_config<1, 1, LOAD_PLAIN>(g, per_sm)
                              : walk_config<0, 1, LOAD_PLAIN>(g, per_sm);
-    if (e == cudaSuccess)
-        e = val_mode ? walk_config<1, 2, LOAD_PLAIN>(g, per_sm) : walk_config<0, 2, LOAD_PLAIN>(g, per_sm);
+    if (e == cudaSuccess && val_mode) e = walk_config<1, 2, LOAD_PLAIN>(g, per_sm);
+    if (e == cudaSuccess && !val_mode) e = offsets_config(g);
     sm_count();
     return e;
 }
@@ -1130,6 +1439,12 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     ta.G = ws.x;
     ta.st = st;
     ta.maxw = ws.misc;
+    ta.ef_hdr = ws.ef_hdr;
+    ta.ef_cp = ws.ef_cp;
+    ta.ef_seg = ws.ef_seg;
+    ta.seg_merge = ws.seg_merge;
+    ta.inf_src = ws.inf_src;
+    ta.inf_seg = ws.inf_seg;
     ta.wait_ns = kWaitLimitNs;
 
     timing_mark(0, s);
@@ -1170,7 +1485,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     if (e != cudaSuccess) return e;
     timing_mark(2, s);
     e = val_mode ? launch_walk<1, 2>(g, ta, tma_codes, tma_pc, tma_mask, tma, s)
-                 : launch_walk<0, 2>(g, ta, tma_codes, tma_pc, tma_mask, tma, s);
+                 : launch_offsets(g, ta, s);
     timing_mark(3, s);
     timing_set_count(3);
     return e;

@@ -79,6 +79,15 @@ struct FwdWork {
     void *x;               // [T*pmax*nf] u128 forest values (G after resolve)
     void *dl0, *dl1;       // [T*pmax*nf] u128 pending scatter buffers
     uint32_t *J0, *J1;     // [T*pmax] jump pointers
+    // counts: the entry forest of every tile (the union of the in-tile paths
+    // downstream of its entry cells), recorded by pass 1 for pass 2
+    uint32_t *ef_hdr;      // [T*4] entry-forest cells, segments, inflow links, 0
+    uint32_t *ef_cp;       // [T*th*tw] cell word index << 16 | position along its segment
+    uint16_t *ef_seg;      // [T*th*tw] segment of the cell
+    uint32_t *seg_merge;   // [T*pmax] segment -> (segment << 16 | position on it)
+                           //   where it joins, 0xFFFFFFFF if it ends at an exit or sink
+    uint32_t *inf_src;     // [T*(pmax+8)] inflow link: slot id of the exit outside
+    uint16_t *inf_seg;     // [T*(pmax+8)] inflow link: segment it feeds
     int kmax;              // number of jump rounds
 };
 
