@@ -807,7 +807,35 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
         } else if constexpr (PASS == 1) {
             // Algorithm 2 for the entry cells: the exit each one's path
             // reaches (the last valid cell of the tile on it, if on the
-            // perimeter and an exit); one entry per lane at a time            if (tid == 0) a.nexit[t] = (uint32_t)nexits;
+            // perimeter and an exit); one entry per lane at a time
+            for (int e = tid; e < s_nent; e += nt) {
+                const int slot = pent[e];
+                int r, c;
+                cell_of(slot, h, w, r, c);
+                int cur = (r + 1) * W2 + c + 1, steps = 0;
+                W wc = word[cur];
+                for (;;) {
+                    const uint32_t sc = (uint32_t)(wc >> SUCC) & SUCC_NONE;
+                    if (sc == SUCC_NONE) break;
+                    const W wn = word[sc];
+                    if ((wn >> CNT) >= SENT_CNT) break;  // leaves the tile or the data
+                    if (++steps > h * w) {              // a cycle: the path never ends
+                        cur = -1;
+                        break;
+                    }
+                    cur = (int)sc;
+                    wc = wn;
+                }
+                uint16_t lk = LINK_TERM;
+                if (cur >= 0) {
+                    const int hr = (int)__umulhi((uint32_t)cur, rdiv), rr = hr - 1, cc = cur - hr * W2 - 1;
+                    if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
+                }
+                a.link[tbase + slot] = lk;
+            }
+        }
+        if constexpr (PASS == 1) {
+            if (tid == 0) a.nexit[t] = (uint32_t)nexits;
             __syncthreads();
             // cells still waiting for an inflow lie on a cycle inside the
             // tile (a cycle cell misses exactly its predecessor on the
