@@ -473,10 +473,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             mbar_fence_init();
         }
     }
-    for (int wi = tid; wi < NWD; wi += nt) {
-        word[wi] = 0;
-        if (RETAIN) tag[wi] = 0;
-    }
+    for (int wi = tid; wi < NWD; wi += nt) word[wi] = 0;
     __syncthreads();
     auto issue = [&](int64_t tn) {  // one thread: stage tile tn's codes (TMA: one raster only)
         const int tyn = (int)(tn / a.one.tiles_x), txn = (int)(tn - (int64_t)tyn * a.one.tiles_x);
@@ -762,6 +759,9 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             // Each walk's claimed run is a segment: the cells of segment e at
             // positions 0, 1, ... in path order.
             const size_t efb = (size_t)t * th * tw;
+            // the claim tags share memory with the walks' queues: clear them
+            for (int wi = tid; wi < NWD; wi += nt) tag[wi] = 0;
+            __syncthreads();
             for (int e = tid; e < s_nent; e += nt) {
                 const int slot = pent[e];
                 int r, c;
@@ -844,7 +844,6 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             for (int wi = tid; wi < NWD; wi += nt) {
                 const W wv = word[wi];
                 word[wi] = 0;
-                if (RETAIN) tag[wi] = 0;
                 const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
                 if ((wv >> CNT) == 1) {
                     ++ncyc;
@@ -972,6 +971,10 @@ __global__ void __launch_bounds__(128) k_offsets(const __grid_constant__ TileArg
             continue;
         }
         const int p = (int)(m >> 16);
+        if (p >= nseg) {  // never: a join names a segment of this tile
+            par[e] = -1;
+            continue;
+        }
         par[e] = p;
         mpos[e] = (uint16_t)(m & 0xFFFFu);
         atomicAdd(&pend[p], 1);
