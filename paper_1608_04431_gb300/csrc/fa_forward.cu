@@ -798,7 +798,11 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 const int slot = pent[e];
                 if (prank[slot] != LINK_TERM) continue;  // an exit links to itself
                 int x = e;
-                for (int hop = 0; hop < ne && segjoin[x] != NO_JOIN; ++hop) x = (int)(segjoin[x] >> 16);
+                for (int hop = 0; hop < ne && segjoin[x] != NO_JOIN; ++hop) {
+                    const int y = (int)(segjoin[x] >> 16);
+                    if ((unsigned)y >= (unsigned)ne) break;  // never: joins name walks of this tile
+                    x = y;
+                }
                 a.link[tbase + slot] = segjoin[x] == NO_JOIN ? segend[x] : LINK_TERM;
             }
             if (tid == 0)
