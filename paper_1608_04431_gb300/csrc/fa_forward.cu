@@ -121,38 +121,48 @@ __host__ __device__ inline size_t packed_buf_bytes(int th, int tw) {
 enum { LOAD_PLAIN = 0, LOAD_TMA = 1, LOAD_TMA_PACKED = 2 };
 
 // ---------------------------------------------------------------------------
-// Cell words.  The cells of a tile are numbered ci = r * tw + c (tile row r,
-// tile column c, nominal tile width tw), at most MAX_TILE_CELLS of them, so a
-// cell index fits 14 bits and SUCC_NONE (no downstream cell inside the tile:
-// NoFlow, or flow that leaves the tile) is never one.  Pending-inflow counts
-// sit in the top four bits.  A cell that is not a valid cell of the tile
-// (NoData, invalid, outside a ragged tile) holds the count SENT_CNT = 15: a
-// valid cell whose code points into a NoData cell of the tile still names it
-// as its successor, and the at most eight walks that reach it each take one
-// off the count, so it never reads as complete (0) or as the last inflow (1).
-// After the walks a valid cell's count is 0, or 1 if it lies on a cycle (its
-// predecessor on the cycle never completes), and any other cell's is >= 7.
-// Each cell's word is built by its owner from the codes alone (the inflows
-// are counted by looking at the neighbours' codes), so no shared-memory
-// atomics are needed before the walks.
+// Cell words.  The words of a tile and of the one-cell ring around it are
+// numbered wi = (r + 1) * W2 + (c + 1), W2 = tw + 2 (tile row r, tile column
+// c; the ring at r = -1, r = th, c = -1, c = tw), at most 2^14 - 1 of them,
+// so a word index fits 14 bits and SUCC_NONE is never one.  Pending-inflow
+// counts sit in the top four bits.  Every word that is not a valid cell of
+// the tile (NoData, off the raster, outside a ragged tile, or the ring) holds
+// the count SENT_CNT: at most eight cells add one to it and a walk reaching
+// it takes one off again, so it never reads as complete (0) or as the last
+// inflow (1) and its sums are never used.  A cell's successor is simply the
+// word its code points at, so the one-pass init needs neither the target's
+// code nor bounds; a walk that reaches a SENT_CNT word stops there.
 // ---------------------------------------------------------------------------
 constexpr int MAX_TILE_CELLS = 8192;
+constexpr int MAX_TILE_WORDS = 16383;
 constexpr uint32_t SUCC_NONE = 0x3FFFu;
-constexpr uint32_t SENT_CNT = 15;
+constexpr uint32_t SENT_CNT = 7;
 constexpr uint32_t NO_JOIN = 0xFFFFFFFFu;  // an entry-forest segment that joins no other
 
-// counts: (pending << 28) | (successor << 14) | partial sum (a tile sum is at
-// most 8192 < 2^14).  Sums that walks bring to a NoData cell may carry into
-// its successor bits, never into its count.
-constexpr int CW_SUCC = 14, CW_CNT = 28;
-constexpr uint32_t CW_ACC = (1u << 14) - 1, CW_ONE = 1u << 28,
-                   CW_SENT = (SENT_CNT << 28) | (SUCC_NONE << 14);
-// float weights: (pending << 28) | GW_VALID | (mask of the neighbours
-// draining into the cell << GW_PM) | successor; the sums live in a separate
-// array of compensated float pairs.
+__host__ __device__ inline int tile_words(int th, int tw) { return (th + 2) * (tw + 2); }
+
+// counts: (pending << CNT) | (successor << SUCC) | partial sum; 32-bit words
+// in pass 1 (a tile sum is at most 8192 < 2^14), 64-bit words in pass 2,
+// where the flow entering from other tiles (up to 2^46 cells) is added.
+// Sums that walks bring to a SENT_CNT word may carry into its successor bits,
+// never into its count.
+template <class W> struct CountWord;
+template <> struct CountWord<uint32_t> {
+    static constexpr int SUCC = 14, CNT = 28;
+    static constexpr uint32_t ACC = (1u << 14) - 1, ONE = 1u << 28, SENT = SENT_CNT << 28;
+};
+template <> struct CountWord<unsigned long long> {
+    static constexpr int SUCC = 46, CNT = 60;
+    static constexpr unsigned long long ACC = (1ull << 46) - 1, ONE = 1ull << 60,
+                                        SENT = (unsigned long long)SENT_CNT << 60;
+};
+// float weights: (pending << GW_CNT) | GW_VALID for a valid cell of the tile
+// | (mask of the neighbours draining into the cell << GW_PM) | successor; the
+// sums live in a separate array of compensated float pairs.  (A valid cell
+// may have up to eight pending inflows, so the flag, not the count, tells it
+// from a SENT_CNT word before the walks.)
 constexpr int GW_PM = 14, GW_CNT = 28;
-constexpr uint32_t GW_ONE = 1u << GW_CNT, GW_SENT = (SENT_CNT << GW_CNT) | SUCC_NONE,
-                   GW_VALID = 1u << 27;
+constexpr uint32_t GW_ONE = 1u << GW_CNT, GW_SENT = SENT_CNT << GW_CNT, GW_VALID = 1u << 27;
 
 // Threads of a tile block: one per 32 cells, at least a warp, at most 256.
 __host__ __device__ inline int walk_threads(int th, int tw) {
@@ -163,17 +173,16 @@ __host__ __device__ inline int walk_threads(int th, int tw) {
 
 // Shared memory of k_walk<MODE, PASS, LOAD> for a tile shape.
 __host__ __device__ inline size_t walk_smem_bytes(int th, int tw, int mode, int pass, int load) {
-    const size_t n = (size_t)th * tw, pm = (size_t)(2 * th + 2 * tw);
+    const size_t nwd = (size_t)tile_words(th, tw), pm = (size_t)(2 * th + 2 * tw);
     size_t b = 128;  // alignment slack of the dynamic window
     b += code_buf_bytes(th, tw) + (load == LOAD_TMA_PACKED ? packed_buf_bytes(th, tw) : 0);
-    b += n * 4;                                     // cell words
+    b += nwd * ((mode == 0 && pass == 2) ? 8 : 4);  // cell words
     b = (b + 15) & ~size_t(15);
-    if (mode == 1) b += n * 8;                      // float pair sums
-    // queued walk starts (counts, pass 1: then the entry walks' claim tags),
-    // room for four per group of four cells
-    b += (((n + 3) / 4) * 4) * ((mode == 0 && pass == 1) ? 4 : 2);
+    if (mode == 1) b += nwd * 8;                     // float pair sums
+    // queued walk starts (counts, pass 1: then the entry walks' claim tags)
+    b += nwd * ((mode == 0 && pass == 1) ? 4 : 2);
     b = (b + 15) & ~size_t(15);
-    b += pm * 4 + pm * 2 + pm * 2 + pm;             // exit targets, exit ranks, entry list, inflow masks
+    b += pm * 4 + pm * 2 + pm * 2 + pm;              // exit targets, exit ranks, entry list, inflow masks
     if (mode == 0 && pass == 1) b = ((b + 3) & ~size_t(3)) + pm * 4 + pm * 2;  // segment joins and ends
     return (b + 15) & ~size_t(15);
 }
@@ -190,6 +199,7 @@ __host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
 
 __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
     if (th < 1 || tw < 1 || (int64_t)th * tw > MAX_TILE_CELLS) return false;
+    if ((int64_t)(th + 2) * (tw + 2) > MAX_TILE_WORDS) return false;
     for (int pass = 1; pass <= 2; ++pass)
         if (walk_smem_bytes(th, tw, valm, pass, LOAD_TMA_PACKED) > 227 * 1024) return false;
     return offsets_smem_bytes(th, tw) <= 227 * 1024;
@@ -330,27 +340,16 @@ __device__ __forceinline__ uint32_t outside_slot(const RasterDesc &ras, const Ti
 // The walks of one tile (Algorithm 1).  Warp w holds the queue q[0 .. qn) of
 // the cells with no inflow inside the tile from its share of the tile; idle
 // lanes take the next queued cells in lane order and walk them downstream.
-// A cell's sum is final when its walk starts (a queued cell) or when the walk
-// bringing its last inflow arrives; if `out` is set it is written there
-// (out + r * po + c for cell r * tw + c).  Returns the lane's number of
-// completed cells.
 // ---------------------------------------------------------------------------
-template <int MODE>
-__device__ __forceinline__ int walk_tile(uint32_t *word, FF *val, const uint16_t *q, int qn,
-                                         const int *nb, uint32_t *out, int64_t po, int tw,
-                                         uint32_t rdiv) {
+template <int MODE, class W>
+__device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, int qn,
+                                          const int *nb) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     int pos = 0;              // next queue entry (warp-uniform)
-    int done = 0;
     bool act = false;
-    uint32_t cur = 0;         // the lane's cell (its sum is final)
-    uint32_t sc = SUCC_NONE;  // its successor
-    uint32_t acc = 0;         // counts: its sum
-    auto emit = [&](uint32_t ci, uint32_t v) {
-        const int r = tw > 1 ? (int)__umulhi(ci, rdiv) : (int)ci;
-        out[(int64_t)r * po + ((int)ci - r * tw)] = v;
-    };
+    uint32_t sc = SUCC_NONE;  // successor of the lane's cell
+    W acc = 0;                // counts: the lane's cell's sum
     for (;;) {
         const uint32_t idle = __ballot_sync(0xffffffffu, !act);
         if (pos >= qn) {
@@ -358,112 +357,96 @@ __device__ __forceinline__ int walk_tile(uint32_t *word, FF *val, const uint16_t
         } else if (idle) {
             const int my = pos + __popc(idle & lt);
             if (!act && my < qn) {
-                cur = q[my];
-                const uint32_t wv = word[cur];
+                const W wv = word[q[my]];
                 if constexpr (MODE == 0) {
-                    acc = wv & CW_ACC;
-                    sc = (wv >> CW_SUCC) & SUCC_NONE;
-                    if (out) emit(cur, acc);
+                    acc = wv & CountWord<W>::ACC;
+                    sc = (uint32_t)(wv >> CountWord<W>::SUCC) & SUCC_NONE;
                 } else {
-                    sc = wv & SUCC_NONE;
-                    if (out) emit(cur, __float_as_uint(ff_round(val[cur])));
+                    sc = (uint32_t)wv & SUCC_NONE;
                 }
-                ++done;
                 act = true;
             }
             pos += __popc(idle);
         }
         if (!act) continue;
         if (sc == SUCC_NONE) {
-            act = false;  // NoFlow, or the flow leaves the tile here
+            act = false;  // NoFlow: the path ends here
         } else if constexpr (MODE == 0) {
-            const uint32_t old = atomicAdd(&word[sc], acc - CW_ONE);
-            act = (old >> CW_CNT) == 1;  // the last inflow: continue from sc
-            if (act) {
-                acc += old & CW_ACC;
-                cur = sc;
-                sc = (old >> CW_SUCC) & SUCC_NONE;
-                if (out) emit(cur, acc);
-                ++done;
-            }
+            const W old = atomicAdd(&word[sc], acc - CountWord<W>::ONE);
+            act = (old >> CountWord<W>::CNT) == 1;  // the last inflow: continue from sc
+            acc += old & CountWord<W>::ACC;
+            sc = (uint32_t)(old >> CountWord<W>::SUCC) & SUCC_NONE;
         } else {
-            const uint32_t old = atom_add_acq_rel(&word[sc], 0u - GW_ONE);
+            const uint32_t old = atom_add_acq_rel(reinterpret_cast<uint32_t *>(&word[sc]), 0u - GW_ONE);
             act = (old >> GW_CNT) == 1;
             if (act) {  // complete: own weight plus inflows in a fixed order
-                cur = sc;
-                FF v = val[cur];
+                const int t = (int)sc;
+                FF v = val[t];
                 uint32_t pm = (old >> GW_PM) & 0xFFu;
                 while (pm) {
                     const int j = __ffs(pm) - 1;
                     pm &= pm - 1u;
-                    v = ff_add(v, val[(int)cur + nb[j]]);
+                    v = ff_add(v, val[t + nb[j]]);
                 }
-                val[cur] = v;
+                val[t] = v;
                 sc = old & SUCC_NONE;
-                if (out) emit(cur, __float_as_uint(ff_round(v)));
-                ++done;
             }
         }
     }
-    return done;
 }
 
 // ---------------------------------------------------------------------------
 // Tile pass.  PASS 1: Algorithm 1 per field, then A_loc at the exits, the
 // exit targets and ranks, and the exit each entry cell's path reaches
-// (Algorithm 2); for counts (RETAIN) A_loc also goes to the output raster and
-// the walks from the entry cells record the tile's entry forest for pass 2.
-// PASS 2 (float weights only; counts finish in k_offsets): Algorithm 1 per
-// field with the resolved inflow added at the entry cells (Algorithm 3),
-// writing the output.  MODE 0: unit weights, integer counts; MODE 1: float
-// weights (nf fields).
+// (Algorithm 2).  PASS 2: Algorithm 1 per field with the resolved inflow
+// added at the entry cells (Algorithm 3), writing the output.  MODE 0: unit
+// weights, integer counts; MODE 1: float weights (nf fields).
 // Persistent CTAs: each block takes tiles t = blockIdx.x, + gridDim.x, ...
 // With TMA the codes of the next tile are staged into shared memory while the
-// current one is walked (they are no longer read by then).
+// current one is walked (they are no longer read by then).  The words are
+// zero when a tile starts (cleared by the previous tile's last pass), so one
+// pass sets every word: each valid cell adds its own (successor, weight) and
+// one pending inflow to its successor's word, every other word its SENT_CNT.
 // ---------------------------------------------------------------------------
 template <int MODE, int PASS, int LOAD>
 __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_constant__ TileArgs A,
                                                                 const __grid_constant__ CUtensorMap tmap) {
+    typedef typename std::conditional<MODE == 0 && PASS == 2, unsigned long long, uint32_t>::type W;
     const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_flags, s_nent, s_nef, s_ninf, s_valid, s_done;
+    __shared__ int s_flags, s_nent, s_nef, s_ninf;
     __shared__ int s_nb[8];
     __shared__ __align__(8) uint64_t s_bar;
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
     const int th = a.th, tw = a.tw;
     const int S = tile_stride(tw);
-    const int n = th * tw;
-    // groups of four cells of a row when the width allows, else single cells
-    const int cpg = (tw & 3) == 0 ? 4 : 1, gpr = tw / cpg, G = th * gpr;
-    // ci / tw = umulhi(ci, rdiv) and g / gpr = umulhi(g, gdiv), exact for
-    // indices below 2^13 (the rounding error ci / 2^32 stays below 1 / tw)
-    const uint32_t rdiv = tw > 1 ? 0xFFFFFFFFu / (uint32_t)tw + 1u : 0u;
-    const uint32_t gdiv = gpr > 1 ? 0xFFFFFFFFu / (uint32_t)gpr + 1u : 0u;
+    const int W2 = tw + 2, NWD = tile_words(th, tw);
+    // wi / W2 as umulhi(wi, rdiv), exact for wi < 2^14 and 3 <= W2 <= 8194
+    // (the rounding error wi / 2^32 stays below 1 / W2)
+    const uint32_t rdiv = 0xFFFFFFFFu / (uint32_t)W2 + 1u;
     const int64_t T = a.T;
     const int nf = a.nf;
-    constexpr bool RETAIN = MODE == 0 && PASS == 1;      // counts: A_loc stays in the output
-    constexpr bool OUTPUT = RETAIN || PASS == 2;         // the walks write the output
-    constexpr int CNT = MODE == 0 ? CW_CNT : GW_CNT;
-    constexpr int SUCC = MODE == 0 ? CW_SUCC : 0;
-    constexpr uint32_t SENT = MODE == 0 ? CW_SENT : GW_SENT;
+    const W SENT = MODE == 0 ? (W)CountWord<W>::SENT : (W)GW_SENT;
+    constexpr int CNT = MODE == 0 ? CountWord<W>::CNT : GW_CNT;
+    constexpr int SUCC = MODE == 0 ? CountWord<W>::SUCC : 0;
 
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem) + 127) &
                                                 ~uintptr_t(127));
     uint8_t *cbuf = base;                                  // byte codes of the tile and its halo
     uint8_t *stage = base + code_buf_bytes(th, tw);        // packed: the TMA stage
     uint8_t *p = stage + (LOAD == LOAD_TMA_PACKED ? packed_buf_bytes(th, tw) : 0);
-    uint32_t *word = reinterpret_cast<uint32_t *>(p);
-    p += (size_t)n * 4;
+    W *word = reinterpret_cast<W *>(p);
+    p += (size_t)NWD * sizeof(W);
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     FF *val = reinterpret_cast<FF *>(p);
-    if (MODE == 1) p += (size_t)n * sizeof(FF);
+    if (MODE == 1) p += (size_t)NWD * sizeof(FF);
+    constexpr bool RETAIN = MODE == 0 && PASS == 1;     // counts: A_loc stays in the output
     uint16_t *queue = reinterpret_cast<uint16_t *>(p);     // walk starts
     uint32_t *tag = reinterpret_cast<uint32_t *>(p);       // RETAIN, after the walks: claim tags
-    p += (size_t)((n + 3) & ~3) * (RETAIN ? 4 : 2);
+    p += (size_t)NWD * (RETAIN ? 4 : 2);
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     uint32_t *pexit = reinterpret_cast<uint32_t *>(p);     // slot -> global slot id of its exit target
     p += (size_t)a.pmax * 4;
@@ -481,11 +464,8 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     int nbad = 0, ncyc = 0, nonfinite = 0, ovf = 0;
     long long fbad = NO_INDEX;
     uint32_t gmaxw = 0;
-    // this warp's share of the groups and of the queue
-    const int gw0 = (int)((int64_t)G * warp / nw), gw1 = (int)((int64_t)G * (warp + 1) / nw);
-    uint16_t *wq = queue + gw0 * cpg;
 
-    if (tid < 8) s_nb[tid] = dir_dr(tid + 1) * tw + dir_dc(tid + 1);
+    if (tid < 8) s_nb[tid] = dir_dr(tid + 1) * W2 + dir_dc(tid + 1);
     if (tid == 0) {
         s_flags = 0;
         if (LOAD != LOAD_PLAIN) {
@@ -493,6 +473,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             mbar_fence_init();
         }
     }
+    for (int wi = tid; wi < NWD; wi += nt) word[wi] = 0;
     __syncthreads();
     auto issue = [&](int64_t tn) {  // one thread: stage tile tn's codes (TMA: one raster only)
         const int tyn = (int)(tn / a.one.tiles_x), txn = (int)(tn - (int64_t)tyn * a.one.tiles_x);
@@ -510,8 +491,8 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     bool timed_out = false;
     for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++it) {
         const RasterDesc &ras = raster_of(a, t);
-        const int lt_ = (int)(t - ras.tile_base);
-        const int ty = lt_ / ras.tiles_x, tx = lt_ - ty * ras.tiles_x;
+        const int lt = (int)(t - ras.tile_base);
+        const int ty = lt / ras.tiles_x, tx = lt - ty * ras.tiles_x;
         const int64_t R0 = (int64_t)ty * th, C0 = (int64_t)tx * tw;
         const int h = (int)min((int64_t)th, ras.rows - R0);
         const int w = (int)min((int64_t)tw, ras.cols - C0);
@@ -526,8 +507,6 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             s_nent = 0;
             s_nef = 0;
             s_ninf = 0;
-            s_valid = 0;
-            s_done = 0;
         }
 
         // [phase] codes of the tile and its one-cell halo ring
@@ -561,171 +540,93 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             __syncthreads();
         }
 
-        // [phase] init, one pass, no atomics: each cell's word from the codes
-        // alone.  A valid cell counts the neighbours inside the tile whose
-        // code points at it (its pending inflows; for float weights also
-        // which ones), names its successor (the tile cell its code points at,
-        // SUCC_NONE if that is outside the tile), and notes the neighbours
-        // outside the tile that drain into it (the inflow of a perimeter
-        // cell).  Cells with no pending inflow go to the warp's queue.
-        // Groups of four cells of a row are done with byte-wise compares.
-        int qn = 0, nval = 0;
-        for (int g0 = gw0; g0 < gw1; g0 += 32) {
-            const int g = g0 + lane;
-            uint32_t leafm = 0;  // cells of the group that start a walk (bit i)
-            int ci0 = 0;
-            if (g < gw1) {
-                const int r = gpr > 1 ? (int)__umulhi((uint32_t)g, gdiv) : g;
-                const int c = (g - r * gpr) * cpg;
-                ci0 = r * tw + c;
-                // a valid cell of the group: its word, successor, exit, inflow
-                auto cell = [&](int i, uint32_t k, uint32_t cnt, uint32_t pm, uint32_t rm) -> uint32_t {
-                    uint32_t sc = SUCC_NONE;
-                    if (k <= 8u) {
-                        const int dr = dir_dr((int)k), dc = dir_dc((int)k);
-                        const int tr = r + dr, tc = c + i + dc;
-                        if ((unsigned)tr < (unsigned)h && (unsigned)tc < (unsigned)w) {
-                            sc = (uint32_t)(ci0 + i + dr * tw + dc);
-                        } else if (PASS == 1 && vcode(cbuf[(tr + 1) * S + X0 + tc])) {
-                            // an exit: its flow enters the neighbouring tile
-                            pexit[slot_of(r, c + i, h, w)] = outside_slot(ras, a, ty, tx, R0, C0, h, w, tr, tc);
-                        }
-                    }
-                    if (cnt == 0) leafm |= 1u << i;
-                    if (rm) {  // an entry cell: outside neighbours drain into it
-                        const int slot = slot_of(r, c + i, h, w);
-                        pinf[slot] = (uint8_t)rm;
-                        if constexpr (PASS == 1) {
-                            const int e = atomicAdd(&s_nent, 1);
-                            pent[e] = (uint16_t)slot;
-                            if constexpr (RETAIN) {
-                                // inflow links: the exit outside (its slot id)
-                                // and the segment (entry) it feeds
-                                const int j0 = atomicAdd(&s_ninf, __popc(rm));
-                                const size_t infb = (size_t)t * (a.pmax + 8);
-                                for (int jj = 0; rm; ++jj) {
-                                    const int j = __ffs(rm) - 1;
-                                    rm &= rm - 1u;
-                                    a.inf_src[infb + j0 + jj] = outside_slot(
-                                        ras, a, ty, tx, R0, C0, h, w, r + dir_dr(j + 1), c + i + dir_dc(j + 1));
-                                    a.inf_seg[infb + j0 + jj] = (uint16_t)e;
-                                }
-                            }
-                        }
-                    }
-                    return MODE == 0 ? (cnt << CW_CNT) | (sc << CW_SUCC) | 1u
-                                     : (cnt << GW_CNT) | GW_VALID | (pm << GW_PM) | sc;
-                };
-                auto nodata = [&](int i) -> uint32_t {  // in the tile but not a valid cell
-                    if constexpr (OUTPUT) {
-                        for (int f = 0; f < nf; ++f)
-                            reinterpret_cast<uint32_t *>(ras.out[f])[(size_t)(R0 + r) * ras.po + C0 + c + i] = 0u;
-                    }
-                    return SENT;
-                };
-                if (cpg == 4) {
-                    uint32_t wv[4] = {SENT, SENT, SENT, SENT};
-                    if (r < h) {
-                        const int xb = (r + 1) * S + X0 + c;
-                        const uint32_t own = *reinterpret_cast<const uint32_t *>(cbuf + xb);
-                        const uint32_t inw = c + 4 <= w ? 0xFFFFFFFFu : (c >= w ? 0u : ((1u << (8 * (w - c))) - 1u));
-                        const uint32_t vb = __vcmpgtu4(own, 0u) & __vcmpltu4(own, 0x0A0A0A0Au) & inw;
-                        if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
-                            const uint32_t bad = __vcmpgtu4(own, 0x09090909u) & inw;
-                            if (bad) {
-                                nbad += __popc(bad) >> 3;
-                                fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c + ((__ffs(bad) - 1) >> 3))));
-                            }
-                        }
-                        // the codes of the rows above, at and below, columns c-4 .. c+7
-                        uint32_t Lw[3], Mw[3], Rw[3];
-#pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            const uint8_t *rb = cbuf + xb + (d - 1) * S;
-                            Lw[d] = *reinterpret_cast<const uint32_t *>(rb - 4);
-                            Mw[d] = *reinterpret_cast<const uint32_t *>(rb);
-                            Rw[d] = *reinterpret_cast<const uint32_t *>(rb + 4);
-                        }
-                        const uint32_t rowup = r > 0 ? ~0u : 0u, rowdn = r < h - 1 ? ~0u : 0u;
-                        const uint32_t left = c > 0 ? ~0u : 0xFFFFFF00u;
-                        const uint32_t right = (inw >> 8) | (c + 4 < w ? 0xFF000000u : 0u);
-                        uint32_t cnt4 = 0, pm4 = 0, ring4 = 0;
-#pragma unroll
-                        for (int k = 1; k <= 8; ++k) {
-                            const int dr = dir_dr(k), dc = dir_dc(k), d = dr + 1;
-                            // byte i: the code of cell i's neighbour in direction k
-                            const uint32_t nbw = dc == 0 ? Mw[d]
-                                                 : (dc < 0 ? __funnelshift_r(Lw[d], Mw[d], 24)
-                                                           : __funnelshift_r(Mw[d], Rw[d], 8));
-                            const uint32_t m = __vcmpeq4(nbw, (uint32_t)dir_rev(k) * 0x01010101u) & vb & 0x01010101u;
-                            const uint32_t ink = (dr < 0 ? rowup : (dr > 0 ? rowdn : ~0u)) &
-                                                 (dc < 0 ? left : (dc > 0 ? right : ~0u));
-                            cnt4 += m & ink;
-                            if (MODE == 1) pm4 |= (m & ink) << (k - 1);
-                            ring4 |= (m & ~ink) << (k - 1);
-                        }
-                        nval += __popc(vb) >> 3;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            if (!((inw >> (8 * i)) & 1u)) continue;
-                            if (!((vb >> (8 * i)) & 1u)) {
-                                wv[i] = nodata(i);
-                                continue;
-                            }
-                            wv[i] = cell(i, (own >> (8 * i)) & 0xFFu, (cnt4 >> (8 * i)) & 0xFFu,
-                                         (pm4 >> (8 * i)) & 0xFFu, (ring4 >> (8 * i)) & 0xFFu);
-                        }
-                    }
-                    *reinterpret_cast<uint4 *>(word + ci0) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-                } else {
-                    uint32_t wv = SENT;
-                    if (r < h && c < w) {
-                        const int xi = (r + 1) * S + X0 + c;
-                        const uint32_t k = cbuf[xi];
-                        if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
-                            if (k > 9u) {
-                                ++nbad;
-                                fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
-                            }
-                        }
-                        if (vcode(k)) {
-                            uint32_t cnt = 0, pm = 0, rm = 0;
-#pragma unroll
-                            for (int kk = 1; kk <= 8; ++kk) {
-                                const int dr = dir_dr(kk), dc = dir_dc(kk);
-                                if ((int)cbuf[xi + dr * S + dc] != dir_rev(kk)) continue;
-                                if ((unsigned)(r + dr) < (unsigned)h && (unsigned)(c + dc) < (unsigned)w) {
-                                    ++cnt;
-                                    pm |= 1u << (kk - 1);
-                                } else {
-                                    rm |= 1u << (kk - 1);
-                                }
-                            }
-                            ++nval;
-                            wv = cell(0, k, cnt, MODE == 1 ? pm : 0u, rm);
-                        } else {
-                            wv = nodata(0);
-                        }
-                    }
-                    word[ci0] = wv;
+        // [phase] init, one pass over every word (tile and ring): a valid
+        // cell adds its own successor and unit weight to its word and one
+        // pending inflow (with its direction bit for float weights) to the
+        // word its code points at; any other word adds its SENT_CNT
+        for (int wi = tid; wi < NWD; wi += nt) {
+            const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
+            const bool tile = (unsigned)r < (unsigned)h && (unsigned)c < (unsigned)w;
+            const uint32_t k = tile ? cbuf[hr * S + X0 + c] : 0u;
+            if constexpr (LOAD != LOAD_PLAIN && PASS == 1) {  // raw staged codes
+                if (tile && k > 9u) {
+                    ++nbad;
+                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
                 }
             }
-            // queue the group's cells that start a walk (cpg is the same for
-            // every lane)
-            for (int i = 0; i < cpg; ++i) {
-                const bool lf = (leafm >> i) & 1u;
-                const uint32_t b = __ballot_sync(0xffffffffu, lf);
-                if (lf) wq[qn + __popc(b & lt)] = (uint16_t)(ci0 + i);
-                qn += __popc(b);
+            if (!vcode(k)) {
+                atomicAdd(&word[wi], SENT);
+                continue;
+            }
+            uint32_t sc = SUCC_NONE;
+            if (k <= 8u) {
+                sc = (uint32_t)(wi + dir_dr((int)k) * W2 + dir_dc((int)k));
+                if constexpr (MODE == 0) atomicAdd(&word[sc], CountWord<W>::ONE);
+                else atomicAdd(&word[sc], GW_ONE | (1u << (GW_PM + dir_rev((int)k) - 1)));
+            }
+            if constexpr (MODE == 0) atomicAdd(&word[wi], ((W)sc << SUCC) | (W)1);
+            else atomicAdd(&word[wi], sc | GW_VALID);
+        }
+        // the perimeter: exits (flow into a valid cell of another tile) and
+        // the outside neighbours draining into each perimeter cell
+        for (int s = tid; s < P; s += nt) {
+            int r, c;
+            cell_of(s, h, w, r, c);
+            const int k = cbuf[(r + 1) * S + X0 + c];
+            if (!vcode(k)) continue;
+            if (PASS == 1 && k <= 8) {
+                const int tr = r + dir_dr(k), tc = c + dir_dc(k);
+                if (((unsigned)tr >= (unsigned)h || (unsigned)tc >= (unsigned)w) &&
+                    vcode(cbuf[(tr + 1) * S + X0 + tc]))
+                    pexit[s] = outside_slot(ras, a, ty, tx, R0, C0, h, w, tr, tc);
+            }
+            uint32_t m = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int nr = r + dir_dr(j + 1), nc = c + dir_dc(j + 1);
+                if ((unsigned)nr < (unsigned)h && (unsigned)nc < (unsigned)w) continue;
+                const int kh = cbuf[(nr + 1) * S + X0 + nc];
+                if (kh >= 1 && kh <= 8 && nr + dir_dr(kh) == r && nc + dir_dc(kh) == c) m |= 1u << j;
+            }
+            pinf[s] = (uint8_t)m;
+            if (PASS == 1 && m) {
+                const int e = atomicAdd(&s_nent, 1);
+                pent[e] = (uint16_t)s;
+                if constexpr (RETAIN) {
+                    // inflow links: the exit outside (its slot id) and the
+                    // segment (entry) it feeds
+                    const int j0 = atomicAdd(&s_ninf, __popc(m));
+                    const size_t infb = (size_t)t * (a.pmax + 8);
+                    for (int jj = 0; m; ++jj) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1u;
+                        a.inf_src[infb + j0 + jj] =
+                            outside_slot(ras, a, ty, tx, R0, C0, h, w, r + dir_dr(j + 1), c + dir_dc(j + 1));
+                        a.inf_seg[infb + j0 + jj] = (uint16_t)e;
+                    }
+                }
             }
         }
-        nval = __reduce_add_sync(0xffffffffu, nval);
-        if (lane == 0 && nval) atomicAdd(&s_valid, nval);
         if constexpr (LOAD == LOAD_TMA) fence_proxy_async();  // the code buffer is refilled by TMA
         __syncthreads();
         if constexpr (LOAD == LOAD_TMA) {
             if (tid == 0 && t + gridDim.x < T) issue(t + gridDim.x);
         }
+
+        // the cells with no inflow inside the tile start the walks: warp w
+        // queues those of its share of the words (32-word chunks c0 .. c1)
+        const int nch = (NWD + 31) >> 5;
+        const int c0 = (int)((int64_t)nch * warp / nw), c1 = (int)((int64_t)nch * (warp + 1) / nw);
+        uint16_t *wq = queue + c0 * 32;
+        int qn = 0;
+        for (int ch = c0; ch < c1; ++ch) {
+            const int wi = ch * 32 + lane;
+            const bool leaf = wi < NWD && (word[wi] >> CNT) == 0;
+            const uint32_t b = __ballot_sync(0xffffffffu, leaf);
+            if (leaf) wq[qn + __popc(b & ((1u << lane) - 1u))] = (uint16_t)wi;
+            qn += __popc(b);
+        }
+        __syncwarp();
 
         // exit ranks in slot order (pass 1)
         int nexits = 0;
@@ -752,38 +653,42 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
         for (int f = 0; f < nf; ++f) {
             if constexpr (MODE == 1) {
                 const float *wp = ras.w[f];
-                for (int ci = tid; ci < n; ci += nt) {
-                    const uint32_t wv = word[ci];
-                    if (!(wv & GW_VALID)) {  // not a valid cell of the tile
-                        if (f > 0) word[ci] = GW_SENT;
+                for (int wi = tid; wi < NWD; wi += nt) {
+                    const uint32_t wv = word[wi];
+                    if (!(wv & GW_VALID)) {  // not a valid cell of the tile: its sentinel again
+                        if (f > 0)
+                            word[wi] = (wv & ((1u << GW_CNT) - 1u)) |
+                                       ((SENT_CNT + (uint32_t)__popc((wv >> GW_PM) & 0xFFu)) << GW_CNT);
                         continue;
                     }
-                    const int r = tw > 1 ? (int)__umulhi((uint32_t)ci, rdiv) : ci, c = ci - r * tw;
+                    const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
                     const float wf = wp ? wp[(R0 + r) * ras.pw + (C0 + c)] : 1.0f;
                     if constexpr (PASS == 1) {
                         const uint32_t b = __float_as_uint(wf) & 0x7fffffffu;
                         if (b >= 0x7f800000u) nonfinite = 1;
                         gmaxw = max(gmaxw, b);
                     }
-                    val[ci] = FF{wf, 0.0f};
+                    val[wi] = FF{wf, 0.0f};
                     if (f > 0)  // the pending counts again, from the inflow mask
-                        word[ci] = (wv & ((1u << GW_CNT) - 1u)) |
+                        word[wi] = (wv & ((1u << GW_CNT) - 1u)) |
                                    ((uint32_t)__popc((wv >> GW_PM) & 0xFFu) << GW_CNT);
                 }
             }
             if constexpr (PASS == 2) {
                 // the flow entering from other tiles, added at its entry cell
                 // (Algorithm 3), summed over the outside neighbours in a fixed
-                // order, after the cell's own weight is in place
-                __syncthreads();
-                const int qf = fix_scale(a.fcells, *a.maxw);
+                // order (float pairs: after the cell's own weight is in place)
+                if constexpr (MODE == 1) __syncthreads();
+                const int qf = MODE == 1 ? fix_scale(a.fcells, *a.maxw) : 0;
                 for (int s = tid; s < P; s += nt) {
                     uint32_t m = pinf[s];
                     if (!m) continue;
                     int r, c;
                     cell_of(s, h, w, r, c);
-                    const int ci = r * tw + c;
-                    FF v = val[ci];
+                    const int wi = (r + 1) * W2 + c + 1;
+                    FF v;
+                    if constexpr (MODE == 1) v = val[wi];
+                    unsigned long long add = 0;
                     while (m) {
                         const int j = __ffs(m) - 1;
                         m &= m - 1u;
@@ -792,20 +697,19 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                         const uint16_t lk = a.link[src];  // the exit's own rank
                         if (lk == LINK_TERM) continue;
                         const size_t node = (size_t)(src - src % (uint32_t)a.pmax) + lk;
-                        v = ff_add(v, fix2ff(reinterpret_cast<const u128 *>(a.G)[node * nf + f], qf));
+                        if constexpr (MODE == 0) {
+                            add += reinterpret_cast<const unsigned long long *>(a.G)[node];
+                        } else {
+                            v = ff_add(v, fix2ff(reinterpret_cast<const u128 *>(a.G)[node * nf + f], qf));
+                        }
                     }
-                    val[ci] = v;
+                    if constexpr (MODE == 0) word[wi] += (W)add;
+                    else val[wi] = v;
                 }
             }
             __syncthreads();
 
-            uint32_t *out = OUTPUT ? reinterpret_cast<uint32_t *>(ras.out[f]) + (size_t)R0 * ras.po + C0
-                                   : nullptr;
-            int done = walk_tile<MODE>(word, val, wq, qn, s_nb, out, ras.po, tw, rdiv);
-            if (f == 0) {
-                done = __reduce_add_sync(0xffffffffu, done);
-                if (lane == 0 && done) atomicAdd(&s_done, done);
-            }
+            walk_tile<MODE, W>(word, val, wq, qn, s_nb);
             __syncthreads();
 
             if constexpr (PASS == 1) {
@@ -815,29 +719,36 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                     if (rk == LINK_TERM) continue;
                     int r, c;
                     cell_of(s, h, w, r, c);
-                    const int ci = r * tw + c;
+                    const int wi = (r + 1) * W2 + c + 1;
                     double v;
-                    if constexpr (MODE == 0) v = (double)(word[ci] & CW_ACC);
-                    else v = (double)val[ci].hi + (double)val[ci].lo;
+                    if constexpr (MODE == 0) v = (double)(word[wi] & CountWord<W>::ACC);
+                    else v = (double)val[wi].hi + (double)val[wi].lo;
                     a.node_val[(tbase + rk) * nf + f] = v;
+                }
+            } else {
+                // the output raster of field f: A at complete cells, 0 at
+                // NoData (and on cycles); the words are cleared for the next
+                // tile after the last field
+                const bool last = f == nf - 1;
+                for (int wi = tid; wi < NWD; wi += nt) {
+                    const W wv = word[wi];
+                    if (last) word[wi] = 0;
+                    const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
+                    if ((unsigned)r >= (unsigned)h || (unsigned)c >= (unsigned)w) continue;
+                    uint32_t o = 0;
+                    if ((wv >> CNT) == 0) {
+                        if constexpr (MODE == 0) {
+                            const unsigned long long s64 = (unsigned long long)(wv & CountWord<W>::ACC);
+                            ovf |= (s64 >> 32) != 0;
+                            o = (uint32_t)s64;
+                        } else {
+                            o = __float_as_uint(ff_round(val[wi]));
+                        }
+                    }
+                    reinterpret_cast<uint32_t *>(ras.out[f])[(size_t)(R0 + r) * ras.po + C0 + c] = o;
                 }
             }
             if (f + 1 < nf) __syncthreads();
-        }
-
-        if constexpr (PASS == 1) {
-            // cells never completed lie on a cycle inside the tile (a cycle
-            // cell misses exactly its predecessor on the cycle); found by
-            // their count of one when the walks completed fewer cells than
-            // the tile's valid ones
-            if (s_valid != s_done) {
-                for (int ci = tid; ci < n; ci += nt) {
-                    if ((word[ci] >> CNT) != 1) continue;
-                    const int r = tw > 1 ? (int)__umulhi((uint32_t)ci, rdiv) : ci, c = ci - r * tw;
-                    ++ncyc;
-                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
-                }
-            }
         }
 
         if constexpr (RETAIN) {
@@ -849,14 +760,13 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             // positions 0, 1, ... in path order.
             const size_t efb = (size_t)t * th * tw;
             // the claim tags share memory with the walks' queues: clear them
-            for (int i = tid; i < ((n + 3) >> 2); i += nt)
-                reinterpret_cast<uint4 *>(tag)[i] = make_uint4(0u, 0u, 0u, 0u);
+            for (int wi = tid; wi < NWD; wi += nt) tag[wi] = 0;
             __syncthreads();
             for (int e = tid; e < s_nent; e += nt) {
                 const int slot = pent[e];
                 int r, c;
                 cell_of(slot, h, w, r, c);
-                int cur = r * tw + c;
+                int cur = (r + 1) * W2 + c + 1;
                 uint16_t end = LINK_TERM;
                 uint32_t join = NO_JOIN;
                 for (int pos = 0; pos < h * w; ++pos) {
@@ -868,10 +778,10 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                     const int idx = atomicAdd(&s_nef, 1);
                     a.ef_cp[efb + idx] = ((uint32_t)cur << 16) | (uint32_t)pos;
                     a.ef_seg[efb + idx] = (uint16_t)e;
-                    const uint32_t sc = (word[cur] >> SUCC) & SUCC_NONE;
-                    if (sc == SUCC_NONE || (word[sc] >> CNT) >= 2) {
+                    const uint32_t sc = (uint32_t)(word[cur] >> SUCC) & SUCC_NONE;
+                    if (sc == SUCC_NONE || (word[sc] >> CNT) >= SENT_CNT) {
                         // the path leaves the tile here (an exit) or ends
-                        const int rr = tw > 1 ? (int)__umulhi((uint32_t)cur, rdiv) : cur, cc = cur - rr * tw;
+                        const int hr = (int)__umulhi((uint32_t)cur, rdiv), rr = hr - 1, cc = cur - hr * W2 - 1;
                         if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) end = prank[slot_of(rr, cc, h, w)];
                         break;
                     }
@@ -906,14 +816,14 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 const int slot = pent[e];
                 int r, c;
                 cell_of(slot, h, w, r, c);
-                int cur = r * tw + c, steps = 0;
-                uint32_t wc = word[cur];
+                int cur = (r + 1) * W2 + c + 1, steps = 0;
+                W wc = word[cur];
                 for (;;) {
-                    const uint32_t sc = (wc >> SUCC) & SUCC_NONE;
+                    const uint32_t sc = (uint32_t)(wc >> SUCC) & SUCC_NONE;
                     if (sc == SUCC_NONE) break;
-                    const uint32_t wn = word[sc];
-                    if ((wn >> CNT) >= 2) break;  // into NoData
-                    if (++steps > h * w) {        // a cycle: the path never ends
+                    const W wn = word[sc];
+                    if ((wn >> CNT) >= SENT_CNT) break;  // leaves the tile or the data
+                    if (++steps > h * w) {              // a cycle: the path never ends
                         cur = -1;
                         break;
                     }
@@ -922,7 +832,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 }
                 uint16_t lk = LINK_TERM;
                 if (cur >= 0) {
-                    const int rr = tw > 1 ? (int)__umulhi((uint32_t)cur, rdiv) : cur, cc = cur - rr * tw;
+                    const int hr = (int)__umulhi((uint32_t)cur, rdiv), rr = hr - 1, cc = cur - hr * W2 - 1;
                     if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) lk = prank[slot_of(rr, cc, h, w)];
                 }
                 a.link[tbase + slot] = lk;
@@ -930,6 +840,25 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
         }
         if constexpr (PASS == 1) {
             if (tid == 0) a.nexit[t] = (uint32_t)nexits;
+            __syncthreads();
+            // cells still waiting for an inflow lie on a cycle inside the
+            // tile (a cycle cell misses exactly its predecessor on the
+            // cycle); counts: A_loc goes to the output raster (0 at NoData
+            // and on cycles); the words are cleared for the next tile
+            for (int wi = tid; wi < NWD; wi += nt) {
+                const W wv = word[wi];
+                word[wi] = 0;
+                const int hr = (int)__umulhi((uint32_t)wi, rdiv), r = hr - 1, c = wi - hr * W2 - 1;
+                if ((wv >> CNT) == 1) {
+                    ++ncyc;
+                    fbad = min(fbad, (long long)((R0 + r) * ras.cols + (C0 + c)));
+                }
+                if constexpr (RETAIN) {
+                    if ((unsigned)r < (unsigned)h && (unsigned)c < (unsigned)w)
+                        reinterpret_cast<uint32_t *>(ras.out[0])[(size_t)(R0 + r) * ras.po + C0 + c] =
+                            (wv >> CNT) == 0 ? (uint32_t)(wv & CountWord<W>::ACC) : 0u;
+                }
+            }
         }
         __syncthreads();
         // [phase] end
@@ -1000,7 +929,7 @@ __global__ void __launch_bounds__(128) k_offsets(const __grid_constant__ TileArg
     const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
     const int h = (int)min((int64_t)a.th, ras.rows - R0);
     const int w = (int)min((int64_t)a.tw, ras.cols - C0);
-    const int TW = a.tw;  // cells are recorded by their index r * tw + c in the tile
+    const int W2 = a.tw + 2;  // cells are recorded by their word index (r + 1) * W2 + (c + 1)
     const int P = perim_count(h, w);
     const int pm = a.pmax;
     const size_t tb = (size_t)t * pm, eb = (size_t)t * a.th * a.tw, ib = (size_t)t * (pm + 8);
@@ -1175,7 +1104,7 @@ __global__ void __launch_bounds__(128) k_offsets(const __grid_constant__ TileArg
         }
         if (lo > b) o += pre[lo - 1];
         if (!o) continue;
-        const int r = ci / TW, c = ci - r * TW;
+        const int hr = ci / W2, r = hr - 1, c = ci - hr * W2 - 1;
         const size_t oi = (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
         if constexpr (VALM == 0) {
             uint32_t *p = reinterpret_cast<uint32_t *>(ras.out[0]) + oi;
