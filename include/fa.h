@@ -306,8 +306,8 @@ fa_status fa_autotune_batched(const fa_raster *rasters, int32_t n_rasters, int32
  * the process exits), and the call allocates nothing.
  *  - Size limit: rasters whose fa_workspace_size() exceeds
  *    FA_NOALLOC_SCRATCH_BYTES return FA_ERR_TOO_LARGE with nothing enqueued
- *    (with the default 64 x 64 tiles that is about 5.9 million cells: square
- *    rasters up to 2432 x 2432 fit, 2433 x 2433 does not).
+ *    (with the default 64 x 64 tiles that is about 7.2 million cells: square
+ *    rasters up to 2688 x 2688 fit, 2689 x 2689 does not).
  *  - Every call looks up the buffer's device address on the current device
  *    (cudaGetSymbolAddress); the first call on a device may load the
  *    library's module there, so make that first call outside any stream

@@ -1125,7 +1125,7 @@ __global__ void __launch_bounds__(128) k_offsets(const __grid_constant__ TileArg
 // structure shared by all fields
 // ---------------------------------------------------------------------------
 struct ForestArgs {
-    int64_t tiles;
+    int64_t tiles, nodes;  // nodes: tiles * pmax (bounds a walk)
     int pmax, nf;
     int64_t cells;
     int valm;
@@ -1133,9 +1133,10 @@ struct ForestArgs {
     const uint16_t *link;
     const uint32_t *node_dst;
     const double *node_val;
-    void *x, *dl0, *dl1;  // u64 (counts) or u128 (fixed-point sums) per node and field
-    uint32_t *J0, *J1;
-    uint32_t *misc;  // [0] max|w| bits, [1 + k] active nodes in round k
+    void *x;  // u64 (counts) or u128 (fixed-point sums) per node and field
+    uint32_t *J0;  // successor node (the exit its target entry cell links to) or NODE_NONE
+    uint32_t *J1;  // predecessors still to come
+    uint32_t *misc;  // [0] max|w| bits, [1] nodes finished by the walks
     StatusBlock *st;
 };
 
@@ -1150,8 +1151,7 @@ __global__ void k_forest_init(ForestArgs f) {
     const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (tile >= f.tiles) return;
-    V *x = reinterpret_cast<V *>(f.x), *dl0 = reinterpret_cast<V *>(f.dl0),
-      *dl1 = reinterpret_cast<V *>(f.dl1);
+    V *x = reinterpret_cast<V *>(f.x);
     const uint32_t n = f.nexit[tile];
     const int q = f.valm ? fix_scale(f.cells, f.misc[0]) : 0;
     const size_t base = (size_t)tile * f.pmax;
@@ -1162,85 +1162,81 @@ __global__ void k_forest_init(ForestArgs f) {
             const double v = f.node_val[i];
             if constexpr (sizeof(V) == 8) x[i] = (V)v;  // an exact integer count
             else x[i] = f.valm ? d2fix(v, q) : (u128)(unsigned long long)v;
-            dl0[i] = 0;
-            dl1[i] = 0;
         }
         const uint32_t dst = f.node_dst[node];
         const uint16_t l = f.link[dst];
         f.J0[node] = l == LINK_TERM ? NODE_NONE : (dst / f.pmax) * f.pmax + l;
+        f.J1[node] = 0;
     }
 }
 
-// One doubling round: x_{k+1}(v) = x_k(v) + sum over u with J_k(u) = v of
-// x_k(u), J_{k+1} = J_k o J_k.  After rounds 0..m-1 every node holds the sum
-// of A_loc over all nodes at most 2^m - 1 links upstream, i.e. the product
-// (I + P)(I + P^2)...(I + P^(2^(m-1))) applied to A_loc, which equals
-// (I - P)^-1 A_loc once 2^m exceeds the longest path.  Integer adds: the
-// order in which they land does not matter.
+// The exit forest solved the way a tile is (Algorithm 1 on the perimeter
+// graph of Section 3.2): J1 counts each node's predecessors (k_forest_indeg);
+// then every node without one starts a walk (k_forest_walk) that adds its
+// finished value G into its successor's and moves on when it brought the
+// successor's last inflow, so each node is passed on once.  Values and counts
+// are separate words in global memory: a walk makes its adds visible (fence)
+// before it takes one off the count, and the walk that takes the last one
+// reads the successor's value only after that (fence, loads that bypass L1).
+// Integer adds: the order in which they land does not matter.
 template <class V>
-__global__ void k_forest_round(ForestArgs f, int k) {
-    if (k > 0 && f.misc[k] == 0) return;  // round k-1 moved nothing: done
+__global__ void k_forest_indeg(ForestArgs f) {
+    const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (tile >= f.tiles) return;
+    const uint32_t n = f.nexit[tile];
+    const size_t base = (size_t)tile * f.pmax;
+    for (uint32_t j = lane; j < n; j += 32) {
+        const uint32_t s = f.J0[base + j];
+        if (s != NODE_NONE) atomicAdd(&f.J1[s], 1u);
+    }
+}
+
+__device__ __forceinline__ unsigned long long load_cg(const unsigned long long *p) { return __ldcg(p); }
+__device__ __forceinline__ u128 load_cg(const u128 *p) {
+    const unsigned long long *q = reinterpret_cast<const unsigned long long *>(p);
+    return (u128)__ldcg(q) | ((u128)__ldcg(q + 1) << 64);
+}
+
+template <class V>
+__global__ void k_forest_walk(ForestArgs f) {
     const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (tile >= f.tiles) return;
     V *x = reinterpret_cast<V *>(f.x);
-    V *dprev = reinterpret_cast<V *>((k & 1) ? f.dl0 : f.dl1);
-    V *dcur = reinterpret_cast<V *>((k & 1) ? f.dl1 : f.dl0);
-    const uint32_t *Jc = (k & 1) ? f.J1 : f.J0;
-    uint32_t *Jn = (k & 1) ? f.J0 : f.J1;
     const uint32_t n = f.nexit[tile];
     const size_t base = (size_t)tile * f.pmax;
-    int nact = 0;
+    int done = 0;
     for (uint32_t j = lane; j < n; j += 32) {
-        const size_t node = base + j;
-        const uint32_t jj = Jc[node];
-        for (int q = 0; q < f.nf; ++q) {
-            const size_t i = node * f.nf + q;
-            V xv = x[i];
-            if (k > 0) {
-                const V d = dprev[i];
-                if (d) {
-                    xv += d;
-                    x[i] = xv;
-                    dprev[i] = 0;
-                }
-            }
-            if (jj != NODE_NONE) atomic_add_v(&dcur[(size_t)jj * f.nf + q], xv);
-        }
-        if (jj != NODE_NONE) {
-            Jn[node] = Jc[jj];
-            ++nact;
-        } else {
-            Jn[node] = NODE_NONE;
+        size_t u = base + j;
+        if (f.J1[u] != 0) continue;  // waits for inflow: another walk finishes it
+        ++done;
+        for (int64_t steps = 0; steps <= f.nodes; ++steps) {
+            const uint32_t v = f.J0[u];
+            if (v == NODE_NONE) break;  // its path ends inside the target tile
+            for (int q = 0; q < f.nf; ++q)
+                atomic_add_v(&x[(size_t)v * f.nf + q], load_cg(&x[u * f.nf + q]));
+            __threadfence();
+            if (atomicSub(&f.J1[v], 1u) != 1u) break;  // not the last inflow of v
+            __threadfence();
+            u = v;
+            ++done;
         }
     }
-    nact = warp_sum(nact);
-    if (lane == 0 && nact) atomicAdd(&f.misc[1 + k], (uint32_t)nact);
+    done = warp_sum(done);
+    if (lane == 0 && done) atomicAdd(&f.misc[1], (uint32_t)done);
 }
 
-// Absorb whatever is still pending and flag nodes whose paths never ended
-// (a cross-tile cycle).
+// Nodes whose count never reached zero lie on a cycle across tiles.
 template <class V>
-__global__ void k_forest_final(ForestArgs f, int kmax) {
+__global__ void k_forest_final(ForestArgs f) {
     const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (tile >= f.tiles) return;
-    V *x = reinterpret_cast<V *>(f.x), *dl0 = reinterpret_cast<V *>(f.dl0),
-      *dl1 = reinterpret_cast<V *>(f.dl1);
-    const bool live = f.misc[kmax] != 0;
-    const uint32_t *Jl = (kmax & 1) ? f.J1 : f.J0;
     const uint32_t n = f.nexit[tile];
     const size_t base = (size_t)tile * f.pmax;
     int ncyc = 0;
-    for (uint32_t j = lane; j < n; j += 32) {
-        const size_t node = base + j;
-        for (int q = 0; q < f.nf; ++q) {
-            const size_t i = node * f.nf + q;
-            const V d = dl0[i] + dl1[i];
-            if (d) x[i] += d;
-        }
-        if (live && Jl[node] != NODE_NONE) ++ncyc;
-    }
+    for (uint32_t j = lane; j < n; j += 32) ncyc += f.J1[base + j] != 0;
     ncyc = warp_sum(ncyc);
     if (lane == 0 && ncyc) status_report(f.st, FA_FLAG_CYCLE, ncyc, NO_INDEX);
 }
@@ -1299,8 +1295,6 @@ size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry
     w.node_dst = c.take<uint32_t>(S);
     w.node_val = c.take<double>(SV);
     w.x = c.take<u128>(SV);
-    w.dl0 = c.take<u128>(SV);
-    w.dl1 = c.take<u128>(SV);
     w.J0 = c.take<uint32_t>(S);
     w.J1 = c.take<uint32_t>(S);
     const size_t cells = T * (size_t)g.th * g.tw, inf = T * (size_t)(g.pmax + 8);
@@ -1491,6 +1485,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
 
     ForestArgs f;
     f.tiles = ta.T;
+    f.nodes = ta.T * g.pmax;
     f.pmax = g.pmax;
     f.nf = ta.nf;
     f.cells = ta.fcells;
@@ -1500,8 +1495,6 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     f.node_dst = ws.node_dst;
     f.node_val = ws.node_val;
     f.x = ws.x;
-    f.dl0 = ws.dl0;
-    f.dl1 = ws.dl1;
     f.J0 = ws.J0;
     f.J1 = ws.J1;
     f.misc = ws.misc;
@@ -1509,12 +1502,14 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     const unsigned fb = (unsigned)((f.tiles * 32 + 255) / 256);
     if (val_mode) {
         k_forest_init<u128><<<fb, 256, 0, s>>>(f);
-        for (int k = 0; k < ws.kmax; ++k) k_forest_round<u128><<<fb, 256, 0, s>>>(f, k);
-        k_forest_final<u128><<<fb, 256, 0, s>>>(f, ws.kmax);
+        k_forest_indeg<u128><<<fb, 256, 0, s>>>(f);
+        k_forest_walk<u128><<<fb, 256, 0, s>>>(f);
+        k_forest_final<u128><<<fb, 256, 0, s>>>(f);
     } else {
         k_forest_init<unsigned long long><<<fb, 256, 0, s>>>(f);
-        for (int k = 0; k < ws.kmax; ++k) k_forest_round<unsigned long long><<<fb, 256, 0, s>>>(f, k);
-        k_forest_final<unsigned long long><<<fb, 256, 0, s>>>(f, ws.kmax);
+        k_forest_indeg<unsigned long long><<<fb, 256, 0, s>>>(f);
+        k_forest_walk<unsigned long long><<<fb, 256, 0, s>>>(f);
+        k_forest_final<unsigned long long><<<fb, 256, 0, s>>>(f);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

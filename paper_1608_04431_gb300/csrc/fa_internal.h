@@ -77,8 +77,7 @@ struct FwdWork {
     uint32_t *node_dst;    // [T*pmax] exit rank -> global slot id of its target cell
     double *node_val;      // [T*pmax*nf] exit rank -> tile-local accumulation A_loc
     void *x;               // [T*pmax*nf] u128 forest values (G after resolve)
-    void *dl0, *dl1;       // [T*pmax*nf] u128 pending scatter buffers
-    uint32_t *J0, *J1;     // [T*pmax] jump pointers
+    uint32_t *J0, *J1;     // [T*pmax] successor node, predecessors still to come
     // counts: the entry forest of every tile (the union of the in-tile paths
     // downstream of its entry cells), recorded by pass 1 for pass 2
     uint32_t *ef_hdr;      // [T*4] entry-forest cells, segments, inflow links, 0
