@@ -64,7 +64,7 @@ extern "C" int32_t fa_kernel_launches(int64_t rows, int64_t cols, const fa_optio
     Geom g;
     if (!make_geom(rows, cols, opts, g)) return -1;
     if (rows == 0 || cols == 0) return 1;  // the status reset only
-    return 7;  // status reset, pass 1, forest init, in-degree, walk, final, pass 2
+    return 8;  // status reset, pass 1, forest init, in-degree, starts, walk, final, pass 2
 }
 
 extern "C" size_t fa_workspace_size(int64_t rows, int64_t cols, const fa_options *opts) {

@@ -1172,7 +1172,8 @@ __global__ void k_forest_init(ForestArgs f) {
 
 // The exit forest solved the way a tile is (Algorithm 1 on the perimeter
 // graph of Section 3.2): J1 counts each node's predecessors (k_forest_indeg);
-// then every node without one starts a walk (k_forest_walk) that adds its
+// the nodes without one are marked (k_forest_leaves) and each starts a walk
+// (k_forest_walk) that adds its
 // finished value G into its successor's and moves on when it brought the
 // successor's last inflow, so each node is passed on once.  Values and counts
 // are separate words in global memory: a walk makes its adds visible (fence)
@@ -1192,6 +1193,20 @@ __global__ void k_forest_indeg(ForestArgs f) {
     }
 }
 
+// Marks the nodes without predecessors (the walks start there) before any
+// walk runs: a count that the walks bring to zero must not pass for one.
+constexpr uint32_t WALK_START = 0x80000000u;
+template <class V>
+__global__ void k_forest_leaves(ForestArgs f) {
+    const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (tile >= f.tiles) return;
+    const uint32_t n = f.nexit[tile];
+    const size_t base = (size_t)tile * f.pmax;
+    for (uint32_t j = lane; j < n; j += 32)
+        if (f.J1[base + j] == 0) f.J1[base + j] = WALK_START;
+}
+
 __device__ __forceinline__ unsigned long long load_cg(const unsigned long long *p) { return __ldcg(p); }
 __device__ __forceinline__ u128 load_cg(const u128 *p) {
     const unsigned long long *q = reinterpret_cast<const unsigned long long *>(p);
@@ -1209,7 +1224,7 @@ __global__ void k_forest_walk(ForestArgs f) {
     int done = 0;
     for (uint32_t j = lane; j < n; j += 32) {
         size_t u = base + j;
-        if (f.J1[u] != 0) continue;  // waits for inflow: another walk finishes it
+        if (f.J1[u] != WALK_START) continue;  // waits for inflow: another walk finishes it
         ++done;
         for (int64_t steps = 0; steps <= f.nodes; ++steps) {
             const uint32_t v = f.J0[u];
@@ -1236,7 +1251,7 @@ __global__ void k_forest_final(ForestArgs f) {
     const uint32_t n = f.nexit[tile];
     const size_t base = (size_t)tile * f.pmax;
     int ncyc = 0;
-    for (uint32_t j = lane; j < n; j += 32) ncyc += f.J1[base + j] != 0;
+    for (uint32_t j = lane; j < n; j += 32) ncyc += f.J1[base + j] != 0 && f.J1[base + j] != WALK_START;
     ncyc = warp_sum(ncyc);
     if (lane == 0 && ncyc) status_report(f.st, FA_FLAG_CYCLE, ncyc, NO_INDEX);
 }
@@ -1503,11 +1518,13 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     if (val_mode) {
         k_forest_init<u128><<<fb, 256, 0, s>>>(f);
         k_forest_indeg<u128><<<fb, 256, 0, s>>>(f);
+        k_forest_leaves<u128><<<fb, 256, 0, s>>>(f);
         k_forest_walk<u128><<<fb, 256, 0, s>>>(f);
         k_forest_final<u128><<<fb, 256, 0, s>>>(f);
     } else {
         k_forest_init<unsigned long long><<<fb, 256, 0, s>>>(f);
         k_forest_indeg<unsigned long long><<<fb, 256, 0, s>>>(f);
+        k_forest_leaves<unsigned long long><<<fb, 256, 0, s>>>(f);
         k_forest_walk<unsigned long long><<<fb, 256, 0, s>>>(f);
         k_forest_final<unsigned long long><<<fb, 256, 0, s>>>(f);
     }
