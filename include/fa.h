@@ -385,6 +385,45 @@ fa_status fa_accumulate_absorb(const uint8_t *codes, int64_t rows, int64_t cols,
                                void *stream);
 
 /*
+ * Out-of-core accumulation: unit-weight counts of a raster whose codes and
+ * output stay in HOST memory, for rasters larger than the device (Section 1
+ * sets rasters beyond one machine's memory as the aim; Section 3 with EVICT:
+ * only one block and the perimeter data are held at once).  The raster is cut
+ * into outer blocks of block_rows x block_cols cells;
+ * each block's codes, with a one-cell ring, are copied to the device twice:
+ * pass A solves the block by the tile pipeline of fa_accumulate and records
+ * its perimeter graph (Algorithm 2 at block level), the perimeter graphs of
+ * all blocks are solved on the device (Section 3.2), and pass C solves the
+ * block again, adds the flow entering from other blocks along its paths
+ * (Algorithm 3) and copies the block's counts out.  Copies run on two streams
+ * of the library's own, overlapping the solves when the host buffers are
+ * pinned; the call is SYNCHRONOUS (it returns after the last copy out).
+ *   codes       [rows x pitch_codes] one byte per cell, HOST memory (pinned
+ *               or pageable); FA_CODES_NIBBLE is not accepted.
+ *   out         [rows x pitch_out] uint64 counts, HOST memory; exact for any
+ *               raster size; 0 at NoData.
+ *   block_rows, block_cols  outer block shape (0 = 16384; a side longer
+ *               than the raster's is cut to it); perim(block) =
+ *               2 (block_rows + block_cols) - 4 must be <= 65534, and
+ *               blocks x perim < 2^32 - 1.
+ *   workspace   device, >= fa_ooc_workspace_size(), 256-byte aligned: two
+ *               code buffers, one uint32 and two uint64 block buffers, the
+ *               tile pipeline's workspace for one block, and about 28 bytes
+ *               per perimeter slot of every block.
+ *   opts        tile shape and flags for the block solves (as fa_accumulate).
+ * Returns the decoded device status (as fa_status_read: BAD_CODE, CYCLE, ...)
+ * after completion, FA_ERR_INVALID_ARG / FA_ERR_WORKSPACE for bad arguments
+ * (nothing enqueued) or FA_ERR_CUDA.  d_status as in fa_accumulate.  Results
+ * equal fa_accumulate's counts on the same raster, cell for cell.
+ */
+size_t fa_ooc_workspace_size(int64_t rows, int64_t cols, int64_t block_rows, int64_t block_cols,
+                             const fa_options *opts);
+fa_status fa_accumulate_ooc(const uint8_t *codes, int64_t rows, int64_t cols, int64_t pitch_codes,
+                            uint64_t *out, int64_t pitch_out, int64_t block_rows,
+                            int64_t block_cols, void *workspace, size_t ws_bytes,
+                            const fa_options *opts, int32_t *d_status, void *stream);
+
+/*
  * Copies the device status block back (synchronises `stream`) and maps it to
  * the most severe fa_status: BAD_CODE, then CYCLE, NONFINITE, TIMEOUT, then
  * FA_WARN_OVERFLOW, else FA_OK.  count / first_index may be NULL.

@@ -82,6 +82,11 @@ def _configure(lib):
     lib.fa_oracle_outlet_sum_u32.argtypes = [p, i64, i64, i64, p, i64, p, i64, i64, i64,
                                              ctypes.POINTER(ctypes.c_uint64), pi64]
     lib.fa_oracle_outlet_sum_u32.restype = None
+    lib.fa_oracle_residual_u64_rows.argtypes = [p, i64, i64, i64, p, i64, p, i64, i64, i64, pi64]
+    lib.fa_oracle_residual_u64_rows.restype = ctypes.c_int64
+    lib.fa_oracle_outlet_sum_u64.argtypes = [p, i64, i64, i64, p, i64, p, i64, i64, i64,
+                                             ctypes.POINTER(ctypes.c_uint64), pi64]
+    lib.fa_oracle_outlet_sum_u64.restype = None
     return lib
 
 
@@ -236,22 +241,51 @@ def outlet_sum_u32(codes, A, r_begin: int = 0, r_end: int | None = None, mask=No
     return int(s.value), int(nv.value)
 
 
+def residual_u64_rows(codes, A, r_begin: int, r_end: int, mask=None):
+    """The Eq. 1 residual check on uint64 counts (exact, no wrap-around) on
+    rows r_begin..r_end-1: (mismatches, first_index)."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    A = np.ascontiguousarray(A).view(np.uint64)
+    first = ctypes.c_int64(-1)
+    bad = _load().fa_oracle_residual_u64_rows(_p(codes), R, C, C, _p(mask), C, _p(A), C,
+                                              int(r_begin), int(r_end), ctypes.byref(first))
+    return int(bad), int(first.value)
+
+
+def outlet_sum_u64(codes, A, r_begin: int = 0, r_end: int | None = None, mask=None):
+    """Conservation on rows r_begin..r_end-1 for uint64 counts: (sum of A over
+    terminal cells, number of valid cells)."""
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    A = np.ascontiguousarray(A).view(np.uint64)
+    s, nv = ctypes.c_uint64(0), ctypes.c_int64(0)
+    _load().fa_oracle_outlet_sum_u64(_p(codes), R, C, C, _p(mask), C, _p(A), C, int(r_begin),
+                                     int(R if r_end is None else r_end), ctypes.byref(s),
+                                     ctypes.byref(nv))
+    return int(s.value), int(nv.value)
+
+
 def verify_counts_u32(codes, A, threads: int = 1, band: int = 1024, mask=None):
-    """Complete check of uint32 counts on an acyclic raster of any size: the
-    Eq. 1 residual at every cell and conservation, over row bands in a pool
-    of host threads (the C calls release the interpreter lock).  Returns a
-    dict with mismatches, first mismatching index, outlet sum, valid cells
-    and whether conservation holds exactly and modulo 2^32."""
+    """Complete check of uint32 counts (uint64 when A holds 64-bit integers)
+    on an acyclic raster of any size: the Eq. 1 residual at every cell and
+    conservation, over row bands in a pool of host threads (the C calls
+    release the interpreter lock).  Returns a dict with mismatches, first
+    mismatching index, outlet sum, valid cells and whether conservation holds
+    exactly and modulo 2^32."""
     from concurrent.futures import ThreadPoolExecutor
 
     codes, mask = _prep(codes, mask)
-    A = np.ascontiguousarray(A, dtype=np.uint32)
+    wide = np.asarray(A).dtype.itemsize == 8
+    A = np.ascontiguousarray(A).view(np.uint64) if wide else np.ascontiguousarray(A, dtype=np.uint32)
+    res_rows = residual_u64_rows if wide else residual_u32_rows
+    osum = outlet_sum_u64 if wide else outlet_sum_u32
     R = codes.shape[0]
     bands = [(r, min(R, r + band)) for r in range(0, R, band)]
 
     def one(b):
-        bad, f = residual_u32_rows(codes, A, b[0], b[1], mask)
-        s, nv = outlet_sum_u32(codes, A, b[0], b[1], mask)
+        bad, f = res_rows(codes, A, b[0], b[1], mask)
+        s, nv = osum(codes, A, b[0], b[1], mask)
         return bad, f, s, nv
 
     with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:

@@ -361,6 +361,61 @@ void fa_oracle_outlet_sum_u32(const uint8_t *codes, int64_t rows, int64_t cols, 
 }
 
 /*
+ * The residual check and the conservation sum for uint64 counts (results too
+ * large for uint32, as from rasters of 2^32 cells or more): the same Eq. 1
+ * test, A(p) == 1 + sum of A(n) over the neighbours n with d(n) = p, in exact
+ * uint64 arithmetic with no wrap-around, on rows r_begin .. r_end - 1.
+ */
+int64_t fa_oracle_residual_u64_rows(const uint8_t *codes, int64_t rows, int64_t cols,
+                                    int64_t pitch, const uint8_t *mask, int64_t mpitch,
+                                    const uint64_t *A64, int64_t apitch, int64_t r_begin,
+                                    int64_t r_end, int64_t *first) {
+    raster R = {codes, mask, rows, cols, pitch, mpitch};
+    int64_t bad = 0, f = -1;
+    if (r_begin < 0) r_begin = 0;
+    if (r_end > rows) r_end = rows;
+    for (int64_t r = r_begin; r < r_end; ++r)
+        for (int64_t c = 0; c < cols; ++c) {
+            uint64_t expect;
+            if (!valid_cell(&R, r, c)) {
+                expect = 0;
+            } else {
+                expect = 1;
+                for (int k = 1; k <= 8; ++k) {
+                    int64_t rr = r + ODR[k], cc = c + ODC[k];
+                    if (!valid_cell(&R, rr, cc)) continue;
+                    if (downstream(&R, rr, cc) == r * cols + c) expect += A64[rr * apitch + cc];
+                }
+            }
+            if (A64[r * apitch + c] != expect) {
+                if (f < 0) f = r * cols + c;
+                ++bad;
+            }
+        }
+    if (first) *first = f;
+    return bad;
+}
+
+void fa_oracle_outlet_sum_u64(const uint8_t *codes, int64_t rows, int64_t cols, int64_t pitch,
+                              const uint8_t *mask, int64_t mpitch, const uint64_t *A64,
+                              int64_t apitch, int64_t r_begin, int64_t r_end,
+                              uint64_t *outlet_sum, int64_t *n_valid) {
+    raster R = {codes, mask, rows, cols, pitch, mpitch};
+    uint64_t s = 0;
+    int64_t nv = 0;
+    if (r_begin < 0) r_begin = 0;
+    if (r_end > rows) r_end = rows;
+    for (int64_t r = r_begin; r < r_end; ++r)
+        for (int64_t c = 0; c < cols; ++c) {
+            if (!valid_cell(&R, r, c)) continue;
+            ++nv;
+            if (downstream(&R, r, c) < 0) s += A64[r * apitch + c];
+        }
+    *outlet_sum = s;
+    *n_valid = nv;
+}
+
+/*
  * D8 flow codes from elevations, the step before accumulation (Section 2: a
  * non-divergent metric sends a cell's flow to a single neighbour; D8 takes the
  * steepest descent; flats are routed towards lower terrain only; Fig. 1 treats

@@ -36,6 +36,7 @@ __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumula
            "fa_autotune_batched", "autotune", "autotune_batched", "fa_d8_codes", "d8_codes",
            "fa_recode", "recode", "pack_codes", "PackedCodes", "power_of_two_table",
            "fa_absorb_workspace_size", "fa_accumulate_absorb", "absorb",
+           "fa_ooc_workspace_size", "fa_accumulate_ooc", "accumulate_ooc",
            "FlowAccError", "options"]
 
 
@@ -164,6 +165,30 @@ def fa_accumulate_adjoint(codes, mask, grad_out, grad_w, workspace, opts=None, d
         _ptr(codes), rows, cols, _pitch(codes), _ptr(mask), _pitch(mask), _ptr(grad_out),
         _pitch(grad_out), _ptr(grad_w), _pitch(grad_w), _ptr(workspace), workspace.numel(),
         ctypes.byref(_with_format(codes, opts)), _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_ooc_workspace_size(rows: int, cols: int, block_rows: int = 0, block_cols: int = 0,
+                          opts: fa_options | None = None) -> int:
+    return _lib.load().fa_ooc_workspace_size(rows, cols, block_rows, block_cols,
+                                             ctypes.byref(opts or fa_options()))
+
+
+def fa_accumulate_ooc(codes, out, block_rows, block_cols, workspace, opts=None, d_status=None,
+                      stream=None) -> int:
+    """fa_accumulate_ooc: uint64 counts of a raster in HOST memory (codes:
+    uint8 [R, C] CPU tensor, out: int64/uint64 [R, C] CPU tensor), solved on
+    the device block by block; synchronous, returns the decoded status."""
+    rows, cols = codes.shape
+    if codes.is_cuda or out.is_cuda:
+        raise TypeError("fa_accumulate_ooc takes host (CPU) tensors")
+    if out.element_size() != 8:
+        raise TypeError("out must be a 64-bit integer tensor")
+    empty = rows == 0 or cols == 0
+    return _lib.load().fa_accumulate_ooc(
+        None if empty else _ptr(codes), rows, cols, cols if empty else _pitch(codes),
+        None if empty else _ptr(out), cols if empty else _pitch(out), block_rows, block_cols,
+        _ptr(workspace), workspace.numel(), ctypes.byref(opts or fa_options()), _ptr(d_status),
+        _stream_ptr(stream))
 
 
 def fa_absorb_workspace_size(rows: int, cols: int, opts: fa_options | None = None) -> int:
@@ -423,6 +448,33 @@ def accumulate(codes: torch.Tensor, weights: torch.Tensor | None = None,
         st, _, _ = fa_status_read(None, ws, stream)
         if st < 0:
             raise FlowAccError(st, "fa_accumulate (device)")
+    return out
+
+
+def accumulate_ooc(codes, block=None, tile=None, out=None, device=None, stream=None,
+                   check: bool = True):
+    """Counts of a raster held in host memory (uint8 [R, C] CPU tensor or
+    numpy array), solved on `device` one outer block at a time (block: None =
+    16384 x 16384, or (h, w)).  Returns uint64 counts as an int64 CPU tensor
+    (bit pattern of the uint64; counts stay below 2^63).  check=True raises
+    FlowAccError on any device-reported error."""
+    if not isinstance(codes, torch.Tensor):
+        codes = torch.from_numpy(codes)
+    if codes.dtype != torch.uint8 or codes.is_cuda or codes.dim() != 2:
+        raise TypeError("codes must be a 2-D uint8 host tensor")
+    R, C = codes.shape
+    if out is None:
+        out = torch.empty((R, C), dtype=torch.int64)
+    bh, bw = block if block is not None else (0, 0)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    opts = options(tile)
+    n = fa_ooc_workspace_size(R, C, bh, bw, opts)
+    if n == 0:
+        raise FlowAccError(FA_ERR_INVALID_ARG, "fa_ooc_workspace_size")
+    ws = workspace(n, dev)
+    st = fa_accumulate_ooc(codes, out, bh, bw, ws, opts, None, stream)
+    if st not in (FA_OK, FA_WARN_OVERFLOW) and (check or st in (FA_ERR_INVALID_ARG, FA_ERR_WORKSPACE, FA_ERR_CUDA)):
+        raise FlowAccError(st, "fa_accumulate_ooc")
     return out
 
 

@@ -86,6 +86,9 @@ SIGNATURES = {
     "fa_plan_launch": (_I32, [_P, _P]),
     "fa_plan_destroy": (None, [_P]),
     "fa_selftest_wait_timeout": (_I32, [_I64, _P, _P]),
+    "fa_ooc_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, _OPT]),
+    "fa_accumulate_ooc": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _I64, _I64, _P, _SZ, _OPT, _P,
+                                 _P]),
     "fa_timing_enable": (None, [_I32]),
     "fa_timing_read": (_I32, [ctypes.POINTER(ctypes.c_float), _I32]),
 }

@@ -1,20 +1,26 @@
 // Forward D8 flow accumulation: tile passes and perimeter-graph resolve.
 //
 // Pipeline for one raster, or a batch of rasters each carrying up to
-// FA_MAX_FIELDS weight fields (Section 3 of the paper, EVICT strategy: the
-// tile is solved again in the finalising pass):
+// FA_MAX_FIELDS weight fields (Section 3 of the paper):
 //   pass 1  k_walk<M, 1>    per tile: Algorithm 1 in shared memory, then the
 //                           perimeter data of Section 3.2: A_loc at every exit
 //                           cell and the exit cell its flow enters in the
 //                           neighbouring tile; Algorithm 2 (the exit each entry
 //                           cell's path reaches) by walking the entry paths.
+//                           Counts (M = 0) leave A_loc in the output raster and
+//                           record the walked entry paths (the entry forest).
 //   resolve k_forest_*      the global flow graph over exit cells
 //                           (Section 3.2): G(e) = A_loc(e) + sum of G over the
 //                           exits whose flow enters the tile at a cell linked
-//                           to e, by pointer-jumping rounds.
-//   pass 2  k_walk<M, 2>    per tile: Algorithm 1 again with the flow that
-//                           enters from other tiles added to the weight of its
-//                           entry cell (Algorithm 3, Section 3.3), writing A.
+//                           to e, by last-arriver walks over the exit nodes
+//                           (Algorithm 1 on the perimeter graph).
+//   pass 2  counts: k_offsets  per tile: the flow entering at each entry cell
+//                           added along its recorded path in the output
+//                           (Algorithm 3, Section 3.3; A_loc retained, the
+//                           codes are not read again);
+//           float: k_walk<1, 2>  per tile: Algorithm 1 again with the flow
+//                           entering from other tiles added to the weight of
+//                           its entry cell, writing A (EVICT).
 //
 // Algorithm 1 inside a tile: every cell's in-tile dependency count (its
 // in-degree) is gathered first; the cells with none start a walk.  A walk
@@ -1273,7 +1279,8 @@ bool make_geom(int64_t rows, int64_t cols, const fa_options *opts, Geom &g) {
     int th = 64, tw = 64;
     if (opts && opts->tile_h) th = opts->tile_h;
     if (opts && opts->tile_w) tw = opts->tile_w;
-    if (th < 1 || tw < 1 || (int64_t)th * tw > MAX_TILE_CELLS) return false;
+    // any form's largest tile (the forward kernels' own limit is tile_shape_ok)
+    if (th < 1 || tw < 1 || (int64_t)th * tw > 16384) return false;
     if (rows < 0 || cols < 0) return false;
     g.rows = rows;
     g.cols = cols;
@@ -1536,6 +1543,37 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     timing_mark(3, s);
     timing_set_count(3);
     return e;
+}
+
+cudaError_t resolve_exit_forest_u64(int64_t groups, int pmax, const uint32_t *nexit,
+                                    const uint16_t *link, const uint32_t *node_dst,
+                                    const double *node_val, unsigned long long *x, uint32_t *J0,
+                                    uint32_t *J1, uint32_t *misc, void *status, cudaStream_t s) {
+    if (groups == 0) return cudaSuccess;
+    ForestArgs f;
+    std::memset(&f, 0, sizeof(f));
+    f.tiles = groups;
+    f.nodes = groups * pmax;
+    f.pmax = pmax;
+    f.nf = 1;
+    f.cells = 0;
+    f.valm = 0;
+    f.nexit = nexit;
+    f.link = link;
+    f.node_dst = node_dst;
+    f.node_val = node_val;
+    f.x = x;
+    f.J0 = J0;
+    f.J1 = J1;
+    f.misc = misc;
+    f.st = reinterpret_cast<StatusBlock *>(status);
+    const unsigned fb = (unsigned)((groups * 32 + 255) / 256);
+    k_forest_init<unsigned long long><<<fb, 256, 0, s>>>(f);
+    k_forest_indeg<unsigned long long><<<fb, 256, 0, s>>>(f);
+    k_forest_leaves<unsigned long long><<<fb, 256, 0, s>>>(f);
+    k_forest_walk<unsigned long long><<<fb, 256, 0, s>>>(f);
+    k_forest_final<unsigned long long><<<fb, 256, 0, s>>>(f);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,

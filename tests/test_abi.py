@@ -246,6 +246,40 @@ def test_absorb_host_logic_without_gpu(lib):
     assert call(nbytes=64) == _lib.FA_ERR_WORKSPACE
 
 
+def test_ooc_host_logic_without_gpu(lib):
+    """Out-of-core entry: workspace sizing follows the block plan, and bad
+    arguments return before any stream or copy is made."""
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: validation fails first
+    o = _lib.fa_options()
+    size = lib.fa_ooc_workspace_size
+    a = size(1000, 1000, 100, 100, ctypes.byref(o))
+    b = size(1000, 1000, 200, 200, ctypes.byref(o))
+    assert 0 < a < b  # bigger blocks: bigger buffers, fewer perimeter slots do not win
+    assert size(1000, 1000, 0, 0, ctypes.byref(o)) == size(1000, 1000, 1000, 1000, ctypes.byref(o))
+    assert size(40000, 40000, 16384, 16384, ctypes.byref(o)) > 0     # 65532 perimeter slots
+    assert size(40000, 40000, 16384, 16385, ctypes.byref(o)) > 0     # 65534: the last that fits
+    assert size(40000, 40000, 16385, 16385, ctypes.byref(o)) == 0    # 65536 slots
+    assert size(100, 100, -1, 10, ctypes.byref(o)) == 0
+    nib = _lib.fa_options(0, 0, 0, 1)
+    assert size(100, 100, 10, 10, ctypes.byref(nib)) == 0
+    badtile = _lib.fa_options(128, 128, 0, 0)
+    assert size(100, 100, 10, 10, ctypes.byref(badtile)) == 0
+
+    def call(codes=fake, pc=10, out=fake, po=10, ws=fake, nbytes=1 << 30, bh=5, bw=5, opts=o):
+        return lib.fa_accumulate_ooc(codes, 10, 10, pc, out, po, bh, bw, ws, nbytes,
+                                     ctypes.byref(opts), None, None)
+
+    assert call(codes=None) == _lib.FA_ERR_INVALID_ARG
+    assert call(out=None) == _lib.FA_ERR_INVALID_ARG
+    assert call(pc=9) == _lib.FA_ERR_INVALID_ARG
+    assert call(po=9) == _lib.FA_ERR_INVALID_ARG
+    assert call(bh=-2) == _lib.FA_ERR_INVALID_ARG
+    assert call(opts=nib) == _lib.FA_ERR_INVALID_ARG
+    assert call(ws=None) == _lib.FA_ERR_WORKSPACE
+    assert call(ws=ctypes.c_void_p((1 << 20) + 16)) == _lib.FA_ERR_WORKSPACE
+    assert call(nbytes=64) == _lib.FA_ERR_WORKSPACE
+
+
 def test_header_is_plain_c(tmp_path):
     """include/*.h is a C ABI: it must compile as C99 with warnings as errors."""
     import shutil

@@ -575,3 +575,32 @@ def test_absorb_residual_on_a_dem(oracle_mod):
                     s -= float(a[rr, cc]) * A[rr, cc]
             resid[r, c] = abs(s) / max(A[r, c], 1.0)
     assert resid.max() < 1e-12
+
+
+def test_uint64_checks_do_not_wrap(oracle_mod):
+    """The uint64 forms of the residual and conservation checks: zero
+    mismatches on the oracle's own counts and on the all-east closed form, and
+    a count off by exactly 2^32, invisible to the uint32 forms, is found."""
+    codes = synth.dem_codes(80, 96, 64)
+    A = oracle_mod.counts(codes).values.astype(np.uint64)
+    assert oracle_mod.residual_u64_rows(codes, A, 0, 80) == (0, -1)
+    v = oracle_mod.verify_counts_u32(codes, A, threads=2, band=7)
+    assert v["mismatches"] == 0 and v["conserved"]
+    B = A.copy()
+    B[30, 40] += np.uint64(1 << 32)
+    assert oracle_mod.residual_u32(codes, B.astype(np.uint32))[0] == 0
+    bad, first = oracle_mod.residual_u64_rows(codes, B, 0, 80)
+    assert bad >= 1 and first <= 30 * 96 + 40
+    rows, cols = 5, 11
+    east = np.full((rows, cols), 1, np.uint8)
+    Ae = np.tile(np.arange(1, cols + 1, dtype=np.uint64), (rows, 1))
+    assert oracle_mod.residual_u64_rows(east, Ae, 0, rows) == (0, -1)
+    assert oracle_mod.outlet_sum_u64(east, Ae) == (rows * cols, rows * cols)
+    Ai = Ae.copy()
+    Ai[2, 3] += np.uint64(1 << 32)  # an inner cell: it and its downstream cell disagree
+    assert oracle_mod.residual_u64_rows(east, Ai, 0, rows) == (2, 2 * cols + 3)
+    Ae[2, cols - 1] += np.uint64(1 << 32)  # a terminal cell: conservation breaks by 2^32
+    s, nv = oracle_mod.outlet_sum_u64(east, Ae)
+    assert s - nv == 1 << 32
+    v = oracle_mod.verify_counts_u32(east, Ae.astype(np.int64))
+    assert not v["conserved"] and v["conserved_mod_2_32"] and v["mismatches"] == 1

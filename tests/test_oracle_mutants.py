@@ -100,6 +100,13 @@ C_MUTANTS = {
     "absorption: own weight absorbed too": (
         "        out[c] += w ? (double)w[r * wpitch + cc] : 1.0;",
         "        out[c] += (w ? (double)w[r * wpitch + cc] : 1.0) * (double)a[r * apitch + cc];"),
+    "uint64 residual: the expected count kept in 32 bits": (
+        "            uint64_t expect;", "            uint32_t expect;"),
+    "uint64 residual: the cell's own unit left out": (
+        "                expect = 1;", "                expect = 0;"),
+    "uint64 conservation: every valid cell counted as a terminal": (
+        "            if (downstream(&R, r, c) < 0) s += A64[r * apitch + c];",
+        "            s += A64[r * apitch + c];"),
     "D8: ties go to the later direction": (
         "                if (slope > best) {", "                if (slope >= best) {"),
     "D8: no distance factor on diagonals": (
