@@ -8,11 +8,14 @@
  * The library computes it with the paper's tile decomposition (Section 3):
  * a per-tile solve (Algorithm 1) that also links each perimeter cell to the
  * tile exit its flow path reaches (Algorithm 2), a global solve over those
- * perimeter links (Section 3.2), and a finalising per-tile pass that solves
- * each tile again with the flow entering it from other tiles added at its
- * entry cells (Algorithm 3, Section 3.3; the EVICT strategy of Section 3:
- * nothing per cell is kept between the passes, the codes and weights are read
- * twice and the output written once).
+ * perimeter links (Section 3.2), and a finalising per-tile pass (Algorithm 3,
+ * Section 3.3) that adds the flow entering each tile from other tiles.  For
+ * counts the first pass leaves each tile's own accumulation in the output and
+ * the finalising pass adds the entering flow along the in-tile path of each
+ * entry cell (the codes are read twice, the output written once and updated
+ * on those paths); for float sums the finalising pass solves each tile again
+ * with the entering flow added at its entry cells (the EVICT strategy of
+ * Section 3: codes and weights read twice, the output written once).
  *
  * Raster conventions (all entry points):
  *  - Row-major, row 0 = north; every raster argument has its own row pitch in
@@ -88,12 +91,15 @@ typedef enum { FA_OUT_U32 = 0, FA_OUT_F32 = 1 } fa_out_dtype;
 #define FA_FLAG_TIMEOUT 8
 #define FA_FLAG_NONFINITE 16
 
-/* Tile shape: 0 = library default (64 x 64).  1 <= tile_h, tile_w and
- * tile_h * tile_w <= 8192 (a tile cell's index fits 14 bits); the tile's
- * shared memory must also fit, which rules out only very narrow, tall tiles
- * (the staged codes take (tile_h + 2) * (tile_w + 32 rounded up to a multiple
- * of 16) bytes).  Other shapes return FA_ERR_INVALID_ARG.  Results do not depend on the tile shape, except for
- * the rounding of floating-point sums.
+/* Tile shape: 0 = library default (64 x 64).  For fa_accumulate, batches,
+ * fa_accumulate_noalloc and the out-of-core blocks: 1 <= tile_h, tile_w,
+ * tile_h * tile_w <= 8192 and (tile_h + 2) * (tile_w + 2) <= 16383 (the words
+ * of a tile and its one-cell ring are numbered in 14 bits); the tile's shared
+ * memory must also fit, which rules out only very narrow, tall tiles (the
+ * staged codes take (tile_h + 2) * (tile_w + 32 rounded up to a multiple of
+ * 16) bytes).  The adjoint and absorption forms state their own limits.
+ * Other shapes return FA_ERR_INVALID_ARG.  Results do not depend on the tile
+ * shape, except for the rounding of floating-point sums.
  * flags: FA_OPT_NO_TMA disables staging code tiles into shared memory with the
  * Tensor Memory Accelerator (used for single rasters when they allow it:
  * 16-byte aligned codes and pitch, tile width a multiple of 16 (32 for packed
@@ -306,8 +312,8 @@ fa_status fa_autotune_batched(const fa_raster *rasters, int32_t n_rasters, int32
  * the process exits), and the call allocates nothing.
  *  - Size limit: rasters whose fa_workspace_size() exceeds
  *    FA_NOALLOC_SCRATCH_BYTES return FA_ERR_TOO_LARGE with nothing enqueued
- *    (with the default 64 x 64 tiles that is about 7.2 million cells: square
- *    rasters up to 2688 x 2688 fit, 2689 x 2689 does not).
+ *    (with the default 64 x 64 tiles that is about 23 million cells: square
+ *    rasters up to 4800 x 4800 fit, 4801 x 4801 does not).
  *  - Every call looks up the buffer's device address on the current device
  *    (cudaGetSymbolAddress); the first call on a device may load the
  *    library's module there, so make that first call outside any stream

@@ -7,17 +7,16 @@
 //                           cell and the exit cell its flow enters in the
 //                           neighbouring tile; Algorithm 2 (the exit each entry
 //                           cell's path reaches) by walking the entry paths.
-//                           Counts (M = 0) leave A_loc in the output raster and
-//                           record the walked entry paths (the entry forest).
+//                           Counts (M = 0) leave A_loc in the output raster.
 //   resolve k_forest_*      the global flow graph over exit cells
 //                           (Section 3.2): G(e) = A_loc(e) + sum of G over the
 //                           exits whose flow enters the tile at a cell linked
 //                           to e, by last-arriver walks over the exit nodes
 //                           (Algorithm 1 on the perimeter graph).
-//   pass 2  counts: k_offsets  per tile: the flow entering at each entry cell
-//                           added along its recorded path in the output
+//   pass 2  counts: k_addin  per tile: the flow entering at each entry cell
+//                           added along its in-tile path in the output
 //                           (Algorithm 3, Section 3.3; A_loc retained, the
-//                           codes are not read again);
+//                           codes staged again, only the entry paths walked);
 //           float: k_walk<1, 2>  per tile: Algorithm 1 again with the flow
 //                           entering from other tiles added to the weight of
 //                           its entry cell, writing A (EVICT).
@@ -64,8 +63,7 @@ struct TileArgs {
     const void *G;  // resolved perimeter graph: u64 counts or u128 fixed-point sums, [node * nf + f]
     StatusBlock *st;
     uint32_t *maxw;
-    uint32_t *ef_hdr, *ef_cp, *seg_merge, *inf_src;  // counts: the entry forests (pass 1 -> pass 2)
-    uint16_t *ef_seg, *inf_seg;
+    const unsigned long long *infl;  // counts: flow arriving at each perimeter slot (pass 2)
     // batches: a table of rasters (nullptr for one raster), each with its
     // tiles numbered from its tile_base in one global tile sequence
     const RasterDesc *rtab;
@@ -143,7 +141,6 @@ constexpr int MAX_TILE_CELLS = 8192;
 constexpr int MAX_TILE_WORDS = 16383;
 constexpr uint32_t SUCC_NONE = 0x3FFFu;
 constexpr uint32_t SENT_CNT = 7;
-constexpr uint32_t NO_JOIN = 0xFFFFFFFFu;  // an entry-forest segment that joins no other
 
 __host__ __device__ inline int tile_words(int th, int tw) { return (th + 2) * (tw + 2); }
 
@@ -185,21 +182,9 @@ __host__ __device__ inline size_t walk_smem_bytes(int th, int tw, int mode, int 
     b += nwd * ((mode == 0 && pass == 2) ? 8 : 4);  // cell words
     b = (b + 15) & ~size_t(15);
     if (mode == 1) b += nwd * 8;                     // float pair sums
-    // queued walk starts (counts, pass 1: then the entry walks' claim tags)
-    b += nwd * ((mode == 0 && pass == 1) ? 4 : 2);
+    b += nwd * 2;                                    // queued walk starts
     b = (b + 15) & ~size_t(15);
     b += pm * 4 + pm * 2 + pm * 2 + pm;              // exit targets, exit ranks, entry list, inflow masks
-    if (mode == 0 && pass == 1) b = ((b + 3) & ~size_t(3)) + pm * 4 + pm * 2;  // segment joins and ends
-    return (b + 15) & ~size_t(15);
-}
-
-__host__ __device__ inline size_t offsets_smem_bytes(int th, int tw) {
-    // segments: at most one per perimeter cell
-    const size_t pc = (size_t)perim_count(th, tw);
-    size_t b = pc * 16;                       // inflow per segment (graph scale), then prefix sums
-    b += pc * 8 * 2;                          // inflow at the tile scale, flow at the end
-    b += pc * 4 * 2 + (pc + 1) * 4;           // join target, pending joins / fill, bucket start
-    b += pc * 2 * 2;                          // join position, joins grouped by target
     return (b + 15) & ~size_t(15);
 }
 
@@ -208,7 +193,7 @@ __host__ __device__ inline bool tile_shape_ok(int th, int tw, int valm) {
     if ((int64_t)(th + 2) * (tw + 2) > MAX_TILE_WORDS) return false;
     for (int pass = 1; pass <= 2; ++pass)
         if (walk_smem_bytes(th, tw, valm, pass, LOAD_TMA_PACKED) > 227 * 1024) return false;
-    return offsets_smem_bytes(th, tw) <= 227 * 1024;
+    return true;
 }
 
 // Code of raster column gc in a row of packed codes: low nibble for even
@@ -356,25 +341,9 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, i
     bool act = false;
     uint32_t sc = SUCC_NONE;  // successor of the lane's cell
     W acc = 0;                // counts: the lane's cell's sum
-    for (;;) {
-        const uint32_t idle = __ballot_sync(0xffffffffu, !act);
-        if (pos >= qn) {
-            if (idle == 0xffffffffu) break;
-        } else if (idle) {
-            const int my = pos + __popc(idle & lt);
-            if (!act && my < qn) {
-                const W wv = word[q[my]];
-                if constexpr (MODE == 0) {
-                    acc = wv & CountWord<W>::ACC;
-                    sc = (uint32_t)(wv >> CountWord<W>::SUCC) & SUCC_NONE;
-                } else {
-                    sc = (uint32_t)wv & SUCC_NONE;
-                }
-                act = true;
-            }
-            pos += __popc(idle);
-        }
-        if (!act) continue;
+    // one step of the lane's walk: hand the flow to the successor; go on
+    // from it only if this brought its last pending inflow
+    auto step = [&]() {
         if (sc == SUCC_NONE) {
             act = false;  // NoFlow: the path ends here
         } else if constexpr (MODE == 0) {
@@ -398,7 +367,29 @@ __device__ __forceinline__ void walk_tile(W *word, FF *val, const uint16_t *q, i
                 sc = old & SUCC_NONE;
             }
         }
+    };
+    // while the warp's queue lasts, idle lanes take its next cells
+    while (pos < qn) {
+        const uint32_t idle = __ballot_sync(0xffffffffu, !act);
+        if (idle) {
+            const int my = pos + __popc(idle & lt);
+            if (!act && my < qn) {
+                const W wv = word[q[my]];
+                if constexpr (MODE == 0) {
+                    acc = wv & CountWord<W>::ACC;
+                    sc = (uint32_t)(wv >> CountWord<W>::SUCC) & SUCC_NONE;
+                } else {
+                    sc = (uint32_t)wv & SUCC_NONE;
+                }
+                act = true;
+            }
+            pos += __popc(idle);
+        }
+        if (act) step();
     }
+    // then each lane finishes its own walk (the long last walks: no refill
+    // bookkeeping per step)
+    while (act) step();
 }
 
 // ---------------------------------------------------------------------------
@@ -421,7 +412,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_warp[33];
-    __shared__ int s_flags, s_nent, s_nef, s_ninf;
+    __shared__ int s_flags, s_nent;
     __shared__ int s_nb[8];
     __shared__ __align__(8) uint64_t s_bar;
 
@@ -451,8 +442,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     if (MODE == 1) p += (size_t)NWD * sizeof(FF);
     constexpr bool RETAIN = MODE == 0 && PASS == 1;     // counts: A_loc stays in the output
     uint16_t *queue = reinterpret_cast<uint16_t *>(p);     // walk starts
-    uint32_t *tag = reinterpret_cast<uint32_t *>(p);       // RETAIN, after the walks: claim tags
-    p += (size_t)NWD * (RETAIN ? 4 : 2);
+    p += (size_t)NWD * 2;
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     uint32_t *pexit = reinterpret_cast<uint32_t *>(p);     // slot -> global slot id of its exit target
     p += (size_t)a.pmax * 4;
@@ -461,11 +451,6 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
     uint16_t *pent = reinterpret_cast<uint16_t *>(p);      // the entry cells' slots
     p += (size_t)a.pmax * 2;
     uint8_t *pinf = p;                                     // slot -> neighbours outside draining in
-    p += a.pmax;
-    p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
-    uint32_t *segjoin = reinterpret_cast<uint32_t *>(p);   // RETAIN: segment -> where it joins another
-    p += (size_t)a.pmax * 4;
-    uint16_t *segend = reinterpret_cast<uint16_t *>(p);    // RETAIN: segment -> the exit it ends at
 
     int nbad = 0, ncyc = 0, nonfinite = 0, ovf = 0;
     long long fbad = NO_INDEX;
@@ -509,11 +494,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             prank[s] = LINK_TERM;
             pinf[s] = 0;
         }
-        if (tid == 0) {
-            s_nent = 0;
-            s_nef = 0;
-            s_ninf = 0;
-        }
+        if (tid == 0) s_nent = 0;
 
         // [phase] codes of the tile and its one-cell halo ring
         if constexpr (LOAD != LOAD_PLAIN) {
@@ -595,23 +576,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
                 if (kh >= 1 && kh <= 8 && nr + dir_dr(kh) == r && nc + dir_dc(kh) == c) m |= 1u << j;
             }
             pinf[s] = (uint8_t)m;
-            if (PASS == 1 && m) {
-                const int e = atomicAdd(&s_nent, 1);
-                pent[e] = (uint16_t)s;
-                if constexpr (RETAIN) {
-                    // inflow links: the exit outside (its slot id) and the
-                    // segment (entry) it feeds
-                    const int j0 = atomicAdd(&s_ninf, __popc(m));
-                    const size_t infb = (size_t)t * (a.pmax + 8);
-                    for (int jj = 0; m; ++jj) {
-                        const int j = __ffs(m) - 1;
-                        m &= m - 1u;
-                        a.inf_src[infb + j0 + jj] =
-                            outside_slot(ras, a, ty, tx, R0, C0, h, w, r + dir_dr(j + 1), c + dir_dc(j + 1));
-                        a.inf_seg[infb + j0 + jj] = (uint16_t)e;
-                    }
-                }
-            }
+            if (PASS == 1 && m) pent[atomicAdd(&s_nent, 1)] = (uint16_t)s;
         }
         if constexpr (LOAD == LOAD_TMA) fence_proxy_async();  // the code buffer is refilled by TMA
         __syncthreads();
@@ -757,64 +722,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
             if (f + 1 < nf) __syncthreads();
         }
 
-        if constexpr (RETAIN) {
-            // Algorithm 2 for the entry cells, recording the tile's entry
-            // forest for pass 2: the path of entry e is walked once, claiming
-            // its cells (tag (e + 1) << 16 | position); a walk that reaches a
-            // cell claimed by another walk stops and records the join there.
-            // Each walk's claimed run is a segment: the cells of segment e at
-            // positions 0, 1, ... in path order.
-            const size_t efb = (size_t)t * th * tw;
-            // the claim tags share memory with the walks' queues: clear them
-            for (int wi = tid; wi < NWD; wi += nt) tag[wi] = 0;
-            __syncthreads();
-            for (int e = tid; e < s_nent; e += nt) {
-                const int slot = pent[e];
-                int r, c;
-                cell_of(slot, h, w, r, c);
-                int cur = (r + 1) * W2 + c + 1;
-                uint16_t end = LINK_TERM;
-                uint32_t join = NO_JOIN;
-                for (int pos = 0; pos < h * w; ++pos) {
-                    const uint32_t old = atomicCAS(&tag[cur], 0u, ((uint32_t)(e + 1) << 16) | (uint32_t)pos);
-                    if (old != 0) {  // joins segment (old >> 16) - 1 at its position old & 0xFFFF
-                        join = old - (1u << 16);
-                        break;
-                    }
-                    const int idx = atomicAdd(&s_nef, 1);
-                    a.ef_cp[efb + idx] = ((uint32_t)cur << 16) | (uint32_t)pos;
-                    a.ef_seg[efb + idx] = (uint16_t)e;
-                    const uint32_t sc = (uint32_t)(word[cur] >> SUCC) & SUCC_NONE;
-                    if (sc == SUCC_NONE || (word[sc] >> CNT) >= SENT_CNT) {
-                        // the path leaves the tile here (an exit) or ends
-                        const int hr = (int)__umulhi((uint32_t)cur, rdiv), rr = hr - 1, cc = cur - hr * W2 - 1;
-                        if (rr == 0 || cc == 0 || rr == h - 1 || cc == w - 1) end = prank[slot_of(rr, cc, h, w)];
-                        break;
-                    }
-                    cur = (int)sc;
-                }
-                segend[e] = end;
-                segjoin[e] = join;
-            }
-            __syncthreads();
-            // the entries' links: follow the joins to the segment that ends
-            const int ne = s_nent;
-            for (int e = tid; e < ne; e += nt) {
-                a.seg_merge[tbase + e] = segjoin[e];
-                const int slot = pent[e];
-                if (prank[slot] != LINK_TERM) continue;  // an exit links to itself
-                int x = e;
-                for (int hop = 0; hop < ne && segjoin[x] != NO_JOIN; ++hop) {
-                    const int y = (int)(segjoin[x] >> 16);
-                    if ((unsigned)y >= (unsigned)ne) break;  // never: joins name walks of this tile
-                    x = y;
-                }
-                a.link[tbase + slot] = segjoin[x] == NO_JOIN ? segend[x] : LINK_TERM;
-            }
-            if (tid == 0)
-                reinterpret_cast<uint4 *>(a.ef_hdr)[t] =
-                    make_uint4((uint32_t)s_nef, (uint32_t)ne, (uint32_t)s_ninf, 0u);
-        } else if constexpr (PASS == 1) {
+        if constexpr (PASS == 1) {
             // Algorithm 2 for the entry cells: the exit each one's path
             // reaches (the last valid cell of the tile on it, if on the
             // perimeter and an exit); one entry per lane at a time
@@ -909,221 +817,193 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 2) k_walk(const __grid_co
 }
 
 // ---------------------------------------------------------------------------
-// pass 2: add the flow entering each tile to the cells downstream of its entry
-// cells.  in(e), the flow arriving at entry e from outside, follows e's path:
-// every cell of segment e gets in(e), and from the cell where segment q joins
-// segment e onwards every cell also gets F(q), the flow at the end of q
-// (in(q) plus the F of every segment joining q).  So the offset of the cell at
-// position j of segment e is in(e) + sum of F(q) over the segments q joining e
-// at positions <= j.  Codes are not needed: pass 1 recorded the segments.
+// Pass 2 for counts (Algorithm 3, Section 3.3).  Pass 1 left A_loc in the
+// output.  The flow arriving at entry cell p from outside, in(p), is the sum
+// of G over the exits outside the tile that drain into p (the resolve added
+// each exit's G to the perimeter slot of the cell it drains into), and it
+// reaches every cell on p's path inside the tile; where paths merge, each
+// adds its own in(p) below the merge.  So this pass stages the tile's codes
+// again (two buffers: the next tile's copy overlaps this tile's walks) and
+// walks each entry's path, adding in(p) to the output as reductions in L2.
+// Integer adds: their order does not matter.  Whether a count of the tile
+// can reach 2^32 is known up front (A_loc plus the tile's whole inflow bounds
+// every count); only then are the adds made as atomics that return the old
+// value, to flag the overflow.
 // ---------------------------------------------------------------------------
-template <int VALM>
-__global__ void __launch_bounds__(128) k_offsets(const __grid_constant__ TileArgs A) {
-    typedef typename std::conditional<VALM == 0, unsigned long long, long long>::type OV;
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int s_emax;
+constexpr int ADDIN_THREADS = 128;
+
+__host__ __device__ inline size_t addin_smem_bytes(int th, int tw, int load) {
+    const size_t cb = code_buf_bytes(th, tw), pb = packed_buf_bytes(th, tw);
+    const size_t bufs = load == LOAD_TMA ? 2 * cb : (load == LOAD_TMA_PACKED ? cb + 2 * pb : cb);
+    const int pm = 2 * th + 2 * tw;
+    return 128 + bufs + (size_t)pm * 8 + (size_t)pm * 2 + 16;
+}
+
+template <int LOAD>
+__global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constant__ TileArgs A,
+                                                          const __grid_constant__ CUtensorMap tmap) {
     const TileArgs &a = A;
-    const int64_t t = blockIdx.x;
-    const uint4 hd = reinterpret_cast<const uint4 *>(a.ef_hdr)[t];
-    const int nef = (int)hd.x, nseg = (int)hd.y, ninf = (int)hd.z;
-    if (nseg == 0 || nef == 0) return;  // no flow enters this tile
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ int s_n, s_flags;
+    __shared__ unsigned long long s_tot;
+    __shared__ __align__(8) uint64_t s_bar[2];
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const RasterDesc &ras = raster_of(a, t);
-    const int lt = (int)(t - ras.tile_base);
-    const int ty = lt / ras.tiles_x, tx = lt - ty * ras.tiles_x;
-    const int64_t R0 = (int64_t)ty * a.th, C0 = (int64_t)tx * a.tw;
-    const int h = (int)min((int64_t)a.th, ras.rows - R0);
-    const int w = (int)min((int64_t)a.tw, ras.cols - C0);
-    const int W2 = a.tw + 2;  // cells are recorded by their word index (r + 1) * W2 + (c + 1)
-    const int P = perim_count(h, w);
-    const int pm = a.pmax;
-    const size_t tb = (size_t)t * pm, eb = (size_t)t * a.th * a.tw, ib = (size_t)t * (pm + 8);
+    const int th = a.th, tw = a.tw, S = tile_stride(tw);
+    const int64_t T = a.T;
 
-    // one segment per entry cell: nseg <= perimeter cells of the nominal tile
-    const int pc = perim_count(a.th, a.tw);
-    u128 *inS = reinterpret_cast<u128 *>(smem);  // [pc] in(e), perimeter-graph scale
-    OV *pre = reinterpret_cast<OV *>(inS);       //   later: prefix sums of F over grouped joins
-    OV *inT = reinterpret_cast<OV *>(inS + pc);  // [pc] in(e), this tile's scale
-    OV *F = inT + pc;                            // [pc] flow at the end of segment e
-    int *par = reinterpret_cast<int *>(F + pc);  // [pc] segment e joins, or -1
-    int *pend = par + pc;                        // [pc] joins into e not yet summed
-    int *mfill = pend;                           //   later: fill counts of the groups
-    int *moff = pend + pc;                       // [pc + 1] start of e's joins in mlist
-    uint16_t *mpos = reinterpret_cast<uint16_t *>(moff + pc + 1);  // [pc] position e joins at
-    uint16_t *mlist = mpos + pc;                 // [pc] joining segments grouped by target
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem) + 127) &
+                                                ~uintptr_t(127));
+    const size_t cbb = code_buf_bytes(th, tw), pbb = packed_buf_bytes(th, tw);
+    // TMA targets: two code buffers (bytes), or two packed stages spread into
+    // one code buffer; plain loads fill the one code buffer
+    uint8_t *cb0 = base;
+    uint8_t *cb1 = LOAD == LOAD_TMA ? base + cbb : base;
+    uint8_t *st0 = base + cbb, *st1 = base + cbb + pbb;
+    uint8_t *p = base + (LOAD == LOAD_TMA ? 2 * cbb : (LOAD == LOAD_TMA_PACKED ? cbb + 2 * pbb : cbb));
+    unsigned long long *pin = reinterpret_cast<unsigned long long *>(p);  // entry -> in(p)
+    p += (size_t)a.pmax * 8;
+    uint16_t *pent = reinterpret_cast<uint16_t *>(p);                    // entry -> its slot
 
-    if (tid == 0) s_emax = INT_MIN;
-    for (int e = tid; e < nseg; e += nt) {
-        inS[e] = 0;
-        pend[e] = 0;
-        moff[e] = 0;
-    }
-    __syncthreads();
-
-    // ---- in(e) = sum of G over the exits outside draining into entry e
-    for (int j = tid; j < ninf; j += nt) {
-        const uint32_t src = a.inf_src[ib + j];
-        const uint16_t lk = a.link[src];
-        if (lk == LINK_TERM) continue;  // never: a cell draining into this tile is an exit
-        const size_t gi = src - src % (uint32_t)pm + lk;
-        if constexpr (VALM == 0)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&inS[a.inf_seg[ib + j]]),
-                      reinterpret_cast<const unsigned long long *>(a.G)[gi]);
-        else
-            atomic_add_u128(&inS[a.inf_seg[ib + j]], reinterpret_cast<const u128 *>(a.G)[gi]);
-    }
-    // ---- the join tree of the segments
-    for (int e = tid; e < nseg; e += nt) {
-        const uint32_t m = a.seg_merge[tb + e];
-        if (m == NO_JOIN) {
-            par[e] = -1;
-            continue;
-        }
-        const int p = (int)(m >> 16);
-        if (p >= nseg) {  // never: a join names a segment of this tile
-            par[e] = -1;
-            continue;
-        }
-        par[e] = p;
-        mpos[e] = (uint16_t)(m & 0xFFFFu);
-        atomicAdd(&pend[p], 1);
-        atomicAdd(&moff[p], 1);
-    }
-    __syncthreads();
-    const int qf = VALM ? fix_scale(a.fcells, *a.maxw) : 0;
-    if constexpr (VALM == 1) {
-        int emax = INT_MIN;
-        for (int e = tid; e < nseg; e += nt) {
-            if (inS[e] == 0) continue;
-            int ex;
-            frexp(fabs(fix2d(inS[e], qf)), &ex);
-            emax = max(emax, ex);
-        }
-        if (emax != INT_MIN) atomicMax(&s_emax, emax);
-        __syncthreads();
-        if (s_emax == INT_MIN) return;  // no inflow at all
-    }
-    // offsets of this tile stay below P * max|in(e)| < 2^(emax + log2 P)
-    int qo = 0;
-    if constexpr (VALM == 1) {
-        int lp = 0;
-        while ((1 << lp) < P) ++lp;
-        qo = 62 - (s_emax + lp + 1);
-    }
-    for (int e = tid; e < nseg; e += nt) {
-        OV v;
-        if constexpr (VALM == 0) {
-            v = (OV)inS[e];
+    // thread 0 keeps the copies' bookkeeping: the parity each buffer's
+    // barrier completes next and whether a copy into it is in flight
+    uint32_t ph0 = 0, ph1 = 0;
+    bool fl0 = false, fl1 = false;
+    auto issue = [&](int64_t tn, int b) {  // one thread: stage tile tn's codes into buffer b
+        const int tyn = (int)(tn / a.one.tiles_x), txn = (int)(tn - (int64_t)tyn * a.one.tiles_x);
+        uint64_t *bar = &s_bar[b];
+        if constexpr (LOAD == LOAD_TMA_PACKED) {  // x in bytes: (C0 - PX0) / 2, a multiple of 16
+            mbar_expect_tx(bar, (uint32_t)((th + 2) * packed_box_bytes(tw)));
+            tma_load_2d(b ? st1 : st0, &tmap, (txn * tw - PX0) / 2, tyn * th - 1, bar);
         } else {
-            const int sh = qf - qo;  // from the graph scale to this tile's scale
-            const i128 si = (i128)inS[e];
-            v = (OV)(sh >= 0 ? (sh < 127 ? (si >> sh) : (si < 0 ? -1 : 0)) : (si << (-sh)));
+            mbar_expect_tx(bar, (uint32_t)((th + 2) * S));
+            tma_load_2d(b ? cb1 : cb0, &tmap, txn * tw - X0, tyn * th - 1, bar);
         }
-        inT[e] = v;
-        F[e] = v;
+        if (b) fl1 = true;
+        else fl0 = true;
+    };
+    if (tid == 0) {
+        s_flags = 0;
+        if (LOAD != LOAD_PLAIN) {
+            mbar_init(&s_bar[0], 1);
+            mbar_init(&s_bar[1], 1);
+            mbar_fence_init();
+        }
     }
     __syncthreads();
+    if (LOAD != LOAD_PLAIN && tid == 0) {
+        if (blockIdx.x < T) issue(blockIdx.x, 0);
+        if (blockIdx.x + gridDim.x < T) issue(blockIdx.x + gridDim.x, 1);
+    }
 
-    // ---- F over the join tree, leaves first (one warp; the rounds end when
-    // no segment became ready, at the latest after nseg rounds)
-    if (warp == 0) {
-        for (int round = 0; round <= nseg; ++round) {
-            bool any = false;
-            for (int e = lane; e < nseg; e += 32)
-                if (pend[e] == 0) {
-                    pend[e] = -2;  // ready: every join into e is summed
-                    any = true;
-                }
-            if (!__any_sync(0xffffffffu, any)) break;
-            __syncwarp();
-            for (int e = lane; e < nseg; e += 32) {
-                if (pend[e] != -2) continue;
-                pend[e] = -1;
-                const int p = par[e];
-                if (p >= 0) {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&F[p]),
-                              (unsigned long long)F[e]);
-                    atomicSub(&pend[p], 1);
-                }
-            }
-            __syncwarp();
-        }
-        // group the joins by target: exclusive scan of the counts
-        int run = 0;
-        for (int b0 = 0; b0 < nseg; b0 += 32) {
-            const int e = b0 + lane;
-            const int cnt = e < nseg ? moff[e] : 0;
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (e < nseg) moff[e] = run + incl - cnt;
-            run += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (lane == 0) moff[nseg] = run;
-    }
-    __syncthreads();
-    for (int e = tid; e < nseg; e += nt) mfill[e] = 0;
-    __syncthreads();
-    for (int e = tid; e < nseg; e += nt) {
-        const int p = par[e];
-        if (p >= 0) mlist[moff[p] + atomicAdd(&mfill[p], 1)] = (uint16_t)e;
-    }
-    __syncthreads();
-    // each target: its joins by position, then running sums of their F
-    for (int p = tid; p < nseg; p += nt) {
-        const int b = moff[p], n = moff[p + 1] - b;
-        for (int i = 1; i < n; ++i) {  // insertion sort (join lists are short)
-            const uint16_t x = mlist[b + i];
-            int j = i - 1;
-            while (j >= 0 && mpos[mlist[b + j]] > mpos[x]) {
-                mlist[b + j + 1] = mlist[b + j];
-                --j;
-            }
-            mlist[b + j + 1] = x;
-        }
-        OV run = 0;
-        for (int i = 0; i < n; ++i) {
-            run += F[mlist[b + i]];
-            pre[b + i] = run;
-        }
-    }
-    __syncthreads();
-
-    // ---- every forest cell: read-modify-write its output
     int ovf = 0;
-    const double inv = ldexp(1.0, -qo);
-    for (int j = tid; j < nef; j += nt) {
-        const uint32_t cp = a.ef_cp[eb + j];
-        const int e = a.ef_seg[eb + j];
-        const int ci = (int)(cp >> 16), pos = (int)(cp & 0xFFFFu);
-        OV o = inT[e];
-        int lo = moff[e], hi = moff[e + 1];  // joins into e at positions <= pos
-        const int b = lo;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((int)mpos[mlist[mid]] <= pos) lo = mid + 1;
-            else hi = mid;
+    int it = 0;
+    bool timed_out = false;
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++it) {
+        const int bi = it & 1;
+        const RasterDesc &ras = raster_of(a, t);
+        const int lt = (int)(t - ras.tile_base);
+        const int ty = lt / ras.tiles_x, tx = lt - ty * ras.tiles_x;
+        const int64_t R0 = (int64_t)ty * th, C0 = (int64_t)tx * tw;
+        const int h = (int)min((int64_t)th, ras.rows - R0);
+        const int w = (int)min((int64_t)tw, ras.cols - C0);
+        const int P = perim_count(h, w);
+        if (tid == 0) {
+            s_n = 0;
+            s_tot = 0;
         }
-        if (lo > b) o += pre[lo - 1];
-        if (!o) continue;
-        const int hr = ci / W2, r = hr - 1, c = ci - hr * W2 - 1;
-        const size_t oi = (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
-        if constexpr (VALM == 0) {
-            uint32_t *p = reinterpret_cast<uint32_t *>(ras.out[0]) + oi;
-            const unsigned long long s64 = (unsigned long long)*p + o;
-            if (s64 >> 32) ovf = 1;
-            *p = (uint32_t)s64;
+        uint8_t *cbuf = LOAD == LOAD_TMA ? (bi ? cb1 : cb0) : cb0;
+        __syncthreads();
+
+        // ---- entry cells: the perimeter slots that receive flow from outside
+        const size_t tbase = (size_t)t * a.pmax;
+        for (int s = tid; s < P; s += nt) {
+            const unsigned long long in = a.infl[tbase + s];
+            if (!in) continue;
+            const int e = atomicAdd(&s_n, 1);
+            pent[e] = (uint16_t)s;
+            pin[e] = in;
+            atomicAdd(&s_tot, in);
+        }
+
+        // ---- codes of the tile and its ring
+        if constexpr (LOAD != LOAD_PLAIN) {
+            if (tid == 0) {
+                const bool ok = mbar_wait(&s_bar[bi], bi ? ph1 : ph0, a.wait_ns);
+                if (ok) {
+                    if (bi) { ph1 ^= 1u; fl1 = false; }
+                    else { ph0 ^= 1u; fl0 = false; }
+                } else {
+                    s_flags |= FA_FLAG_TIMEOUT;
+                }
+            }
+            __syncthreads();
+            if (s_flags & FA_FLAG_TIMEOUT) {
+                timed_out = true;
+                break;
+            }
+            if constexpr (LOAD == LOAD_TMA_PACKED) {
+                const uint8_t *stage = bi ? st1 : st0;
+                const int PB = packed_box_bytes(tw), W4 = S >> 2;
+                for (int i = tid; i < (th + 2) * W4; i += nt) {
+                    const int hr = i / W4, wd = i - hr * W4;
+                    uint32_t v = spread_nibbles(*reinterpret_cast<const uint16_t *>(stage + hr * PB + 2 * wd + 8));
+                    const int64_t keep = ras.cols - (C0 - X0 + 4 * wd);  // cells of the word inside
+                    if (keep < 4) v = keep <= 0 ? 0u : (v & ((1u << (8 * keep)) - 1u));
+                    reinterpret_cast<uint32_t *>(cbuf + hr * S)[wd] = v;
+                }
+                fence_proxy_async();
+                __syncthreads();
+                if (tid == 0 && t + 2 * (int64_t)gridDim.x < T) issue(t + 2 * (int64_t)gridDim.x, bi);
+            }
         } else {
-            float *p = reinterpret_cast<float *>(ras.out[0]) + oi;
-            *p = (float)((double)*p + (double)o * inv);
+            int nb0 = 0;
+            long long fb0 = NO_INDEX;
+            load_codes(ras, cbuf, R0, C0, h, w, S, a.nib != 0, false, nb0, fb0);
+            __syncthreads();
+        }
+
+        // ---- each entry's path inside the tile receives its in(p)
+        const int ne = s_n;
+        const bool safe = s_tot + (unsigned long long)h * w < (1ull << 32);  // no count reaches 2^32
+        uint32_t *out = reinterpret_cast<uint32_t *>(ras.out[0]);
+        for (int e = tid; e < ne; e += nt) {
+            int r, c;
+            cell_of(pent[e], h, w, r, c);
+            const unsigned long long v = pin[e];
+            for (int stp = 0; stp < h * w; ++stp) {
+                uint32_t *o = out + (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
+                if (safe) {
+                    atomicAdd(o, (uint32_t)v);  // result unused: a reduction
+                } else {
+                    const uint32_t old = atomicAdd(o, (uint32_t)v);
+                    if ((v >> 32) || (unsigned long long)old + (uint32_t)v >= (1ull << 32)) ovf = 1;
+                }
+                const int k = cbuf[(r + 1) * S + X0 + c];
+                if (k < 1 || k > 8) break;  // NoFlow: the path ends
+                const int tr = r + dir_dr(k), tc = c + dir_dc(k);
+                if ((unsigned)tr >= (unsigned)h || (unsigned)tc >= (unsigned)w) break;  // leaves the tile
+                if (!vcode(cbuf[(tr + 1) * S + X0 + tc])) break;  // into NoData: the flow leaves
+                r = tr;
+                c = tc;
+            }
+        }
+        if constexpr (LOAD == LOAD_TMA) fence_proxy_async();  // the buffer is refilled by TMA
+        __syncthreads();
+        if constexpr (LOAD == LOAD_TMA) {
+            if (tid == 0 && t + 2 * (int64_t)gridDim.x < T) issue(t + 2 * (int64_t)gridDim.x, bi);
         }
     }
     ovf = __syncthreads_or(ovf);
-    if (tid == 0 && ovf) status_report(a.st, FA_FLAG_OVERFLOW, 0, NO_INDEX);
+    if (tid == 0) {
+        int fl = s_flags | (ovf ? FA_FLAG_OVERFLOW : 0);
+        if (fl) status_report(a.st, fl, 0, NO_INDEX);
+        // a wait that ran out may leave copies in flight into this block's
+        // shared memory: wait for them once more (bounded) before exiting
+        if (LOAD != LOAD_PLAIN && timed_out) {
+            if (fl0) mbar_wait(&s_bar[0], ph0, a.wait_ns);
+            if (fl1) mbar_wait(&s_bar[1], ph1, a.wait_ns);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1144,6 +1024,7 @@ struct ForestArgs {
     uint32_t *J1;  // predecessors still to come
     uint32_t *misc;  // [0] max|w| bits, [1] nodes finished by the walks
     StatusBlock *st;
+    unsigned long long *infl;  // counts: per perimeter slot, the flow arriving from outside, or NULL
 };
 
 // Node values: uint64 counts (unit weights) or 128-bit fixed-point sums.
@@ -1161,6 +1042,8 @@ __global__ void k_forest_init(ForestArgs f) {
     const uint32_t n = f.nexit[tile];
     const int q = f.valm ? fix_scale(f.cells, f.misc[0]) : 0;
     const size_t base = (size_t)tile * f.pmax;
+    if (f.infl)
+        for (int j = lane; j < f.pmax; j += 32) f.infl[base + j] = 0;
     for (uint32_t j = lane; j < n; j += 32) {
         const size_t node = base + j;
         for (int k = 0; k < f.nf; ++k) {
@@ -1258,6 +1141,14 @@ __global__ void k_forest_final(ForestArgs f) {
     const size_t base = (size_t)tile * f.pmax;
     int ncyc = 0;
     for (uint32_t j = lane; j < n; j += 32) ncyc += f.J1[base + j] != 0 && f.J1[base + j] != WALK_START;
+    if constexpr (sizeof(V) == 8) {
+        // counts: each exit's G to the perimeter slot of the cell it drains
+        // into, for the finalising pass (Algorithm 3's offsets)
+        if (f.infl) {
+            const V *x = reinterpret_cast<const V *>(f.x);
+            for (uint32_t j = lane; j < n; j += 32) atomicAdd(&f.infl[f.node_dst[base + j]], x[base + j]);
+        }
+    }
     ncyc = warp_sum(ncyc);
     if (lane == 0 && ncyc) status_report(f.st, FA_FLAG_CYCLE, ncyc, NO_INDEX);
 }
@@ -1319,13 +1210,7 @@ size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry
     w.x = c.take<u128>(SV);
     w.J0 = c.take<uint32_t>(S);
     w.J1 = c.take<uint32_t>(S);
-    const size_t cells = T * (size_t)g.th * g.tw, inf = T * (size_t)(g.pmax + 8);
-    w.ef_hdr = c.take<uint32_t>(T * 4);
-    w.ef_cp = c.take<uint32_t>(cells);
-    w.ef_seg = c.take<uint16_t>(cells);
-    w.seg_merge = c.take<uint32_t>(S);
-    w.inf_src = c.take<uint32_t>(inf);
-    w.inf_seg = c.take<uint16_t>(inf);
+    w.infl = c.take<unsigned long long>(S);
     (void)dry;
     return c.used() + 256;
 }
@@ -1430,15 +1315,32 @@ static cudaError_t launch_walk_k(const Geom &g, const TileArgs &ta, const CUtens
     return cudaGetLastError();
 }
 
-static cudaError_t offsets_config(const Geom &g) {
+// Shared-memory limit and blocks per SM of k_addin<LOAD> (as walk_config).
+template <int LOAD>
+static cudaError_t addin_config(const Geom &g, int &blocks_per_sm) {
     static int configured = 0;
-    return set_smem(k_offsets<0>, offsets_smem_bytes(g.th, g.tw), configured);
+    static int per_sm = 0, per_sm_smem = -1;
+    const size_t smem = addin_smem_bytes(g.th, g.tw, LOAD);
+    cudaError_t e = set_smem(k_addin<LOAD>, smem, configured);
+    if (e != cudaSuccess) return e;
+    if (per_sm_smem != (int)smem) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_addin<LOAD>, ADDIN_THREADS, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        per_sm_smem = (int)smem;
+    }
+    blocks_per_sm = per_sm;
+    return cudaSuccess;
 }
 
-static cudaError_t launch_offsets(const Geom &g, const TileArgs &ta, cudaStream_t s) {
-    cudaError_t e = offsets_config(g);
+template <int LOAD>
+static cudaError_t launch_addin_k(const Geom &g, const TileArgs &ta, const CUtensorMap &m,
+                                  cudaStream_t s) {
+    int per_sm = 1;
+    cudaError_t e = addin_config<LOAD>(g, per_sm);
     if (e != cudaSuccess) return e;
-    k_offsets<0><<<(unsigned)ta.T, 128, offsets_smem_bytes(g.th, g.tw), s>>>(ta);
+    const unsigned grid = (unsigned)std::min<int64_t>(ta.T, (int64_t)per_sm * sm_count());
+    k_addin<LOAD><<<grid, ADDIN_THREADS, addin_smem_bytes(g.th, g.tw, LOAD), s>>>(ta, m);
     return cudaGetLastError();
 }
 
@@ -1454,6 +1356,17 @@ static cudaError_t launch_walk(const Geom &g, const TileArgs &ta, const uint8_t 
     return launch_walk_k<MODE, PASS, LOAD_PLAIN>(g, ta, m, s);
 }
 
+static cudaError_t launch_addin(const Geom &g, const TileArgs &ta, const uint8_t *codes, int64_t pc,
+                                const uint8_t *mask, bool allow_tma, cudaStream_t s) {
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    const bool packed = g.code_format == FA_CODES_NIBBLE;
+    if (allow_tma && make_code_map(g, codes, pc, mask, packed, &m))
+        return packed ? launch_addin_k<LOAD_TMA_PACKED>(g, ta, m, s)
+                      : launch_addin_k<LOAD_TMA>(g, ta, m, s);
+    return launch_addin_k<LOAD_PLAIN>(g, ta, m, s);
+}
+
 // Sets the kernels' shared-memory limits and caches their occupancy and the SM
 // count ahead of a stream capture (done on first use otherwise).  Batches
 // never stage codes by TMA.
@@ -1462,7 +1375,7 @@ cudaError_t prepare_forward(const Geom &g, int val_mode) {
     cudaError_t e = val_mode ? walk_config<1, 1, LOAD_PLAIN>(g, per_sm)
                              : walk_config<0, 1, LOAD_PLAIN>(g, per_sm);
     if (e == cudaSuccess && val_mode) e = walk_config<1, 2, LOAD_PLAIN>(g, per_sm);
-    if (e == cudaSuccess && !val_mode) e = offsets_config(g);
+    if (e == cudaSuccess && !val_mode) e = addin_config<LOAD_PLAIN>(g, per_sm);
     sm_count();
     return e;
 }
@@ -1490,12 +1403,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     ta.G = ws.x;
     ta.st = st;
     ta.maxw = ws.misc;
-    ta.ef_hdr = ws.ef_hdr;
-    ta.ef_cp = ws.ef_cp;
-    ta.ef_seg = ws.ef_seg;
-    ta.seg_merge = ws.seg_merge;
-    ta.inf_src = ws.inf_src;
-    ta.inf_seg = ws.inf_seg;
+    ta.infl = ws.infl;
     ta.wait_ns = kWaitLimitNs;
 
     timing_mark(0, s);
@@ -1521,6 +1429,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     f.J1 = ws.J1;
     f.misc = ws.misc;
     f.st = st;
+    f.infl = val_mode ? nullptr : ws.infl;
     const unsigned fb = (unsigned)((f.tiles * 32 + 255) / 256);
     if (val_mode) {
         k_forest_init<u128><<<fb, 256, 0, s>>>(f);
@@ -1539,7 +1448,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     if (e != cudaSuccess) return e;
     timing_mark(2, s);
     e = val_mode ? launch_walk<1, 2>(g, ta, tma_codes, tma_pc, tma_mask, tma, s)
-                 : launch_offsets(g, ta, s);
+                 : launch_addin(g, ta, tma_codes, tma_pc, tma_mask, tma, s);
     timing_mark(3, s);
     timing_set_count(3);
     return e;

@@ -71,23 +71,15 @@ struct Carver {
 // values sit at node * nf + f.
 struct FwdWork {
     void *status;          // StatusBlock (16 bytes)
-    uint32_t *misc;        // [0] max |w| bits, [1..] per-round active counts
+    uint32_t *misc;        // [0] max |w| bits, [1] nodes finished by the resolve walks
     uint32_t *nexit;       // [T] exits per tile
     uint16_t *link;        // [T*pmax] perimeter slot -> exit rank its path reaches, 0xFFFF = none
     uint32_t *node_dst;    // [T*pmax] exit rank -> global slot id of its target cell
     double *node_val;      // [T*pmax*nf] exit rank -> tile-local accumulation A_loc
     void *x;               // [T*pmax*nf] u128 forest values (G after resolve)
     uint32_t *J0, *J1;     // [T*pmax] successor node, predecessors still to come
-    // counts: the entry forest of every tile (the union of the in-tile paths
-    // downstream of its entry cells), recorded by pass 1 for pass 2
-    uint32_t *ef_hdr;      // [T*4] entry-forest cells, segments, inflow links, 0
-    uint32_t *ef_cp;       // [T*th*tw] cell word index << 16 | position along its segment
-    uint16_t *ef_seg;      // [T*th*tw] segment of the cell
-    uint32_t *seg_merge;   // [T*pmax] segment -> (segment << 16 | position on it)
-                           //   where it joins, 0xFFFFFFFF if it ends at an exit or sink
-    uint32_t *inf_src;     // [T*(pmax+8)] inflow link: slot id of the exit outside
-    uint16_t *inf_seg;     // [T*(pmax+8)] inflow link: segment it feeds
-    int kmax;              // number of jump rounds
+    unsigned long long *infl;  // [T*pmax] counts: flow arriving at each perimeter slot from outside
+    int kmax;              // rounds of a pointer-jumping solve over T*pmax nodes (absorption)
 };
 
 size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry);

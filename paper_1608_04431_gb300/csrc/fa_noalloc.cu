@@ -43,11 +43,9 @@ extern "C" fa_status fa_accumulate_noalloc(const uint8_t *codes, int64_t rows, i
     if (out_dtype != FA_OUT_U32 && out_dtype != FA_OUT_F32) return FA_ERR_INVALID_ARG;
     if (out_dtype == FA_OUT_U32 && weights) return FA_ERR_INVALID_ARG;
     if (!forward_tile_ok(g, out_dtype == FA_OUT_F32 ? 1 : 0)) return FA_ERR_INVALID_ARG;
-    {
-        FwdWork need;
-        if (carve_forward(nullptr, 0, g, need, true) > (size_t)FA_NOALLOC_SCRATCH_BYTES)
-            return FA_ERR_TOO_LARGE;
-    }
+    // the limit callers can query: fa_workspace_size (the forward pass needs
+    // no more than that)
+    if (fa_workspace_size(rows, cols, opts) > (size_t)FA_NOALLOC_SCRATCH_BYTES) return FA_ERR_TOO_LARGE;
     const bool empty = rows == 0 || cols == 0;
     if (!empty) {
         if (!codes || !out) return FA_ERR_INVALID_ARG;

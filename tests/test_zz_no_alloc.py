@@ -109,10 +109,10 @@ def test_noalloc_rejects_rasters_beyond_its_buffer():
     assert st == fa.FA_ERR_TOO_LARGE
 
 
-@pytest.mark.parametrize("n,fits", [(2600, True), (2688, True), (2689, False)])
+@pytest.mark.parametrize("n,fits", [(4700, True), (4800, True), (4801, False)])
 def test_noalloc_size_boundary(n, fits):
     """The limit stated in include/fa.h for the default 64 x 64 tiles: square
-    rasters up to 2688 x 2688 pass the size check, 2689 x 2689 does not.  NULL
+    rasters up to 4800 x 4800 pass the size check, 4801 x 4801 does not.  NULL
     buffers make an accepted size fail the later pointer check, so nothing is
     ever enqueued."""
     lib = fa._lib.load()
