@@ -194,6 +194,52 @@ def traffic_for(kernel: str, cells: int = ROWS * COLS, path=None):
     return int(round(rec["bytes_per_launch"] * cells / rec.get("launch_cells", cells)))
 
 
+# forward kernels by phase, as ncu names them ("void fa::k_walk<0, 1, 1>(fa::TileArgs, ...)")
+TRAFFIC_PHASES = [
+    ("pass1_tile_solve", r"k_walk<0, 1,"),
+    ("perimeter_graph_resolve", r"k_forest_"),
+    ("pass2_tile_finalize", r"k_addin<"),
+    ("f32_pass1_tile_solve", r"k_walk<1, 1,"),
+    ("f32_pass2_tile_solve", r"k_walk<1, 2,"),
+]
+
+
+def record_traffic(csv_path: str, cells: int, desc: str, out_path=None) -> dict:
+    """profiles/traffic.json from an ncu --csv capture with the metrics
+    dram__bytes_read.sum, dram__bytes_write.sum and smsp__inst_executed.sum:
+    per phase, the bytes and warp instructions of one call (the first
+    captured launches of the phase's kernels), with the hash of the kernel
+    sources they belong to."""
+    import csv
+
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    launches = {}
+    for r in csv.DictReader(lines):
+        d = launches.setdefault(int(r["ID"]), {"name": r["Kernel Name"]})
+        d[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+    ids = sorted(launches)
+    out = {}
+    for phase, key in TRAFFIC_PHASES:
+        hit = [i for i in ids if key in launches[i]["name"]]
+        if not hit:
+            continue
+        # one call: the resolve is five launches, a tile pass one
+        first = hit[:5 if phase == "perimeter_graph_resolve" else 1]
+        rd = sum(launches[i].get("dram__bytes_read.sum", 0.0) for i in first)
+        wr = sum(launches[i].get("dram__bytes_write.sum", 0.0) for i in first)
+        inst = sum(launches[i].get("smsp__inst_executed.sum", 0.0) for i in first)
+        out[phase] = {"kernel": "; ".join(sorted({launches[i]["name"].split("(")[0] for i in first})),
+                      "launches": len(first), "bytes_per_launch": int(rd + wr),
+                      "dram_read": rd, "dram_write": wr,
+                      "warp_instructions_per_launch": int(inst), "launch_cells": int(cells),
+                      "measured_on": desc, "source_sha1": source_sha1()}
+    with open(out_path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    return out
+
+
 def issue_roofline(kernel: str, ms: float, sm_mhz: float, sms: int, path=None,
                    cells: int = ROWS * COLS):
     """The kernel's achieved instruction issue rate against the GPU's ceiling:
@@ -499,13 +545,106 @@ def host_available_bytes() -> int:
     return 0
 
 
+class HostPinned:
+    """A host array whose pages are page-locked by cudaHostRegister, so that
+    copies to and from it run at the link's rate.  Unlike the caching host
+    allocator behind pin_memory(), which rounds a request up to a power of
+    two (80 GB would take 128 GB), it locks exactly the bytes it holds.
+    close() unlocks them; the array is freed with the object."""
+
+    def __init__(self, shape, dtype):
+        import torch
+
+        self.a = np.empty(shape, dtype)
+        self.t = torch.from_numpy(self.a)
+        err = torch.cuda.cudart().cudaHostRegister(self.a.ctypes.data, self.a.nbytes, 0)
+        if int(err) != 0:
+            raise RuntimeError(f"cudaHostRegister of {self.a.nbytes / 1e9:.1f} GB failed ({int(err)})")
+        self.locked = True
+
+    def close(self):
+        import torch
+
+        if self.locked:
+            torch.cuda.cudart().cudaHostUnregister(self.a.ctypes.data)
+            self.locked = False
+
+
+def parity_counts_u32(codes_h, got_h):
+    """The headline's complete check (oracle): the Eq. 1 residual at every
+    cell and conservation, over row bands on all host cores."""
+    import oracle
+
+    t0 = time.perf_counter()
+    v = oracle.verify_counts_u32(codes_h, got_h, threads=os.cpu_count() or 1, band=1024)
+    return {"vs_oracle": "Eq. 1 residual at every cell and conservation" + (
+                " exact" if v["mismatches"] == 0 and v["conserved"] else
+                (" (conserved modulo 2^32)" if v["mismatches"] == 0 and v["conserved_mod_2_32"]
+                 else ": MISMATCH")),
+            "residual_mismatches": v["mismatches"], "first_mismatch": v["first"],
+            "outlet_sum": v["outlet_sum"], "valid_cells": v["n_valid"],
+            "check_s": round(time.perf_counter() - t0, 1),
+            "note": "the residual check is complete for integer counts on an acyclic raster"}
+
+
+def parity_counts_u64(codes_h, o64):
+    """The same complete check on uint64 counts (no wrap-around)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    v = oracle.verify_counts_u32(codes_h, o64, threads=os.cpu_count() or 1, band=1024)
+    return {"vs_oracle": "uint64 Eq. 1 residual at every cell and exact conservation" + (
+                "" if v["mismatches"] == 0 and v["conserved"] else ": MISMATCH"),
+            "residual_mismatches": v["mismatches"], "first_mismatch": v["first"],
+            "outlet_sum": v["outlet_sum"], "valid_cells": v["n_valid"],
+            "check_s": round(time.perf_counter() - t0, 1)}
+
+
+F32_SAMPLE_SEED, F32_SAMPLE_N, F32_BORDER_N = 504, 4096, 256
+
+
+def parity_f32_sampled(codes_h, w_d, out_d):
+    """Float32 sums at full size on sampled cells: 4096 cells uniform over the
+    raster and 256 on its border (outlets), seeded; each cell's FP64 value
+    comes from the oracle's search of its upstream area, and the result must
+    lie within 2e-5 of it, relatively (weights >= 0)."""
+    import torch
+
+    import oracle
+
+    R, C = codes_h.shape
+    g = np.random.default_rng(F32_SAMPLE_SEED)
+    inner = g.integers(0, R * C, F32_SAMPLE_N)
+    side = g.integers(0, 4, F32_BORDER_N)
+    t = g.integers(0, max(R, C), F32_BORDER_N)
+    br = np.where(side == 0, 0, np.where(side == 1, R - 1, t % R))
+    bc = np.where(side == 2, 0, np.where(side == 3, C - 1, t % C))
+    cells = np.unique(np.concatenate([inner, br * C + bc])).astype(np.int64)
+    got = out_d.view(-1)[torch.from_numpy(cells).to(out_d.device)].double().cpu().numpy()
+    t0 = time.perf_counter()
+    w_h = w_d.cpu().numpy()
+    ref, size = oracle.upstream_sums(codes_h, cells, w_h, threads=os.cpu_count() or 1)
+    dt = time.perf_counter() - t0
+    del w_h
+    ok = size > 0
+    err = np.abs(got[ok] - ref[ok])
+    rel = err / np.maximum(np.abs(ref[ok]), 1e-300)
+    return {"vs_oracle": ("within 2e-5 relative on every sampled cell"
+                          if bool((err <= 2e-5 * np.abs(ref[ok])).all()) else "MISMATCH"),
+            "cells_checked": int(ok.sum()), "sample": f"{F32_SAMPLE_N} uniform + {F32_BORDER_N} "
+            f"border cells (seed {F32_SAMPLE_SEED})", "max_rel_err": float(rel.max()),
+            "largest_area_cells": int(size.max()), "area_cells_total": int(size[ok].sum()),
+            "check_s": round(dt, 1),
+            "oracle": "FP64 sum over each cell's upstream area, searched against the flow"}
+
+
 def leg_ooc(fa, codes_h, reps: int):
     """Out-of-core counts: the headline raster's codes in pinned host memory,
     uint64 counts written to pinned host memory, solved on the device in
     16384 x 16384 outer blocks (two code copies in, one uint64 copy out per
     cell).  Timed on the host clock around the synchronous call.  Returns the
-    record and the uint64 counts (as int64) for the parity check, or (record,
-    None) when the host lacks the memory for the output."""
+    record and the page-locked uint64 counts for the parity check, or
+    (record, None) when the host lacks the memory for the output."""
     import torch
 
     R, C = codes_h.shape
@@ -515,7 +654,8 @@ def leg_ooc(fa, codes_h, reps: int):
         return {"skipped": f"host memory: {avail / 1e9:.0f} GB available, the uint64 output "
                            f"needs {need / 1e9:.0f} GB"}, None
     c_h = torch.from_numpy(codes_h)
-    out64 = torch.empty((R, C), dtype=torch.int64).pin_memory()
+    pinned = HostPinned((R, C), np.int64)
+    out64 = pinned.t
     opts = fa.options(None)
     n_ws = fa.fa_ooc_workspace_size(R, C, 0, 0, opts)
     work = torch.empty(n_ws, dtype=torch.uint8, device="cuda")
@@ -535,7 +675,7 @@ def leg_ooc(fa, codes_h, reps: int):
            "out": "uint64 (exact beyond 2^32)"}
     del work
     torch.cuda.empty_cache()
-    return rec, out64
+    return rec, pinned
 
 
 def headline_codes(args, dev):
@@ -589,6 +729,13 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up and timed steps (for ncu): no clock sampling, phase "
                          "timing, extra legs or CPU baseline")
+    ap.add_argument("--profile-f32", action="store_true",
+                    help="with --profile: after the timed steps, three calls of the float32 "
+                         "form (w ~ U[0, 1)) on the same raster")
+    ap.add_argument("--record-traffic", metavar="CSV",
+                    help="write profiles/traffic.json from an ncu --csv capture of the forward "
+                         "kernels (dram bytes, warp instructions) and exit; the capture's "
+                         "raster is described by --workload/--scale-coarse/--size")
     ap.add_argument("--profile-absorb", action="store_true",
                     help="with --profile: after the timed steps, three calls of the absorption "
                          "form on the same raster")
@@ -599,6 +746,16 @@ def main():
     args = ap.parse_args()
     if args.size != ROWS:
         ROWS = COLS = args.size
+    if args.record_traffic:
+        if args.workload == "scale":
+            n = (args.scale_coarse * SCALE_F) ** 2
+            desc = (f"{args.scale_coarse * SCALE_F}^2 band-generated scale raster "
+                    f"(coarse {args.scale_coarse}^2 x{SCALE_F}, seeds {SCALE_SEED}/{SCALE_NSEED})")
+        else:
+            n = ROWS * COLS
+            desc = f"{ROWS}^2 spectral DEM seed {SEED}"
+        print(json.dumps(record_traffic(args.record_traffic, n, desc), indent=1))
+        return
     if args.profile:
         args.no_extra = args.no_cpu_baseline = True
     if args.warmup < 3:
@@ -670,6 +827,18 @@ def main():
     value = job_throughput(cells, ms_max, ws)
 
     if args.profile:
+        if args.profile_f32:
+            g = torch.Generator(device=dev)
+            g.manual_seed(WSEED)
+            w_d = torch.rand(codes_d.shape, generator=g, device=dev, dtype=torch.float32)
+            out_f = torch.empty(codes_d.shape, dtype=torch.float32, device=dev)
+            for _ in range(3):
+                s = fa.fa_accumulate(codes_d, w_d, None, out_f, fa.FA_OUT_F32, work, opts, None,
+                                     stream)
+                if s != fa.FA_OK:
+                    raise fa.FlowAccError(s, "fa_accumulate f32")
+            torch.cuda.synchronize()
+            del w_d, out_f
         if args.profile_absorb:
             g = torch.Generator(device=dev)
             g.manual_seed(WSEED)
@@ -732,13 +901,16 @@ def main():
     if overflow:
         line["status"] = "FA_WARN_OVERFLOW (a count reached 2^32; outputs are mod 2^32)"
 
-    got_h = codes_h = ooc_out = None
+    codes_h = None
     forms = {}
+    check = not args.no_cpu_baseline and rank == 0  # the oracle's checks run on rank 0
     if not args.no_extra:
         # end to end through the public API from pinned host buffers
-        h_codes = torch.empty((R, C), dtype=torch.uint8).pin_memory()
+        pc = HostPinned((R, C), np.uint8)
+        h_codes = pc.t
         h_codes.copy_(codes_d)
-        h_out = torch.empty((R, C), dtype=torch.uint32).pin_memory()
+        po = HostPinned((R, C), np.int32)
+        h_out = po.t
         ke = 3 if cells > 2e9 else max(5, args.steps // 4)
 
         def step_e2e():
@@ -757,10 +929,21 @@ def main():
         line["e2e"] = {"value": job_throughput(cells, mse, ws), "unit": "cells/s",
                        "h2d_bytes_per_step": int(cells), "d2h_bytes_per_step": int(cells * 4),
                        "ms_per_step": mse, "steps": ke}
-        codes_h = h_codes.numpy()
-        got_h = h_out.view(torch.int32).numpy().view(np.uint32)
+        codes_h = pc.a
+        if check:
+            line["parity"] = parity_counts_u32(codes_h, po.a.view(np.uint32))
+        del h_out
+        po.close()
+        del po
+
+        # out of core: the same raster from host memory, uint64 counts to host memory
         ooc_rec, ooc_out = leg_ooc(fa, codes_h, 2)
+        if ooc_out is not None:
+            if check:
+                ooc_rec["parity"] = parity_counts_u64(codes_h, ooc_out.a.view(np.uint64))
+            ooc_out.close()
         forms["out_of_core"] = ooc_rec
+        del ooc_out
 
         # float32 weights on the headline raster: w ~ U[0, 1), drawn on the device
         del out_d
@@ -786,9 +969,9 @@ def main():
             "workload": WORKLOAD, "ms": msf_h, "cells_per_s": cells / (msf_h / 1e3),
             "tile": list(tile), "bytes_per_cell": BYTES_PER_CELL_F32,
             "hbm_frac_step": cells * BYTES_PER_CELL_F32 / (msf_h / 1e3) / 1e9 / peak,
-            "status": int(stf),
-            "parity_vs_oracle": ("FP32 parity at 1e10 unverified: the FP64 oracle needs about "
-                                 "300 GB of host memory" if cells > 2e9 else "see forms")}
+            "status": int(stf)}
+        if check:
+            forms["headline_f32"]["parity"] = parity_f32_sampled(codes_h, w_d, outf)
         del w_d, outf
     del codes_d, work
     torch.cuda.empty_cache()
@@ -817,41 +1000,6 @@ def main():
                                           f"raster as a raster of their own ({sample.size:.3g} "
                                           f"cells, {dt:.1f} s)"}
         del res
-        if got_h is not None:
-            t0 = time.perf_counter()
-            v = oracle.verify_counts_u32(codes_h, got_h, threads=os.cpu_count() or 1,
-                                         band=1024)
-            line["parity"] = {
-                "vs_oracle": "Eq. 1 residual at every cell and conservation" + (
-                    " exact" if v["mismatches"] == 0 and v["conserved"] else
-                    (" (conserved modulo 2^32)" if v["mismatches"] == 0 and v["conserved_mod_2_32"]
-                     else ": MISMATCH")),
-                "residual_mismatches": v["mismatches"], "first_mismatch": v["first"],
-                "outlet_sum": v["outlet_sum"], "valid_cells": v["n_valid"],
-                "check_s": round(time.perf_counter() - t0, 1),
-                "note": "the residual check is complete for integer counts on an acyclic raster"}
-        if ooc_out is not None:
-            t0 = time.perf_counter()
-            o64 = ooc_out.numpy().view(np.uint64)
-            v = oracle.verify_counts_u32(codes_h, o64, threads=os.cpu_count() or 1, band=1024)
-            from concurrent.futures import ThreadPoolExecutor
-
-            def band_cmp(r):  # numpy releases the interpreter lock in these calls
-                b = o64[r:r + 1024]
-                return (got_h is not None and np.array_equal(b.astype(np.uint32), got_h[r:r + 1024]),
-                        int(b.max()))
-
-            with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-                cmp = list(ex.map(band_cmp, range(0, o64.shape[0], 1024)))
-            same = all(c[0] for c in cmp)
-            forms["out_of_core"]["parity"] = {
-                "vs_oracle": "uint64 Eq. 1 residual at every cell and exact conservation" + (
-                    "" if v["mismatches"] == 0 and v["conserved"] else ": MISMATCH"),
-                "residual_mismatches": v["mismatches"], "outlet_sum": v["outlet_sum"],
-                "valid_cells": v["n_valid"], "max_count": max(c[1] for c in cmp),
-                "low_32_bits_equal_in_core": same,
-                "check_s": round(time.perf_counter() - t0, 1)}
-            del o64, ooc_out
         if dem_got is not None:
             dcodes = synth.dem_codes(ROWS, COLS, SEED)
             ref = oracle.counts(dcodes).values.astype(np.uint32)

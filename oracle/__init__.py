@@ -87,6 +87,8 @@ def _configure(lib):
     lib.fa_oracle_outlet_sum_u64.argtypes = [p, i64, i64, i64, p, i64, p, i64, i64, i64,
                                              ctypes.POINTER(ctypes.c_uint64), pi64]
     lib.fa_oracle_outlet_sum_u64.restype = None
+    lib.fa_oracle_upstream_sums.argtypes = [p, i64, i64, i64, p, i64, p, i64, p, i64, p, p]
+    lib.fa_oracle_upstream_sums.restype = ctypes.c_int64
     return lib
 
 
@@ -264,6 +266,41 @@ def outlet_sum_u64(codes, A, r_begin: int = 0, r_end: int | None = None, mask=No
                                      int(R if r_end is None else r_end), ctypes.byref(s),
                                      ctypes.byref(nv))
     return int(s.value), int(nv.value)
+
+
+def upstream_sums(codes, cells, w=None, mask=None, threads: int = 1):
+    """Eq. 1's solution at the given flat cell indices (r * cols + c), each
+    from its upstream area gathered by a search against the flow: (FP64
+    values, area sizes); size -1 (value NaN) marks a cell on a cycle.  Work
+    is the total size of the areas, so it suits samples of a raster of any
+    size; queries are split over `threads` host threads."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    codes, mask = _prep(codes, mask)
+    R, C = codes.shape
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float32)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.empty(cells.size, dtype=np.float64)
+    size = np.empty(cells.size, dtype=np.int64)
+    lib = _load()
+    chunks = np.array_split(np.arange(cells.size), max(1, min(threads, cells.size)))
+
+    def one(ix):
+        if ix.size == 0:
+            return 0
+        lo = int(ix[0])
+        n = lib.fa_oracle_upstream_sums(
+            _p(codes), R, C, C, _p(mask), C, _p(w), C,
+            ctypes.c_void_p(cells.ctypes.data + 8 * lo), int(ix.size),
+            ctypes.c_void_p(out.ctypes.data + 8 * lo), ctypes.c_void_p(size.ctypes.data + 8 * lo))
+        if n < 0:
+            raise MemoryError("upstream_sums: stack allocation failed")
+        return n
+
+    with ThreadPoolExecutor(max_workers=len(chunks)) as ex:
+        list(ex.map(one, chunks))
+    return out, size
 
 
 def verify_counts_u32(codes, A, threads: int = 1, band: int = 1024, mask=None):

@@ -416,6 +416,67 @@ void fa_oracle_outlet_sum_u64(const uint8_t *codes, int64_t rows, int64_t cols, 
 }
 
 /*
+ * Eq. 1's solution at chosen cells, one query at a time, from its plain
+ * meaning: A(p) is the sum of w over p's upstream area, the valid cells whose
+ * flow path passes through p, p included.  The area is gathered by a
+ * depth-first search against the flow: from a cell u, every valid neighbour n
+ * with d(n) = u belongs to it.  Each cell has a single downstream cell, so
+ * the area is a tree and no cell is reached twice; only a query on a cycle
+ * would never end, so the search stops after as many cells as the raster has
+ * and reports size -1 (value NaN) for it.  Sums in FP64, w == NULL meaning
+ * unit weights; a NoData query gets 0 and size 0.  Returns the number of
+ * cells visited over all queries, or -1 if the stack could not be allocated.
+ */
+int64_t fa_oracle_upstream_sums(const uint8_t *codes, int64_t rows, int64_t cols, int64_t pitch,
+                                const uint8_t *mask, int64_t mpitch, const float *w,
+                                int64_t wpitch, const int64_t *query, int64_t nq, double *out,
+                                int64_t *size) {
+    raster R = {codes, mask, rows, cols, pitch, mpitch};
+    int64_t cap = 1024, visited = 0;
+    int64_t *stack = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+    if (!stack) return -1;
+    for (int64_t q = 0; q < nq; ++q) {
+        const int64_t p = query[q];
+        out[q] = 0.0;
+        size[q] = 0;
+        if (!valid_cell(&R, p / cols, p % cols)) continue;
+        double sum = 0.0;
+        int64_t n = 0, top = 0;
+        stack[top++] = p;
+        while (top > 0 && n <= rows * cols) {
+            const int64_t u = stack[--top];
+            const int64_t r = u / cols, c = u % cols;
+            sum += w ? (double)w[r * wpitch + c] : 1.0;
+            ++n;
+            for (int k = 1; k <= 8; ++k) {
+                const int64_t rr = r + ODR[k], cc = c + ODC[k];
+                if (!valid_cell(&R, rr, cc) || downstream(&R, rr, cc) != u) continue;
+                if (top == cap) {
+                    int64_t *grown = (int64_t *)realloc(stack, (size_t)(2 * cap) * sizeof(int64_t));
+                    if (!grown) {
+                        free(stack);
+                        return -1;
+                    }
+                    stack = grown;
+                    cap *= 2;
+                }
+                stack[top++] = rr * cols + cc;
+            }
+        }
+        visited += n;
+        if (top > 0) {  /* the bound ran out: p lies on a cycle */
+            out[q] = 0.0 / 0.0;
+            size[q] = -1;
+        } else {
+            out[q] = sum;
+            size[q] = n;
+        }
+    }
+    free(stack);
+    return visited;
+}
+
+/*
  * D8 flow codes from elevations, the step before accumulation (Section 2: a
  * non-divergent metric sends a cell's flow to a single neighbour; D8 takes the
  * steepest descent; flats are routed towards lower terrain only; Fig. 1 treats

@@ -604,3 +604,58 @@ def test_uint64_checks_do_not_wrap(oracle_mod):
     assert s - nv == 1 << 32
     v = oracle_mod.verify_counts_u32(east, Ae.astype(np.int64))
     assert not v["conserved"] and v["conserved_mod_2_32"] and v["mismatches"] == 1
+
+
+# ---------------------------------------------------------------------------
+# upstream-area sums at chosen cells (the per-cell definition of Eq. 1's solution)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", _golden.names())
+def test_upstream_sums_golden(oracle_mod, name):
+    """Every exact cell of each hand-worked fixture, queried one by one, gives
+    the fixture's count and, where it has weights, its weighted sum; cycle
+    cells report size -1; NoData cells 0."""
+    fx = _golden.load(name)
+    codes = fx["codes"]
+    mask = fx.get("mask")
+    cells = np.arange(codes.size)
+    if "counts" in fx:
+        v, n = oracle_mod.upstream_sums(codes, cells, None, mask)
+        state = fx.get("state")
+        exact = (state == 1).ravel() if state is not None else np.ones(codes.size, bool)
+        np.testing.assert_array_equal(v[exact], fx["counts"].ravel()[exact].astype(np.float64))
+        np.testing.assert_array_equal(n[exact], fx["counts"].ravel()[exact])
+        if state is not None:
+            assert (n[(state == 2).ravel()] == -1).all()
+    if "weighted" in fx:
+        v, _ = oracle_mod.upstream_sums(codes, cells, fx["weights"], mask)
+        np.testing.assert_array_equal(v, fx["weighted"].ravel())
+
+
+@pytest.mark.parametrize("R,C", [(1, 9), (6, 7), (11, 5)])
+def test_upstream_sums_serpentine(oracle_mod, R, C):
+    """One path through every cell: the cell k steps along it has k + 1 cells
+    upstream, and with weights w their prefix sum."""
+    codes = synth.serpentine_codes(R, C)
+    k = synth.serpentine_index(R, C).ravel()
+    v, n = oracle_mod.upstream_sums(codes, np.arange(R * C), threads=3)
+    np.testing.assert_array_equal(n, k + 1)
+    w = synth.uniform_weights((R, C), 71)
+    order = np.argsort(k)
+    prefix = np.cumsum(w.ravel()[order].astype(np.float64))
+    v, _ = oracle_mod.upstream_sums(codes, np.arange(R * C), w)
+    np.testing.assert_allclose(v[order], prefix, rtol=1e-12)
+
+
+def test_upstream_sums_match_the_queue_solution(oracle_mod):
+    """Two formulations of Eq. 1, the search against the flow per cell and
+    the queue order over the raster, agree on a DEM with NoData, a mask and
+    weights (FP64; sums in different orders)."""
+    codes = synth.dem_codes(70, 90, 72)
+    mask = (synth.rng(73).random(codes.shape) < 0.02).astype(np.uint8)
+    w = synth.lognormal_weights(codes.shape, 74)
+    ref = oracle_mod.weighted(codes, w, mask)
+    cells = synth.rng(75).choice(codes.size, 500, replace=False)
+    v, n = oracle_mod.upstream_sums(codes, cells, w, mask, threads=4)
+    np.testing.assert_allclose(v, ref.values.ravel()[cells], rtol=1e-12)
+    cnt = oracle_mod.counts(codes, mask)
+    np.testing.assert_array_equal(n, cnt.values.ravel()[cells].astype(np.int64))

@@ -107,6 +107,12 @@ C_MUTANTS = {
     "uint64 conservation: every valid cell counted as a terminal": (
         "            if (downstream(&R, r, c) < 0) s += A64[r * apitch + c];",
         "            s += A64[r * apitch + c];"),
+    "upstream sums: the query cell's own weight skipped": (
+        "            sum += w ? (double)w[r * wpitch + c] : 1.0;",
+        "            sum += u == p ? 0.0 : (w ? (double)w[r * wpitch + c] : 1.0);"),
+    "upstream sums: every valid neighbour taken as upstream": (
+        "                if (!valid_cell(&R, rr, cc) || downstream(&R, rr, cc) != u) continue;",
+        "                if (!valid_cell(&R, rr, cc)) continue;"),
     "D8: ties go to the later direction": (
         "                if (slope > best) {", "                if (slope >= best) {"),
     "D8: no distance factor on diagonals": (
