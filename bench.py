@@ -32,6 +32,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -197,10 +198,11 @@ def traffic_for(kernel: str, cells: int = ROWS * COLS, path=None):
 # forward kernels by phase, as ncu names them ("void fa::k_walk<0, 1, 1>(fa::TileArgs, ...)")
 TRAFFIC_PHASES = [
     ("pass1_tile_solve", r"k_walk<0, 1,"),
-    ("perimeter_graph_resolve", r"k_forest_"),
-    ("pass2_tile_finalize", r"k_addin<"),
+    ("perimeter_graph_resolve", r"k_forest_\w+<unsigned long long>"),
+    ("pass2_tile_finalize", r"k_addin<\d, 0>"),
     ("f32_pass1_tile_solve", r"k_walk<1, 1,"),
-    ("f32_pass2_tile_solve", r"k_walk<1, 2,"),
+    ("f32_perimeter_graph_resolve", r"k_forest_\w+<unsigned __int128>"),
+    ("f32_pass2_tile_finalize", r"k_addin<\d, 1>"),
 ]
 
 
@@ -221,11 +223,11 @@ def record_traffic(csv_path: str, cells: int, desc: str, out_path=None) -> dict:
     ids = sorted(launches)
     out = {}
     for phase, key in TRAFFIC_PHASES:
-        hit = [i for i in ids if key in launches[i]["name"]]
+        hit = [i for i in ids if re.search(key, launches[i]["name"])]
         if not hit:
             continue
         # one call: the resolve is five launches, a tile pass one
-        first = hit[:5 if phase == "perimeter_graph_resolve" else 1]
+        first = hit[:5 if "resolve" in phase else 1]
         rd = sum(launches[i].get("dram__bytes_read.sum", 0.0) for i in first)
         wr = sum(launches[i].get("dram__bytes_write.sum", 0.0) for i in first)
         inst = sum(launches[i].get("smsp__inst_executed.sum", 0.0) for i in first)
@@ -546,28 +548,43 @@ def host_available_bytes() -> int:
 
 
 class HostPinned:
-    """A host array whose pages are page-locked by cudaHostRegister, so that
-    copies to and from it run at the link's rate.  Unlike the caching host
-    allocator behind pin_memory(), which rounds a request up to a power of
-    two (80 GB would take 128 GB), it locks exactly the bytes it holds.
-    close() unlocks them; the array is freed with the object."""
+    """A page-locked host array of exactly the requested size (cudaHostAlloc
+    through the CUDA runtime library), so that copies to and from it run at
+    the link's rate.  The caching host allocator behind pin_memory() rounds a
+    request up to a power of two (80 GB would take 128 GB of a host with 200).
+    close() frees it."""
+
+    _rt = None
+
+    @classmethod
+    def _runtime(cls):
+        if cls._rt is None:
+            import ctypes
+            import glob
+
+            libs = sorted(glob.glob("/usr/local/cuda/lib64/libcudart.so.*")) or ["libcudart.so"]
+            cls._rt = ctypes.CDLL(libs[-1])
+        return cls._rt
 
     def __init__(self, shape, dtype):
+        import ctypes
+
         import torch
 
-        self.a = np.empty(shape, dtype)
+        n = int(np.prod(shape)) * np.dtype(dtype).itemsize
+        self.p = ctypes.c_void_p()
+        err = self._runtime().cudaHostAlloc(ctypes.byref(self.p), ctypes.c_size_t(max(n, 1)), 0)
+        if err != 0:
+            raise RuntimeError(f"cudaHostAlloc of {n / 1e9:.1f} GB failed ({err})")
+        buf = (ctypes.c_uint8 * max(n, 1)).from_address(self.p.value)
+        self.a = np.frombuffer(buf, dtype=dtype, count=int(np.prod(shape))).reshape(shape)
         self.t = torch.from_numpy(self.a)
-        err = torch.cuda.cudart().cudaHostRegister(self.a.ctypes.data, self.a.nbytes, 0)
-        if int(err) != 0:
-            raise RuntimeError(f"cudaHostRegister of {self.a.nbytes / 1e9:.1f} GB failed ({int(err)})")
-        self.locked = True
 
     def close(self):
-        import torch
-
-        if self.locked:
-            torch.cuda.cudart().cudaHostUnregister(self.a.ctypes.data)
-            self.locked = False
+        if self.p:
+            del self.t, self.a
+            self._runtime().cudaFreeHost(self.p)
+            self.p = None
 
 
 def parity_counts_u32(codes_h, got_h):
