@@ -199,10 +199,10 @@ def traffic_for(kernel: str, cells: int = ROWS * COLS, path=None):
 TRAFFIC_PHASES = [
     ("pass1_tile_solve", r"k_walk<0, 1,"),
     ("perimeter_graph_resolve", r"k_forest_\w+<unsigned long long>"),
-    ("pass2_tile_finalize", r"k_addin<\d, 0>"),
+    ("pass2_tile_finalize", r"k_addin<"),
     ("f32_pass1_tile_solve", r"k_walk<1, 1,"),
     ("f32_perimeter_graph_resolve", r"k_forest_\w+<unsigned __int128>"),
-    ("f32_pass2_tile_finalize", r"k_addin<\d, 1>"),
+    ("f32_pass2_tile_solve", r"k_walk<1, 2,"),
 ]
 
 
