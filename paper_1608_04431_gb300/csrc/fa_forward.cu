@@ -845,6 +845,8 @@ __global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constan
     const TileArgs &a = A;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_n, s_flags;
+    __shared__ int s_oc[8];          // code k -> step in the staged codes
+    __shared__ long long s_oo[8];    // code k -> step in the output raster (its pitch)
     __shared__ unsigned long long s_tot;
     __shared__ __align__(8) uint64_t s_bar[2];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -962,7 +964,25 @@ __global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constan
             __syncthreads();
         }
 
-        // ---- each entry's path inside the tile receives its in(p)
+        // ---- each entry's path inside the tile receives its in(p).  The
+        // staged codes outside the tile (the ring, and the frame beyond a
+        // ragged tile) get the bit 0x80, so that one test on the next cell's
+        // code tells "leaves the tile" and "into NoData" both; a step is then
+        // two code reads, two table steps and the output update.
+        const int W2 = tw + 2;
+        for (int i = tid; i < (th + 2 - h) * W2; i += nt) {  // rows -1 and h .. th
+            const int q = i / W2, c = i - q * W2 - 1, hr = q == 0 ? 0 : h + q;
+            cbuf[hr * S + X0 + c] |= 0x80;
+        }
+        for (int i = tid; i < h * (tw + 2 - w); i += nt) {   // columns -1 and w .. tw of rows 0 .. h-1
+            const int nc = tw + 2 - w, r = i / nc, q = i - r * nc, c = q == 0 ? -1 : w + q - 1;
+            cbuf[(r + 1) * S + X0 + c] |= 0x80;
+        }
+        if (tid < 8) {
+            s_oc[tid] = dir_dr(tid + 1) * S + dir_dc(tid + 1);
+            s_oo[tid] = (long long)dir_dr(tid + 1) * ras.po + dir_dc(tid + 1);
+        }
+        __syncthreads();
         const int ne = s_n;
         const bool safe = s_tot + (unsigned long long)h * w < (1ull << 32);  // no count reaches 2^32
         uint32_t *out = reinterpret_cast<uint32_t *>(ras.out[0]);
@@ -970,21 +990,21 @@ __global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constan
             int r, c;
             cell_of(pent[e], h, w, r, c);
             const unsigned long long v = pin[e];
+            int ci = (r + 1) * S + X0 + c;
+            uint32_t *o = out + (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
             for (int stp = 0; stp < h * w; ++stp) {
-                uint32_t *o = out + (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
                 if (safe) {
                     atomicAdd(o, (uint32_t)v);  // result unused: a reduction
                 } else {
                     const uint32_t old = atomicAdd(o, (uint32_t)v);
                     if ((v >> 32) || (unsigned long long)old + (uint32_t)v >= (1ull << 32)) ovf = 1;
                 }
-                const int k = cbuf[(r + 1) * S + X0 + c];
-                if (k < 1 || k > 8) break;  // NoFlow: the path ends
-                const int tr = r + dir_dr(k), tc = c + dir_dc(k);
-                if ((unsigned)tr >= (unsigned)h || (unsigned)tc >= (unsigned)w) break;  // leaves the tile
-                if (!vcode(cbuf[(tr + 1) * S + X0 + tc])) break;  // into NoData: the flow leaves
-                r = tr;
-                c = tc;
+                const uint32_t k = cbuf[ci];
+                if (k - 1u >= 8u) break;  // NoFlow: the path ends
+                const int nci = ci + s_oc[k - 1];
+                if ((uint32_t)cbuf[nci] - 1u >= 9u) break;  // leaves the tile, or into NoData
+                ci = nci;
+                o += s_oo[k - 1];
             }
         }
         if constexpr (LOAD == LOAD_TMA) fence_proxy_async();  // the buffer is refilled by TMA
@@ -1062,13 +1082,13 @@ __global__ void k_forest_init(ForestArgs f) {
 // The exit forest solved the way a tile is (Algorithm 1 on the perimeter
 // graph of Section 3.2): J1 counts each node's predecessors (k_forest_indeg);
 // the nodes without one are marked (k_forest_leaves) and each starts a walk
-// (k_forest_walk) that adds its
-// finished value G into its successor's and moves on when it brought the
-// successor's last inflow, so each node is passed on once.  Values and counts
-// are separate words in global memory: a walk makes its adds visible (fence)
+// (k_forest_walk) that adds its finished value G into its successor's and
+// moves on when it brought the successor's last inflow, so each node is
+// passed on once.  Values and counts are separate words in global memory: the
+// count goes down by an acquire-release atomic, so a walk's adds are visible
 // before it takes one off the count, and the walk that takes the last one
-// reads the successor's value only after that (fence, loads that bypass L1).
-// Integer adds: the order in which they land does not matter.
+// reads the successor's value after that (loads that bypass L1).  Integer
+// adds: the order in which they land does not matter.
 template <class V>
 __global__ void k_forest_indeg(ForestArgs f) {
     const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1102,6 +1122,18 @@ __device__ __forceinline__ u128 load_cg(const u128 *p) {
     return (u128)__ldcg(q) | ((u128)__ldcg(q + 1) << 64);
 }
 
+// One pending inflow fewer at a node: acquire-release at GPU scope, so the
+// value adds a walk made before it are visible to the walk that takes the
+// last inflow, which reads the value after it (no separate fences).
+__device__ __forceinline__ uint32_t dec_acq_rel_gpu(uint32_t *p) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(p), "r"(0xFFFFFFFFu)
+                 : "memory");
+    return old;
+}
+
 template <class V>
 __global__ void k_forest_walk(ForestArgs f) {
     const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1120,9 +1152,7 @@ __global__ void k_forest_walk(ForestArgs f) {
             if (v == NODE_NONE) break;  // its path ends inside the target tile
             for (int q = 0; q < f.nf; ++q)
                 atomic_add_v(&x[(size_t)v * f.nf + q], load_cg(&x[u * f.nf + q]));
-            __threadfence();
-            if (atomicSub(&f.J1[v], 1u) != 1u) break;  // not the last inflow of v
-            __threadfence();
+            if (dec_acq_rel_gpu(&f.J1[v]) != 1u) break;  // not the last inflow of v
             u = v;
             ++done;
         }
