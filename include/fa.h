@@ -395,15 +395,16 @@ fa_status fa_accumulate_absorb(const uint8_t *codes, int64_t rows, int64_t cols,
  * output stay in HOST memory, for rasters larger than the device (Section 1
  * sets rasters beyond one machine's memory as the aim; Section 3 with EVICT:
  * only one block and the perimeter data are held at once).  The raster is cut
- * into outer blocks of block_rows x block_cols cells;
- * each block's codes, with a one-cell ring, are copied to the device twice:
- * pass A solves the block by the tile pipeline of fa_accumulate and records
- * its perimeter graph (Algorithm 2 at block level), the perimeter graphs of
- * all blocks are solved on the device (Section 3.2), and pass C solves the
- * block again, adds the flow entering from other blocks along its paths
- * (Algorithm 3) and copies the block's counts out.  Copies run on two streams
- * of the library's own, overlapping the solves when the host buffers are
- * pinned; the call is SYNCHRONOUS (it returns after the last copy out).
+ * into outer blocks of block_rows x block_cols cells; each block's codes,
+ * with a one-cell ring, are copied to the device twice: pass A solves the
+ * block by the tile pipeline of fa_accumulate and records its perimeter graph
+ * (Algorithm 2 at block level), the perimeter graphs of all blocks are solved
+ * on the device (Section 3.2), and pass C solves the block again with the
+ * flow entering from other blocks given to the tile pipeline as extra inflow
+ * at the block's entry cells, which carries it along the paths (Algorithm 3),
+ * and copies the block's counts out.  Copies run on two streams of the
+ * library's own, overlapping the solves when the host buffers are pinned; the
+ * call is SYNCHRONOUS (it returns after the last copy out).
  *   codes       [rows x pitch_codes] one byte per cell, HOST memory (pinned
  *               or pageable); FA_CODES_NIBBLE is not accepted.
  *   out         [rows x pitch_out] uint64 counts, HOST memory; exact for any
@@ -414,8 +415,9 @@ fa_status fa_accumulate_absorb(const uint8_t *codes, int64_t rows, int64_t cols,
  *               blocks x perim < 2^32 - 1.
  *   workspace   device, >= fa_ooc_workspace_size(), 256-byte aligned: two
  *               code buffers, one uint32 and two uint64 block buffers, the
- *               tile pipeline's workspace for one block, and about 28 bytes
- *               per perimeter slot of every block.
+ *               tile pipeline's workspace for one block plus 16 bytes per
+ *               perimeter slot of its tiles, and about 28 bytes per perimeter
+ *               slot of every block.
  *   opts        tile shape and flags for the block solves (as fa_accumulate).
  * Returns the decoded device status (as fa_status_read: BAD_CODE, CYCLE, ...)
  * after completion, FA_ERR_INVALID_ARG / FA_ERR_WORKSPACE for bad arguments

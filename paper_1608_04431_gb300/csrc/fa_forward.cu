@@ -64,6 +64,7 @@ struct TileArgs {
     StatusBlock *st;
     uint32_t *maxw;
     const unsigned long long *infl;  // counts: flow arriving at each perimeter slot (pass 2)
+    unsigned long long *off64;       // counts: if set, pass 2 adds into this uint64 raster instead
     // batches: a table of rasters (nullptr for one raster), each with its
     // tiles numbered from its tile_base in one global tile sequence
     const RasterDesc *rtab;
@@ -986,17 +987,20 @@ __global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constan
         const int ne = s_n;
         const bool safe = s_tot + (unsigned long long)h * w < (1ull << 32);  // no count reaches 2^32
         uint32_t *out = reinterpret_cast<uint32_t *>(ras.out[0]);
+        unsigned long long *o64 = a.off64;  // uint64 offsets (the out-of-core blocks)
         for (int e = tid; e < ne; e += nt) {
             int r, c;
             cell_of(pent[e], h, w, r, c);
             const unsigned long long v = pin[e];
             int ci = (r + 1) * S + X0 + c;
-            uint32_t *o = out + (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
+            size_t oi = (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
             for (int stp = 0; stp < h * w; ++stp) {
-                if (safe) {
-                    atomicAdd(o, (uint32_t)v);  // result unused: a reduction
+                if (o64) {
+                    atomicAdd(o64 + oi, v);  // a reduction
+                } else if (safe) {
+                    atomicAdd(out + oi, (uint32_t)v);  // result unused: a reduction
                 } else {
-                    const uint32_t old = atomicAdd(o, (uint32_t)v);
+                    const uint32_t old = atomicAdd(out + oi, (uint32_t)v);
                     if ((v >> 32) || (unsigned long long)old + (uint32_t)v >= (1ull << 32)) ovf = 1;
                 }
                 const uint32_t k = cbuf[ci];
@@ -1004,7 +1008,7 @@ __global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constan
                 const int nci = ci + s_oc[k - 1];
                 if ((uint32_t)cbuf[nci] - 1u >= 9u) break;  // leaves the tile, or into NoData
                 ci = nci;
-                o += s_oo[k - 1];
+                oi += s_oo[k - 1];
             }
         }
         if constexpr (LOAD == LOAD_TMA) fence_proxy_async();  // the buffer is refilled by TMA
@@ -1045,6 +1049,8 @@ struct ForestArgs {
     uint32_t *misc;  // [0] max|w| bits, [1] nodes finished by the walks
     StatusBlock *st;
     unsigned long long *infl;  // counts: per perimeter slot, the flow arriving from outside, or NULL
+    const unsigned long long *inj;   // counts: per perimeter slot, flow entering from beyond the raster, or NULL
+    const unsigned long long *injx;  // counts: per exit slot, that flow reaching the exit, or NULL
 };
 
 // Node values: uint64 counts (unit weights) or 128-bit fixed-point sums.
@@ -1063,7 +1069,7 @@ __global__ void k_forest_init(ForestArgs f) {
     const int q = f.valm ? fix_scale(f.cells, f.misc[0]) : 0;
     const size_t base = (size_t)tile * f.pmax;
     if (f.infl)
-        for (int j = lane; j < f.pmax; j += 32) f.infl[base + j] = 0;
+        for (int j = lane; j < f.pmax; j += 32) f.infl[base + j] = f.inj ? f.inj[base + j] : 0ull;
     for (uint32_t j = lane; j < n; j += 32) {
         const size_t node = base + j;
         for (int k = 0; k < f.nf; ++k) {
@@ -1076,6 +1082,19 @@ __global__ void k_forest_init(ForestArgs f) {
         const uint16_t l = f.link[dst];
         f.J0[node] = l == LINK_TERM ? NODE_NONE : (dst / f.pmax) * f.pmax + l;
         f.J1[node] = 0;
+    }
+    if constexpr (sizeof(V) == 8) {
+        // flow entering the tile from beyond the raster (an outer block's
+        // inflow) joins the value of the exit its path reaches: injx is
+        // keyed by that exit's slot, whose link is the exit's own rank
+        if (f.injx) {
+            __syncwarp();
+            for (int j = lane; j < f.pmax; j += 32) {
+                const unsigned long long v = f.injx[base + j];
+                const uint16_t l = v ? f.link[base + j] : LINK_TERM;
+                if (l != LINK_TERM) atomicAdd(&x[base + l], (V)v);
+            }
+        }
     }
 }
 
@@ -1414,7 +1433,8 @@ cudaError_t prepare_forward(const Geom &g, int val_mode) {
 // described by `ta` (one raster, or a batch through ta.rtab).
 static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const FwdWork &ws,
                                 void *status, const uint8_t *tma_codes, int64_t tma_pc,
-                                const uint8_t *tma_mask, cudaStream_t s) {
+                                const uint8_t *tma_mask, cudaStream_t s,
+                                const PipeHooks *hooks = nullptr) {
     StatusBlock *st = reinterpret_cast<StatusBlock *>(status ? status : ws.status);
     k_init_status<<<1, 64, 0, s>>>(st, ws.misc, 2 + ws.kmax);
     cudaError_t e = cudaGetLastError();
@@ -1434,6 +1454,7 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     ta.st = st;
     ta.maxw = ws.misc;
     ta.infl = ws.infl;
+    ta.off64 = hooks ? hooks->off64 : nullptr;
     ta.wait_ns = kWaitLimitNs;
 
     timing_mark(0, s);
@@ -1460,6 +1481,8 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
     f.misc = ws.misc;
     f.st = st;
     f.infl = val_mode ? nullptr : ws.infl;
+    f.inj = (hooks && !val_mode) ? hooks->inj : nullptr;
+    f.injx = (hooks && !val_mode) ? hooks->injx : nullptr;
     const unsigned fb = (unsigned)((f.tiles * 32 + 255) / 256);
     if (val_mode) {
         k_forest_init<u128><<<fb, 256, 0, s>>>(f);
@@ -1541,6 +1564,28 @@ cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, cons
     Geom g1 = g;
     g1.nf = 1;
     return run_pipeline(g1, ta, val_mode, ws, status, codes, pc, mask, s);
+}
+
+cudaError_t launch_forward_hooked(const Geom &g, const uint8_t *codes, int64_t pc, void *out,
+                                  int64_t po, const FwdWork &ws, void *status, const PipeHooks &hooks,
+                                  cudaStream_t s) {
+    TileArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    RasterDesc &r = ta.one;
+    r.codes = codes;
+    r.pc = pc;
+    r.out[0] = out;
+    r.po = po;
+    r.rows = g.rows;
+    r.cols = g.cols;
+    r.tiles_x = g.tiles_x;
+    r.tiles_y = g.tiles_y;
+    ta.nr = 1;
+    ta.T = (g.rows == 0 || g.cols == 0) ? 0 : g.tiles();
+    ta.fcells = g.rows * g.cols;
+    Geom g1 = g;
+    g1.nf = 1;
+    return run_pipeline(g1, ta, 0, ws, status, codes, pc, nullptr, s, &hooks);
 }
 
 cudaError_t launch_forward_batched(const Geom &g, const RasterDesc *d_tab, int nr, int64_t T,

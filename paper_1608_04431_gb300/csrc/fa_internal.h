@@ -119,6 +119,22 @@ cudaError_t launch_forward_batched(const Geom &g, const RasterDesc *d_tab, int n
                                    int64_t cells_bound, int val_mode, const FwdWork &ws,
                                    void *status, cudaStream_t s);
 
+// Additions to a counts pipeline for rasters that are blocks of a larger one
+// (the out-of-core form), all indexed tile * pmax + slot: inj is flow entering
+// the block at that perimeter slot from outside it (added along the slot's
+// path in the tile), injx the same flow at the slot of the exit cell that
+// path reaches (added to that exit's value before the resolve), or NULL;
+// off64, if set, receives the flow that enters each tile (from other tiles or
+// from outside the block) as uint64 offsets per cell (pitch of the output),
+// instead of adding it to the uint32 output, which then holds only A_loc.
+struct PipeHooks {
+    const unsigned long long *inj, *injx;
+    unsigned long long *off64;
+};
+cudaError_t launch_forward_hooked(const Geom &g, const uint8_t *codes, int64_t pc, void *out,
+                                  int64_t po, const FwdWork &ws, void *status, const PipeHooks &hooks,
+                                  cudaStream_t s);
+
 // Launch the whole forward pipeline on `stream`.  val_mode 0: uint32 counts
 // (weights must be NULL); 1: float32 output (weights or unit).
 cudaError_t launch_forward(const Geom &g, const uint8_t *codes, int64_t pc, const uint8_t *mask,

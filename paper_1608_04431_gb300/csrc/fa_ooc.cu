@@ -12,13 +12,16 @@
 //           and the target of every cell whose flow enters another block (an
 //           outer exit), and for every cell receiving flow from another block
 //           (an outer entry) the outer exit its path inside the block reaches
-//           (Algorithm 2 at the block level);
+//           (Algorithm 2 at the block level, hopping over the block's own
+//           tile links between the first and the last tile of the path);
 //   resolve the outer exits' graph (Section 3.2), solved on the device by the
 //           walks of the tile resolve;
-//   pass C  per block again (EVICT): codes copied in, the block accumulated
-//           again, and the flow entering each outer entry (the sum of G over
-//           the outer exits draining into it) added to every cell of its path
-//           inside the block (Algorithm 3); the block's counts, uint64, are
+//   pass C  per block again (EVICT): codes copied in and the block solved
+//           again by the tile pipeline with the flow entering each outer entry
+//           (the sum of G over the outer exits draining into it) handed to it
+//           as extra inflow at that entry, so that the pipeline's own resolve
+//           and finalising pass carry it along the paths (Algorithm 3); the
+//           tile-local sums plus the uint64 offsets are the block's counts,
 //           copied out.
 // Codes are copied on a second stream into one of two device buffers while
 // the other is in use (with pinned host memory the copies overlap the work).
@@ -78,23 +81,6 @@ __device__ __forceinline__ uint32_t ooc_inflow_mask(const OocBlock &k, int r, in
     return m;
 }
 
-// Follows the path from block cell (r, c) while it stays on valid cells of
-// the block; returns the last cell reached (r, c updated) and whether the path
-// ended there normally (false on a cycle: the step bound ran out).
-__device__ __forceinline__ bool ooc_follow(const OocBlock &k, int &r, int &c) {
-    const int64_t bound = (int64_t)k.hb * k.wb;
-    for (int64_t s = 0; s <= bound; ++s) {
-        const uint32_t code = ooc_code(k, r, c);
-        if (code < 1 || code > 8) return true;  // NoFlow (or not a valid cell)
-        const int tr = r + dir_dr((int)code), tc = c + dir_dc((int)code);
-        if ((unsigned)tr >= (unsigned)k.hb || (unsigned)tc >= (unsigned)k.wb) return true;
-        if (ooc_code(k, tr, tc) - 1u >= 9u) return true;  // into NoData
-        r = tr;
-        c = tc;
-    }
-    return false;
-}
-
 // Pass A, outer exits: every block-perimeter cell whose flow enters a valid
 // cell of another block gets a rank (node id b * pmax + rank), its target's
 // global slot id and its block-local accumulation A_loc.
@@ -121,9 +107,48 @@ __global__ void k_ooc_exits(OocGrid g, OocBlock k, const uint32_t *A, uint32_t *
     link[base + s] = lk;
 }
 
-// Pass A, outer entries: the outer exit each one's path inside the block
-// reaches (an exit links to itself already).
-__global__ void k_ooc_links(OocGrid g, OocBlock k, uint16_t *link) {
+// The inner tiles of a block (the tile pipeline's decomposition of it).
+struct InnerGeo {
+    int th, tw, tiles_x, pmax;
+};
+
+// Inner tile and slot of block cell (r, c), and the tile's extent.
+__device__ __forceinline__ void inner_slot(const InnerGeo &ig, const OocBlock &k, int r, int c,
+                                           int &T, int &sl) {
+    const int ty = r / ig.th, tx = c / ig.tw;
+    const int R0 = ty * ig.th, C0 = tx * ig.tw;
+    const int ht = min(ig.th, k.hb - R0), wt = min(ig.tw, k.wb - C0);
+    T = ty * ig.tiles_x + tx;
+    sl = slot_of(r - R0, c - C0, ht, wt);
+}
+
+// Follows the path from block cell (r, c) inside its inner tile.  Returns 1
+// when the next cell is a valid cell of the block in another inner tile
+// ((r, c) is then an exit of its tile), 0 when the path ends in the tile (at
+// NoFlow, NoData, a cycle, or a cell whose flow leaves the block); (r, c) is
+// the last cell reached in the tile.
+__device__ __forceinline__ int follow_in_tile(const InnerGeo &ig, const OocBlock &k, int &r, int &c) {
+    const int R0 = (r / ig.th) * ig.th, C0 = (c / ig.tw) * ig.tw;
+    for (int s = 0; s <= ig.th * ig.tw; ++s) {
+        const uint32_t code = ooc_code(k, r, c);
+        if (code < 1 || code > 8) return 0;
+        const int tr = r + dir_dr((int)code), tc = c + dir_dc((int)code);
+        if ((unsigned)tr >= (unsigned)k.hb || (unsigned)tc >= (unsigned)k.wb) return 0;
+        if (ooc_code(k, tr, tc) - 1u >= 9u) return 0;
+        if ((unsigned)(tr - R0) >= (unsigned)ig.th || (unsigned)(tc - C0) >= (unsigned)ig.tw) return 1;
+        r = tr;
+        c = tc;
+    }
+    return 0;
+}
+
+// Pass A, outer entries, by the block's own perimeter graph: the path from an
+// outer entry is followed cell by cell only inside the inner tile where it
+// starts and the one where it ends; between them it hops from inner exit to
+// inner exit (ilink: slot -> exit rank its path reaches, idst: exit -> slot of
+// its target), as the tile pipeline linked them (Algorithm 2 inside tiles).
+__global__ void k_ooc_links_hop(OocGrid g, OocBlock k, InnerGeo ig, const uint16_t *ilink,
+                                const uint32_t *idst, int64_t inodes, uint16_t *link) {
     const int P = perim_count(k.hb, k.wb);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= P) return;
@@ -133,15 +158,45 @@ __global__ void k_ooc_links(OocGrid g, OocBlock k, uint16_t *link) {
     if (link[base + s] != LINK_TERM) return;
     if (ooc_code(k, r, c) - 1u >= 9u || !ooc_inflow_mask(k, r, c)) return;
     uint16_t lk = LINK_TERM;
-    if (ooc_follow(k, r, c) && (r == 0 || c == 0 || r == k.hb - 1 || c == k.wb - 1))
+    bool ok = true;
+    int64_t hops = 0;
+    while (follow_in_tile(ig, k, r, c) == 1) {
+        // (r, c) is an inner exit: hop along the exits the path passes
+        int T, sl;
+        inner_slot(ig, k, r, c, T, sl);
+        uint16_t il = ilink[(size_t)T * ig.pmax + sl];  // an exit links to its own rank
+        if (il == LINK_TERM) {
+            ok = false;
+            break;
+        }
+        uint32_t dst = idst[(size_t)T * ig.pmax + il];
+        for (il = ilink[dst]; il != LINK_TERM && hops <= inodes; il = ilink[dst], ++hops)
+            dst = idst[(size_t)(dst / ig.pmax) * ig.pmax + il];
+        if (++hops > inodes) {  // a cycle of exits
+            ok = false;
+            break;
+        }
+        // the path ends in the tile of entry slot dst: its cell
+        const int T2 = (int)(dst / ig.pmax), sl2 = (int)(dst - (uint32_t)T2 * ig.pmax);
+        const int ty = T2 / ig.tiles_x, tx = T2 - ty * ig.tiles_x;
+        const int R0 = ty * ig.th, C0 = tx * ig.tw;
+        int lr, lc;
+        cell_of(sl2, min(ig.th, k.hb - R0), min(ig.tw, k.wb - C0), lr, lc);
+        r = R0 + lr;
+        c = C0 + lc;
+    }
+    if (ok && (r == 0 || c == 0 || r == k.hb - 1 || c == k.wb - 1))
         lk = link[base + slot_of(r, c, k.hb, k.wb)];
     link[base + s] = lk;
 }
 
-// Pass C: the flow entering each outer entry (the sum of G over the outer
-// exits draining into it) added to every cell of its path inside the block.
-__global__ void k_ooc_inflow(OocGrid g, OocBlock k, const uint16_t *link,
-                             const unsigned long long *G, unsigned long long *off) {
+// Pass C: the flow entering the block at each outer entry (the sum of G over
+// the outer exits draining into it), handed to the tile pipeline: at the
+// entry's inner slot (added along its path in the tile) and at the slot of
+// the inner exit that path reaches (added to that exit before the resolve).
+__global__ void k_ooc_inject(OocGrid g, OocBlock k, InnerGeo ig, const uint16_t *link,
+                             const unsigned long long *G, unsigned long long *inj,
+                             unsigned long long *injx) {
     const int P = perim_count(k.hb, k.wb);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= P) return;
@@ -159,16 +214,12 @@ __global__ void k_ooc_inflow(OocGrid g, OocBlock k, const uint16_t *link,
         in += G[(size_t)(src - src % (uint32_t)g.pmax) + lk];
     }
     if (!in) return;
-    const int64_t bound = (int64_t)k.hb * k.wb;
-    for (int64_t st = 0; st <= bound; ++st) {
-        atomicAdd(&off[(int64_t)r * k.wb + c], in);
-        const uint32_t code = ooc_code(k, r, c);
-        if (code < 1 || code > 8) break;
-        const int tr = r + dir_dr((int)code), tc = c + dir_dc((int)code);
-        if ((unsigned)tr >= (unsigned)k.hb || (unsigned)tc >= (unsigned)k.wb) break;
-        if (ooc_code(k, tr, tc) - 1u >= 9u) break;
-        r = tr;
-        c = tc;
+    int T, sl;
+    inner_slot(ig, k, r, c, T, sl);
+    inj[(size_t)T * ig.pmax + sl] = in;
+    if (follow_in_tile(ig, k, r, c) == 1) {
+        inner_slot(ig, k, r, c, T, sl);
+        atomicAdd(&injx[(size_t)T * ig.pmax + sl], in);
     }
 }
 
@@ -253,6 +304,7 @@ struct OocWork {
     uint8_t *codes[2];
     uint32_t *A;
     unsigned long long *off[2];
+    unsigned long long *inj, *injx;  // per inner perimeter slot of a block
     void *inner;
 };
 
@@ -274,6 +326,9 @@ size_t carve_ooc(void *ws, size_t bytes, const OocPlan &p, OocWork &w) {
     for (int i = 0; i < 2; ++i) w.codes[i] = c.take<uint8_t>(cbytes);
     w.A = c.take<uint32_t>(cells);
     for (int i = 0; i < 2; ++i) w.off[i] = c.take<unsigned long long>(cells);
+    const size_t islots = (size_t)p.gi.tiles() * p.gi.pmax;
+    w.inj = c.take<unsigned long long>(islots);
+    w.injx = c.take<unsigned long long>(islots);
     w.inner = c.take<uint8_t>(p.inner_ws);
     return c.used();
 }
@@ -381,26 +436,37 @@ extern "C" fa_status fa_accumulate_ooc(const uint8_t *codes, int64_t rows, int64
                 make_geom(k.hb, k.wb, opts, gi);
                 FwdWork iw;
                 if (carve_forward(w.inner, p.inner_ws, gi, iw, false) > p.inner_ws) return cudaErrorInvalidValue;
-                r = launch_forward(gi, k.codes + k.pd + OX, k.pd, nullptr, 0, nullptr, 0, w.A, k.wb, 0,
-                                   iw, w.inner_status, s);
-                if (r != cudaSuccess) return r;
+                const InnerGeo ig{gi.th, gi.tw, gi.tiles_x, gi.pmax};
                 const int P = perim_count(k.hb, k.wb);
                 const int64_t R0 = (int64_t)k.by * p.g.bh, C0 = (int64_t)k.bx * p.g.bw;
+                const int64_t n = (int64_t)k.hb * k.wb;
                 if (pass == 0) {
+                    r = launch_forward(gi, k.codes + k.pd + OX, k.pd, nullptr, 0, nullptr, 0, w.A, k.wb,
+                                       0, iw, w.inner_status, s);
+                    if (r != cudaSuccess) return r;
                     k_ooc_status_merge<<<1, 32, 0, s>>>(
                         reinterpret_cast<const StatusBlock *>(w.inner_status), st, R0, C0, k.wb, p.g.cols);
                     k_ooc_exits<<<grid_for(P, 128), 128, 0, s>>>(p.g, k, w.A, w.nexit, w.link, w.node_dst,
                                                                 w.node_val);
-                    k_ooc_links<<<grid_for(P, 128), 128, 0, s>>>(p.g, k, w.link);
+                    k_ooc_links_hop<<<grid_for(P, 128), 128, 0, s>>>(p.g, k, ig, iw.link, iw.node_dst,
+                                                                    gi.tiles() * gi.pmax, w.link);
                     if ((r = cudaGetLastError()) != cudaSuccess) return r;
                     if ((r = cudaEventRecord(freed[i], s)) != cudaSuccess) return r;
                     continue;
                 }
-                const int64_t n = (int64_t)k.hb * k.wb;
+                // pass C: the block solved again with its inflow from other
+                // blocks injected, the offsets into off[i] (uint64)
+                const size_t islots = (size_t)gi.tiles() * gi.pmax;
+                if ((r = cudaMemsetAsync(w.inj, 0, islots * 8, s)) != cudaSuccess) return r;
+                if ((r = cudaMemsetAsync(w.injx, 0, islots * 8, s)) != cudaSuccess) return r;
+                k_ooc_inject<<<grid_for(P, 128), 128, 0, s>>>(p.g, k, ig, w.link, w.x, w.inj, w.injx);
+                if ((r = cudaGetLastError()) != cudaSuccess) return r;
                 if ((r = cudaStreamWaitEvent(s, drained[i], 0)) != cudaSuccess) return r;
                 if ((r = cudaMemsetAsync(w.off[i], 0, (size_t)n * 8, s)) != cudaSuccess) return r;
-                k_ooc_inflow<<<grid_for(P, 128), 128, 0, s>>>(p.g, k, w.link, w.x, w.off[i]);
-                if ((r = cudaGetLastError()) != cudaSuccess) return r;
+                const PipeHooks hk{w.inj, w.injx, w.off[i]};
+                r = launch_forward_hooked(gi, k.codes + k.pd + OX, k.pd, w.A, k.wb, iw, w.inner_status,
+                                          hk, s);
+                if (r != cudaSuccess) return r;
                 if ((r = cudaEventRecord(freed[i], s)) != cudaSuccess) return r;
                 k_ooc_combine<<<grid_for(n, 256), 256, 0, s>>>(n, w.A, w.off[i]);
                 if ((r = cudaGetLastError()) != cudaSuccess) return r;
