@@ -112,6 +112,6 @@ def test_out_of_core_counts_are_exact_beyond_2_32():
     if avail is not None and avail < need:
         pytest.skip(f"needs {need >> 30} GiB of host memory, {avail >> 30} GiB available")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    r = subprocess.run([sys.executable, "-c", _OOC_CHECK, str(R), str(C)], cwd=root,
+    r = subprocess.run([sys.executable, "-X", "faulthandler", "-c", _OOC_CHECK, str(R), str(C)], cwd=root,
                        capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), (r.returncode, r.stderr[-2000:])
