@@ -416,8 +416,8 @@ fa_status fa_accumulate_absorb(const uint8_t *codes, int64_t rows, int64_t cols,
  *   workspace   device, >= fa_ooc_workspace_size(), 256-byte aligned: two
  *               code buffers, one uint32 and two uint64 block buffers, the
  *               tile pipeline's workspace for one block plus 16 bytes per
- *               perimeter slot of its tiles, and about 28 bytes per perimeter
- *               slot of every block.
+ *               perimeter slot of its tiles, and 38 bytes per perimeter slot
+ *               of every block.
  *   opts        tile shape and flags for the block solves (as fa_accumulate).
  * Returns the decoded device status (as fa_status_read: BAD_CODE, CYCLE, ...)
  * after completion, FA_ERR_INVALID_ARG / FA_ERR_WORKSPACE for bad arguments
@@ -430,6 +430,80 @@ fa_status fa_accumulate_ooc(const uint8_t *codes, int64_t rows, int64_t cols, in
                             uint64_t *out, int64_t pitch_out, int64_t block_rows,
                             int64_t block_cols, void *workspace, size_t ws_bytes,
                             const fa_options *opts, int32_t *d_status, void *stream);
+
+/*
+ * Shard form: fa_accumulate_ooc's three stages run by separate processes
+ * (one per GPU), exchanging only the perimeter records: the paper's two
+ * MapReduces (Section 3, Algorithm 3; Section 4 counts the data sent).  The
+ * raster is cut into outer blocks as in fa_accumulate_ooc (same block_rows,
+ * block_cols, opts in every call of one solve); a shard owns a band of whole
+ * block rows [band0, band1) (blocks band0 * nbx .. band1 * nbx - 1, row-major
+ * block numbering):
+ *   1. every shard:  fa_shard_export   pass A on its blocks -> their records;
+ *   2. gather the records of all blocks in one process;
+ *   3. that process: fa_shard_resolve  the blocks' perimeter graph solved
+ *                    (Section 3.2) -> in(p) for every block perimeter slot;
+ *   4. scatter each shard's part of in(p);
+ *   5. every shard:  fa_shard_finish   pass C on its blocks -> uint64 counts.
+ * The result equals fa_accumulate_ooc's (and fa_accumulate's counts), cell
+ * for cell.  All three calls are SYNCHRONOUS on `stream`; records, in(p),
+ * codes and counts are HOST memory; workspace is device memory of at least
+ * fa_ooc_workspace_size(rows, cols, block_rows, block_cols, opts) bytes,
+ * 256-byte aligned (fa_shard_resolve uses only its perimeter-graph part).
+ * d_status and the returned status as in fa_accumulate_ooc: export reports
+ * invalid codes and in-block cycles of its blocks, resolve cycles through
+ * several blocks, finish its blocks' conditions again.
+ *
+ * fa_shard_geometry: block_grid[0] = nby (block rows), block_grid[1] = nbx
+ * (blocks per block row), *pmax = record slots per block; FA_ERR_INVALID_ARG
+ * where fa_ooc_workspace_size would return 0.
+ *
+ * Records of blocks [b0, b1) (b = band0 * nbx ..), host arrays:
+ *   nexit     [b1 - b0]          uint32 outer exits of each block;
+ *   link      [(b1 - b0) * pmax] uint16 per block perimeter slot (slot
+ *             numbering of the paper's perimeter, clockwise from the block's
+ *             top-left cell): the exit rank its path reaches in the block,
+ *             0xFFFF for none (an exit links to its own rank);
+ *   node_dst  [(b1 - b0) * pmax] uint32 per exit rank: global slot id
+ *             (block * pmax + slot) of the cell its flow enters;
+ *   node_val  [(b1 - b0) * pmax] double per exit rank: its block-local
+ *             accumulation A_loc (an exact integer).
+ * Entries past nexit[b] are 0.  The ranks' order depends on scheduling; the
+ * in(p) and counts computed from them do not.
+ *
+ * Codes: codes points at raster row codes_row0 and holds codes_rows rows of
+ * pitch_codes bytes, which must include every row the band's blocks read:
+ * rows max(band0 * block_rows - 1, 0) .. min(band1 * block_rows + 1, rows) - 1
+ * (the band and its ring rows).
+ *
+ * fa_shard_resolve takes the records of ALL nby * nbx blocks (concatenated in
+ * block order) and writes inflow [nby * nbx * pmax]: per block perimeter slot
+ * the flow entering that cell from other blocks (uint64).  Records are
+ * checked on the host first (nexit <= pmax, targets inside the raster, links
+ * none or an exit of their block): FA_ERR_INVALID_ARG otherwise, nothing run.
+ *
+ * fa_shard_finish takes inflow [(b1 - b0) * pmax] (the band's part, from
+ * slot b0 * pmax) and writes out: raster rows band0 * block_rows ..
+ * min(band1 * block_rows, rows) - 1, row 0 first, pitch_out elements apart.
+ *
+ * An empty band (band0 == band1) is valid: nothing is read or written.
+ */
+fa_status fa_shard_geometry(int64_t rows, int64_t cols, int64_t block_rows, int64_t block_cols,
+                            int64_t *block_grid, int32_t *pmax);
+fa_status fa_shard_export(const uint8_t *codes, int64_t codes_row0, int64_t codes_rows,
+                          int64_t pitch_codes, int64_t rows, int64_t cols, int64_t block_rows,
+                          int64_t block_cols, int64_t band0, int64_t band1, uint32_t *nexit,
+                          uint16_t *link, uint32_t *node_dst, double *node_val, void *workspace,
+                          size_t ws_bytes, const fa_options *opts, int32_t *d_status, void *stream);
+fa_status fa_shard_resolve(int64_t rows, int64_t cols, int64_t block_rows, int64_t block_cols,
+                           const uint32_t *nexit, const uint16_t *link, const uint32_t *node_dst,
+                           const double *node_val, uint64_t *inflow, void *workspace,
+                           size_t ws_bytes, int32_t *d_status, void *stream);
+fa_status fa_shard_finish(const uint8_t *codes, int64_t codes_row0, int64_t codes_rows,
+                          int64_t pitch_codes, int64_t rows, int64_t cols, int64_t block_rows,
+                          int64_t block_cols, int64_t band0, int64_t band1, const uint64_t *inflow,
+                          uint64_t *out, int64_t pitch_out, void *workspace, size_t ws_bytes,
+                          const fa_options *opts, int32_t *d_status, void *stream);
 
 /*
  * Copies the device status block back (synchronises `stream`) and maps it to

@@ -37,6 +37,7 @@ __all__ = ["fa_version", "fa_workspace_size", "fa_kernel_launches", "fa_accumula
            "fa_recode", "recode", "pack_codes", "PackedCodes", "power_of_two_table",
            "fa_absorb_workspace_size", "fa_accumulate_absorb", "absorb",
            "fa_ooc_workspace_size", "fa_accumulate_ooc", "accumulate_ooc",
+           "fa_shard_geometry", "fa_shard_export", "fa_shard_resolve", "fa_shard_finish",
            "FlowAccError", "options"]
 
 
@@ -189,6 +190,63 @@ def fa_accumulate_ooc(codes, out, block_rows, block_cols, workspace, opts=None, 
         None if empty else _ptr(out), cols if empty else _pitch(out), block_rows, block_cols,
         _ptr(workspace), workspace.numel(), ctypes.byref(opts or fa_options()), _ptr(d_status),
         _stream_ptr(stream))
+
+
+def _host(t, what):
+    if t is not None and t.is_cuda:
+        raise TypeError(f"{what} must be a host (CPU) tensor")
+    return t
+
+
+def fa_shard_geometry(rows: int, cols: int, block_rows: int = 0, block_cols: int = 0):
+    """fa_shard_geometry -> (status, nby, nbx, pmax): the outer block grid of
+    the shard form and the record slots per block."""
+    grid = (ctypes.c_int64 * 2)()
+    pmax = ctypes.c_int32(0)
+    st = _lib.load().fa_shard_geometry(rows, cols, block_rows, block_cols, grid, ctypes.byref(pmax))
+    return st, grid[0], grid[1], pmax.value
+
+
+def fa_shard_export(codes, codes_row0, rows, cols, block_rows, block_cols, band0, band1, nexit, link,
+                    node_dst, node_val, workspace, opts=None, d_status=None, stream=None) -> int:
+    """fa_shard_export: pass A on the blocks of block rows [band0, band1).
+    codes: uint8 CPU tensor holding raster rows codes_row0 .. (the band and
+    its ring rows); nexit (32-bit), link (16-bit), node_dst (32-bit) and
+    node_val (float64): CPU tensors receiving the band's records."""
+    for t, what in ((codes, "codes"), (nexit, "nexit"), (link, "link"), (node_dst, "node_dst"),
+                    (node_val, "node_val")):
+        _host(t, what)
+    return _lib.load().fa_shard_export(
+        _ptr(codes), codes_row0, codes.shape[0], _pitch(codes), rows, cols, block_rows, block_cols,
+        band0, band1, _ptr(nexit), _ptr(link), _ptr(node_dst), _ptr(node_val), _ptr(workspace),
+        workspace.numel(), ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_shard_resolve(rows, cols, block_rows, block_cols, nexit, link, node_dst, node_val, inflow,
+                     workspace, d_status=None, stream=None) -> int:
+    """fa_shard_resolve: the records of all blocks (CPU tensors) -> inflow
+    (64-bit CPU tensor, one value per block perimeter slot)."""
+    for t, what in ((nexit, "nexit"), (link, "link"), (node_dst, "node_dst"),
+                    (node_val, "node_val"), (inflow, "inflow")):
+        _host(t, what)
+    return _lib.load().fa_shard_resolve(
+        rows, cols, block_rows, block_cols, _ptr(nexit), _ptr(link), _ptr(node_dst), _ptr(node_val),
+        _ptr(inflow), _ptr(workspace), workspace.numel(), _ptr(d_status), _stream_ptr(stream))
+
+
+def fa_shard_finish(codes, codes_row0, rows, cols, block_rows, block_cols, band0, band1, inflow,
+                    out, workspace, opts=None, d_status=None, stream=None) -> int:
+    """fa_shard_finish: pass C on the blocks of block rows [band0, band1) with
+    the band's in(p) (64-bit CPU tensor); out: 64-bit CPU tensor of the
+    band's raster rows."""
+    for t, what in ((codes, "codes"), (inflow, "inflow"), (out, "out")):
+        _host(t, what)
+    if out.element_size() != 8:
+        raise TypeError("out must be a 64-bit integer tensor")
+    return _lib.load().fa_shard_finish(
+        _ptr(codes), codes_row0, codes.shape[0], _pitch(codes), rows, cols, block_rows, block_cols,
+        band0, band1, _ptr(inflow), _ptr(out), _pitch(out), _ptr(workspace), workspace.numel(),
+        ctypes.byref(opts or fa_options()), _ptr(d_status), _stream_ptr(stream))
 
 
 def fa_absorb_workspace_size(rows: int, cols: int, opts: fa_options | None = None) -> int:
@@ -671,3 +729,6 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+from . import shard  # noqa: E402  (the multi-process form; uses the functions above)

@@ -89,6 +89,12 @@ SIGNATURES = {
     "fa_ooc_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, _OPT]),
     "fa_accumulate_ooc": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _I64, _I64, _P, _SZ, _OPT, _P,
                                  _P]),
+    "fa_shard_geometry": (_I32, [_I64, _I64, _I64, _I64, _P, _P]),
+    "fa_shard_export": (_I32, [_P, _I64, _I64, _I64, _I64, _I64, _I64, _I64, _I64, _I64, _P, _P,
+                               _P, _P, _P, _SZ, _OPT, _P, _P]),
+    "fa_shard_resolve": (_I32, [_I64, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P, _P]),
+    "fa_shard_finish": (_I32, [_P, _I64, _I64, _I64, _I64, _I64, _I64, _I64, _I64, _I64, _P, _P,
+                               _I64, _P, _SZ, _OPT, _P, _P]),
     "fa_timing_enable": (None, [_I32]),
     "fa_timing_read": (_I32, [ctypes.POINTER(ctypes.c_float), _I32]),
 }

@@ -1509,8 +1509,9 @@ static cudaError_t run_pipeline(const Geom &g, TileArgs ta, int val_mode, const 
 
 cudaError_t resolve_exit_forest_u64(int64_t groups, int pmax, const uint32_t *nexit,
                                     const uint16_t *link, const uint32_t *node_dst,
-                                    const double *node_val, unsigned long long *x, uint32_t *J0,
-                                    uint32_t *J1, uint32_t *misc, void *status, cudaStream_t s) {
+                                    const double *node_val, unsigned long long *x,
+                                    unsigned long long *infl, uint32_t *J0, uint32_t *J1,
+                                    uint32_t *misc, void *status, cudaStream_t s) {
     if (groups == 0) return cudaSuccess;
     ForestArgs f;
     std::memset(&f, 0, sizeof(f));
@@ -1529,6 +1530,7 @@ cudaError_t resolve_exit_forest_u64(int64_t groups, int pmax, const uint32_t *ne
     f.J1 = J1;
     f.misc = misc;
     f.st = reinterpret_cast<StatusBlock *>(status);
+    f.infl = infl;
     const unsigned fb = (unsigned)((groups * 32 + 255) / 256);
     k_forest_init<unsigned long long><<<fb, 256, 0, s>>>(f);
     k_forest_indeg<unsigned long long><<<fb, 256, 0, s>>>(f);

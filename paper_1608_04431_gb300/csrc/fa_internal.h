@@ -89,13 +89,16 @@ size_t carve_forward(void *ws, size_t bytes, const Geom &g, FwdWork &w, bool dry
 // nodes (node id = group * pmax + rank, nexit[group] ranks in use); node
 // `id` flows to the node linked from slot node_dst[id] (link[slot] = rank in
 // that slot's group, 0xFFFF = the path ends), with value node_val[id] (an
-// exact integer in a double).  x receives the solved values, J0 and J1 are
-// scratch of groups * pmax words each, misc[0..1] two counters, and a
-// node on a cycle is reported in `status`.
+// exact integer in a double).  x receives the solved values G; infl, if not
+// NULL, receives per slot the sum of G over the nodes whose node_dst is that
+// slot (the flow entering it, Section 3.2's in(p)); J0 and J1 are scratch of
+// groups * pmax words each, misc[0..1] two counters, and a node on a cycle is
+// reported in `status`.
 cudaError_t resolve_exit_forest_u64(int64_t groups, int pmax, const uint32_t *nexit,
                                     const uint16_t *link, const uint32_t *node_dst,
-                                    const double *node_val, unsigned long long *x, uint32_t *J0,
-                                    uint32_t *J1, uint32_t *misc, void *status, cudaStream_t s);
+                                    const double *node_val, unsigned long long *x,
+                                    unsigned long long *infl, uint32_t *J0, uint32_t *J1,
+                                    uint32_t *misc, void *status, cudaStream_t s);
 
 // Phase timing: records an event on `s` at phase boundary `i` (0..kMaxPhase)
 // when enabled; no-op otherwise.

@@ -190,30 +190,20 @@ __global__ void k_ooc_links_hop(OocGrid g, OocBlock k, InnerGeo ig, const uint16
     link[base + s] = lk;
 }
 
-// Pass C: the flow entering the block at each outer entry (the sum of G over
-// the outer exits draining into it), handed to the tile pipeline: at the
-// entry's inner slot (added along its path in the tile) and at the slot of
-// the inner exit that path reaches (added to that exit before the resolve).
-__global__ void k_ooc_inject(OocGrid g, OocBlock k, InnerGeo ig, const uint16_t *link,
-                             const unsigned long long *G, unsigned long long *inj,
-                             unsigned long long *injx) {
+// Pass C: the flow entering the block at each outer entry (in(p), the sum of
+// G over the outer exits draining into it, per perimeter slot of the block),
+// handed to the tile pipeline: at the entry's inner slot (added along its
+// path in the tile) and at the slot of the inner exit that path reaches
+// (added to that exit before the resolve).
+__global__ void k_ooc_inject(OocBlock k, InnerGeo ig, const unsigned long long *inb,
+                             unsigned long long *inj, unsigned long long *injx) {
     const int P = perim_count(k.hb, k.wb);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= P) return;
+    const unsigned long long in = inb[s];
+    if (!in) return;
     int r, c;
     cell_of(s, k.hb, k.wb, r, c);
-    if (ooc_code(k, r, c) - 1u >= 9u) return;
-    uint32_t m = ooc_inflow_mask(k, r, c);
-    unsigned long long in = 0;
-    while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1u;
-        const uint32_t src = ooc_outside_slot(g, k, r + dir_dr(j + 1), c + dir_dc(j + 1));
-        const uint16_t lk = link[src];  // the outer exit's own rank
-        if (lk == LINK_TERM) continue;
-        in += G[(size_t)(src - src % (uint32_t)g.pmax) + lk];
-    }
-    if (!in) return;
     int T, sl;
     inner_slot(ig, k, r, c, T, sl);
     inj[(size_t)T * ig.pmax + sl] = in;
@@ -300,7 +290,8 @@ struct OocWork {
     uint16_t *link;
     uint32_t *node_dst, *J0, *J1;
     double *node_val;
-    unsigned long long *x;
+    unsigned long long *x;    // G per outer exit node
+    unsigned long long *inb;  // in(p) per outer perimeter slot
     uint8_t *codes[2];
     uint32_t *A;
     unsigned long long *off[2];
@@ -323,6 +314,7 @@ size_t carve_ooc(void *ws, size_t bytes, const OocPlan &p, OocWork &w) {
     w.J1 = c.take<uint32_t>(nodes);
     w.node_val = c.take<double>(nodes);
     w.x = c.take<unsigned long long>(nodes);
+    w.inb = c.take<unsigned long long>(nodes);
     for (int i = 0; i < 2; ++i) w.codes[i] = c.take<uint8_t>(cbytes);
     w.A = c.take<uint32_t>(cells);
     for (int i = 0; i < 2; ++i) w.off[i] = c.take<unsigned long long>(cells);
@@ -345,10 +337,30 @@ OocBlock block_of(const OocPlan &p, int64_t b, const uint8_t *buf) {
     return k;
 }
 
-// Copies block k's codes with their one-cell ring from the host raster; ring
+// Host rows of the raster: raster row `row0` at `p`, `nrows` rows of `pitch`
+// bytes (the whole raster, or one shard's band with its ring rows).
+struct HostRows {
+    const uint8_t *p;
+    int64_t row0, nrows, pitch;
+};
+
+// Host uint64 counts: raster row `row0` at `p`, rows of `pitch` elements.
+struct HostOut {
+    uint64_t *p;
+    int64_t row0, pitch;
+};
+
+// Raster rows that the blocks of block rows [by0, by1) read: their own rows
+// and the ring rows above and below, inside the raster.
+void band_rows(const OocPlan &p, int64_t by0, int64_t by1, int64_t &ra, int64_t &rb) {
+    ra = std::max<int64_t>(by0 * p.g.bh - 1, 0);
+    rb = std::min<int64_t>(by1 * p.g.bh + 1, p.g.rows);
+}
+
+// Copies block k's codes with their one-cell ring from the host rows; ring
 // cells outside the raster read 0 (NoData).
-cudaError_t copy_block_in(const OocPlan &p, const OocBlock &k, uint8_t *buf, const uint8_t *codes,
-                          int64_t pitch, cudaStream_t cs) {
+cudaError_t copy_block_in(const OocPlan &p, const OocBlock &k, uint8_t *buf, const HostRows &h,
+                          cudaStream_t cs) {
     const int64_t R0 = (int64_t)k.by * p.g.bh, C0 = (int64_t)k.bx * p.g.bw;
     const int64_t ra = std::max<int64_t>(R0 - 1, 0), rb = std::min<int64_t>(R0 + k.hb + 1, p.g.rows);
     const int64_t ca = std::max<int64_t>(C0 - 1, 0), cb = std::min<int64_t>(C0 + k.wb + 1, p.g.cols);
@@ -358,17 +370,231 @@ cudaError_t copy_block_in(const OocPlan &p, const OocBlock &k, uint8_t *buf, con
         if (e != cudaSuccess) return e;
     }
     return cudaMemcpy2DAsync(buf + (ra - R0 + 1) * k.pd + OX + (ca - C0), (size_t)k.pd,
-                             codes + ra * pitch + ca, (size_t)pitch, (size_t)(cb - ca),
+                             h.p + (ra - h.row0) * h.pitch + ca, (size_t)h.pitch, (size_t)(cb - ca),
                              (size_t)(rb - ra), cudaMemcpyHostToDevice, cs);
 }
 
 unsigned grid_for(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
+
+// The block loop of one call: each block's codes are copied in on stream
+// `cin` into one of two device buffers while the other is in use, and its
+// counts copied out on stream `cout`; events order the buffers between the
+// copy streams and the work stream `s`.
+class BlockLoop {
+  public:
+    BlockLoop(const OocPlan &p, const OocWork &w, StatusBlock *st, const fa_options *opts,
+              cudaStream_t s)
+        : p_(p), w_(w), st_(st), opts_(opts), s_(s) {}
+    BlockLoop(const BlockLoop &) = delete;
+    BlockLoop &operator=(const BlockLoop &) = delete;
+
+    // Creates the copy streams and events; the copies start after the work
+    // enqueued on `s` so far.
+    cudaError_t start() {
+        cudaError_t e = cudaStreamCreateWithFlags(&cin_, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cout_, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaEventCreateWithFlags(&ready_[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed_[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done_[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&drained_[i], cudaEventDisableTiming);
+        }
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaEventRecord(freed_[i], s_);
+            if (e == cudaSuccess) e = cudaEventRecord(drained_[i], s_);
+        }
+        return e;
+    }
+
+    // Pass A over blocks [b0, b1): solve, outer exits and entry links.
+    cudaError_t pass_a(const HostRows &h, int64_t b0, int64_t b1) {
+        for (int64_t b = b0; b < b1; ++b) {
+            const int i = (int)(b & 1);
+            Block x;
+            cudaError_t r = stage_in(h, b, x);
+            if (r != cudaSuccess) return r;
+            r = launch_forward(x.gi, x.k.codes + x.k.pd + OX, x.k.pd, nullptr, 0, nullptr, 0, w_.A,
+                               x.k.wb, 0, x.iw, w_.inner_status, s_);
+            if (r != cudaSuccess) return r;
+            k_ooc_status_merge<<<1, 32, 0, s_>>>(reinterpret_cast<const StatusBlock *>(w_.inner_status),
+                                                st_, x.R0, x.C0, x.k.wb, p_.g.cols);
+            k_ooc_exits<<<grid_for(x.P, 128), 128, 0, s_>>>(p_.g, x.k, w_.A, w_.nexit, w_.link,
+                                                           w_.node_dst, w_.node_val);
+            k_ooc_links_hop<<<grid_for(x.P, 128), 128, 0, s_>>>(p_.g, x.k, x.ig, x.iw.link, x.iw.node_dst,
+                                                               x.gi.tiles() * x.gi.pmax, w_.link);
+            if ((r = cudaGetLastError()) != cudaSuccess) return r;
+            if ((r = cudaEventRecord(freed_[i], s_)) != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    }
+
+    // Pass C over blocks [b0, b1): each block solved again with in(p) (w.inb,
+    // per outer slot) injected, its counts copied out to `o`; merge_status
+    // also folds the block solves' status into the call's.
+    cudaError_t pass_c(const HostRows &h, const HostOut &o, int64_t b0, int64_t b1, bool merge_status) {
+        for (int64_t b = b0; b < b1; ++b) {
+            const int i = (int)(b & 1);
+            Block x;
+            cudaError_t r = stage_in(h, b, x);
+            if (r != cudaSuccess) return r;
+            const size_t islots = (size_t)x.gi.tiles() * x.gi.pmax;
+            if ((r = cudaMemsetAsync(w_.inj, 0, islots * 8, s_)) != cudaSuccess) return r;
+            if ((r = cudaMemsetAsync(w_.injx, 0, islots * 8, s_)) != cudaSuccess) return r;
+            k_ooc_inject<<<grid_for(x.P, 128), 128, 0, s_>>>(x.k, x.ig, w_.inb + (size_t)b * p_.g.pmax,
+                                                            w_.inj, w_.injx);
+            if ((r = cudaGetLastError()) != cudaSuccess) return r;
+            if ((r = cudaStreamWaitEvent(s_, drained_[i], 0)) != cudaSuccess) return r;
+            if ((r = cudaMemsetAsync(w_.off[i], 0, (size_t)x.n * 8, s_)) != cudaSuccess) return r;
+            const PipeHooks hk{w_.inj, w_.injx, w_.off[i]};
+            r = launch_forward_hooked(x.gi, x.k.codes + x.k.pd + OX, x.k.pd, w_.A, x.k.wb, x.iw,
+                                      w_.inner_status, hk, s_);
+            if (r != cudaSuccess) return r;
+            if (merge_status)
+                k_ooc_status_merge<<<1, 32, 0, s_>>>(
+                    reinterpret_cast<const StatusBlock *>(w_.inner_status), st_, x.R0, x.C0, x.k.wb,
+                    p_.g.cols);
+            if ((r = cudaEventRecord(freed_[i], s_)) != cudaSuccess) return r;
+            k_ooc_combine<<<grid_for(x.n, 256), 256, 0, s_>>>(x.n, w_.A, w_.off[i]);
+            if ((r = cudaGetLastError()) != cudaSuccess) return r;
+            if ((r = cudaEventRecord(done_[i], s_)) != cudaSuccess) return r;
+            if ((r = cudaStreamWaitEvent(cout_, done_[i], 0)) != cudaSuccess) return r;
+            r = cudaMemcpy2DAsync(o.p + (x.R0 - o.row0) * o.pitch + x.C0, (size_t)o.pitch * 8, w_.off[i],
+                                  (size_t)x.k.wb * 8, (size_t)x.k.wb * 8, (size_t)x.k.hb,
+                                  cudaMemcpyDeviceToHost, cout_);
+            if (r != cudaSuccess) return r;
+            if ((r = cudaEventRecord(drained_[i], cout_)) != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    }
+
+    // The work stream continues after the last copy out.
+    cudaError_t join() {
+        cudaError_t r = cudaEventRecord(drained_[0], cout_);
+        return r == cudaSuccess ? cudaStreamWaitEvent(s_, drained_[0], 0) : r;
+    }
+
+    // Waits for all three streams (the copies read and write host memory, so
+    // the calls are synchronous); returns the work stream's error.
+    cudaError_t finish() {
+        const cudaError_t e = cudaStreamSynchronize(s_);
+        if (cin_) cudaStreamSynchronize(cin_);
+        if (cout_) cudaStreamSynchronize(cout_);
+        return e;
+    }
+
+    ~BlockLoop() {
+        finish();
+        for (int i = 0; i < 2; ++i) {
+            if (ready_[i]) cudaEventDestroy(ready_[i]);
+            if (freed_[i]) cudaEventDestroy(freed_[i]);
+            if (done_[i]) cudaEventDestroy(done_[i]);
+            if (drained_[i]) cudaEventDestroy(drained_[i]);
+        }
+        if (cin_) cudaStreamDestroy(cin_);
+        if (cout_) cudaStreamDestroy(cout_);
+    }
+
+  private:
+    struct Block {
+        OocBlock k;
+        Geom gi;
+        FwdWork iw;
+        InnerGeo ig;
+        int P;
+        int64_t R0, C0, n;
+    };
+
+    // Block b's codes copied into buffer b & 1 once that buffer is free; the
+    // work stream waits for them.  Fills the block's inner geometry.
+    cudaError_t stage_in(const HostRows &h, int64_t b, Block &x) {
+        const int i = (int)(b & 1);
+        x.k = block_of(p_, b, w_.codes[i]);
+        cudaError_t r = cudaStreamWaitEvent(cin_, freed_[i], 0);
+        if (r == cudaSuccess) r = copy_block_in(p_, x.k, w_.codes[i], h, cin_);
+        if (r == cudaSuccess) r = cudaEventRecord(ready_[i], cin_);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(s_, ready_[i], 0);
+        if (r != cudaSuccess) return r;
+        if (!make_geom(x.k.hb, x.k.wb, opts_, x.gi)) return cudaErrorInvalidValue;
+        if (carve_forward(w_.inner, p_.inner_ws, x.gi, x.iw, false) > p_.inner_ws) return cudaErrorInvalidValue;
+        x.ig = InnerGeo{x.gi.th, x.gi.tw, x.gi.tiles_x, x.gi.pmax};
+        x.P = perim_count(x.k.hb, x.k.wb);
+        x.R0 = (int64_t)x.k.by * p_.g.bh;
+        x.C0 = (int64_t)x.k.bx * p_.g.bw;
+        x.n = (int64_t)x.k.hb * x.k.wb;
+        return cudaSuccess;
+    }
+
+    const OocPlan &p_;
+    const OocWork &w_;
+    StatusBlock *st_;
+    const fa_options *opts_;
+    cudaStream_t s_;
+    cudaStream_t cin_ = nullptr, cout_ = nullptr;
+    cudaEvent_t ready_[2] = {}, freed_[2] = {}, done_[2] = {}, drained_[2] = {};
+};
+
+// Status reset and cleared perimeter records of blocks [b0, b1) on `s`: no
+// exits, every slot's link none (slots past a ragged block's perimeter too).
+cudaError_t reset_records(const OocPlan &p, const OocWork &w, StatusBlock *st, int64_t b0, int64_t b1,
+                          cudaStream_t s) {
+    k_ooc_status_reset<<<1, 32, 0, s>>>(st);
+    cudaError_t r = cudaMemsetAsync(w.misc, 0, 16 * sizeof(uint32_t), s);
+    if (r == cudaSuccess && b1 > b0) r = cudaMemsetAsync(w.nexit + b0, 0, (size_t)(b1 - b0) * 4, s);
+    if (r == cudaSuccess && b1 > b0)
+        r = cudaMemsetAsync(w.link + (size_t)b0 * p.g.pmax, 0xFF, (size_t)(b1 - b0) * p.g.pmax * 2, s);
+    return r == cudaSuccess ? cudaGetLastError() : r;
+}
 
 }  // namespace
 
 }  // namespace fa
 
 using namespace fa;
+
+namespace {
+
+// Workspace and status checks shared by the out-of-core and shard calls.
+fa_status ws_setup(const OocPlan &p, void *workspace, size_t ws_bytes, const int32_t *d_status,
+                   OocWork &w) {
+    if (d_status && ((uintptr_t)d_status & 7)) return FA_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255)) return FA_ERR_WORKSPACE;
+    if (carve_ooc(workspace, ws_bytes, p, w) > ws_bytes) return FA_ERR_WORKSPACE;
+    return FA_OK;
+}
+
+// A shard's band of block rows [band0, band1) and the host rows it was
+// given: raster rows [codes_row0, codes_row0 + codes_rows) must hold every
+// row its blocks read.
+bool band_ok(const OocPlan &p, int64_t band0, int64_t band1, int64_t codes_row0, int64_t codes_rows) {
+    if (band0 < 0 || band1 < band0 || band1 > p.g.nby) return false;
+    if (band1 == band0) return true;
+    int64_t ra, rb;
+    band_rows(p, band0, band1, ra, rb);
+    return codes_row0 >= 0 && codes_rows >= 0 && codes_row0 <= ra && codes_row0 + codes_rows >= rb;
+}
+
+// Records from other processes are checked before they reach the device: at
+// most pmax exits per block, every exit's target a slot of the raster, and
+// the link of that slot none or an exit of its block.
+bool records_ok(const OocPlan &p, const uint32_t *nexit, const uint16_t *link, const uint32_t *node_dst) {
+    const uint64_t pmax = (uint64_t)p.g.pmax, nodes = (uint64_t)p.nb * pmax;
+    for (int64_t b = 0; b < p.nb; ++b)
+        if (nexit[b] > pmax) return false;
+    for (int64_t b = 0; b < p.nb; ++b)
+        for (uint32_t j = 0; j < nexit[b]; ++j) {
+            const uint64_t dst = node_dst[(uint64_t)b * pmax + j];
+            if (dst >= nodes) return false;
+            const uint16_t l = link[dst];
+            if (l != LINK_TERM && l >= nexit[dst / pmax]) return false;
+        }
+    return true;
+}
+
+StatusBlock *status_of(int32_t *d_status, const OocWork &w) {
+    return reinterpret_cast<StatusBlock *>(d_status ? (void *)d_status : w.status);
+}
+
+}  // namespace
 
 extern "C" size_t fa_ooc_workspace_size(int64_t rows, int64_t cols, int64_t block_rows,
                                         int64_t block_cols, const fa_options *opts) {
@@ -387,116 +613,158 @@ extern "C" fa_status fa_accumulate_ooc(const uint8_t *codes, int64_t rows, int64
     if (!ooc_plan(rows, cols, block_rows, block_cols, opts, p)) return FA_ERR_INVALID_ARG;
     const bool empty = rows == 0 || cols == 0;
     if (!empty && (!codes || !out || pitch_codes < cols || pitch_out < cols)) return FA_ERR_INVALID_ARG;
+    OocWork w;
+    const fa_status v = ws_setup(p, workspace, ws_bytes, d_status, w);
+    if (v != FA_OK) return v;
+    cudaStream_t s = (cudaStream_t)stream;
+    StatusBlock *st = status_of(d_status, w);
+    const bool was = timing_swap(false);  // block calls record no phase events
+    cudaError_t e, es;
+    {
+        BlockLoop loop(p, w, st, opts, s);
+        e = reset_records(p, w, st, 0, p.nb, s);
+        if (e == cudaSuccess && !empty) {
+            const HostRows h{codes, 0, rows, pitch_codes};
+            e = loop.start();
+            if (e == cudaSuccess) e = loop.pass_a(h, 0, p.nb);
+            if (e == cudaSuccess)
+                e = resolve_exit_forest_u64(p.nb, p.g.pmax, w.nexit, w.link, w.node_dst, w.node_val, w.x,
+                                            w.inb, w.J0, w.J1, w.misc, st, s);
+            if (e == cudaSuccess) e = loop.pass_c(h, HostOut{out, 0, pitch_out}, 0, p.nb, false);
+            if (e == cudaSuccess) e = loop.join();
+        }
+        es = loop.finish();
+    }
+    timing_swap(was);
+    if (e != cudaSuccess || es != cudaSuccess) return FA_ERR_CUDA;
+    return fa_status_read(d_status, workspace, stream, nullptr, nullptr);
+}
+
+extern "C" fa_status fa_shard_geometry(int64_t rows, int64_t cols, int64_t block_rows,
+                                       int64_t block_cols, int64_t *block_grid, int32_t *pmax) {
+    OocPlan p;
+    if (!block_grid || !pmax || !ooc_plan(rows, cols, block_rows, block_cols, nullptr, p))
+        return FA_ERR_INVALID_ARG;
+    block_grid[0] = p.g.nby;
+    block_grid[1] = p.g.nbx;
+    *pmax = p.g.pmax;
+    return FA_OK;
+}
+
+extern "C" fa_status fa_shard_export(const uint8_t *codes, int64_t codes_row0, int64_t codes_rows,
+                                     int64_t pitch_codes, int64_t rows, int64_t cols,
+                                     int64_t block_rows, int64_t block_cols, int64_t band0,
+                                     int64_t band1, uint32_t *nexit, uint16_t *link,
+                                     uint32_t *node_dst, double *node_val, void *workspace,
+                                     size_t ws_bytes, const fa_options *opts, int32_t *d_status,
+                                     void *stream) {
+    OocPlan p;
+    if (!ooc_plan(rows, cols, block_rows, block_cols, opts, p)) return FA_ERR_INVALID_ARG;
+    if (!band_ok(p, band0, band1, codes_row0, codes_rows)) return FA_ERR_INVALID_ARG;
+    const int64_t b0 = band0 * p.g.nbx, b1 = band1 * p.g.nbx;
+    if (b1 > b0 && (!codes || pitch_codes < cols || !nexit || !link || !node_dst || !node_val))
+        return FA_ERR_INVALID_ARG;
+    OocWork w;
+    const fa_status v = ws_setup(p, workspace, ws_bytes, d_status, w);
+    if (v != FA_OK) return v;
+    cudaStream_t s = (cudaStream_t)stream;
+    StatusBlock *st = status_of(d_status, w);
+    const size_t n0 = (size_t)b0 * p.g.pmax, nn = (size_t)(b1 - b0) * p.g.pmax;
+    const bool was = timing_swap(false);
+    cudaError_t e, es;
+    {
+        BlockLoop loop(p, w, st, opts, s);
+        e = reset_records(p, w, st, b0, b1, s);
+        if (e == cudaSuccess && nn) e = cudaMemsetAsync(w.node_dst + n0, 0, nn * 4, s);
+        if (e == cudaSuccess && nn) e = cudaMemsetAsync(w.node_val + n0, 0, nn * 8, s);
+        if (e == cudaSuccess && nn) {
+            e = loop.start();
+            if (e == cudaSuccess) e = loop.pass_a(HostRows{codes, codes_row0, codes_rows, pitch_codes}, b0, b1);
+            if (e == cudaSuccess) e = loop.join();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(nexit, w.nexit + b0, (size_t)(b1 - b0) * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(link, w.link + n0, nn * 2, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(node_dst, w.node_dst + n0, nn * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(node_val, w.node_val + n0, nn * 8, cudaMemcpyDeviceToHost, s);
+        }
+        es = loop.finish();
+    }
+    timing_swap(was);
+    if (e != cudaSuccess || es != cudaSuccess) return FA_ERR_CUDA;
+    return fa_status_read(d_status, workspace, stream, nullptr, nullptr);
+}
+
+extern "C" fa_status fa_shard_resolve(int64_t rows, int64_t cols, int64_t block_rows,
+                                      int64_t block_cols, const uint32_t *nexit, const uint16_t *link,
+                                      const uint32_t *node_dst, const double *node_val,
+                                      uint64_t *inflow, void *workspace, size_t ws_bytes,
+                                      int32_t *d_status, void *stream) {
+    OocPlan p;
+    if (!ooc_plan(rows, cols, block_rows, block_cols, nullptr, p)) return FA_ERR_INVALID_ARG;
+    const size_t nodes = (size_t)p.nb * p.g.pmax;
+    if (nodes && (!nexit || !link || !node_dst || !node_val || !inflow)) return FA_ERR_INVALID_ARG;
+    if (nodes && !records_ok(p, nexit, link, node_dst)) return FA_ERR_INVALID_ARG;
     if (d_status && ((uintptr_t)d_status & 7)) return FA_ERR_INVALID_ARG;
     if (!workspace || ((uintptr_t)workspace & 255)) return FA_ERR_WORKSPACE;
     OocWork w;
-    if (carve_ooc(workspace, ws_bytes, p, w) > ws_bytes) return FA_ERR_WORKSPACE;
+    carve_ooc(workspace, ws_bytes, p, w);
+    if ((uintptr_t)(w.inb + nodes) > (uintptr_t)workspace + ws_bytes) return FA_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    StatusBlock *st = reinterpret_cast<StatusBlock *>(d_status ? (void *)d_status : w.status);
-
-    // copy streams (host -> device codes, device -> host counts) and the
-    // events that order the two buffers of each kind between them and `s`
-    cudaStream_t cin = nullptr, cout = nullptr;
-    cudaEvent_t ready[2] = {}, freed[2] = {}, done[2] = {}, drained[2] = {};
-    cudaError_t e = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&drained[i], cudaEventDisableTiming);
+    StatusBlock *st = status_of(d_status, w);
+    k_ooc_status_reset<<<1, 32, 0, s>>>(st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.misc, 0, 16 * sizeof(uint32_t), s);
+    if (e == cudaSuccess && nodes) {
+        e = cudaMemcpyAsync(w.nexit, nexit, (size_t)p.nb * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w.link, link, nodes * 2, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w.node_dst, node_dst, nodes * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w.node_val, node_val, nodes * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = resolve_exit_forest_u64(p.nb, p.g.pmax, w.nexit, w.link, w.node_dst, w.node_val, w.x,
+                                        w.inb, w.J0, w.J1, w.misc, st, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(inflow, w.inb, nodes * 8, cudaMemcpyDeviceToHost, s);
     }
-    const bool was = timing_swap(false);  // block calls record no phase events
-
-    auto run = [&]() -> cudaError_t {
-        k_ooc_status_reset<<<1, 32, 0, s>>>(st);
-        cudaError_t r = cudaMemsetAsync(w.nexit, 0, (size_t)p.nb * sizeof(uint32_t), s);
-        if (r == cudaSuccess) r = cudaMemsetAsync(w.misc, 0, 16 * sizeof(uint32_t), s);
-        if (r != cudaSuccess || empty) return r;
-        // the copy streams start after the resets above
-        if ((r = cudaEventRecord(freed[0], s)) != cudaSuccess) return r;
-        if ((r = cudaEventRecord(freed[1], s)) != cudaSuccess) return r;
-        if ((r = cudaEventRecord(drained[0], s)) != cudaSuccess) return r;
-        if ((r = cudaEventRecord(drained[1], s)) != cudaSuccess) return r;
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 1) {
-                r = resolve_exit_forest_u64(p.nb, p.g.pmax, w.nexit, w.link, w.node_dst, w.node_val,
-                                            w.x, w.J0, w.J1, w.misc, st, s);
-                if (r != cudaSuccess) return r;
-            }
-            for (int64_t b = 0; b < p.nb; ++b) {
-                const int i = (int)(b & 1);
-                const OocBlock k = block_of(p, b, w.codes[i]);
-                if ((r = cudaStreamWaitEvent(cin, freed[i], 0)) != cudaSuccess) return r;
-                if ((r = copy_block_in(p, k, w.codes[i], codes, pitch_codes, cin)) != cudaSuccess) return r;
-                if ((r = cudaEventRecord(ready[i], cin)) != cudaSuccess) return r;
-                if ((r = cudaStreamWaitEvent(s, ready[i], 0)) != cudaSuccess) return r;
-
-                Geom gi;
-                make_geom(k.hb, k.wb, opts, gi);
-                FwdWork iw;
-                if (carve_forward(w.inner, p.inner_ws, gi, iw, false) > p.inner_ws) return cudaErrorInvalidValue;
-                const InnerGeo ig{gi.th, gi.tw, gi.tiles_x, gi.pmax};
-                const int P = perim_count(k.hb, k.wb);
-                const int64_t R0 = (int64_t)k.by * p.g.bh, C0 = (int64_t)k.bx * p.g.bw;
-                const int64_t n = (int64_t)k.hb * k.wb;
-                if (pass == 0) {
-                    r = launch_forward(gi, k.codes + k.pd + OX, k.pd, nullptr, 0, nullptr, 0, w.A, k.wb,
-                                       0, iw, w.inner_status, s);
-                    if (r != cudaSuccess) return r;
-                    k_ooc_status_merge<<<1, 32, 0, s>>>(
-                        reinterpret_cast<const StatusBlock *>(w.inner_status), st, R0, C0, k.wb, p.g.cols);
-                    k_ooc_exits<<<grid_for(P, 128), 128, 0, s>>>(p.g, k, w.A, w.nexit, w.link, w.node_dst,
-                                                                w.node_val);
-                    k_ooc_links_hop<<<grid_for(P, 128), 128, 0, s>>>(p.g, k, ig, iw.link, iw.node_dst,
-                                                                    gi.tiles() * gi.pmax, w.link);
-                    if ((r = cudaGetLastError()) != cudaSuccess) return r;
-                    if ((r = cudaEventRecord(freed[i], s)) != cudaSuccess) return r;
-                    continue;
-                }
-                // pass C: the block solved again with its inflow from other
-                // blocks injected, the offsets into off[i] (uint64)
-                const size_t islots = (size_t)gi.tiles() * gi.pmax;
-                if ((r = cudaMemsetAsync(w.inj, 0, islots * 8, s)) != cudaSuccess) return r;
-                if ((r = cudaMemsetAsync(w.injx, 0, islots * 8, s)) != cudaSuccess) return r;
-                k_ooc_inject<<<grid_for(P, 128), 128, 0, s>>>(p.g, k, ig, w.link, w.x, w.inj, w.injx);
-                if ((r = cudaGetLastError()) != cudaSuccess) return r;
-                if ((r = cudaStreamWaitEvent(s, drained[i], 0)) != cudaSuccess) return r;
-                if ((r = cudaMemsetAsync(w.off[i], 0, (size_t)n * 8, s)) != cudaSuccess) return r;
-                const PipeHooks hk{w.inj, w.injx, w.off[i]};
-                r = launch_forward_hooked(gi, k.codes + k.pd + OX, k.pd, w.A, k.wb, iw, w.inner_status,
-                                          hk, s);
-                if (r != cudaSuccess) return r;
-                if ((r = cudaEventRecord(freed[i], s)) != cudaSuccess) return r;
-                k_ooc_combine<<<grid_for(n, 256), 256, 0, s>>>(n, w.A, w.off[i]);
-                if ((r = cudaGetLastError()) != cudaSuccess) return r;
-                if ((r = cudaEventRecord(done[i], s)) != cudaSuccess) return r;
-                if ((r = cudaStreamWaitEvent(cout, done[i], 0)) != cudaSuccess) return r;
-                r = cudaMemcpy2DAsync(out + R0 * pitch_out + C0, (size_t)pitch_out * 8, w.off[i],
-                                      (size_t)k.wb * 8, (size_t)k.wb * 8, (size_t)k.hb,
-                                      cudaMemcpyDeviceToHost, cout);
-                if (r != cudaSuccess) return r;
-                if ((r = cudaEventRecord(drained[i], cout)) != cudaSuccess) return r;
-            }
-        }
-        // the caller's stream ends after the last copy out
-        if ((r = cudaEventRecord(drained[0], cout)) != cudaSuccess) return r;
-        return cudaStreamWaitEvent(s, drained[0], 0);
-    };
-    if (e == cudaSuccess) e = run();
-    timing_swap(was);
-    // the call is synchronous: its copies read and write host memory
     const cudaError_t es = cudaStreamSynchronize(s);
-    if (cin) cudaStreamSynchronize(cin);
-    if (cout) cudaStreamSynchronize(cout);
-    for (int i = 0; i < 2; ++i) {
-        if (ready[i]) cudaEventDestroy(ready[i]);
-        if (freed[i]) cudaEventDestroy(freed[i]);
-        if (done[i]) cudaEventDestroy(done[i]);
-        if (drained[i]) cudaEventDestroy(drained[i]);
+    if (e != cudaSuccess || es != cudaSuccess) return FA_ERR_CUDA;
+    return fa_status_read(d_status, workspace, stream, nullptr, nullptr);
+}
+
+extern "C" fa_status fa_shard_finish(const uint8_t *codes, int64_t codes_row0, int64_t codes_rows,
+                                     int64_t pitch_codes, int64_t rows, int64_t cols,
+                                     int64_t block_rows, int64_t block_cols, int64_t band0,
+                                     int64_t band1, const uint64_t *inflow, uint64_t *out,
+                                     int64_t pitch_out, void *workspace, size_t ws_bytes,
+                                     const fa_options *opts, int32_t *d_status, void *stream) {
+    OocPlan p;
+    if (!ooc_plan(rows, cols, block_rows, block_cols, opts, p)) return FA_ERR_INVALID_ARG;
+    if (!band_ok(p, band0, band1, codes_row0, codes_rows)) return FA_ERR_INVALID_ARG;
+    const int64_t b0 = band0 * p.g.nbx, b1 = band1 * p.g.nbx;
+    if (b1 > b0 && (!codes || pitch_codes < cols || !inflow || !out || pitch_out < cols))
+        return FA_ERR_INVALID_ARG;
+    OocWork w;
+    const fa_status v = ws_setup(p, workspace, ws_bytes, d_status, w);
+    if (v != FA_OK) return v;
+    cudaStream_t s = (cudaStream_t)stream;
+    StatusBlock *st = status_of(d_status, w);
+    const size_t n0 = (size_t)b0 * p.g.pmax, nn = (size_t)(b1 - b0) * p.g.pmax;
+    const bool was = timing_swap(false);
+    cudaError_t e, es;
+    {
+        BlockLoop loop(p, w, st, opts, s);
+        e = reset_records(p, w, st, b0, b0, s);
+        if (e == cudaSuccess && nn) e = cudaMemcpyAsync(w.inb + n0, inflow, nn * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && nn) {
+            e = loop.start();
+            if (e == cudaSuccess)
+                e = loop.pass_c(HostRows{codes, codes_row0, codes_rows, pitch_codes},
+                                HostOut{out, band0 * p.g.bh, pitch_out}, b0, b1, true);
+            if (e == cudaSuccess) e = loop.join();
+        }
+        es = loop.finish();
     }
-    if (cin) cudaStreamDestroy(cin);
-    if (cout) cudaStreamDestroy(cout);
+    timing_swap(was);
     if (e != cudaSuccess || es != cudaSuccess) return FA_ERR_CUDA;
     return fa_status_read(d_status, workspace, stream, nullptr, nullptr);
 }
