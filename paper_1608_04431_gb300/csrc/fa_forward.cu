@@ -969,7 +969,8 @@ __global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constan
         // staged codes outside the tile (the ring, and the frame beyond a
         // ragged tile) get the bit 0x80, so that one test on the next cell's
         // code tells "leaves the tile" and "into NoData" both; a step is then
-        // two code reads, two table steps and the output update.
+        // one code read (kept as the next step's code), two table steps and
+        // the output update.
         const int W2 = tw + 2;
         for (int i = tid; i < (th + 2 - h) * W2; i += nt) {  // rows -1 and h .. th
             const int q = i / W2, c = i - q * W2 - 1, hr = q == 0 ? 0 : h + q;
@@ -994,6 +995,7 @@ __global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constan
             const unsigned long long v = pin[e];
             int ci = (r + 1) * S + X0 + c;
             size_t oi = (size_t)(R0 + r) * ras.po + (size_t)(C0 + c);
+            uint32_t k = cbuf[ci];  // the code of the cell the path is at
             for (int stp = 0; stp < h * w; ++stp) {
                 if (o64) {
                     atomicAdd(o64 + oi, v);  // a reduction
@@ -1003,12 +1005,13 @@ __global__ void __launch_bounds__(ADDIN_THREADS, 8) k_addin(const __grid_constan
                     const uint32_t old = atomicAdd(out + oi, (uint32_t)v);
                     if ((v >> 32) || (unsigned long long)old + (uint32_t)v >= (1ull << 32)) ovf = 1;
                 }
-                const uint32_t k = cbuf[ci];
                 if (k - 1u >= 8u) break;  // NoFlow: the path ends
                 const int nci = ci + s_oc[k - 1];
-                if ((uint32_t)cbuf[nci] - 1u >= 9u) break;  // leaves the tile, or into NoData
+                const uint32_t kn = cbuf[nci];
+                if (kn - 1u >= 9u) break;  // leaves the tile, or into NoData
                 ci = nci;
                 oi += s_oo[k - 1];
+                k = kn;  // one code read per step
             }
         }
         if constexpr (LOAD == LOAD_TMA) fence_proxy_async();  // the buffer is refilled by TMA
