@@ -15,14 +15,19 @@
 //           (Algorithm 2 at the block level, hopping over the block's own
 //           tile links between the first and the last tile of the path);
 //   resolve the outer exits' graph (Section 3.2), solved on the device by the
-//           walks of the tile resolve;
+//           walks of the tile resolve, which also give in(p) per block
+//           perimeter slot: the sum of G over the outer exits draining into
+//           that cell;
 //   pass C  per block again (EVICT): codes copied in and the block solved
-//           again by the tile pipeline with the flow entering each outer entry
-//           (the sum of G over the outer exits draining into it) handed to it
-//           as extra inflow at that entry, so that the pipeline's own resolve
+//           again by the tile pipeline with in(p) handed to it as extra
+//           inflow at each outer entry, so that the pipeline's own resolve
 //           and finalising pass carry it along the paths (Algorithm 3); the
 //           tile-local sums plus the uint64 offsets are the block's counts,
 //           copied out.
+// The shard form (fa_shard_export / fa_shard_resolve / fa_shard_finish) runs
+// the same three stages in separate processes: pass A on a band of block
+// rows, the resolve on the gathered records of all blocks, pass C on the band
+// with its part of in(p).
 // Codes are copied on a second stream into one of two device buffers while
 // the other is in use (with pinned host memory the copies overlap the work).
 #include <algorithm>
