@@ -214,3 +214,12 @@ def test_export_and_finish_check_bands_and_rows():
     assert finish(1, 2, 16, 16) == fa.FA_ERR_INVALID_ARG
     assert finish(1, 2, 15, 18, pitch_out=cols - 1) == fa.FA_ERR_INVALID_ARG
     assert finish(1, 2, 15, 18) == fa.FA_ERR_WORKSPACE
+
+
+def test_empty_raster_and_idle_ranks_in_one_process():
+    empty = torch.zeros((0, 9), dtype=torch.uint8)
+    out = shard.accumulate_sharded(empty, 0, (0, 9), (4, 4), stages=OracleStages())
+    assert out.shape == (0, 9)
+    st, nby, nbx, pmax = fa.fa_shard_geometry(0, 9, 4, 4)
+    assert st == fa.FA_OK and nby == 0
+    assert shard.bands(0, 3) == [(0, 0)] * 3
