@@ -237,8 +237,9 @@ void fa_plan_destroy(fa_plan plan);
  * correctly rounded operations (no fused multiply-add), so results are exact
  * and platform-independent.  NaN elevations are not NoData: use the mask.
  * Asynchronous on `stream`; rows or cols == 0 enqueue nothing.  Returns
- * FA_ERR_INVALID_ARG for negative sizes, NULL buffers, pitches below cols or
- * a misaligned dem, FA_ERR_CUDA if the launch fails.
+ * FA_ERR_INVALID_ARG for negative sizes, NULL buffers, pitches below cols,
+ * a misaligned dem or more than 2,097,120 rows, FA_ERR_CUDA if the launch
+ * fails.
  */
 fa_status fa_d8_codes(const float *dem, int64_t rows, int64_t cols, int64_t pitch_dem,
                       const uint8_t *nodata, int64_t pitch_nodata, uint8_t *codes,

@@ -195,7 +195,7 @@ extern "C" fa_status fa_d8_codes(const float *dem, int64_t rows, int64_t cols, i
     D8Args a{dem, pitch_dem, nodata, pitch_nodata, codes, pitch_codes, rows, cols};
     const int64_t G = (cols + 3) >> 2;
     const int64_t chunks = (rows + kRows - 1) / kRows;  // row chunks of kRows
-    if ((chunks + 3) / 4 > 65535) return FA_ERR_INVALID_ARG;  // more than 2^21 rows
+    if ((chunks + 3) / 4 > 65535) return FA_ERR_INVALID_ARG;  // more than 2,097,120 rows
     const dim3 block(64, 4);
     const dim3 grid((unsigned)((G + 63) / 64), (unsigned)((chunks + 3) / 4));
     k_d8<<<grid, block, 0, (cudaStream_t)stream>>>(a);

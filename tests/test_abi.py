@@ -166,6 +166,8 @@ def test_d8_rejects_bad_args_without_gpu(lib):
     assert lib.fa_d8_codes(fake, 5, 5, 5, fake, 2, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
     assert lib.fa_d8_codes(fake + 2, 5, 5, 5, None, 0, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
     assert lib.fa_d8_codes(None, 0, 5, 5, None, 0, None, 5, None) == _lib.FA_OK  # empty
+    # more rows than the launch grid covers (65535 x 4 threads of 8 rows)
+    assert lib.fa_d8_codes(fake, 2097121, 5, 5, None, 0, fake, 5, None) == _lib.FA_ERR_INVALID_ARG
 
 
 def test_packed_codes_host_logic_without_gpu(lib):
