@@ -14,15 +14,33 @@ or any backend that takes CPU tensors).
 The stage calls are the C entry points fa_shard_export / fa_shard_resolve /
 fa_shard_finish (DeviceStages); another object with the same three methods
 can stand in for them, which is how the exchange is tested on CPU ranks.
+
+Failures: a stage that raises on one rank (a bad argument, a CUDA error)
+must not leave the others waiting in a collective, so after each stage the
+ranks agree whether any of them failed (one small all-reduce or broadcast)
+and all raise at the same point.  Conditions the device reports after a
+completed stage (invalid codes, cycles) are combined over all ranks at the
+end, so every rank returns or raises the same status.  A rank that dies
+outright is detected by the process group's own timeout on the others' next
+collective.
 """
 from __future__ import annotations
 
 import torch
 import torch.distributed as dist
 
-from . import (FA_ERR_INVALID_ARG, FA_OK, FA_WARN_OVERFLOW, FlowAccError, fa_ooc_workspace_size,
-               fa_shard_export, fa_shard_finish, fa_shard_geometry, fa_shard_resolve, options,
-               workspace)
+from . import (FA_ERR_BAD_CODE, FA_ERR_CYCLE, FA_ERR_INVALID_ARG, FA_ERR_NONFINITE, FA_ERR_TIMEOUT,
+               FA_OK, FA_WARN_OVERFLOW, FlowAccError, fa_ooc_workspace_size, fa_shard_export,
+               fa_shard_finish, fa_shard_geometry, fa_shard_resolve, options, workspace)
+
+# statuses the device reports after a completed stage, least to most severe
+# (the order fa_status_read uses); any other status is a failed call
+_DEVICE_STATUS = [FA_OK, FA_WARN_OVERFLOW, FA_ERR_TIMEOUT, FA_ERR_NONFINITE, FA_ERR_CYCLE,
+                  FA_ERR_BAD_CODE]
+
+
+class ShardAborted(RuntimeError):
+    """A stage failed on another rank; every rank stops at the same point."""
 
 
 class Records:
@@ -92,7 +110,10 @@ def out_rows(band, block_rows: int, rows: int):
 
 
 class DeviceStages:
-    """The three stages as calls of the CUDA library on the current device."""
+    """The three stages as calls of the CUDA library on the current device:
+    export -> status, resolve -> (in(p), status), finish -> status, where a
+    status is what the device reported after the completed stage; a failed
+    call raises FlowAccError."""
 
     def __init__(self, device=None, tile=None):
         self.device = torch.device(device) if device is not None else torch.device(
@@ -105,33 +126,39 @@ class DeviceStages:
             raise FlowAccError(FA_ERR_INVALID_ARG, "fa_ooc_workspace_size")
         return workspace(n, self.device)
 
-    def export(self, codes, codes_row0, shape, block, band, rec: Records) -> None:
+    def export(self, codes, codes_row0, shape, block, band, rec: Records) -> int:
         rows, cols = shape
         n = (band[1] - band[0]) * _grid(shape, block)[1]
         st = fa_shard_export(codes, codes_row0, rows, cols, block[0], block[1], band[0], band[1],
                              rec.nexit(n), rec.link(n), rec.node_dst(n), rec.node_val(n),
                              self._ws(rows, cols, *block), self.opts)
-        _check(st, "fa_shard_export")
+        return _device_status(st, "fa_shard_export")
 
-    def resolve(self, shape, block, rec: Records) -> torch.Tensor:
+    def resolve(self, shape, block, rec: Records):
         rows, cols = shape
         nb = rec.cap
         inflow = torch.zeros(nb * rec.pmax, dtype=torch.int64)
         st = fa_shard_resolve(rows, cols, block[0], block[1], rec.nexit(nb), rec.link(nb),
                               rec.node_dst(nb), rec.node_val(nb), inflow, self._ws(rows, cols, *block))
-        _check(st, "fa_shard_resolve")
-        return inflow
+        return inflow, _device_status(st, "fa_shard_resolve")
 
-    def finish(self, codes, codes_row0, shape, block, band, inflow, out) -> None:
+    def finish(self, codes, codes_row0, shape, block, band, inflow, out) -> int:
         rows, cols = shape
         st = fa_shard_finish(codes, codes_row0, rows, cols, block[0], block[1], band[0], band[1],
                              inflow, out, self._ws(rows, cols, *block), self.opts)
-        _check(st, "fa_shard_finish")
+        return _device_status(st, "fa_shard_finish")
 
 
-def _check(st, what):
-    if st not in (FA_OK, FA_WARN_OVERFLOW):
+def _device_status(st, what):
+    """A status the device reported after a completed stage, passed on; any
+    other (a failed call) raised."""
+    if st not in _DEVICE_STATUS:
         raise FlowAccError(st, what)
+    return st
+
+
+def _worse(a, b):
+    return a if _DEVICE_STATUS.index(a) >= _DEVICE_STATUS.index(b) else b
 
 
 def _grid(shape, block):
@@ -141,8 +168,17 @@ def _grid(shape, block):
     return nby, nbx, pmax
 
 
+def _agree(flag: int, on: bool, group) -> int:
+    """The largest of every rank's flag (this rank's alone without a group)."""
+    if not on:
+        return flag
+    t = torch.tensor([flag], dtype=torch.int64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return int(t.item())
+
+
 def accumulate_sharded(codes: torch.Tensor, codes_row0: int, shape, block=None, group=None,
-                       stages=None, tile=None) -> torch.Tensor:
+                       stages=None, tile=None, check: bool = True) -> torch.Tensor:
     """Counts of this rank's band of a raster of `shape` (rows, cols), solved
     with every rank of `group` (torch.distributed, initialised; or a single
     process when it is not).  codes: uint8 CPU tensor holding raster rows
@@ -150,7 +186,10 @@ def accumulate_sharded(codes: torch.Tensor, codes_row0: int, shape, block=None, 
     the whole raster with codes_row0 = 0 will do).  block: outer block shape
     (rows, cols); None = 16384 x 16384.  Returns int64 counts (uint64 bit
     patterns) of raster rows out_rows(band) for this rank's band, where band
-    = bands(nby, world)[rank]."""
+    = bands(nby, world)[rank].  check=True raises FlowAccError, on every
+    rank, when the device reported an error on any rank (the most severe
+    one); a stage that fails on some rank raises there and ShardAborted on
+    the others, at the same point."""
     rows, cols = int(shape[0]), int(shape[1])
     bh, bw = (block if block is not None else (16384, 16384))
     bh, bw = min(int(bh), max(rows, 1)), min(int(bw), max(cols, 1))
@@ -163,40 +202,78 @@ def accumulate_sharded(codes: torch.Tensor, codes_row0: int, shape, block=None, 
     band = all_bands[rank]
     cap = max(b1 - b0 for b0, b1 in all_bands) * nbx
     nblk = (band[1] - band[0]) * nbx
+    root = 0 if not on or group is None else dist.get_global_rank(group, 0)
+    status = FA_OK
+
+    def stop(failed, what):
+        # every rank learns whether a stage failed anywhere, then all stop
+        if _agree(1 if failed is not None else 0, on, group):
+            if failed is not None:
+                raise failed
+            raise ShardAborted(f"{what} failed on another rank")
 
     # 1. pass A on this rank's blocks
     mine = Records(cap, pmax)
-    if nblk:
-        stages.export(codes, codes_row0, (rows, cols), (bh, bw), band, mine)
+    failed = None
+    try:
+        if nblk:
+            status = _worse(status, stages.export(codes, codes_row0, (rows, cols), (bh, bw), band, mine))
+    except Exception as e:  # noqa: BLE001  (re-raised below, after the other ranks know)
+        failed = e
+    stop(failed, "the export")
 
     # 2-4. records to rank 0, the blocks' graph solved there, in(p) back
-    root = 0 if not on or group is None else dist.get_global_rank(group, 0)
     recv = torch.zeros(cap * pmax, dtype=torch.int64)
     if rank == 0:
         parts = [mine] if world == 1 else [Records(cap, pmax) for _ in range(world)]
         if world > 1:
             dist.gather(mine.buf, [p.buf for p in parts], dst=root, group=group)
-        full = Records(nby * nbx, pmax)
-        for r, (b0, b1) in enumerate(all_bands):
-            if b1 > b0:
-                full.put(b0 * nbx, parts[r], (b1 - b0) * nbx)
-        inflow = stages.resolve((rows, cols), (bh, bw), full)
-        chunks = []
-        for b0, b1 in all_bands:
-            c = torch.zeros(cap * pmax, dtype=torch.int64)
-            c[: (b1 - b0) * nbx * pmax] = inflow[b0 * nbx * pmax: b1 * nbx * pmax]
-            chunks.append(c)
+        chunks, failed = None, None
+        try:
+            full = Records(nby * nbx, pmax)
+            for r, (b0, b1) in enumerate(all_bands):
+                if b1 > b0:
+                    full.put(b0 * nbx, parts[r], (b1 - b0) * nbx)
+            inflow, st = stages.resolve((rows, cols), (bh, bw), full)
+            status = _worse(status, st)
+            chunks = []
+            for b0, b1 in all_bands:
+                c = torch.zeros(cap * pmax, dtype=torch.int64)
+                c[: (b1 - b0) * nbx * pmax] = inflow[b0 * nbx * pmax: b1 * nbx * pmax]
+                chunks.append(c)
+        except Exception as e:  # noqa: BLE001
+            failed = e
+        flag = torch.tensor([1 if failed is not None else 0], dtype=torch.int64)
+        if world > 1:
+            dist.broadcast(flag, src=root, group=group)
+        if failed is not None:
+            raise failed
         if world > 1:
             dist.scatter(recv, chunks, src=root, group=group)
         else:
             recv = chunks[0]
     else:
         dist.gather(mine.buf, None, dst=root, group=group)
+        flag = torch.zeros(1, dtype=torch.int64)
+        dist.broadcast(flag, src=root, group=group)
+        if int(flag.item()):
+            raise ShardAborted("the resolve failed on the root rank")
         dist.scatter(recv, None, src=root, group=group)
 
     # 5. pass C on this rank's blocks
     r0, r1 = out_rows(band, bh, rows)
     out = torch.zeros((r1 - r0, cols), dtype=torch.int64)
-    if nblk:
-        stages.finish(codes, codes_row0, (rows, cols), (bh, bw), band, recv[: nblk * pmax], out)
+    failed = None
+    try:
+        if nblk:
+            status = _worse(status, stages.finish(codes, codes_row0, (rows, cols), (bh, bw), band,
+                                                  recv[: nblk * pmax], out))
+    except Exception as e:  # noqa: BLE001
+        failed = e
+    stop(failed, "the finish")
+
+    # the most severe condition any rank's device reported
+    status = _DEVICE_STATUS[_agree(_DEVICE_STATUS.index(status), on, group)]
+    if check and status < 0:
+        raise FlowAccError(status, "accumulate_sharded")
     return out

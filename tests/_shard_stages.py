@@ -65,7 +65,8 @@ class Grid:
 
 
 class OracleStages:
-    """export / resolve / finish with the interface of shard.DeviceStages."""
+    """export / resolve / finish with the interface of shard.DeviceStages
+    (statuses: always FA_OK = 0; a cycle raises)."""
 
     @staticmethod
     def _codes(codes, codes_row0, g):
@@ -132,6 +133,7 @@ class OracleStages:
                     rr, cc = tr, tc
                 if end is not None:
                     link[i * g.pmax + s] = link[i * g.pmax + where[end]]
+        return 0
 
     def resolve(self, shape, block, rec):
         g = Grid(shape, block)
@@ -162,7 +164,7 @@ class OracleStages:
         inflow = np.zeros(nb * g.pmax, dtype=np.uint64)
         for u in nodes:
             inflow[int(dst[u])] += np.uint64(G[u])
-        return torch.from_numpy(inflow.view(np.int64))
+        return torch.from_numpy(inflow.view(np.int64)), 0
 
     def finish(self, codes, codes_row0, shape, block, band, inflow, out):
         g = Grid(shape, block)
@@ -181,3 +183,4 @@ class OracleStages:
                 wi[r, c] = v
             extra = oracle.weighted(blk, wi).values
             o[R0 - r0: R0 - r0 + h, C0: C0 + w] = oracle.counts(blk).values + extra.astype(np.uint64)
+        return 0

@@ -43,14 +43,15 @@ def emulate(codes, block, world, stages, tile=None):
         rec = shard.Records(cap, pmax)
         if band[1] > band[0]:
             ra, rb = shard.band_rows(band, bh, rows)
-            stages.export(torch.from_numpy(np.ascontiguousarray(codes[ra:rb])), ra, (rows, cols),
-                          block, band, rec)
+            assert stages.export(torch.from_numpy(np.ascontiguousarray(codes[ra:rb])), ra,
+                                 (rows, cols), block, band, rec) == fa.FA_OK
         parts.append(rec)
     full = shard.Records(nby * nbx, pmax)
     for (b0, b1), rec in zip(bands, parts):
         if b1 > b0:
             full.put(b0 * nbx, rec, (b1 - b0) * nbx)
-    inflow = stages.resolve((rows, cols), block, full)
+    inflow, st = stages.resolve((rows, cols), block, full)
+    assert st == fa.FA_OK
     out = np.zeros((rows, cols), dtype=np.uint64)
     for band in bands:
         if band[1] == band[0]:
@@ -59,8 +60,8 @@ def emulate(codes, block, world, stages, tile=None):
         r0, r1 = shard.out_rows(band, bh, rows)
         o = torch.zeros((r1 - r0, cols), dtype=torch.int64)
         part = inflow[band[0] * nbx * pmax: band[1] * nbx * pmax].clone()
-        stages.finish(torch.from_numpy(np.ascontiguousarray(codes[ra:rb])), ra, (rows, cols), block,
-                      band, part, o)
+        assert stages.finish(torch.from_numpy(np.ascontiguousarray(codes[ra:rb])), ra, (rows, cols),
+                             block, band, part, o) == fa.FA_OK
         out[r0:r1] = o.numpy().view(np.uint64)
     return out, full, inflow.numpy().view(np.uint64)
 
@@ -118,7 +119,8 @@ def test_device_resolve_takes_records_made_elsewhere(oracle_mod):
     codes = synth.acyclic_random_codes(70, 53, 11)
     block = (16, 20)
     _, ref_rec, ref_in = emulate(codes, block, 3, OracleStages())
-    inflow = shard.DeviceStages().resolve((70, 53), block, ref_rec)
+    inflow, st = shard.DeviceStages().resolve((70, 53), block, ref_rec)
+    assert st == fa.FA_OK
     np.testing.assert_array_equal(inflow.numpy().view(np.uint64), ref_in)
 
 
@@ -138,7 +140,7 @@ def test_cycle_through_blocks_is_reported_by_resolve():
     rows, cols = codes.shape
     _, nby, nbx, pmax = fa.fa_shard_geometry(rows, cols, 8, 16)
     rec = shard.Records(nby * nbx, pmax)
-    st.export(torch.from_numpy(codes), 0, (rows, cols), (8, 16), (0, nby), rec)
+    assert st.export(torch.from_numpy(codes), 0, (rows, cols), (8, 16), (0, nby), rec) == fa.FA_OK
     inflow = torch.zeros(nby * nbx * pmax, dtype=torch.int64)
     ws = fa.workspace(fa.fa_ooc_workspace_size(rows, cols, 8, 16), "cuda")
     s = fa.fa_shard_resolve(rows, cols, 8, 16, rec.nexit(2), rec.link(2), rec.node_dst(2),

@@ -223,3 +223,92 @@ def test_empty_raster_and_idle_ranks_in_one_process():
     st, nby, nbx, pmax = fa.fa_shard_geometry(0, 9, 4, 4)
     assert st == fa.FA_OK and nby == 0
     assert shard.bands(0, 3) == [(0, 0)] * 3
+
+
+# ---------------------------------------------------------------------------
+# failures: no rank is left waiting in a collective
+# ---------------------------------------------------------------------------
+class _FailingStages(OracleStages):
+    """Stand-ins that make one stage fail on one rank: raise (a failed call)
+    or report FA_ERR_BAD_CODE (a condition found by the device)."""
+
+    def __init__(self, rank, where, how):
+        self.rank, self.where, self.how = rank, where, how
+
+    def _hit(self, stage):
+        return dist.get_rank() == self.rank and self.where == stage
+
+    def export(self, *args):
+        st = super().export(*args)
+        if self._hit("export"):
+            if self.how == "raise":
+                raise RuntimeError("export broke")
+            return fa.FA_ERR_BAD_CODE
+        return st
+
+    def resolve(self, *args):
+        if self._hit("resolve"):
+            raise RuntimeError("resolve broke")
+        return super().resolve(*args)
+
+    def finish(self, *args):
+        st = super().finish(*args)
+        if self._hit("finish"):
+            raise RuntimeError("finish broke")
+        return st
+
+
+def _rank_fail(rank, ws, port, case, fail, check, res):
+    import datetime
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        rows, cols, seed, block = case
+        codes = torch.from_numpy(_codes(rows, cols, seed))
+        try:
+            out = shard.accumulate_sharded(codes, 0, (rows, cols), block,
+                                           stages=_FailingStages(*fail), check=check)
+            res[rank] = ("ok", out.numpy().tobytes())
+        except fa.FlowAccError as e:
+            res[rank] = ("status", e.status)
+        except shard.ShardAborted:
+            res[rank] = ("aborted", None)
+        except RuntimeError as e:
+            res[rank] = ("raised", str(e))
+    finally:
+        dist.destroy_process_group()
+
+
+def _run_fail(fail, check=True, ws=2, name="ragged"):
+    mgr = mp.get_context("spawn").Manager()
+    res = mgr.dict()
+    mp.start_processes(_rank_fail, args=(ws, _free_port(), CASES[name], fail, check, res),
+                       nprocs=ws, join=True, start_method="spawn")
+    return [res[r] for r in range(ws)]
+
+
+@pytest.mark.parametrize("fail,expect", [
+    ((1, "export", "raise"), [("aborted", None), ("raised", "export broke")]),
+    ((0, "resolve", "raise"), [("raised", "resolve broke"), ("aborted", None)]),
+    ((1, "finish", "raise"), [("aborted", None), ("raised", "finish broke")]),
+])
+def test_a_failed_stage_stops_every_rank(fail, expect):
+    assert _run_fail(fail) == expect
+
+
+def test_device_conditions_reach_every_rank():
+    got = _run_fail((1, "export", "status"), check=True)
+    assert got == [("status", fa.FA_ERR_BAD_CODE)] * 2
+    got = _run_fail((1, "export", "status"), check=False)
+    rows, cols, seed, block = CASES["ragged"]
+    whole = np.zeros((rows, cols), dtype=np.uint64)
+    bh = Grid((rows, cols), block).bh
+    for r, (kind, raw) in enumerate(got):
+        assert kind == "ok"
+        band = shard.bands(Grid((rows, cols), block).nby, 2)[r]
+        r0, r1 = shard.out_rows(band, bh, rows)
+        whole[r0:r1] = np.frombuffer(raw, dtype=np.uint64).reshape(r1 - r0, cols)
+    assert np.array_equal(whole, _want(_codes(rows, cols, seed)))
