@@ -461,9 +461,11 @@ fa_status fa_accumulate_ooc(const uint8_t *codes, int64_t rows, int64_t cols, in
  *
  * Records of blocks [b0, b1) (b = band0 * nbx ..), host arrays:
  *   nexit     [b1 - b0]          uint32 outer exits of each block;
- *   link      [(b1 - b0) * pmax] uint16 per block perimeter slot (slot
- *             numbering of the paper's perimeter, clockwise from the block's
- *             top-left cell): the exit rank its path reaches in the block,
+ *   link      [(b1 - b0) * pmax] uint16 per block perimeter slot (slots
+ *             clockwise from the block's top-left cell: top row west to
+ *             east, right column north to south, bottom row east to west,
+ *             left column south to north; a one-row or one-column block in
+ *             cell order): the exit rank its path reaches in the block,
  *             0xFFFF for none (an exit links to its own rank);
  *   node_dst  [(b1 - b0) * pmax] uint32 per exit rank: global slot id
  *             (block * pmax + slot) of the cell its flow enters;
@@ -474,8 +476,9 @@ fa_status fa_accumulate_ooc(const uint8_t *codes, int64_t rows, int64_t cols, in
  *
  * Codes: codes points at raster row codes_row0 and holds codes_rows rows of
  * pitch_codes bytes, which must include every row the band's blocks read:
- * rows max(band0 * block_rows - 1, 0) .. min(band1 * block_rows + 1, rows) - 1
- * (the band and its ring rows).
+ * rows max(band0 * bh - 1, 0) .. min(band1 * bh + 1, rows) - 1 (the band and
+ * its ring rows), bh being the block height in use (block_rows, 0 = 16384,
+ * cut to the raster's rows).
  *
  * fa_shard_resolve takes the records of ALL nby * nbx blocks (concatenated in
  * block order) and writes inflow [nby * nbx * pmax]: per block perimeter slot
@@ -484,8 +487,8 @@ fa_status fa_accumulate_ooc(const uint8_t *codes, int64_t rows, int64_t cols, in
  * none or an exit of their block): FA_ERR_INVALID_ARG otherwise, nothing run.
  *
  * fa_shard_finish takes inflow [(b1 - b0) * pmax] (the band's part, from
- * slot b0 * pmax) and writes out: raster rows band0 * block_rows ..
- * min(band1 * block_rows, rows) - 1, row 0 first, pitch_out elements apart.
+ * slot b0 * pmax) and writes out: raster rows band0 * bh ..
+ * min(band1 * bh, rows) - 1, row 0 first, pitch_out elements apart.
  *
  * An empty band (band0 == band1) is valid: nothing is read or written.
  */
