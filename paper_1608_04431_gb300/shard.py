@@ -26,6 +26,9 @@ collective.
 """
 from __future__ import annotations
 
+import os
+
+import numpy as np
 import torch
 import torch.distributed as dist
 
@@ -86,6 +89,27 @@ class Records:
         self.node_dst(at + n)[at * p:].copy_(other.node_dst(n))
         self.nexit(at + n)[at:].copy_(other.nexit(n))
         self.link(at + n)[at * p:].copy_(other.link(n))
+
+
+def _ckpt_save(path: str, arrays: dict, meta: dict) -> None:
+    """Arrays plus integer metadata to an .npz file, written under another
+    name first so that a crash mid-write leaves no file that looks whole."""
+    tmp = path + ".part"
+    with open(tmp, "wb") as f:
+        np.savez(f, **arrays, **{"m_" + k: np.int64(v) for k, v in meta.items()})
+    os.replace(tmp, path)
+
+
+def _ckpt_load(path: str, meta: dict):
+    """The arrays of a file written by _ckpt_save with the same metadata, or
+    None (absent, unreadable or from another solve)."""
+    try:
+        with np.load(path) as z:
+            if any(int(z["m_" + k]) != int(v) for k, v in meta.items()):
+                return None
+            return {k: z[k].copy() for k in z.files if not k.startswith("m_")}
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def bands(nby: int, world: int):
@@ -178,7 +202,8 @@ def _agree(flag: int, on: bool, group) -> int:
 
 
 def accumulate_sharded(codes: torch.Tensor, codes_row0: int, shape, block=None, group=None,
-                       stages=None, tile=None, check: bool = True) -> torch.Tensor:
+                       stages=None, tile=None, check: bool = True,
+                       checkpoint: str | None = None) -> torch.Tensor:
     """Counts of this rank's band of a raster of `shape` (rows, cols), solved
     with every rank of `group` (torch.distributed, initialised; or a single
     process when it is not).  codes: uint8 CPU tensor holding raster rows
@@ -189,7 +214,18 @@ def accumulate_sharded(codes: torch.Tensor, codes_row0: int, shape, block=None, 
     = bands(nby, world)[rank].  check=True raises FlowAccError, on every
     rank, when the device reported an error on any rank (the most severe
     one); a stage that fails on some rank raises there and ShardAborted on
-    the others, at the same point."""
+    the others, at the same point.
+
+    checkpoint: a directory all ranks can write (shared, or the same path on
+    each node for its ranks' files and rank 0's).  Each rank keeps its
+    band's records there after pass A and rank 0 keeps in(p) after the
+    resolve; a later call on the same raster with the same blocks and number
+    of ranks loads them instead of repeating that work, so a solve that
+    stopped during the finish resumes at the finish.  (The paper's
+    discussion of robustness describes caching the tiles' perimeter data and
+    the global solution this way, and leaves it out of its implementation.)
+    The files are checked against the raster shape, blocks and ranks, not
+    against the codes: a directory serves one raster."""
     rows, cols = int(shape[0]), int(shape[1])
     bh, bw = (block if block is not None else (16384, 16384))
     bh, bw = min(int(bh), max(rows, 1)), min(int(bw), max(cols, 1))
@@ -212,12 +248,24 @@ def accumulate_sharded(codes: torch.Tensor, codes_row0: int, shape, block=None, 
                 raise failed
             raise ShardAborted(f"{what} failed on another rank")
 
-    # 1. pass A on this rank's blocks
+    meta = dict(rows=rows, cols=cols, bh=bh, bw=bw, world=world)
+    rec_path = os.path.join(checkpoint, f"records_{rank}_of_{world}.npz") if checkpoint else None
+    in_path = os.path.join(checkpoint, f"inflow_of_{world}.npz") if checkpoint else None
+
+    # 1. pass A on this rank's blocks (or its records kept by an earlier call)
     mine = Records(cap, pmax)
     failed = None
     try:
-        if nblk:
-            status = _worse(status, stages.export(codes, codes_row0, (rows, cols), (bh, bw), band, mine))
+        kept = _ckpt_load(rec_path, dict(meta, rank=rank)) if rec_path else None
+        if kept is not None and kept["buf"].size == mine.buf.numel():
+            mine.buf.copy_(torch.from_numpy(kept["buf"]))
+            status = _worse(status, int(kept["status"]))
+        elif nblk:
+            st = stages.export(codes, codes_row0, (rows, cols), (bh, bw), band, mine)
+            status = _worse(status, st)
+            if rec_path:
+                _ckpt_save(rec_path, {"buf": mine.buf.numpy(), "status": np.int64(st)},
+                           dict(meta, rank=rank))
     except Exception as e:  # noqa: BLE001  (re-raised below, after the other ranks know)
         failed = e
     stop(failed, "the export")
@@ -230,11 +278,17 @@ def accumulate_sharded(codes: torch.Tensor, codes_row0: int, shape, block=None, 
             dist.gather(mine.buf, [p.buf for p in parts], dst=root, group=group)
         chunks, failed = None, None
         try:
-            full = Records(nby * nbx, pmax)
-            for r, (b0, b1) in enumerate(all_bands):
-                if b1 > b0:
-                    full.put(b0 * nbx, parts[r], (b1 - b0) * nbx)
-            inflow, st = stages.resolve((rows, cols), (bh, bw), full)
+            kept = _ckpt_load(in_path, meta) if in_path else None
+            if kept is not None and kept["inflow"].size == nby * nbx * pmax:
+                inflow, st = torch.from_numpy(kept["inflow"]), int(kept["status"])
+            else:
+                full = Records(nby * nbx, pmax)
+                for r, (b0, b1) in enumerate(all_bands):
+                    if b1 > b0:
+                        full.put(b0 * nbx, parts[r], (b1 - b0) * nbx)
+                inflow, st = stages.resolve((rows, cols), (bh, bw), full)
+                if in_path:
+                    _ckpt_save(in_path, {"inflow": inflow.numpy(), "status": np.int64(st)}, meta)
             status = _worse(status, st)
             chunks = []
             for b0, b1 in all_bands:

@@ -312,3 +312,141 @@ def test_device_conditions_reach_every_rank():
         r0, r1 = shard.out_rows(band, bh, rows)
         whole[r0:r1] = np.frombuffer(raw, dtype=np.uint64).reshape(r1 - r0, cols)
     assert np.array_equal(whole, _want(_codes(rows, cols, seed)))
+
+
+# ---------------------------------------------------------------------------
+# checkpoint and resume: records kept after pass A, in(p) after the resolve
+# ---------------------------------------------------------------------------
+class _CountingStages(OracleStages):
+    def __init__(self, fail_finish_rank=None):
+        self.calls = {"export": 0, "resolve": 0, "finish": 0}
+        self.fail_finish_rank = fail_finish_rank
+
+    def export(self, *args):
+        self.calls["export"] += 1
+        return super().export(*args)
+
+    def resolve(self, *args):
+        self.calls["resolve"] += 1
+        return super().resolve(*args)
+
+    def finish(self, *args):
+        self.calls["finish"] += 1
+        rank = dist.get_rank() if dist.is_initialized() else 0
+        if self.fail_finish_rank == rank:
+            raise RuntimeError("crash during the finish")
+        return super().finish(*args)
+
+
+def test_checkpoint_resumes_at_the_finish(tmp_path):
+    rows, cols, seed, block = CASES["ragged"]
+    codes = torch.from_numpy(_codes(rows, cols, seed))
+    want = _want(codes.numpy())
+    first = _CountingStages(fail_finish_rank=0)
+    with pytest.raises(RuntimeError, match="crash"):
+        shard.accumulate_sharded(codes, 0, (rows, cols), block, stages=first, checkpoint=str(tmp_path))
+    assert first.calls == {"export": 1, "resolve": 1, "finish": 1}
+    again = _CountingStages()
+    out = shard.accumulate_sharded(codes, 0, (rows, cols), block, stages=again, checkpoint=str(tmp_path))
+    assert again.calls == {"export": 0, "resolve": 0, "finish": 1}
+    assert np.array_equal(out.numpy().view(np.uint64), want)
+    # files of another block shape do not apply; a damaged file is redone
+    other = _CountingStages()
+    out = shard.accumulate_sharded(codes, 0, (rows, cols), (8, 20), stages=other, checkpoint=str(tmp_path))
+    assert other.calls == {"export": 1, "resolve": 1, "finish": 1}
+    assert np.array_equal(out.numpy().view(np.uint64), want)
+    (tmp_path / "records_0_of_1.npz").write_bytes(b"not an npz file")
+    redo = _CountingStages()
+    out = shard.accumulate_sharded(codes, 0, (rows, cols), (8, 20), stages=redo, checkpoint=str(tmp_path))
+    assert redo.calls == {"export": 1, "resolve": 0, "finish": 1}
+    assert np.array_equal(out.numpy().view(np.uint64), want)
+
+
+def _rank_ckpt(rank, ws, port, case, ckpt, fail_rank, res):
+    import datetime
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        rows, cols, seed, block = case
+        codes = torch.from_numpy(_codes(rows, cols, seed))
+        st = _CountingStages(fail_finish_rank=fail_rank)
+        try:
+            out = shard.accumulate_sharded(codes, 0, (rows, cols), block, stages=st, checkpoint=ckpt)
+            res[rank] = ("ok", dict(st.calls), out.numpy().tobytes())
+        except (RuntimeError, shard.ShardAborted) as e:
+            res[rank] = (type(e).__name__, dict(st.calls), None)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_checkpoint_resume_on_gloo_ranks(tmp_path):
+    ws, name = 2, "ragged"
+    rows, cols, seed, block = CASES[name]
+
+    def run(fail_rank):
+        mgr = mp.get_context("spawn").Manager()
+        res = mgr.dict()
+        mp.start_processes(_rank_ckpt, args=(ws, _free_port(), CASES[name], str(tmp_path), fail_rank,
+                                             res), nprocs=ws, join=True, start_method="spawn")
+        return [res[r] for r in range(ws)]
+
+    first = run(fail_rank=1)
+    assert [k for k, _, _ in first] == ["ShardAborted", "RuntimeError"]
+    assert [c["export"] for _, c, _ in first] == [1, 1] and first[0][1]["resolve"] == 1
+    again = run(fail_rank=None)
+    assert all(k == "ok" for k, _, _ in again)
+    assert [c for _, c, _ in again] == [{"export": 0, "resolve": 0, "finish": 1}] * 2
+    got = np.zeros((rows, cols), dtype=np.uint64)
+    g = Grid((rows, cols), block)
+    for r, (_, _, raw) in enumerate(again):
+        r0, r1 = shard.out_rows(shard.bands(g.nby, ws)[r], g.bh, rows)
+        got[r0:r1] = np.frombuffer(raw, dtype=np.uint64).reshape(r1 - r0, cols)
+    assert np.array_equal(got, _want(_codes(rows, cols, seed)))
+
+
+# ---------------------------------------------------------------------------
+# rank loss, injected on the host: a rank that exits mid-solve
+# ---------------------------------------------------------------------------
+class _DiesInExport(OracleStages):
+    def export(self, *args):
+        if dist.get_rank() == 1:
+            os._exit(3)  # the process is gone, with nothing in flight
+        return super().export(*args)
+
+
+def _rank_lost(rank, ws, port, case, res):
+    import datetime
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws,
+                            timeout=datetime.timedelta(seconds=30))
+    rows, cols, seed, block = case
+    codes = torch.from_numpy(_codes(rows, cols, seed))
+    try:
+        shard.accumulate_sharded(codes, 0, (rows, cols), block, stages=_DiesInExport())
+        res[rank] = "finished"
+    except Exception as e:  # noqa: BLE001  (whatever the backend raises for a lost peer)
+        res[rank] = "raised " + type(e).__name__
+    try:
+        dist.destroy_process_group()
+    except Exception:  # noqa: BLE001
+        pass
+
+
+def test_a_lost_rank_makes_the_others_raise_not_hang():
+    mgr = mp.get_context("spawn").Manager()
+    res = mgr.dict()
+    ctx = mp.start_processes(_rank_lost, args=(2, _free_port(), CASES["ragged"], res), nprocs=2,
+                             join=False, start_method="spawn")
+    for p in ctx.processes:
+        p.join(timeout=120)
+    alive = [p for p in ctx.processes if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank was still waiting after its peer exited"
+    assert ctx.processes[1].exitcode == 3
+    assert ctx.processes[0].exitcode == 0 and res[0].startswith("raised")
