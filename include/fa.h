@@ -393,7 +393,7 @@ fa_status fa_accumulate_absorb(const uint8_t *codes, int64_t rows, int64_t cols,
 
 /*
  * Out-of-core accumulation: unit-weight counts of a raster whose codes and
- * output stay in HOST memory, for rasters larger than the device (Section 1
+ * output stay in HOST memory, for rasters larger than the device (Section 2
  * sets rasters beyond one machine's memory as the aim; Section 3 with EVICT:
  * only one block and the perimeter data are held at once).  The raster is cut
  * into outer blocks of block_rows x block_cols cells; each block's codes,

@@ -1,7 +1,7 @@
 // Out-of-core accumulation: rasters whose codes and counts stay in host
 // memory, processed on the device one outer block at a time.
 //
-// The paper's stated aim (Section 1) is rasters larger than the memory of
+// The paper's stated aim (Section 2) is rasters larger than the memory of
 // any one machine, with only one tile and the producer's perimeter data held
 // at once (Section 3, EVICT).  Here the raster is split into outer blocks
 // (block_rows x block_cols cells); each block is solved on the device by the
