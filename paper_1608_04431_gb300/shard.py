@@ -27,6 +27,7 @@ collective.
 from __future__ import annotations
 
 import os
+import zipfile
 
 import numpy as np
 import torch
@@ -108,7 +109,7 @@ def _ckpt_load(path: str, meta: dict):
             if any(int(z["m_" + k]) != int(v) for k, v in meta.items()):
                 return None
             return {k: z[k].copy() for k in z.files if not k.startswith("m_")}
-    except (OSError, ValueError, KeyError):
+    except (OSError, ValueError, KeyError, EOFError, zipfile.BadZipFile):
         return None
 
 

@@ -360,6 +360,12 @@ def test_checkpoint_resumes_at_the_finish(tmp_path):
     out = shard.accumulate_sharded(codes, 0, (rows, cols), (8, 20), stages=redo, checkpoint=str(tmp_path))
     assert redo.calls == {"export": 1, "resolve": 0, "finish": 1}
     assert np.array_equal(out.numpy().view(np.uint64), want)
+    whole = (tmp_path / "inflow_of_1.npz").read_bytes()
+    (tmp_path / "inflow_of_1.npz").write_bytes(whole[: len(whole) // 2])  # cut short
+    redo = _CountingStages()
+    out = shard.accumulate_sharded(codes, 0, (rows, cols), (8, 20), stages=redo, checkpoint=str(tmp_path))
+    assert redo.calls == {"export": 0, "resolve": 1, "finish": 1}
+    assert np.array_equal(out.numpy().view(np.uint64), want)
 
 
 def _rank_ckpt(rank, ws, port, case, ckpt, fail_rank, res):
