@@ -20,9 +20,10 @@
  * Raster conventions (all entry points):
  *  - Row-major, row 0 = north; every raster argument has its own row pitch in
  *    ELEMENTS (>= cols).  All raster pointers are DEVICE pointers owned by the
- *    caller; the library never allocates device memory on these paths: all
- *    scratch comes from the caller's workspace (size from *_workspace_size),
- *    which must be 256-byte aligned.
+ *    caller (except for the out-of-core and shard entry points, whose rasters
+ *    and records are HOST memory); the library never allocates device memory
+ *    on these paths: all scratch comes from the caller's workspace (size from
+ *    *_workspace_size), which must be 256-byte aligned.
  *  - Codes, one byte per cell: 0 = NoData, 1..8 = E, NE, N, NW, W, SW, S, SE
  *    (offsets (0,+1) (-1,+1) (-1,0) (-1,-1) (0,-1) (+1,-1) (+1,0) (+1,+1)),
  *    9 = NoFlow.  Codes 10..255 are invalid: reported as FA_ERR_BAD_CODE in the
