@@ -21,8 +21,13 @@ ranks agree whether any of them failed (one small all-reduce or broadcast)
 and all raise at the same point.  Conditions the device reports after a
 completed stage (invalid codes, cycles) are combined over all ranks at the
 end, so every rank returns or raises the same status.  A rank that dies
-outright is detected by the process group's own timeout on the others' next
-collective.
+outright makes the others' next collective fail: at once where the backend
+sees the connection close (gloo), at the latest after the process group's
+timeout.
+
+Checkpoints: with a checkpoint directory each rank keeps its records after
+pass A and rank 0 keeps in(p) after the resolve, so that a solve stopped
+later resumes at the finish (accumulate_sharded).
 """
 from __future__ import annotations
 
